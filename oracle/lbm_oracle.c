@@ -1,0 +1,557 @@
+/*
+ * Oracle for the pseudopotential multiphase lattice Boltzmann step with the
+ * high-order-difference (HDM) interaction of Qin, Zhao, Chen, Zhang & Wen,
+ * "A pseudopotential multiphase lattice Boltzmann model based on high-order
+ * difference" (arXiv:1712.06079).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, FP64 CPU statement
+ * of what the GPU path computes.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or constant generator with the CUDA library.
+ *
+ * Every step follows the paper's equations in the paper's order:
+ *   Eq. 3   density and momentum moments
+ *   Sec. 5  Hu scaling p = k p_EOS; Eq. 24, 27, 28, 29 equations of state
+ *   Eq. 8   U = p - rho c_s^2;  Eq. 21  Phi = sqrt|U|
+ *   Eq. 20  HDM first derivative, solved as the periodic (cyclic) tridiagonal
+ *           system it is, by the chasing (Thomas) method plus a
+ *           Sherman-Morrison correction for the two corner entries
+ *   Eq. 15  weighted CDM (the comparison arm), scaled by 1/c_s^2
+ *   Eq. 22  Shan-Chen force in Phi form;  Eq. 7  Zhang-Chen force -grad U
+ *   Eq. 10  Kupershtokh exact-difference forcing;  Eq. 2 equilibrium
+ *   Eq. 1   BGK collision and streaming on the periodic lattice
+ *   Eq. 11  the observable half-step velocity
+ * plus the Maxwell equal-area construction (Sec. 5.2) and the critical point.
+ *
+ * No FMA contraction, no fast math: compile with -ffp-contract=off.
+ * Threads (OpenMP) split the lattice by rows only; every cell's arithmetic and
+ * every reduction order is independent of the thread count.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { ORC_VDW = 0, ORC_CS = 1, ORC_PR = 2, ORC_RK = 3, ORC_RKS = 4 };
+enum { ORC_SC = 0, ORC_ZC = 1 };
+enum { ORC_HDM = 0, ORC_CDM = 1 };
+
+typedef struct {
+    int nx, ny;
+    int eos;      /* ORC_VDW .. ORC_RKS */
+    int force;    /* ORC_SC (Eq. 22) or ORC_ZC (Eq. 7) */
+    int grad;     /* ORC_HDM (Eq. 20) or ORC_CDM (Eq. 15) */
+    int pad;
+    double a, b, R, omega;
+    double T;     /* absolute temperature */
+    double Tc;    /* critical temperature (used by the alpha(T) of PR and RKS) */
+    double k;     /* Hu scaling of the EOS, Sec. 5 */
+    double tau;   /* BGK relaxation time, Eq. 1 */
+} orc_params;
+
+/* D2Q9 velocity set and weights (Eq. 2 "D2Q9 model"; the paper does not print
+ * them -- these are the standard 4/9, 1/9, 1/36). */
+static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double W9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+static const double CS2 = 1.0 / 3.0;  /* c_s^2 of D2Q9, Sec. 2 */
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int wrap(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Equations of state (Sec. 5.2).                                            */
+/* ------------------------------------------------------------------------ */
+
+/* alpha(T) of Eq. 27 (RK: 1/sqrt(T)), Eq. 28 (PR: Soave-type with omega) and
+ * the RKS form given after Eq. 27. VdW and CS have none (returned as 1). */
+static double orc_alpha(int eos, double omega, double T, double Tc) {
+    double m, s;
+    switch (eos) {
+    case ORC_PR:
+        m = 0.37464 + 1.54226 * omega - 0.26992 * omega * omega;
+        s = 1.0 + m * (1.0 - sqrt(T / Tc));
+        return s * s;
+    case ORC_RKS:
+        m = 0.480 + 1.574 * omega - 0.176 * omega * omega;
+        s = 1.0 + m * (1.0 - sqrt(T / Tc));
+        return s * s;
+    case ORC_RK:
+        return 1.0 / sqrt(T);
+    default:
+        return 1.0;
+    }
+}
+
+/* p_EOS(rho) and dp_EOS/drho at temperature T with a given alpha.
+ * VdW Eq. 24; RK/RKS Eq. 27; PR Eq. 28; CS Eq. 29 with the standard
+ * Carnahan-Starling denominator (1 - b rho/4)^3. */
+static void eos_eval(int eos, double a, double b, double R, double T,
+                     double alpha, double rho, double *p, double *dp) {
+    double rep, drep, att, datt;
+    if (eos == ORC_CS) {
+        double e = b * rho / 4.0;
+        double num = 1.0 + e + e * e - e * e * e;
+        double om = 1.0 - e;
+        double den = om * om * om;
+        double Z = num / den;
+        /* dZ/de = [(1 + 2e - 3e^2)(1-e) + 3 num] / (1-e)^4 */
+        double dZ = ((1.0 + 2.0 * e - 3.0 * e * e) * om + 3.0 * num) / (den * om);
+        rep = rho * R * T * Z;
+        drep = R * T * (Z + e * dZ);
+        att = a * rho * rho;
+        datt = 2.0 * a * rho;
+    } else {
+        double om = 1.0 - b * rho;
+        rep = rho * R * T / om;
+        drep = R * T / (om * om);
+        if (eos == ORC_VDW) {
+            att = a * rho * rho;
+            datt = 2.0 * a * rho;
+        } else if (eos == ORC_PR) {
+            double den = 1.0 + 2.0 * b * rho - b * b * rho * rho;
+            att = a * alpha * rho * rho / den;
+            datt = 2.0 * a * alpha * rho * (1.0 + b * rho) / (den * den);
+        } else { /* RK, RKS */
+            double den = 1.0 + b * rho;
+            att = a * alpha * rho * rho / den;
+            datt = a * alpha * rho * (2.0 + b * rho) / (den * den);
+        }
+    }
+    if (p) *p = rep - att;
+    if (dp) *dp = drep - datt;
+}
+
+static void eos_at(const orc_params *q, double rho, double *p, double *dp) {
+    double al = orc_alpha(q->eos, q->omega, q->T, q->Tc);
+    eos_eval(q->eos, q->a, q->b, q->R, q->T, al, rho, p, dp);
+}
+
+/* Vectorised p_EOS and dp/drho at the params' temperature (no Hu scaling). */
+void orc_p_eos(const orc_params *q, const double *rho, double *p, double *dp, int n) {
+    for (int i = 0; i < n; ++i) eos_at(q, rho[i], p ? &p[i] : NULL, dp ? &dp[i] : NULL);
+}
+
+/* Largest admissible density (repulsive-term pole): 1/b, or 4/b for CS. */
+static double rho_pole(int eos, double b) { return eos == ORC_CS ? 4.0 / b : 1.0 / b; }
+
+/* ------------------------------------------------------------------------ */
+/* Critical point: the maximum over rho of the spinodal temperature T_sp(rho),
+ * where dp/drho(rho, T_sp) = 0.  dp/drho rises with T at fixed rho for every
+ * EOS here, so T_sp(rho) is a bisection in T.  For PR and RKS alpha is taken
+ * as 1 (its value at T = Tc by construction); for RK alpha = 1/sqrt(T).      */
+/* ------------------------------------------------------------------------ */
+
+static double crit_alpha(int eos, double T) {
+    return eos == ORC_RK ? 1.0 / sqrt(T) : 1.0;
+}
+
+static double spinodal_T(int eos, double a, double b, double R, double rho) {
+    double lo = 1e-12, hi = 1.0, dp;
+    /* grow hi until dp/drho > 0 */
+    for (int it = 0; it < 200; ++it) {
+        eos_eval(eos, a, b, R, hi, crit_alpha(eos, hi), rho, NULL, &dp);
+        if (dp > 0) break;
+        lo = hi;
+        hi *= 2.0;
+    }
+    eos_eval(eos, a, b, R, lo, crit_alpha(eos, lo), rho, NULL, &dp);
+    if (dp > 0) return 0.0; /* no spinodal at this density */
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        eos_eval(eos, a, b, R, mid, crit_alpha(eos, mid), rho, NULL, &dp);
+        if (dp > 0) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* Returns 0 on success. */
+int orc_critical_point(int eos, double a, double b, double R, double *Tc, double *rhoc) {
+    double pole = rho_pole(eos, b);
+    /* coarse scan on a fine grid, then golden-section refinement */
+    int N = 4000, ibest = -1;
+    double best = -1.0;
+    for (int i = 1; i < N; ++i) {
+        double rho = pole * i / N;
+        double t = spinodal_T(eos, a, b, R, rho);
+        if (t > best) { best = t; ibest = i; }
+    }
+    if (ibest < 0 || best <= 0) return 1;
+    double lo = pole * (ibest - 1) / N, hi = pole * (ibest + 1) / N;
+    const double g = 0.5 * (sqrt(5.0) - 1.0);
+    double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+    double f1 = spinodal_T(eos, a, b, R, x1), f2 = spinodal_T(eos, a, b, R, x2);
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * pole; ++it) {
+        if (f1 < f2) { lo = x1; x1 = x2; f1 = f2; x2 = lo + g * (hi - lo); f2 = spinodal_T(eos, a, b, R, x2); }
+        else { hi = x2; x2 = x1; f2 = f1; x1 = hi - g * (hi - lo); f1 = spinodal_T(eos, a, b, R, x1); }
+    }
+    double rc = 0.5 * (lo + hi);
+    *rhoc = rc;
+    *Tc = spinodal_T(eos, a, b, R, rc);
+    if (f1 > *Tc) *Tc = f1;
+    if (f2 > *Tc) *Tc = f2;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Maxwell equal-area construction (Sec. 5.2): find p_s, rho_g < rho_l with   */
+/* p(rho_g) = p(rho_l) = p_s and  int_{rho_g}^{rho_l} (p - p_s)/rho^2 drho = 0 */
+/* (equal areas in the p-v plane, v = 1/rho).  The integral is taken in       */
+/* s = ln(rho) by composite Simpson; p_s by bisection.                         */
+/* ------------------------------------------------------------------------ */
+
+static double p_of(const orc_params *q, double rho) {
+    double p;
+    eos_at(q, rho, &p, NULL);
+    return p;
+}
+
+static double root_p(const orc_params *q, double ps, double lo, double hi) {
+    /* p increasing on [lo, hi]; find p(rho) = ps */
+    for (int it = 0; it < 300; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (p_of(q, mid) < ps) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static double area(const orc_params *q, double ps, double rg, double rl) {
+    int n = 20000; /* even */
+    double s0 = log(rg), s1 = log(rl), h = (s1 - s0) / n, acc = 0.0;
+    for (int i = 0; i <= n; ++i) {
+        double s = s0 + h * i, rho = exp(s);
+        double g = (p_of(q, rho) - ps) / rho; /* (p - ps)/rho^2 * drho/ds */
+        double wgt = (i == 0 || i == n) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        acc += wgt * g;
+    }
+    return acc * h / 3.0;
+}
+
+static double golden_extremum(const orc_params *q, double lo, double hi, int sign) {
+    const double g = 0.5 * (sqrt(5.0) - 1.0);
+    double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+    double f1 = sign * p_of(q, x1), f2 = sign * p_of(q, x2);
+    for (int it = 0; it < 300 && hi - lo > 1e-16 * hi; ++it) {
+        if (f1 < f2) { lo = x1; x1 = x2; f1 = f2; x2 = lo + g * (hi - lo); f2 = sign * p_of(q, x2); }
+        else { hi = x2; x2 = x1; f2 = f1; x1 = hi - g * (hi - lo); f1 = sign * p_of(q, x1); }
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* Returns 0 on success, 1 if the isotherm has no van der Waals loop. */
+int orc_maxwell(const orc_params *q, double *rho_g, double *rho_l, double *p_sat) {
+    double pole = rho_pole(q->eos, q->b);
+    /* locate the spinodal maximum and minimum on a log grid */
+    int N = 20000;
+    double lmin = log(pole * 1e-14), lmax = log(pole * (1.0 - 1e-9));
+    double prev2 = 0, prev = 0;
+    int imax = -1, imin = -1;
+    for (int i = 0; i < N; ++i) {
+        double rho = exp(lmin + (lmax - lmin) * i / (N - 1));
+        double p = p_of(q, rho);
+        if (i >= 2) {
+            if (imax < 0 && prev > prev2 && prev >= p) imax = i - 1;
+            else if (imax >= 0 && imin < 0 && prev < prev2 && prev <= p) { imin = i - 1; break; }
+        }
+        prev2 = prev;
+        prev = p;
+    }
+    if (imax < 0 || imin < 0) return 1;
+    double r_at = exp(lmin + (lmax - lmin) * (imax - 1) / (N - 1));
+    double r_bt = exp(lmin + (lmax - lmin) * (imax + 1) / (N - 1));
+    double rs1 = golden_extremum(q, r_at, r_bt, +1);
+    r_at = exp(lmin + (lmax - lmin) * (imin - 1) / (N - 1));
+    r_bt = exp(lmin + (lmax - lmin) * (imin + 1) / (N - 1));
+    double rs2 = golden_extremum(q, r_at, r_bt, -1);
+    double pmax = p_of(q, rs1), pmin = p_of(q, rs2);
+    double lo = pmin > 0 ? pmin : 0.0, hi = pmax;
+    double rg = 0, rl = 0;
+    for (int it = 0; it < 200; ++it) {
+        double ps = 0.5 * (lo + hi);
+        if (ps <= lo || ps >= hi) break;
+        rg = root_p(q, ps, 0.0, rs1);
+        rl = root_p(q, ps, rs2, pole);
+        double A = area(q, ps, rg, rl);
+        if (A > 0) lo = ps; else hi = ps;
+    }
+    double ps = 0.5 * (lo + hi);
+    *rho_g = root_p(q, ps, 0.0, rs1);
+    *rho_l = root_p(q, ps, rs2, pole);
+    if (p_sat) *p_sat = ps;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Equilibrium, Eq. 2.                                                        */
+/* ------------------------------------------------------------------------ */
+
+void orc_feq(double rho, double ux, double uy, double *feq) {
+    double uu = ux * ux + uy * uy;
+    for (int i = 0; i < 9; ++i) {
+        double eu = EX[i] * ux + EY[i] * uy;
+        feq[i] = rho * W9[i] * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Derivative operators.                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Thomas ("chasing") solve of a tridiagonal system
+ *   sub[i] x[i-1] + dia[i] x[i] + sup[i] x[i+1] = r[i]. */
+static void thomas(int n, const double *sub, const double *dia, const double *sup,
+                   const double *r, double *x, double *c) {
+    double m = dia[0];
+    c[0] = sup[0] / m;
+    x[0] = r[0] / m;
+    for (int i = 1; i < n; ++i) {
+        m = dia[i] - sub[i] * c[i - 1];
+        c[i] = sup[i] / m;
+        x[i] = (r[i] - sub[i] * x[i - 1]) / m;
+    }
+    for (int i = n - 2; i >= 0; --i) x[i] -= c[i] * x[i + 1];
+}
+
+/* HDM first derivative of one periodic line u[0..n-1] (h = 1), Eq. 20:
+ *   (1/3) d[i-1] + d[i] + (1/3) d[i+1]
+ *        = (1/9)(u[i+2]-u[i-2])/4 + (14/9)(u[i+1]-u[i-1])/2,
+ * indices taken modulo n.  The periodic system is cyclic tridiagonal; it is
+ * solved by Thomas on the matrix with modified corners plus a Sherman-Morrison
+ * rank-one correction.  n = 1, 2 are solved directly. */
+void orc_hdm_line(const double *u, double *d, int n) {
+    if (n <= 0) return;
+    double *r = (double *)malloc(sizeof(double) * (size_t)n * 7);
+    double *sub = r + n, *dia = sub + n, *sup = dia + n, *y = sup + n, *z = y + n, *c = z + n;
+    for (int i = 0; i < n; ++i)
+        r[i] = (1.0 / 9.0) * (u[wrap(i + 2, n)] - u[wrap(i - 2, n)]) / 4.0
+             + (14.0 / 9.0) * (u[wrap(i + 1, n)] - u[wrap(i - 1, n)]) / 2.0;
+    if (n == 1) {
+        d[0] = r[0] / (1.0 + 2.0 / 3.0);
+    } else if (n == 2) {
+        /* both neighbours of a cell are the other cell: [[1,2/3],[2/3,1]] */
+        double det = 1.0 - 4.0 / 9.0;
+        d[0] = (r[0] - (2.0 / 3.0) * r[1]) / det;
+        d[1] = (r[1] - (2.0 / 3.0) * r[0]) / det;
+    } else {
+        const double off = 1.0 / 3.0, alpha = 1.0 / 3.0, beta = 1.0 / 3.0;
+        double gamma = -1.0;
+        for (int i = 0; i < n; ++i) { sub[i] = off; dia[i] = 1.0; sup[i] = off; }
+        dia[0] = 1.0 - gamma;
+        dia[n - 1] = 1.0 - alpha * beta / gamma;
+        thomas(n, sub, dia, sup, r, y, c);
+        /* rank-one part u = (gamma, 0, ..., 0, alpha)^T; solve B z = u */
+        for (int i = 0; i < n; ++i) r[i] = 0.0;
+        r[0] = gamma;
+        r[n - 1] = alpha;
+        thomas(n, sub, dia, sup, r, z, c);
+        double fact = (y[0] + beta * y[n - 1] / gamma) / (1.0 + z[0] + beta * z[n - 1] / gamma);
+        for (int i = 0; i < n; ++i) d[i] = y[i] - fact * z[i];
+    }
+    free(r);
+}
+
+/* 2D HDM gradient: Eq. 20 along every row (d/dx) and every column (d/dy). */
+void orc_hdm_grad(const double *q, double *gx, double *gy, int nx, int ny) {
+#pragma omp parallel
+    {
+        int nmax = nx > ny ? nx : ny;
+        double *lin = (double *)malloc(sizeof(double) * (size_t)nmax * 2);
+        double *lout = lin + nmax;
+#pragma omp for schedule(static)
+        for (int y = 0; y < ny; ++y) orc_hdm_line(q + (size_t)y * nx, gx + (size_t)y * nx, nx);
+#pragma omp for schedule(static)
+        for (int x = 0; x < nx; ++x) {
+            for (int y = 0; y < ny; ++y) lin[y] = q[(size_t)y * nx + x];
+            orc_hdm_line(lin, lout, ny);
+            for (int y = 0; y < ny; ++y) gy[(size_t)y * nx + x] = lout[y];
+        }
+        free(lin);
+    }
+}
+
+/* 2D weighted CDM, Eq. 15, with the 1/c_s^2 factor so that a linear field has
+ * unit slope: d/dx q = (1/c_s^2) sum_i w_i q(x + e_i) e_ix. */
+void orc_cdm_grad(const double *q, double *gx, double *gy, int nx, int ny) {
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double sx = 0.0, sy = 0.0;
+            for (int i = 1; i < 9; ++i) {
+                double v = q[(size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx)];
+                sx += W9[i] * v * EX[i];
+                sy += W9[i] * v * EY[i];
+            }
+            gx[(size_t)y * nx + x] = sx / CS2;
+            gy[(size_t)y * nx + x] = sy / CS2;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interaction force from the density field.                                  */
+/*   U = k p_EOS - rho c_s^2 (Eq. 8 with Hu's scaling, Sec. 5)                 */
+/*   SC (Eq. 22): Phi = sqrt|U| (Eq. 21), F = -2 s Phi grad Phi, s = sign of U */
+/*                at the cell (s = +1 for U >= 0)                             */
+/*   ZC (Eq. 7):  F = -grad U                                                  */
+/* ------------------------------------------------------------------------ */
+
+void orc_force(const orc_params *q, const double *rho, double *Fx, double *Fy) {
+    size_t n = (size_t)q->nx * q->ny;
+    double *U = (double *)malloc(sizeof(double) * n * 4);
+    double *fld = U + n, *gx = fld + n, *gy = gx + n;
+    for (size_t c = 0; c < n; ++c) {
+        double p;
+        eos_at(q, rho[c], &p, NULL);
+        U[c] = q->k * p - rho[c] * CS2;
+        fld[c] = (q->force == ORC_SC) ? sqrt(fabs(U[c])) : U[c];
+    }
+    if (q->grad == ORC_HDM) orc_hdm_grad(fld, gx, gy, q->nx, q->ny);
+    else orc_cdm_grad(fld, gx, gy, q->nx, q->ny);
+    for (size_t c = 0; c < n; ++c) {
+        if (q->force == ORC_SC) {
+            double s = U[c] >= 0.0 ? 1.0 : -1.0;
+            Fx[c] = -2.0 * s * fld[c] * gx[c];
+            Fy[c] = -2.0 * s * fld[c] * gy[c];
+        } else {
+            Fx[c] = -gx[c];
+            Fy[c] = -gy[c];
+        }
+    }
+    free(U);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lattice state: f[i * nx*ny + y*nx + x] (i = 0..8).                          */
+/* ------------------------------------------------------------------------ */
+
+/* Initial distributions f = f^eq(rho, u) (the paper is silent; standard). */
+void orc_init(const orc_params *q, const double *rho, const double *ux, const double *uy, double *f) {
+    size_t n = (size_t)q->nx * q->ny;
+    double fe[9];
+    for (size_t c = 0; c < n; ++c) {
+        orc_feq(rho[c], ux ? ux[c] : 0.0, uy ? uy[c] : 0.0, fe);
+        for (int i = 0; i < 9; ++i) f[i * n + c] = fe[i];
+    }
+}
+
+/* Density and bare velocity, Eq. 3. */
+static void moments_bare(const orc_params *q, const double *f, double *rho, double *ux, double *uy) {
+    size_t n = (size_t)q->nx * q->ny;
+#pragma omp parallel for schedule(static)
+    for (long long cc = 0; cc < (long long)n; ++cc) {
+        size_t c = (size_t)cc;
+        double r = 0, jx = 0, jy = 0;
+        for (int i = 0; i < 9; ++i) {
+            double v = f[i * n + c];
+            r += v;
+            jx += EX[i] * v;
+            jy += EY[i] * v;
+        }
+        rho[c] = r;
+        ux[c] = jx / r;
+        uy[c] = jy / r;
+    }
+}
+
+typedef struct {
+    double *rho, *ux, *uy, *Fx, *Fy;
+} orc_work;
+
+static int work_alloc(orc_work *w, size_t n) {
+    w->rho = (double *)malloc(sizeof(double) * n * 5);
+    if (!w->rho) return 1;
+    w->ux = w->rho + n; w->uy = w->ux + n; w->Fx = w->uy + n; w->Fy = w->Fx + n;
+    return 0;
+}
+
+/* One time step, Eq. 1 with Eq. 10 forcing:
+ *   f_i*(x) = f_i - (f_i - f^eq(rho,u))/tau + [f^eq(rho,u+du) - f^eq(rho,u)],
+ *   du = F/rho (dt = 1),  then  f_i(x + e_i, t+1) = f_i*(x). */
+static void step_with(const orc_params *q, const double *f, double *fout, orc_work *w) {
+    int nx = q->nx, ny = q->ny;
+    size_t n = (size_t)nx * ny;
+    moments_bare(q, f, w->rho, w->ux, w->uy);
+    orc_force(q, w->rho, w->Fx, w->Fy);
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
+            double r = w->rho[c], ux = w->ux[c], uy = w->uy[c];
+            double dux = w->Fx[c] / r, duy = w->Fy[c] / r;
+            double fe[9], fs[9];
+            orc_feq(r, ux, uy, fe);
+            orc_feq(r, ux + dux, uy + duy, fs);
+            for (int i = 0; i < 9; ++i) {
+                double fi = f[i * n + c];
+                double post = fi - (fi - fe[i]) / q->tau + (fs[i] - fe[i]);
+                size_t d = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+                fout[i * n + d] = post;
+            }
+        }
+}
+
+/* One step from f into fout (allocates its own work space). Returns 0 on success. */
+int orc_step(const orc_params *q, const double *f, double *fout) {
+    orc_work w;
+    if (work_alloc(&w, (size_t)q->nx * q->ny)) return 1;
+    step_with(q, f, fout, &w);
+    free(w.rho);
+    return 0;
+}
+
+/* nsteps steps in place on f. Returns 0 on success. */
+int orc_run(const orc_params *q, double *f, int nsteps) {
+    size_t n = (size_t)q->nx * q->ny;
+    orc_work w;
+    double *g = (double *)malloc(sizeof(double) * n * 9);
+    if (!g || work_alloc(&w, n)) { free(g); return 1; }
+    double *src = f, *dst = g;
+    for (int s = 0; s < nsteps; ++s) {
+        step_with(q, src, dst, &w);
+        double *t = src; src = dst; dst = t;
+    }
+    if (src != f) memcpy(f, src, sizeof(double) * n * 9);
+    free(g);
+    free(w.rho);
+    return 0;
+}
+
+/* Observable moments: rho (Eq. 3) and the half-step velocity v of Eq. 11,
+ * rho v = sum_i e_i f_i + F/2. */
+int orc_moments(const orc_params *q, const double *f, double *rho, double *vx, double *vy) {
+    size_t n = (size_t)q->nx * q->ny;
+    orc_work w;
+    if (work_alloc(&w, n)) return 1;
+    moments_bare(q, f, w.rho, w.ux, w.uy);
+    orc_force(q, w.rho, w.Fx, w.Fy);
+    for (size_t c = 0; c < n; ++c) {
+        double r = w.rho[c];
+        rho[c] = r;
+        if (vx) vx[c] = w.ux[c] + 0.5 * w.Fx[c] / r;
+        if (vy) vy[c] = w.uy[c] + 0.5 * w.Fy[c] / r;
+    }
+    free(w.rho);
+    return 0;
+}
