@@ -1,0 +1,306 @@
+"""Throughput benchmark of the D2Q9 HDM pseudopotential step on GB300.
+
+Workload (one "step" = one lattice time step of the whole hot path: density,
+EOS/potential, HDM gradient, force, exact-difference forcing, BGK, periodic
+streaming): spinodal decomposition on a 4096 x 4096 periodic lattice,
+Carnahan-Starling EOS (a = 1, b = 4, R = 1) at T/Tc = 0.7, Hu scaling k = 0.04,
+Shan-Chen form with the HDM gradient, tau = 1, FP32 SoA distributions,
+initialised at the mean of the coexistence densities with 1 % seeded relative
+noise.  The distributions (2 x 604 MB) are larger than L2, so every timed
+step streams from HBM without an explicit flush.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(on the host cores, a bounded 1024 x 1024 sample of the same recipe per step).
+Under torchrun each rank runs its own replica of the lattice (no exchange:
+the lattices are independent problems), timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 4096
+TR, EOS, K_HU, TAU = 0.7, "cs", 0.04, 1.0
+METRIC = "D2Q9 HDM-pseudopotential MLUPS (spinodal 4096^2, FP32)"
+UNIT = "MLUPS"
+FALLBACK_HBM_GBS = 6800.0
+# Algorithmic HBM bytes per cell update of each kernel (FP32):
+#   potential pass: read 9 f (36 B) + write q (4 B)
+#   collide pass:   read 9 f (36 B) + read q (4 B) + write 9 f (36 B)
+#   fused step:     read 9 f (36 B) + write 9 f (36 B) + read q (4 B) + write q (4 B)
+ALGO_BYTES = {"potential": 40, "collide": 76, "fused_step": 80}
+STEP_MIN_BYTES = 72  # 9 f in + 9 f out: the method's minimum per cell update
+
+
+def workload_config():
+    return {"workload": f"spinodal {NX}x{NY} periodic, CS a=1 b=4 T/Tc={TR}, SC force, HDM gradient, "
+                        f"k={K_HU}, tau={TAU}, FP32 SoA",
+            "nx": NX, "ny": NY, "eos": EOS, "Tr": TR, "force": "sc", "grad": "hdm", "k": K_HU, "tau": TAU,
+            "l2": "inputs larger than L2 (f = 2 x 604 MB), no flush"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm_gb_s"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except (ValueError, OSError):
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1712_06079_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except ValueError:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_digest") != source_digest():
+        return None
+    return e.get("bytes_per_launch_full_size")
+
+
+def oracle_sample(n: int, steps: int):
+    """Time the oracle on an n x n lattice of the same recipe; returns (MLUPS, threads, seconds)."""
+    import oracle
+    from paper_1712_06079_gb300 import inputs
+    oracle.set_threads(oracle.max_threads())
+    op = oracle.params_at(n, n, EOS, 1.0, 4.0, TR, k=K_HU, tau=TAU, force="sc", grad="hdm")
+    f = oracle.init(op, inputs.spinodal(n, n, inputs.CS_TR07_MEAN))
+    t0 = time.perf_counter()
+    oracle.run(op, f, steps)
+    dt = time.perf_counter() - t0
+    return n * n * steps / dt / 1e6, oracle.max_threads(), dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = 1024
+    for _ in range(args.warmup):
+        oracle_sample(n, 1)
+    mlups, cores, dt = oracle_sample(n, args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(),
+        "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step = one oracle step of a {n}x{n} lattice of the same recipe"},
+        "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1712_06079_gb300 import inputs, lbm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    params = lbm.Params(nx=NX, ny=NY, eos=EOS, a=1.0, b=4.0, Tr=TR, k=K_HU, tau=TAU, force="sc", grad="hdm",
+                        prec="f32", stream=stream.cuda_stream)
+    rho0 = inputs.spinodal(NX, NY, inputs.CS_TR07_MEAN, seed=inputs.DEFAULT_SEED + rank)
+    cells = NX * NY
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    lat = lbm.Lattice(params)
+    lat.init_density(rho0)
+    lat.step(args.warmup)
+    lat.sync()
+    # --- device-timed region: inputs resident in HBM ---
+    barrier()
+    torch.cuda.synchronize()
+    lat.set_timing(True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        t0.record(stream)
+        for _ in range(args.steps):
+            lat.step(1)
+        t1.record(stream)
+        t1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = t0.elapsed_time(t1)
+    timing = lat.timing()
+    lat.set_timing(False)
+    lat.sync()
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * cells * args.steps / (ms * 1e-3) / 1e6
+
+    # --- end to end through the C ABI with host buffers ---
+    host_rho = np.ascontiguousarray(rho0)
+    barrier()
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    lat.init_density(host_rho)
+    lat.step(args.steps)
+    r, vx, vy = lat.moments()
+    e2e_s = time.perf_counter() - te
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = world * cells * args.steps / e2e_s / 1e6
+    assert np.isfinite(r).all()
+    lat.close()
+
+    if rank != 0:
+        return 0
+    kern = timing["kernels"]
+    dominant = max(kern, key=lambda k: kern[k]["ms"])
+    avg_ms = kern[dominant]["ms"] / kern[dominant]["count"]
+    achieved = ALGO_BYTES[dominant] * cells / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    clk = clocks.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(),
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "algo_bytes_per_cell": ALGO_BYTES[dominant],
+                     "traffic": ncu_traffic(dominant),
+                     "step_frac_of_min_bytes": STEP_MIN_BYTES * value * 1e6 / world / (peak * 1e9)},
+        "kernels_ms_per_launch": {k: v["ms"] / v["count"] for k, v in kern.items()},
+        "gpu_launches": timing["launches"],
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": cells * 4 / args.steps,
+                "d2h_bytes_per_step": (3 * cells * 4 + 4) / args.steps,
+                "note": "init_density from host FP64 rho (converted to FP32 in pinned staging), "
+                        "K steps, moments (rho, vx, vy) back to host FP64"},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        # bounded oracle sample: the same recipe on 1024 x 1024, enough steps for ~10 s
+        m1, cores, dt = oracle_sample(1024, 2)
+        steps = max(2, min(200, int(10.0 / max(dt / 2, 1e-3))))
+        mlups, cores, dt = oracle_sample(1024, steps)
+        line["cpu_baseline"] = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{steps} oracle steps of a 1024x1024 lattice of the same recipe "
+                                          f"({dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) D2Q9 pseudopotential lattice
+ * Boltzmann step with the high-order-difference (HDM) interaction force of
+ * Qin, Zhao, Chen, Zhang & Wen, "A pseudopotential multiphase lattice
+ * Boltzmann model based on high-order difference" (arXiv:1712.06079).
+ *
+ * One time step (Sec. 2 and Sec. 4 of the paper) is
+ *   rho = sum_i f_i, rho u = sum_i e_i f_i                        (Eq. 3)
+ *   p = k p_EOS(rho, T)  (Hu scaling, Sec. 5; EOS Eq. 24, 27-29)
+ *   U = p - rho c_s^2 (Eq. 8),  Phi = sqrt|U| (Eq. 21)
+ *   grad by the HDM compact scheme of Eq. 20 (or the CDM of Eq. 15)
+ *   F = -2 s Phi grad Phi (Shan-Chen form, Eq. 22; s = sign U at the cell)
+ *     or F = -grad U      (Zhang-Chen form, Eq. 7)
+ *   f_i* = f_i - (f_i - f_i^eq(rho,u))/tau
+ *          + f_i^eq(rho, u + F/rho) - f_i^eq(rho, u)           (Eq. 1, 2, 10)
+ *   f_i(x + e_i, t+1) = f_i*(x)  on a lattice periodic in x and y  (Eq. 1)
+ *
+ * Conventions shared by every entry point:
+ *  - Fields are row-major, x fastest: index = y * nx + x, nx * ny entries.
+ *  - Distributions are SoA: f[i * nx*ny + y*nx + x], i = 0..8 in the order
+ *    rest, +x, +y, -x, -y, (+1,+1), (-1,+1), (-1,-1), (+1,-1).
+ *  - "host" arrays are caller-owned CPU memory, copied in or out before the
+ *    call returns; "device" arrays are caller-owned CUDA device memory of the
+ *    context's precision (float for LBM_F32, double for LBM_F64), used on the
+ *    context's stream without synchronisation.
+ *  - The context owns all device memory it allocates; lbm_destroy frees it.
+ *  - Errors are status codes, never exceptions or aborts.  A failed call
+ *    leaves a message retrievable by lbm_last_error.  A context whose device
+ *    error word reports instability (NaN or rho <= 0) answers
+ *    LBM_E_UNSTABLE to lbm_step until it is re-initialised.
+ *  - Work is queued on params.stream (a cudaStream_t; NULL = the legacy
+ *    default stream).  lbm_step is asynchronous; lbm_sync, lbm_moments,
+ *    lbm_get_f and lbm_observables synchronise the stream and check the
+ *    device error word.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+typedef struct lbm_batch lbm_batch;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_E_INVALID = 1,  /* bad argument (null pointer, size, parameter range) */
+    LBM_E_NOMEM = 2,    /* device or host allocation failed */
+    LBM_E_CUDA = 3,     /* a CUDA runtime call failed */
+    LBM_E_UNSTABLE = 4, /* the device error word saw a NaN or rho <= 0 */
+    LBM_E_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+    LBM_E_STATE = 6     /* call out of order (e.g. step before init) */
+} lbm_status;
+
+/* Equations of state (Sec. 5.2): van der Waals (Eq. 24), Carnahan-Starling
+ * (Eq. 29, with the standard (1 - b rho/4)^3 denominator), Peng-Robinson
+ * (Eq. 28), Redlich-Kwong with alpha = 1/sqrt(T) (Eq. 27) and its Soave form
+ * (alpha(T) given after Eq. 27). */
+typedef enum { LBM_EOS_VDW = 0, LBM_EOS_CS = 1, LBM_EOS_PR = 2, LBM_EOS_RK = 3, LBM_EOS_RKS = 4 } lbm_eos;
+/* Interaction form: Shan-Chen effective mass (Eq. 4 rewritten as Eq. 22) or
+ * Zhang-Chen potential (Eq. 7 with U of Eq. 8). */
+typedef enum { LBM_FORCE_SC = 0, LBM_FORCE_ZC = 1 } lbm_force;
+/* Gradient operator: HDM compact scheme (Eq. 20) or weighted CDM (Eq. 15). */
+typedef enum { LBM_GRAD_HDM = 0, LBM_GRAD_CDM = 1 } lbm_grad;
+typedef enum { LBM_F32 = 0, LBM_F64 = 1 } lbm_prec;
+
+typedef struct {
+    int nx, ny;      /* lattice size, >= 1 each, periodic in both axes (Sec. 5.2) */
+    int prec;        /* lbm_prec: arithmetic and storage precision of f */
+    int eos;         /* lbm_eos */
+    int force;       /* lbm_force */
+    int grad;        /* lbm_grad */
+    int hdm_radius;  /* truncation radius K of the explicit form of Eq. 20;
+                        0 = automatic (18 for F32, 40 for F64); max 48 */
+    int reserved;    /* must be 0 */
+    double a, b, R;  /* EOS constants (Sec. 5.2: a = 9/49, b = 2/21 VdW; a = 1,
+                        b = 4 CS; R = 1) */
+    double omega;    /* acentric factor for PR and RKS (0.344 water) */
+    double Tr;       /* reduced temperature T/Tc, > 0 */
+    double Tc;       /* critical temperature; 0 = computed by lbm_critical_point */
+    double k;        /* Hu scaling p = k p_EOS (Sec. 5; 0.01 VdW, 0.02 RK,
+                        0.04 PR and CS in Sec. 5.2) */
+    double tau;      /* BGK relaxation time (Eq. 1), > 0.5 */
+    void *stream;    /* cudaStream_t for all work of this context, or NULL */
+} lbm_params;
+
+/* FP64 reductions over the lattice (Sec. 5.2 coexistence, Sec. 5.4 spurious
+ * currents).  v is the half-step velocity of Eq. 11. */
+typedef struct {
+    double mass;       /* sum_x rho */
+    double mom_x;      /* sum_x rho v_x */
+    double mom_y;      /* sum_x rho v_y */
+    double max_speed;  /* max_x |v| */
+    double rho_min, rho_max;
+} lbm_obs;
+
+/* Device-time accounting of lbm_step, for roofline measurements.  When
+ * enabled, lbm_step records a CUDA event pair on the context's stream around
+ * every kernel it launches; lbm_get_timing synchronises and sums them.  The
+ * kernel slots are: 0 potential pass, 1 force/collide/stream pass, 2 fused
+ * single-pass step, 3 unused. */
+typedef struct {
+    long long steps;            /* steps issued while timing was enabled */
+    long long launches;         /* kernels launched by lbm_step while enabled */
+    double ms_kernel[4];        /* summed device time per kernel slot */
+    long long count_kernel[4];  /* launches per kernel slot */
+} lbm_timing;
+
+/* Critical point (Tc, rho_c) of an EOS with alpha = 1 (PR, RKS) or
+ * alpha = 1/sqrt(T) (RK), i.e. dp/drho = d2p/drho2 = 0 (Sec. 5.2).  Host-only
+ * FP64 computation.  Returns LBM_E_INVALID for an unknown EOS or
+ * non-positive constants. */
+lbm_status lbm_critical_point(int eos, double a, double b, double R, double *Tc, double *rho_c);
+
+/* Weights of the explicit form of the periodic HDM operator (Eq. 20): on a
+ * periodic line of n points the solution of the tridiagonal system is
+ *   d_i = sum_{j=1..K} w[j] (u_{i+j} - u_{i-j}),
+ * with w folded over the period.  Writes w[0..radius] (w[0] = 0) and the
+ * effective radius min(radius, (n-1)/2) to *k_eff.  Host-only, FP64. */
+lbm_status lbm_hdm_weights(int n, int radius, double *w, int *k_eff);
+
+/* Create a context for one lattice (validates p, resolves Tc, allocates the
+ * two distribution buffers, the potential field and reduction scratch on the
+ * current CUDA device).  *out is set to NULL on failure. */
+lbm_status lbm_create(const lbm_params *p, lbm_ctx **out);
+
+/* f = f^eq(rho, u) (Eq. 2) from host FP64 fields rho (> 0), ux, uy
+ * (NULL = zero velocity).  Clears the error state.  Blocks until the copy
+ * has been issued and the init kernels are queued. */
+lbm_status lbm_init_density(lbm_ctx *c, const double *rho, const double *ux, const double *uy);
+
+/* Same from device arrays of the context precision (ux/uy may be NULL). */
+lbm_status lbm_init_density_device(lbm_ctx *c, const void *rho, const void *ux, const void *uy);
+
+/* Set or read the full distribution state f (host FP64, 9*nx*ny entries,
+ * SoA as above).  lbm_set_f clears the error state. */
+lbm_status lbm_set_f(lbm_ctx *c, const double *f);
+lbm_status lbm_get_f(lbm_ctx *c, double *f);
+
+/* Advance nsteps >= 0 time steps (Eq. 1).  Asynchronous on the context's
+ * stream.  Returns LBM_E_STATE before any init, LBM_E_UNSTABLE if a previous
+ * synchronising call saw the device error word set. */
+lbm_status lbm_step(lbm_ctx *c, int nsteps);
+
+/* Wait for the context's stream and check the device error word. */
+lbm_status lbm_sync(lbm_ctx *c);
+
+/* Density (Eq. 3) and half-step velocity v (Eq. 11) of the current state into
+ * host FP64 arrays (vx, vy may be NULL).  Synchronising. */
+lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy);
+
+/* Same into device arrays of the context precision; asynchronous. */
+lbm_status lbm_moments_device(lbm_ctx *c, void *rho, void *vx, void *vy);
+
+/* FP64 lattice reductions of the current state.  Synchronising. */
+lbm_status lbm_observables(lbm_ctx *c, lbm_obs *out);
+
+/* Enable (1) or disable (0) the event accounting of lbm_step; enabling
+ * resets the counters.  Not synchronising. */
+lbm_status lbm_set_timing(lbm_ctx *c, int enable);
+
+/* Read the accounting (synchronising).  Kernels launched while timing was
+ * disabled are not counted. */
+lbm_status lbm_get_timing(lbm_ctx *c, lbm_timing *out);
+
+/* Free everything the context owns.  NULL is a no-op. */
+void lbm_destroy(lbm_ctx *c);
+
+/* Message of the last failed call on c (or of the last failed lbm_create
+ * when c is NULL).  Never NULL. */
+const char *lbm_last_error(const lbm_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,479 @@
+// C ABI of the library (include/lbm.h): context life cycle, parameter
+// validation, host<->device marshalling and the launch sequence of a step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_params p{};
+    double T = 0, Tc = 0, alpha = 1;
+    int kx = 0, ky = 0;
+    double wx[kMaxRadius + 1] = {}, wy[kMaxRadius + 1] = {};
+    size_t esz = 4;               // bytes per value (float or double)
+    long long n = 0;              // cells
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;                  // f[cur] holds the current state
+    void *q = nullptr;            // potential field of the current pass
+    void *mom = nullptr;          // rho, vx, vy scratch (3 n values), lazily allocated
+    double *partial = nullptr;    // reduction partials
+    lbm_obs *obs_dev = nullptr;
+    int *err = nullptr;           // device error word
+    cudaStream_t stream = nullptr;
+    bool initialized = false;
+    bool unstable = false;
+    std::string msg;
+    // pinned host staging for precision conversion of host fields
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    // event accounting of lbm_step (lbm_set_timing)
+    bool timing = false;
+    lbm_timing tm{};
+    struct Pending { cudaEvent_t a, b; int slot; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+std::string g_create_error = "no error";
+
+lbm_status fail(lbm_ctx *c, lbm_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->msg = buf; else g_create_error = buf;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, LBM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(c, expr, what)                                   \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+double alpha_of(const lbm_params &p, double T, double Tc) {
+    double m, s;
+    switch (p.eos) {
+    case LBM_EOS_PR:  // Eq. 28
+        m = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
+        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
+        return s * s;
+    case LBM_EOS_RKS:  // Soave form after Eq. 27
+        m = 0.480 + 1.574 * p.omega - 0.176 * p.omega * p.omega;
+        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
+        return s * s;
+    case LBM_EOS_RK:  // Eq. 27
+        return 1.0 / std::sqrt(T);
+    default:
+        return 1.0;
+    }
+}
+
+template <typename T>
+Model<T> model_of(const lbm_ctx *c) {
+    Model<T> m{};
+    m.nx = c->p.nx;
+    m.ny = c->p.ny;
+    m.eos = c->p.eos;
+    m.kx = c->kx;
+    m.ky = c->ky;
+    m.RT = (T)(c->p.R * c->T);
+    m.a = (T)c->p.a;
+    m.b = (T)c->p.b;
+    m.aal = (T)(c->p.a * c->alpha);
+    m.k = (T)c->p.k;
+    m.omega = (T)(1.0 / c->p.tau);
+    for (int j = 0; j <= kMaxRadius; ++j) {
+        m.wx[j] = (T)c->wx[j];
+        m.wy[j] = (T)c->wy[j];
+    }
+    return m;
+}
+
+bool is_f64(const lbm_ctx *c) { return c->p.prec == LBM_F64; }
+bool is_sc(const lbm_ctx *c) { return c->p.force == LBM_FORCE_SC; }
+bool is_cdm(const lbm_ctx *c) { return c->p.grad == LBM_GRAD_CDM; }
+
+cudaError_t take_event(lbm_ctx *c, cudaEvent_t *ev) {
+    if (!c->event_pool.empty()) {
+        *ev = c->event_pool.back();
+        c->event_pool.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreate(ev);
+}
+
+// Resolve recorded event pairs into the per-slot sums (synchronises on them).
+cudaError_t resolve_timing(lbm_ctx *c) {
+    for (auto &p : c->pending) {
+        cudaError_t e = cudaEventSynchronize(p.b);
+        if (e != cudaSuccess) return e;
+        float ms = 0;
+        e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess) return e;
+        c->tm.ms_kernel[p.slot] += ms;
+        c->tm.count_kernel[p.slot] += 1;
+        c->event_pool.push_back(p.a);
+        c->event_pool.push_back(p.b);
+    }
+    c->pending.clear();
+    return cudaSuccess;
+}
+
+// Launch one kernel of a step through `fn`, bracketed by an event pair when
+// timing is enabled.
+template <typename Fn>
+cudaError_t timed_launch(lbm_ctx *c, int slot, Fn fn) {
+    if (!c->timing) return fn();
+    if (c->pending.size() >= 8192) {
+        cudaError_t e = resolve_timing(c);
+        if (e != cudaSuccess) return e;
+    }
+    cudaEvent_t a, b;
+    cudaError_t e = take_event(c, &a);
+    if (e == cudaSuccess) e = take_event(c, &b);
+    if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
+    if (e == cudaSuccess) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+    if (e != cudaSuccess) return e;
+    c->pending.push_back({a, b, slot});
+    c->tm.launches += 1;
+    return cudaSuccess;
+}
+
+// One time step: potential of f[cur] into q, then force/collide/stream into f[1-cur].
+template <typename T>
+cudaError_t step_once(lbm_ctx *c, const Model<T> &m) {
+    const T *f = (const T *)c->f[c->cur];
+    T *g = (T *)c->f[1 - c->cur];
+    cudaError_t e = timed_launch(c, 0, [&] { return launch_potential<T>(m, is_sc(c), f, (T *)c->q, c->err, c->stream); });
+    if (e != cudaSuccess) return e;
+    e = timed_launch(c, 1, [&] { return launch_collide<T>(m, is_sc(c), is_cdm(c), f, (const T *)c->q, g, c->stream); });
+    if (e != cudaSuccess) return e;
+    if (c->timing) c->tm.steps += 1;
+    c->cur = 1 - c->cur;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t moments_into(lbm_ctx *c, T *r, T *vx, T *vy) {
+    Model<T> m = model_of<T>(c);
+    const T *f = (const T *)c->f[c->cur];
+    cudaError_t e = launch_potential<T>(m, is_sc(c), f, (T *)c->q, c->err, c->stream);
+    if (e != cudaSuccess) return e;
+    return launch_moments<T>(m, is_sc(c), is_cdm(c), f, (const T *)c->q, r, vx, vy, c->stream);
+}
+
+lbm_status ensure_mom(lbm_ctx *c) {
+    if (c->mom) return LBM_OK;
+    CK(c, cudaMalloc(&c->mom, 3 * c->n * c->esz), "cudaMalloc(moments)");
+    return LBM_OK;
+}
+
+lbm_status read_error_word(lbm_ctx *c) {
+    int h = 0;
+    CK(c, cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read error word");
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (h & kErrUnstable) {
+        c->unstable = true;
+        return fail(c, LBM_E_UNSTABLE, "unstable: NaN or non-positive density on the lattice");
+    }
+    if (h & kErrTimeout) return fail(c, LBM_E_TIMEOUT, "a device-side wait timed out");
+    if (h & kErrBounds) return fail(c, LBM_E_CUDA, "a device-side bounds check failed");
+    return LBM_OK;
+}
+
+lbm_status check_ready(lbm_ctx *c) {
+    if (!c) return LBM_E_INVALID;
+    if (!c->initialized) return fail(c, LBM_E_STATE, "lattice not initialised (call lbm_init_density or lbm_set_f)");
+    if (c->unstable) return fail(c, LBM_E_UNSTABLE, "lattice is in the error state; re-initialise it");
+    return LBM_OK;
+}
+
+lbm_status mark_initialized(lbm_ctx *c) {
+    CK(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");
+    c->initialized = true;
+    c->unstable = false;
+    return LBM_OK;
+}
+
+lbm_status ensure_stage(lbm_ctx *c, size_t bytes) {
+    if (c->stage_bytes >= bytes) return LBM_OK;
+    CK(c, cudaStreamSynchronize(c->stream), "sync before staging realloc");
+    if (c->stage) cudaFreeHost(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    CK(c, cudaHostAlloc(&c->stage, bytes, cudaHostAllocDefault), "cudaHostAlloc(stage)");
+    c->stage_bytes = bytes;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
+    if (!out) return fail(nullptr, LBM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, LBM_E_INVALID, "params is NULL");
+    if (p->nx < 1 || p->ny < 1) return fail(nullptr, LBM_E_INVALID, "nx, ny must be >= 1 (got %d, %d)", p->nx, p->ny);
+    if ((long long)p->nx * p->ny > (1LL << 31)) return fail(nullptr, LBM_E_INVALID, "lattice larger than 2^31 cells");
+    if (p->prec != LBM_F32 && p->prec != LBM_F64) return fail(nullptr, LBM_E_INVALID, "prec must be LBM_F32 or LBM_F64");
+    if (p->eos < LBM_EOS_VDW || p->eos > LBM_EOS_RKS) return fail(nullptr, LBM_E_INVALID, "unknown eos %d", p->eos);
+    if (p->force != LBM_FORCE_SC && p->force != LBM_FORCE_ZC) return fail(nullptr, LBM_E_INVALID, "unknown force form");
+    if (p->grad != LBM_GRAD_HDM && p->grad != LBM_GRAD_CDM) return fail(nullptr, LBM_E_INVALID, "unknown gradient");
+    if (p->hdm_radius < 0 || p->hdm_radius > kMaxRadius)
+        return fail(nullptr, LBM_E_INVALID, "hdm_radius must be in [0, %d]", kMaxRadius);
+    if (p->reserved != 0) return fail(nullptr, LBM_E_INVALID, "reserved must be 0");
+    if (!(p->a >= 0) || !(p->b > 0) || !(p->R > 0)) return fail(nullptr, LBM_E_INVALID, "need a >= 0, b > 0, R > 0");
+    if (!(p->Tr > 0) || !std::isfinite(p->Tr)) return fail(nullptr, LBM_E_INVALID, "Tr must be > 0");
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(nullptr, LBM_E_INVALID, "tau must be > 0.5");
+    if (!std::isfinite(p->k) || !std::isfinite(p->omega)) return fail(nullptr, LBM_E_INVALID, "k, omega must be finite");
+
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_E_NOMEM, "host allocation failed");
+    c->p = *p;
+    c->stream = (cudaStream_t)p->stream;
+    c->esz = p->prec == LBM_F64 ? sizeof(double) : sizeof(float);
+    c->n = (long long)p->nx * p->ny;
+    if (p->Tc > 0) {
+        c->Tc = p->Tc;
+    } else {
+        double rc;
+        if (p->a <= 0 || lbm_critical_point(p->eos, p->a, p->b, p->R, &c->Tc, &rc) != LBM_OK) {
+            delete c;
+            return fail(nullptr, LBM_E_INVALID, "no critical point for these EOS constants; pass Tc explicitly");
+        }
+    }
+    c->T = p->Tr * c->Tc;
+    c->alpha = alpha_of(*p, c->T, c->Tc);
+    int radius = p->hdm_radius ? p->hdm_radius : (p->prec == LBM_F64 ? 40 : 18);
+    lbm_hdm_weights(p->nx, radius, c->wx, &c->kx);
+    lbm_hdm_weights(p->ny, radius, c->wy, &c->ky);
+
+    auto bail = [&](cudaError_t e, const char *what) {
+        lbm_status st = (e == cudaErrorMemoryAllocation) ? LBM_E_NOMEM : LBM_E_CUDA;
+        fail(nullptr, st, "%s: %s", what, cudaGetErrorString(e));
+        lbm_destroy(c);
+        return st;
+    };
+    cudaError_t e;
+    size_t fbytes = (size_t)kQ * c->n * c->esz;
+    if ((e = cudaMalloc(&c->f[0], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f0)");
+    if ((e = cudaMalloc(&c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
+    if ((e = cudaMalloc(&c->q, (size_t)c->n * c->esz)) != cudaSuccess) return bail(e, "cudaMalloc(q)");
+    if ((e = cudaMalloc(&c->partial, sizeof(double) * 6 * observables_partial_count())) != cudaSuccess)
+        return bail(e, "cudaMalloc(partial)");
+    if ((e = cudaMalloc(&c->obs_dev, sizeof(lbm_obs))) != cudaSuccess) return bail(e, "cudaMalloc(obs)");
+    if ((e = cudaMalloc(&c->err, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc(err)");
+    if ((e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)) != cudaSuccess) return bail(e, "cudaMemset(err)");
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_density_device(lbm_ctx *c, const void *rho, const void *ux, const void *uy) {
+    if (!c) return LBM_E_INVALID;
+    if (!rho) return fail(c, LBM_E_INVALID, "rho is NULL");
+    c->cur = 0;
+    cudaError_t e;
+    if (is_f64(c))
+        e = launch_init<double>(model_of<double>(c), (const double *)rho, (const double *)ux, (const double *)uy,
+                                (double *)c->f[0], c->stream);
+    else
+        e = launch_init<float>(model_of<float>(c), (const float *)rho, (const float *)ux, (const float *)uy,
+                               (float *)c->f[0], c->stream);
+    CK(c, e, "init kernel");
+    return mark_initialized(c);
+}
+
+lbm_status lbm_init_density(lbm_ctx *c, const double *rho, const double *ux, const double *uy) {
+    if (!c) return LBM_E_INVALID;
+    if (!rho) return fail(c, LBM_E_INVALID, "rho is NULL");
+    for (long long i = 0; i < c->n; ++i)
+        if (!(rho[i] > 0) || !std::isfinite(rho[i])) return fail(c, LBM_E_INVALID, "rho[%lld] is not a positive finite number", i);
+    lbm_status st = ensure_mom(c);
+    if (st != LBM_OK) return st;
+    char *dev = (char *)c->mom;
+    size_t fb = c->n * c->esz;
+    const double *src[3] = {rho, ux, uy};
+    if (!is_f64(c) && (st = ensure_stage(c, 3 * fb)) != LBM_OK) return st;
+    CK(c, cudaStreamSynchronize(c->stream), "sync before staging");  // stage may still feed an earlier copy
+    for (int k = 0; k < 3; ++k) {
+        if (!src[k]) continue;
+        if (is_f64(c)) {
+            CK(c, cudaMemcpyAsync(dev + k * fb, src[k], fb, cudaMemcpyHostToDevice, c->stream), "copy init field");
+        } else {
+            float *h = (float *)c->stage + k * c->n;
+            for (long long i = 0; i < c->n; ++i) h[i] = (float)src[k][i];
+            CK(c, cudaMemcpyAsync(dev + k * fb, h, fb, cudaMemcpyHostToDevice, c->stream), "copy init field");
+        }
+    }
+    return lbm_init_density_device(c, dev, ux ? dev + fb : nullptr, uy ? dev + 2 * fb : nullptr);
+}
+
+lbm_status lbm_set_f(lbm_ctx *c, const double *f) {
+    if (!c) return LBM_E_INVALID;
+    if (!f) return fail(c, LBM_E_INVALID, "f is NULL");
+    size_t cnt = (size_t)kQ * c->n;
+    c->cur = 0;
+    if (is_f64(c)) {
+        CK(c, cudaMemcpyAsync(c->f[0], f, cnt * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy f");
+        CK(c, cudaStreamSynchronize(c->stream), "sync f copy");
+    } else {
+        lbm_status st = ensure_stage(c, cnt * sizeof(float));
+        if (st != LBM_OK) return st;
+        CK(c, cudaStreamSynchronize(c->stream), "sync before staging");
+        float *h = (float *)c->stage;
+        for (size_t i = 0; i < cnt; ++i) h[i] = (float)f[i];
+        CK(c, cudaMemcpyAsync(c->f[0], h, cnt * sizeof(float), cudaMemcpyHostToDevice, c->stream), "copy f");
+        CK(c, cudaStreamSynchronize(c->stream), "sync f copy");
+    }
+    return mark_initialized(c);
+}
+
+lbm_status lbm_get_f(lbm_ctx *c, double *f) {
+    lbm_status st = check_ready(c);
+    if (st != LBM_OK) return st;
+    if (!f) return fail(c, LBM_E_INVALID, "f is NULL");
+    size_t cnt = (size_t)kQ * c->n;
+    if (is_f64(c)) {
+        CK(c, cudaMemcpyAsync(f, c->f[c->cur], cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy f");
+        CK(c, cudaStreamSynchronize(c->stream), "sync f copy");
+    } else {
+        lbm_status st2 = ensure_stage(c, cnt * sizeof(float));
+        if (st2 != LBM_OK) return st2;
+        float *h = (float *)c->stage;
+        CK(c, cudaMemcpyAsync(h, c->f[c->cur], cnt * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy f");
+        CK(c, cudaStreamSynchronize(c->stream), "sync f copy");
+        for (size_t i = 0; i < cnt; ++i) f[i] = h[i];
+    }
+    return read_error_word(c);
+}
+
+lbm_status lbm_step(lbm_ctx *c, int nsteps) {
+    lbm_status st = check_ready(c);
+    if (st != LBM_OK) return st;
+    if (nsteps < 0) return fail(c, LBM_E_INVALID, "nsteps must be >= 0");
+    if (is_f64(c)) {
+        Model<double> m = model_of<double>(c);
+        for (int s = 0; s < nsteps; ++s) CK(c, step_once<double>(c, m), "step");
+    } else {
+        Model<float> m = model_of<float>(c);
+        for (int s = 0; s < nsteps; ++s) CK(c, step_once<float>(c, m), "step");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx *c) {
+    if (!c) return LBM_E_INVALID;
+    return read_error_word(c);
+}
+
+lbm_status lbm_moments_device(lbm_ctx *c, void *rho, void *vx, void *vy) {
+    lbm_status st = check_ready(c);
+    if (st != LBM_OK) return st;
+    if (!rho || !vx || !vy) return fail(c, LBM_E_INVALID, "rho, vx, vy must be non-NULL device arrays");
+    cudaError_t e = is_f64(c) ? moments_into<double>(c, (double *)rho, (double *)vx, (double *)vy)
+                              : moments_into<float>(c, (float *)rho, (float *)vx, (float *)vy);
+    CK(c, e, "moments kernel");
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy) {
+    lbm_status st = check_ready(c);
+    if (st != LBM_OK) return st;
+    if (!rho) return fail(c, LBM_E_INVALID, "rho is NULL");
+    if ((st = ensure_mom(c)) != LBM_OK) return st;
+    char *dev = (char *)c->mom;
+    size_t fb = c->n * c->esz;
+    if ((st = lbm_moments_device(c, dev, dev + fb, dev + 2 * fb)) != LBM_OK) return st;
+    double *dst[3] = {rho, vx, vy};
+    if (is_f64(c)) {
+        for (int k = 0; k < 3; ++k)
+            if (dst[k]) CK(c, cudaMemcpyAsync(dst[k], dev + k * fb, fb, cudaMemcpyDeviceToHost, c->stream), "copy moments");
+        CK(c, cudaStreamSynchronize(c->stream), "sync moments");
+    } else {
+        if ((st = ensure_stage(c, 3 * fb)) != LBM_OK) return st;
+        float *h = (float *)c->stage;
+        for (int k = 0; k < 3; ++k)
+            if (dst[k]) CK(c, cudaMemcpyAsync(h + k * c->n, dev + k * fb, fb, cudaMemcpyDeviceToHost, c->stream), "copy moments");
+        CK(c, cudaStreamSynchronize(c->stream), "sync moments");
+        for (int k = 0; k < 3; ++k)
+            if (dst[k])
+                for (long long i = 0; i < c->n; ++i) dst[k][i] = h[k * c->n + i];
+    }
+    return read_error_word(c);
+}
+
+lbm_status lbm_observables(lbm_ctx *c, lbm_obs *out) {
+    lbm_status st = check_ready(c);
+    if (st != LBM_OK) return st;
+    if (!out) return fail(c, LBM_E_INVALID, "out is NULL");
+    if ((st = ensure_mom(c)) != LBM_OK) return st;
+    char *dev = (char *)c->mom;
+    size_t fb = c->n * c->esz;
+    if ((st = lbm_moments_device(c, dev, dev + fb, dev + 2 * fb)) != LBM_OK) return st;
+    cudaError_t e = is_f64(c) ? launch_observables<double>(c->n, (double *)dev, (double *)(dev + fb),
+                                                           (double *)(dev + 2 * fb), c->partial, c->obs_dev, c->stream)
+                              : launch_observables<float>(c->n, (float *)dev, (float *)(dev + fb),
+                                                          (float *)(dev + 2 * fb), c->partial, c->obs_dev, c->stream);
+    CK(c, e, "observables kernel");
+    CK(c, cudaMemcpyAsync(out, c->obs_dev, sizeof(lbm_obs), cudaMemcpyDeviceToHost, c->stream), "copy observables");
+    return read_error_word(c);
+}
+
+lbm_status lbm_set_timing(lbm_ctx *c, int enable) {
+    if (!c) return LBM_E_INVALID;
+    if (enable) {
+        CK(c, resolve_timing(c), "resolve timing events");
+        c->tm = lbm_timing{};
+    }
+    c->timing = enable != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_timing(lbm_ctx *c, lbm_timing *out) {
+    if (!c) return LBM_E_INVALID;
+    if (!out) return fail(c, LBM_E_INVALID, "out is NULL");
+    CK(c, resolve_timing(c), "resolve timing events");
+    *out = c->tm;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->q);
+    cudaFree(c->mom);
+    cudaFree(c->partial);
+    cudaFree(c->obs_dev);
+    cudaFree(c->err);
+    if (c->stage) cudaFreeHost(c->stage);
+    for (auto &p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto ev : c->event_pool) cudaEventDestroy(ev);
+    delete c;
+}
+
+const char *lbm_last_error(const lbm_ctx *c) {
+    return c ? c->msg.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

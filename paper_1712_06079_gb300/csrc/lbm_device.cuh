@@ -1,0 +1,87 @@
+// Device-side building blocks of the D2Q9 pseudopotential step (sm_103a).
+//
+// D2Q9 ordering (Eq. 2, "D2Q9 model"; the paper does not print it):
+//   i : 0     1     2     3     4     5      6      7       8
+//   e : (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+//   w : 4/9, 1/9 for the axes, 1/36 for the diagonals.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+constexpr int kQ = 9;
+constexpr int kMaxRadius = 48;  // largest HDM truncation radius accepted
+
+__host__ __device__ __forceinline__ constexpr int ex(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int ey(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+template <typename T>
+__host__ __device__ __forceinline__ constexpr T wq(int i) {
+    return i == 0 ? T(4.0 / 9.0) : (i < 5 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+}
+
+// Error word bits written by kernels (read back by lbm_sync).
+constexpr int kErrUnstable = 1;  // NaN or rho <= 0 seen
+constexpr int kErrTimeout = 2;   // a bounded device-side wait gave up
+constexpr int kErrBounds = 4;    // a self-checked index fell outside a buffer
+
+// Per-launch constants of the model, in the working precision.
+template <typename T>
+struct Model {
+    int nx, ny;
+    int eos;       // lbm_eos
+    int kx, ky;    // HDM stencil radius along x and y (already folded to the period)
+    T RT;          // R * T
+    T a, b;
+    T aal;         // a * alpha(T) (PR, RK, RKS)
+    T k;           // Hu scaling
+    T omega;       // 1 / tau
+    T wx[kMaxRadius + 1];  // explicit HDM weights along x (w[0] unused)
+    T wy[kMaxRadius + 1];  // ... along y
+};
+
+// p_EOS(rho) at the model's temperature (Eq. 24, 27, 28, 29); no Hu factor.
+template <typename T>
+__device__ __forceinline__ T p_eos(const Model<T> &m, T rho) {
+    if (m.eos == LBM_EOS_CS) {
+        T e = m.b * rho * T(0.25);
+        T om = T(1) - e;
+        return rho * m.RT * (T(1) + e + e * e - e * e * e) / (om * om * om) - m.a * rho * rho;
+    }
+    T rep = rho * m.RT / (T(1) - m.b * rho);
+    if (m.eos == LBM_EOS_VDW) return rep - m.a * rho * rho;
+    if (m.eos == LBM_EOS_PR) return rep - m.aal * rho * rho / (T(1) + T(2) * m.b * rho - m.b * m.b * rho * rho);
+    return rep - m.aal * rho * rho / (T(1) + m.b * rho);  // RK, RKS
+}
+
+// Interaction potential U = k p_EOS - rho c_s^2 (Eq. 8 with Hu scaling).
+template <typename T>
+__device__ __forceinline__ T potential_u(const Model<T> &m, T rho) {
+    return m.k * p_eos(m, rho) - rho * T(1.0 / 3.0);
+}
+
+// Field stored for the gradient: SC (Eq. 21/22) keeps the signed root
+// q = s sqrt|U| (the stencil uses |q| = Phi, the cell itself s Phi);
+// ZC (Eq. 7) keeps U.
+template <typename T>
+__device__ __forceinline__ T potential_field(const Model<T> &m, T rho, bool sc) {
+    T U = potential_u(m, rho);
+    if (!sc) return U;
+    return U >= T(0) ? sqrt(U) : -sqrt(-U);
+}
+
+// Periodic wrap of an index that may lie several periods outside [0, n).
+__device__ __forceinline__ int wrap_index(int i, int n) {
+    while (i < 0) i += n;
+    while (i >= n) i -= n;
+    return i;
+}
+
+}  // namespace lbm

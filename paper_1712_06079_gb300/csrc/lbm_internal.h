@@ -1,0 +1,37 @@
+// Internal (C++) launch interface between the C ABI and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// f = f^eq(rho, u) (Eq. 2); ux/uy may be null (zero velocity).
+template <typename T>
+cudaError_t launch_init(const Model<T> &m, const T *rho, const T *ux, const T *uy, T *f, cudaStream_t s);
+
+// Pass 1 of a step: rho = sum_i f_i (Eq. 3) and the potential field
+// (Eq. 8 / Eq. 21) into q; flags NaN or rho <= 0 in *err.
+template <typename T>
+cudaError_t launch_potential(const Model<T> &m, bool sc, const T *f, T *q, int *err, cudaStream_t s);
+
+// Pass 2 of a step: HDM (Eq. 20) or CDM (Eq. 15) gradient of q, force
+// (Eq. 22 / Eq. 7), exact-difference forcing + BGK (Eq. 1, 10) and periodic
+// push streaming from f into fout.
+template <typename T>
+cudaError_t launch_collide(const Model<T> &m, bool sc, bool cdm, const T *f, const T *q, T *fout, cudaStream_t s);
+
+// rho (Eq. 3) and the half-step velocity v (Eq. 11) of state f with its q.
+template <typename T>
+cudaError_t launch_moments(const Model<T> &m, bool sc, bool cdm, const T *f, const T *q, T *rho, T *vx, T *vy,
+                           cudaStream_t s);
+
+// FP64 reductions of (rho, vx, vy) over n cells into *out (device memory).
+// partial must hold observables_partial_count() * 6 doubles.
+int observables_partial_count();
+template <typename T>
+cudaError_t launch_observables(long long n, const T *rho, const T *vx, const T *vy, double *partial, lbm_obs *out,
+                               cudaStream_t s);
+
+}  // namespace lbm

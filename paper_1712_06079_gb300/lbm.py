@@ -1,0 +1,233 @@
+"""ctypes binding of ``liblbm.so`` (C ABI in ``include/lbm.h``).
+
+Argument marshalling only: every step of the lattice update runs in the CUDA
+kernels of the library.  If the library has not been built this module raises
+on first use; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, E_INVALID, E_NOMEM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE = range(7)
+EOS = {"vdw": 0, "cs": 1, "pr": 2, "rk": 3, "rks": 4}
+FORCE = {"sc": 0, "zc": 1}
+GRAD = {"hdm": 0, "cdm": 1}
+PREC = {"f32": 0, "f64": 1}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lbm status {status}: {msg}")
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("prec", ctypes.c_int), ("eos", ctypes.c_int),
+                ("force", ctypes.c_int), ("grad", ctypes.c_int), ("hdm_radius", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("R", ctypes.c_double), ("omega", ctypes.c_double), ("Tr", ctypes.c_double),
+                ("Tc", ctypes.c_double), ("k", ctypes.c_double), ("tau", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class _Obs(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("mom_x", ctypes.c_double), ("mom_y", ctypes.c_double),
+                ("max_speed", ctypes.c_double), ("rho_min", ctypes.c_double), ("rho_max", ctypes.c_double)]
+
+
+class _Timing(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("launches", ctypes.c_longlong),
+                ("ms_kernel", ctypes.c_double * 4), ("count_kernel", ctypes.c_longlong * 4)]
+
+
+# kernel slots of lbm_timing
+KERNEL_SLOTS = ("potential", "collide", "fused_step", "unused")
+
+# name -> (restype, argtypes) of every entry point declared in include/lbm.h
+_D = ctypes.POINTER(ctypes.c_double)
+_V = ctypes.c_void_p
+SIGNATURES = {
+    "lbm_critical_point": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D]),
+    "lbm_hdm_weights": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_create": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.POINTER(_V)]),
+    "lbm_init_density": (ctypes.c_int, [_V, _D, _D, _D]),
+    "lbm_init_density_device": (ctypes.c_int, [_V, _V, _V, _V]),
+    "lbm_set_f": (ctypes.c_int, [_V, _D]),
+    "lbm_get_f": (ctypes.c_int, [_V, _D]),
+    "lbm_step": (ctypes.c_int, [_V, ctypes.c_int]),
+    "lbm_sync": (ctypes.c_int, [_V]),
+    "lbm_moments": (ctypes.c_int, [_V, _D, _D, _D]),
+    "lbm_moments_device": (ctypes.c_int, [_V, _V, _V, _V]),
+    "lbm_observables": (ctypes.c_int, [_V, ctypes.POINTER(_Obs)]),
+    "lbm_set_timing": (ctypes.c_int, [_V, ctypes.c_int]),
+    "lbm_get_timing": (ctypes.c_int, [_V, ctypes.POINTER(_Timing)]),
+    "lbm_destroy": (None, [_V]),
+    "lbm_last_error": (ctypes.c_char_p, [_V]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load liblbm.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with paper_1712_06079_gb300.build.build() "
+                                   "(or __graft_entry__.build()); there is no CPU fallback")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def critical_point(eos: str, a: float, b: float, R: float = 1.0):
+    Tc, rc = ctypes.c_double(), ctypes.c_double()
+    st = load().lbm_critical_point(EOS[eos], a, b, R, ctypes.byref(Tc), ctypes.byref(rc))
+    if st != OK:
+        raise LBMError(st, "lbm_critical_point failed")
+    return Tc.value, rc.value
+
+
+def hdm_weights(n: int, radius: int):
+    w = np.zeros(radius + 1)
+    k = ctypes.c_int()
+    st = load().lbm_hdm_weights(n, radius, _dp(w), ctypes.byref(k))
+    if st != OK:
+        raise LBMError(st, "lbm_hdm_weights failed")
+    return w, k.value
+
+
+@dataclasses.dataclass
+class Params:
+    nx: int
+    ny: int
+    eos: str = "cs"
+    a: float = 1.0
+    b: float = 4.0
+    R: float = 1.0
+    omega: float = 0.0
+    Tr: float = 0.8
+    Tc: float = 0.0
+    k: float = 1.0
+    tau: float = 1.0
+    force: str = "sc"
+    grad: str = "hdm"
+    prec: str = "f32"
+    hdm_radius: int = 0
+    stream: int = 0  # cudaStream_t as an integer (torch.cuda.Stream.cuda_stream), 0 = default
+
+    def c(self) -> _Params:
+        return _Params(self.nx, self.ny, PREC[self.prec], EOS[self.eos], FORCE[self.force], GRAD[self.grad],
+                       self.hdm_radius, 0, self.a, self.b, self.R, self.omega, self.Tr, self.Tc, self.k,
+                       self.tau, ctypes.c_void_p(self.stream or None))
+
+
+class Lattice:
+    """One periodic D2Q9 lattice behind an ``lbm_ctx``."""
+
+    def __init__(self, params: Params):
+        self.params = params
+        self._lib = load()
+        h = ctypes.c_void_p()
+        st = self._lib.lbm_create(ctypes.byref(params.c()), ctypes.byref(h))
+        if st != OK:
+            raise LBMError(st, self._lib.lbm_last_error(None).decode())
+        self._h = h
+        self.shape = (params.ny, params.nx)
+        self.dtype = np.float64 if params.prec == "f64" else np.float32
+
+    def _check(self, st: int):
+        if st != OK:
+            raise LBMError(st, self._lib.lbm_last_error(self._h).decode())
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def init_density(self, rho, ux=None, uy=None):
+        c = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape)
+        rho, ux, uy = c(rho), c(ux), c(uy)
+        self._check(self._lib.lbm_init_density(self._h, _dp(rho), _dp(ux), _dp(uy)))
+
+    def init_density_device(self, rho_ptr: int, ux_ptr: int = 0, uy_ptr: int = 0):
+        self._check(self._lib.lbm_init_density_device(self._h, rho_ptr or None, ux_ptr or None, uy_ptr or None))
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape((9,) + self.shape)
+        self._check(self._lib.lbm_set_f(self._h, _dp(f)))
+
+    def get_f(self) -> np.ndarray:
+        f = np.empty((9,) + self.shape)
+        self._check(self._lib.lbm_get_f(self._h, _dp(f)))
+        return f
+
+    def step(self, n: int = 1):
+        self._check(self._lib.lbm_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._lib.lbm_sync(self._h))
+
+    def moments(self):
+        r, vx, vy = (np.empty(self.shape) for _ in range(3))
+        self._check(self._lib.lbm_moments(self._h, _dp(r), _dp(vx), _dp(vy)))
+        return r, vx, vy
+
+    def moments_device(self, rho_ptr: int, vx_ptr: int, vy_ptr: int):
+        self._check(self._lib.lbm_moments_device(self._h, rho_ptr, vx_ptr, vy_ptr))
+
+    def observables(self) -> dict:
+        o = _Obs()
+        self._check(self._lib.lbm_observables(self._h, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in _Obs._fields_}
+
+    def set_timing(self, enable: bool):
+        self._check(self._lib.lbm_set_timing(self._h, 1 if enable else 0))
+
+    def timing(self) -> dict:
+        t = _Timing()
+        self._check(self._lib.lbm_get_timing(self._h, ctypes.byref(t)))
+        return {"steps": t.steps, "launches": t.launches,
+                "kernels": {KERNEL_SLOTS[i]: {"ms": t.ms_kernel[i], "count": t.count_kernel[i]}
+                            for i in range(4) if t.count_kernel[i]}}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.lbm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,101 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and
+loads, exports every entry point ``include/*.h`` declares, validates
+parameters before touching the device, and its host-only set-up math agrees
+with the oracle (critical points; the explicit HDM weights reproduce the
+oracle's cyclic tridiagonal solve of Eq. 20)."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_06079_gb300 import build, lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lbm.load()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert "lbm_create" in names and "lbm_step" in names and "lbm_destroy" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding knows the signature of each
+    assert set(names) <= set(lbm.SIGNATURES), set(names) - set(lbm.SIGNATURES)
+
+
+@pytest.mark.parametrize("eos,a,b", [("vdw", 9 / 49, 2 / 21), ("cs", 1.0, 4.0), ("pr", 2 / 49, 2 / 21),
+                                     ("rk", 2 / 49, 2 / 21), ("rks", 9 / 49, 2 / 21), ("cs", 0.3, 1.7)])
+def test_critical_point_matches_oracle(lib, eos, a, b):
+    Tc, rc = lbm.critical_point(eos, a, b)
+    To, ro = oracle.critical_point(eos, a, b)
+    assert Tc == pytest.approx(To, rel=1e-13)
+    assert rc == pytest.approx(ro, rel=1e-7)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 9, 16, 17, 40, 81, 128, 1000])
+def test_hdm_weights_reproduce_cyclic_solve(lib, n):
+    # the explicit folded stencil equals the exact periodic solve of Eq. 20
+    for radius in (40, 48):
+        w, ke = lbm.hdm_weights(n, radius)
+        assert ke == min(radius, (n - 1) // 2)
+        rng = np.random.default_rng(n)
+        u = rng.standard_normal(n)
+        d = np.zeros(n)
+        for j in range(1, ke + 1):
+            d += w[j] * (np.roll(u, -j) - np.roll(u, j))
+        assert np.allclose(d, oracle.hdm_line(u), rtol=0, atol=5e-15 * max(1, np.abs(u).max()) * 10)
+
+
+def test_hdm_weights_known_values(lib):
+    # N = 8 folds to rational weights [221, -75, 25]/252 (and 0 at j = 4)
+    w, ke = lbm.hdm_weights(8, 40)
+    assert ke == 3
+    assert np.allclose(w[1:4], np.array([221, -75, 25]) / 252, rtol=0, atol=1e-15)
+    # long lines: consistency sum_j 2 j w_j = 1 (exact first derivative of a line)
+    w, ke = lbm.hdm_weights(4096, 40)
+    assert np.sum(2 * np.arange(41) * w) == pytest.approx(1.0, abs=1e-14)
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-1), dict(tau=0.5), dict(Tr=0.0), dict(hdm_radius=49),
+                                 dict(b=0.0), dict(prec="bogus")])
+def test_create_rejects_bad_params_before_device_work(lib, bad):
+    p = lbm.Params(nx=16, ny=16)
+    if bad.get("prec") == "bogus":
+        c = p.c()
+        c.prec = 7
+    else:
+        for k, v in bad.items():
+            setattr(p, k, v)
+        c = p.c()
+    import ctypes
+    h = ctypes.c_void_p()
+    st = lib.lbm_create(ctypes.byref(c), ctypes.byref(h))
+    assert st == lbm.E_INVALID
+    assert h.value is None
+    assert lib.lbm_last_error(None)
+
+
+def test_null_handles_are_safe(lib):
+    import ctypes
+    lib.lbm_destroy(None)
+    assert lib.lbm_step(None, 1) == lbm.E_INVALID
+    assert lib.lbm_sync(None) == lbm.E_INVALID
+    assert lib.lbm_create(None, None) == lbm.E_INVALID
+    assert lib.lbm_last_error(None)

@@ -1,0 +1,167 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+identical seeded inputs.
+
+Bars: FP64 path within 1e-12 relative per step (element by element over all
+nine populations); FP32 path within 1e-5 relative on rho after 1000 steps for
+the relaxing droplet and flat-interface workloads; observables in FP64."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_06079_gb300 import inputs, lbm
+
+pytestmark = pytest.mark.gpu
+
+EOS = inputs.EOS_TABLE
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1712_06079_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def make(nx, ny, eos="cs", Tr=0.8, force="sc", grad="hdm", tau=1.0, prec="f64", k=None, radius=0):
+    t = EOS[eos]
+    kk = t["k"] if k is None else k
+    gp = lbm.Params(nx=nx, ny=ny, eos=eos, a=t["a"], b=t["b"], omega=t["omega"], Tr=Tr, k=kk, tau=tau,
+                    force=force, grad=grad, prec=prec, hdm_radius=radius)
+    op = oracle.params_at(nx, ny, eos, t["a"], t["b"], Tr, omega=t["omega"], k=kk, tau=tau, force=force, grad=grad)
+    return gp, op
+
+
+def perturbed_state(op, rho, seed):
+    # f^eq(rho, u) with a small seeded velocity and an off-equilibrium part
+    ny, nx = rho.shape
+    xi = inputs.uniform01(seed, 11 * nx * ny).reshape(11, ny, nx)
+    ux, uy = 0.02 * (xi[0] - 0.5), 0.02 * (xi[1] - 0.5)
+    f = oracle.init(op, rho, ux, uy)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    return f * (1.0 + 1e-3 * (xi[2:] - 0.5) * w / w.max())
+
+
+CASES_F64 = [
+    # (nx, ny, eos, Tr, force, grad, tau)
+    (128, 128, "cs", 0.8, "sc", "hdm", 1.0),    # droplet workload
+    (1024, 8, "pr", 0.7, "zc", "hdm", 1.0),     # flat interface, folded y stencil
+    (1024, 8, "pr", 0.7, "zc", "cdm", 1.0),
+    (96, 40, "vdw", 0.9, "sc", "cdm", 0.8),
+    (37, 23, "rk", 0.75, "zc", "hdm", 1.3),     # ragged tiles, odd sizes
+    (8, 8, "cs", 0.8, "sc", "hdm", 1.0),        # smaller than the stencil
+    (3, 5, "vdw", 0.8, "zc", "hdm", 1.0),
+    (1, 16, "cs", 0.8, "sc", "hdm", 1.0),       # degenerate axis: d/dx = 0
+    (200, 1, "pr", 0.8, "sc", "hdm", 1.0),
+    (70, 90, "rks", 0.8, "sc", "hdm", 1.0),
+]
+
+
+@pytest.mark.parametrize("nx,ny,eos,Tr,force,grad,tau", CASES_F64)
+def test_f64_one_step_parity(nx, ny, eos, Tr, force, grad, tau):
+    gp, op = make(nx, ny, eos, Tr, force, grad, tau)
+    g, l, _ = oracle.maxwell(op)
+    rho = inputs.droplet(nx, ny, min(nx, ny) / 4, g, l) if min(nx, ny) > 8 else inputs.slab(nx, ny, g, l)
+    f0 = perturbed_state(op, rho, seed=nx * 1000 + ny)
+    with lbm.Lattice(gp) as lat:
+        lat.set_f(f0)
+        lat.step(1)
+        fg = lat.get_f()
+    fo = oracle.step(op, f0)
+    rel = np.abs(fg - fo) / np.abs(fo)
+    assert rel.max() < 1e-12, rel.max()
+
+
+def test_f64_moments_and_observables_parity():
+    gp, op = make(128, 96, "cs", 0.8, "sc", "hdm")
+    g, l, _ = oracle.maxwell(op)
+    f0 = perturbed_state(op, inputs.droplet(128, 96, 25, g, l), seed=5)
+    with lbm.Lattice(gp) as lat:
+        lat.set_f(f0)
+        r, vx, vy = lat.moments()
+        obs = lat.observables()
+    ro, vxo, vyo = oracle.moments(op, f0)
+    assert np.allclose(r, ro, rtol=1e-13, atol=0)
+    scale = np.abs(vxo).max()
+    assert np.abs(vx - vxo).max() < 1e-12 * scale and np.abs(vy - vyo).max() < 1e-12 * scale
+    assert obs["mass"] == pytest.approx(ro.sum(), rel=1e-13)
+    assert obs["mom_x"] == pytest.approx((ro * vxo).sum(), abs=1e-12 * ro.sum() * scale)
+    assert obs["max_speed"] == pytest.approx(np.sqrt(vxo ** 2 + vyo ** 2).max(), rel=1e-12)
+    assert obs["rho_min"] == pytest.approx(ro.min(), rel=1e-14)
+    assert obs["rho_max"] == pytest.approx(ro.max(), rel=1e-14)
+
+
+def test_f64_droplet_2000_steps():
+    # workload: 128^2 CS Tr=0.8 droplet R=30, SC + HDM, tau = 1, 2000 steps
+    gp, op = make(128, 128, "cs", 0.8, "sc", "hdm")
+    g, l, _ = oracle.maxwell(op)
+    rho0 = inputs.droplet(128, 128, 30, g, l)
+    with lbm.Lattice(gp) as lat:
+        lat.init_density(rho0)
+        lat.step(2000)
+        r, vx, vy = lat.moments()
+        obs = lat.observables()
+    fo = oracle.run(op, oracle.init(op, rho0), 2000)
+    ro, vxo, vyo = oracle.moments(op, fo)
+    assert np.abs(r - ro).max() / ro.max() < 1e-10
+    assert np.sqrt(vx ** 2 + vy ** 2).max() == pytest.approx(np.sqrt(vxo ** 2 + vyo ** 2).max(), rel=1e-7)
+    assert abs(obs["mass"] - rho0.sum()) / rho0.sum() < 1e-13
+
+
+@pytest.mark.parametrize("case", ["droplet", "slab"])
+def test_f32_1000_steps_against_f64_oracle(case):
+    if case == "droplet":
+        gp, op = make(128, 128, "cs", 0.8, "sc", "hdm", prec="f32")
+        g, l, _ = oracle.maxwell(op)
+        rho0 = inputs.droplet(128, 128, 30, g, l)
+    else:
+        gp, op = make(1024, 8, "pr", 0.7, "zc", "hdm", prec="f32")
+        g, l, _ = oracle.maxwell(op)
+        rho0 = inputs.slab(1024, 8, g, l)
+    with lbm.Lattice(gp) as lat:
+        lat.init_density(rho0)
+        lat.step(1000)
+        r, _, _ = lat.moments()
+    ro, _, _ = oracle.moments(op, oracle.run(op, oracle.init(op, rho0), 1000))
+    err = np.max(np.abs(r - ro) / np.abs(ro))
+    assert err < 1e-5, err
+
+
+def test_f32_one_step_full_size_spinodal():
+    # the throughput workload at full size: 4096^2 CS Tr=0.7, mean of the
+    # coexistence pair with 1 % relative noise; one step against the oracle
+    n = 4096
+    gp, op = make(n, n, "cs", 0.7, "sc", "hdm", prec="f32")
+    rho0 = inputs.spinodal(n, n, inputs.CS_TR07_MEAN)
+    with lbm.Lattice(gp) as lat:
+        lat.init_density(rho0)
+        lat.step(1)
+        r, vx, _ = lat.moments()
+    oracle.set_threads(oracle.max_threads())
+    ro, vxo, _ = oracle.moments(op, oracle.step(op, oracle.init(op, rho0)))
+    assert np.max(np.abs(r - ro) / ro) < 2e-6
+    assert np.max(np.abs(vx - vxo)) < 1e-6 * np.abs(vxo).max() + 1e-9
+
+
+def test_unstable_state_is_reported_and_cleared():
+    gp, op = make(32, 32, "cs", 0.8, "sc", "hdm")
+    f = oracle.init(op, np.full((32, 32), 0.1))
+    f[:, 5, 7] = -0.01  # negative density at one cell
+    with lbm.Lattice(gp) as lat:
+        lat.set_f(f)
+        lat.step(1)
+        with pytest.raises(lbm.LBMError) as ei:
+            lat.sync()
+        assert ei.value.status == lbm.E_UNSTABLE
+        with pytest.raises(lbm.LBMError):
+            lat.step(1)
+        lat.init_density(np.full((32, 32), 0.1))
+        lat.step(3)
+        lat.sync()
+
+
+def test_step_before_init_is_rejected():
+    gp, _ = make(16, 16)
+    with lbm.Lattice(gp) as lat:
+        with pytest.raises(lbm.LBMError) as ei:
+            lat.step(1)
+        assert ei.value.status == lbm.E_STATE
