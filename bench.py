@@ -288,15 +288,19 @@ def run_ours(args):
 
 
 def main():
+    global NX, NY
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=NX, help="lattice size (default: the 4096 x 4096 workload)")
+    ap.add_argument("--ny", type=int, default=NY)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    NX, NY = args.nx, args.ny
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -64,6 +64,9 @@ typedef enum { LBM_FORCE_SC = 0, LBM_FORCE_ZC = 1 } lbm_force;
 /* Gradient operator: HDM compact scheme (Eq. 20) or weighted CDM (Eq. 15). */
 typedef enum { LBM_GRAD_HDM = 0, LBM_GRAD_CDM = 1 } lbm_grad;
 typedef enum { LBM_F32 = 0, LBM_F64 = 1 } lbm_prec;
+/* LBM_FLAG_TWO_PASS: never use the single-pass FP32 step kernel (keep the
+ * potential pass + collide pass form even where the fused kernel applies). */
+enum { LBM_FLAG_TWO_PASS = 1 };
 
 typedef struct {
     int nx, ny;      /* lattice size, >= 1 each, periodic in both axes (Sec. 5.2) */
@@ -73,7 +76,7 @@ typedef struct {
     int grad;        /* lbm_grad */
     int hdm_radius;  /* truncation radius K of the explicit form of Eq. 20;
                         0 = automatic (18 for F32, 40 for F64); max 48 */
-    int reserved;    /* must be 0 */
+    int flags;       /* bit set of LBM_FLAG_* (0 = defaults) */
     double a, b, R;  /* EOS constants (Sec. 5.2: a = 9/49, b = 2/21 VdW; a = 1,
                         b = 4 CS; R = 1) */
     double omega;    /* acentric factor for PR and RKS (0.344 water) */

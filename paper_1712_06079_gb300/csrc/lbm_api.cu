@@ -23,6 +23,9 @@ struct lbm_ctx {
     void *f[2] = {nullptr, nullptr};
     int cur = 0;                  // f[cur] holds the current state
     void *q = nullptr;            // potential field of the current pass
+    bool fused = false;           // FP32 single-pass step in use
+    void *qpad[2] = {nullptr, nullptr};  // padded potential of f[0] / f[1] (fused path)
+    bool qpad_valid = false;      // qpad[cur] holds the potential of f[cur]
     void *mom = nullptr;          // rho, vx, vy scratch (3 n values), lazily allocated
     double *partial = nullptr;    // reduction partials
     lbm_obs *obs_dev = nullptr;
@@ -170,6 +173,27 @@ cudaError_t step_once(lbm_ctx *c, const Model<T> &m) {
     return cudaSuccess;
 }
 
+// One time step by the single-pass FP32 kernel.
+cudaError_t step_fused(lbm_ctx *c, const Model<float> &m) {
+    const float *f = (const float *)c->f[c->cur];
+    cudaError_t e;
+    if (!c->qpad_valid) {
+        e = timed_launch(c, 0, [&] {
+            return launch_potential_padded(m, is_sc(c), f, (float *)c->qpad[c->cur], c->err, c->stream);
+        });
+        if (e != cudaSuccess) return e;
+        c->qpad_valid = true;
+    }
+    e = timed_launch(c, 2, [&] {
+        return launch_fused_step(m, is_sc(c), f, (const float *)c->qpad[c->cur], (float *)c->f[1 - c->cur],
+                                 (float *)c->qpad[1 - c->cur], c->err, c->stream);
+    });
+    if (e != cudaSuccess) return e;
+    if (c->timing) c->tm.steps += 1;
+    c->cur = 1 - c->cur;
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t moments_into(lbm_ctx *c, T *r, T *vx, T *vy) {
     Model<T> m = model_of<T>(c);
@@ -209,6 +233,7 @@ lbm_status mark_initialized(lbm_ctx *c) {
     CK(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");
     c->initialized = true;
     c->unstable = false;
+    c->qpad_valid = false;
     return LBM_OK;
 }
 
@@ -239,7 +264,7 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if (p->grad != LBM_GRAD_HDM && p->grad != LBM_GRAD_CDM) return fail(nullptr, LBM_E_INVALID, "unknown gradient");
     if (p->hdm_radius < 0 || p->hdm_radius > kMaxRadius)
         return fail(nullptr, LBM_E_INVALID, "hdm_radius must be in [0, %d]", kMaxRadius);
-    if (p->reserved != 0) return fail(nullptr, LBM_E_INVALID, "reserved must be 0");
+    if (p->flags & ~LBM_FLAG_TWO_PASS) return fail(nullptr, LBM_E_INVALID, "unknown flags 0x%x", p->flags);
     if (!(p->a >= 0) || !(p->b > 0) || !(p->R > 0)) return fail(nullptr, LBM_E_INVALID, "need a >= 0, b > 0, R > 0");
     if (!(p->Tr > 0) || !std::isfinite(p->Tr)) return fail(nullptr, LBM_E_INVALID, "Tr must be > 0");
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(nullptr, LBM_E_INVALID, "tau must be > 0.5");
@@ -277,6 +302,13 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if ((e = cudaMalloc(&c->f[0], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f0)");
     if ((e = cudaMalloc(&c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
     if ((e = cudaMalloc(&c->q, (size_t)c->n * c->esz)) != cudaSuccess) return bail(e, "cudaMalloc(q)");
+    c->fused = p->prec == LBM_F32 && !(p->flags & LBM_FLAG_TWO_PASS) &&
+               fused_step_supported(model_of<float>(c), p->grad == LBM_GRAD_CDM, radius);
+    if (c->fused) {
+        size_t qb = sizeof(float) * (size_t)fused_q_pitch(p->nx) * p->ny;
+        if ((e = cudaMalloc(&c->qpad[0], qb)) != cudaSuccess) return bail(e, "cudaMalloc(qpad0)");
+        if ((e = cudaMalloc(&c->qpad[1], qb)) != cudaSuccess) return bail(e, "cudaMalloc(qpad1)");
+    }
     if ((e = cudaMalloc(&c->partial, sizeof(double) * 6 * observables_partial_count())) != cudaSuccess)
         return bail(e, "cudaMalloc(partial)");
     if ((e = cudaMalloc(&c->obs_dev, sizeof(lbm_obs))) != cudaSuccess) return bail(e, "cudaMalloc(obs)");
@@ -372,6 +404,9 @@ lbm_status lbm_step(lbm_ctx *c, int nsteps) {
     if (is_f64(c)) {
         Model<double> m = model_of<double>(c);
         for (int s = 0; s < nsteps; ++s) CK(c, step_once<double>(c, m), "step");
+    } else if (c->fused) {
+        Model<float> m = model_of<float>(c);
+        for (int s = 0; s < nsteps; ++s) CK(c, step_fused(c, m), "fused step");
     } else {
         Model<float> m = model_of<float>(c);
         for (int s = 0; s < nsteps; ++s) CK(c, step_once<float>(c, m), "step");
@@ -462,6 +497,8 @@ void lbm_destroy(lbm_ctx *c) {
     cudaFree(c->f[0]);
     cudaFree(c->f[1]);
     cudaFree(c->q);
+    cudaFree(c->qpad[0]);
+    cudaFree(c->qpad[1]);
     cudaFree(c->mom);
     cudaFree(c->partial);
     cudaFree(c->obs_dev);

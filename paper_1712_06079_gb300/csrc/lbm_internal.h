@@ -34,4 +34,15 @@ template <typename T>
 cudaError_t launch_observables(long long n, const T *rho, const T *vx, const T *vy, double *partial, lbm_obs *out,
                                cudaStream_t s);
 
+// Single-pass FP32 step (fused_step.cu): reads f(t) and the padded potential
+// q(t), writes f(t+1) and the padded potential of f(t+1).  The padded
+// potential has fused_q_pitch(nx) floats per row, column x stored at x + 24,
+// with periodic images in the 24 ghost columns on each side.
+bool fused_step_supported(const Model<float> &m, bool cdm, int radius);
+int fused_q_pitch(int nx);
+cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float *f, float *qpad, int *err,
+                                    cudaStream_t s);
+cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, const float *qin, float *fout,
+                              float *qout, int *err, cudaStream_t s);
+
 }  // namespace lbm

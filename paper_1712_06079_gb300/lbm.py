@@ -20,6 +20,7 @@ EOS = {"vdw": 0, "cs": 1, "pr": 2, "rk": 3, "rks": 4}
 FORCE = {"sc": 0, "zc": 1}
 GRAD = {"hdm": 0, "cdm": 1}
 PREC = {"f32": 0, "f64": 1}
+FLAG_TWO_PASS = 1
 
 _lib = None
 _lock = threading.Lock()
@@ -34,7 +35,7 @@ class LBMError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("prec", ctypes.c_int), ("eos", ctypes.c_int),
                 ("force", ctypes.c_int), ("grad", ctypes.c_int), ("hdm_radius", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("flags", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double),
                 ("R", ctypes.c_double), ("omega", ctypes.c_double), ("Tr", ctypes.c_double),
                 ("Tc", ctypes.c_double), ("k", ctypes.c_double), ("tau", ctypes.c_double),
                 ("stream", ctypes.c_void_p)]
@@ -139,11 +140,12 @@ class Params:
     grad: str = "hdm"
     prec: str = "f32"
     hdm_radius: int = 0
+    two_pass: bool = False  # LBM_FLAG_TWO_PASS: never use the single-pass FP32 kernel
     stream: int = 0  # cudaStream_t as an integer (torch.cuda.Stream.cuda_stream), 0 = default
 
     def c(self) -> _Params:
         return _Params(self.nx, self.ny, PREC[self.prec], EOS[self.eos], FORCE[self.force], GRAD[self.grad],
-                       self.hdm_radius, 0, self.a, self.b, self.R, self.omega, self.Tr, self.Tc, self.k,
+                       self.hdm_radius, FLAG_TWO_PASS if self.two_pass else 0, self.a, self.b, self.R, self.omega, self.Tr, self.Tc, self.k,
                        self.tau, ctypes.c_void_p(self.stream or None))
 
 
