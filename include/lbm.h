@@ -75,7 +75,7 @@ typedef struct {
     int force;       /* lbm_force */
     int grad;        /* lbm_grad */
     int hdm_radius;  /* truncation radius K of the explicit form of Eq. 20;
-                        0 = automatic (18 for F32, 40 for F64); max 48 */
+                        0 = automatic (26 for F32, 40 for F64); max 48 */
     int flags;       /* bit set of LBM_FLAG_* (0 = defaults) */
     double a, b, R;  /* EOS constants (Sec. 5.2: a = 9/49, b = 2/21 VdW; a = 1,
                         b = 4 CS; R = 1) */

@@ -287,7 +287,7 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     }
     c->T = p->Tr * c->Tc;
     c->alpha = alpha_of(*p, c->T, c->Tc);
-    int radius = p->hdm_radius ? p->hdm_radius : (p->prec == LBM_F64 ? 40 : 18);
+    int radius = p->hdm_radius ? p->hdm_radius : (p->prec == LBM_F64 ? 40 : 26);
     lbm_hdm_weights(p->nx, radius, c->wx, &c->kx);
     lbm_hdm_weights(p->ny, radius, c->wy, &c->ky);
 

@@ -157,17 +157,22 @@ __global__ void __launch_bounds__(TX *TYT) collide_kernel(Model<T> m, const T *_
         const T vx = ux + Fx * inv, vy = uy + Fy * inv;  // u + du, du = F/rho (Eq. 10)
         const T uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
         const int yp = y + 1 == m.ny ? 0 : y + 1, ym = y == 0 ? m.ny - 1 : y - 1;
+        // f_i* for the eight moving populations; the rest population takes the
+        // remainder so that the collision conserves mass up to rounding
+        T moved = T(0);
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) {
+        for (int i = 1; i < kQ; ++i) {
             const T eu = T(ex(i)) * ux + T(ey(i)) * uy;
             const T ev = T(ex(i)) * vx + T(ey(i)) * vy;
             const T feq = r * wq<T>(i) * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
             const T fsh = r * wq<T>(i) * (T(1) + T(3) * ev + T(4.5) * ev * ev - T(1.5) * vv);
             const T post = fi[i] - (fi[i] - feq) * m.omega + (fsh - feq);
+            moved += post;
             const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
             const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
             fout[i * n + (long long)dys * m.nx + dxs] = post;
         }
+        fout[c] = r - moved;
     }
 }
 

