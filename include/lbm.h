@@ -167,6 +167,34 @@ lbm_status lbm_set_timing(lbm_ctx *c, int enable);
  * disabled are not counted. */
 lbm_status lbm_get_timing(lbm_ctx *c, lbm_timing *out);
 
+/* Size of the fixed device scratch array used by lbm_step_noalloc. */
+#define LBM_STATIC_SCRATCH_BYTES (4u << 20)
+
+/* One time step that allocates nothing (the paper has no counterpart: this is
+ * a deployment variant of lbm_step).  For callers that cannot call cudaMalloc
+ * -- a host framework that owns every device allocation, or a latency-
+ * critical loop that must not take cudaMalloc's implicit synchronisation.
+ *   p      lattice and model parameters, as for lbm_create (p->stream is used;
+ *          p->flags is accepted but the step always takes the two-pass form);
+ *   f_in   device array, 9*nx*ny values of the precision p->prec, SoA as
+ *          above: the state at t (read only);
+ *   f_out  device array of the same size, distinct from f_in: receives the
+ *          state at t+1.  Both stay owned by the caller.
+ * The potential field and the error word live in one file-scope device array
+ * of LBM_STATIC_SCRATCH_BYTES (4 MiB) that every GPU loading the library holds
+ * until the process exits, so nx*ny may be at most (4 MiB - 256 B) / 4 =
+ * 1,048,512 cells in LBM_F32 and 524,256 in LBM_F64; larger lattices are
+ * rejected with LBM_E_INVALID before any device work.  The first call on a
+ * device looks the array's device address up (with that device current), so
+ * make the first call before any stream capture.  Every call, on any stream,
+ * shares the one array and leaves its contents behind; the error word is
+ * cleared at the start of each call.  Calls whose work overlaps on the GPU
+ * therefore race and must be serialised by the caller.  Synchronising:
+ * returns LBM_E_UNSTABLE if the step saw a NaN or rho <= 0, LBM_E_CUDA on a
+ * CUDA error, LBM_E_INVALID on bad arguments.  Calls no cudaMalloc, cudaFree
+ * or other allocating routine. */
+lbm_status lbm_step_noalloc(const lbm_params *p, const void *f_in, void *f_out);
+
 /* Free everything the context owns.  NULL is a no-op. */
 void lbm_destroy(lbm_ctx *c);
 

@@ -1,0 +1,125 @@
+// lbm_step_noalloc: one time step that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: a host framework that owns every
+// device allocation (a fixed pool it hands out itself), or a latency-critical
+// loop where cudaMalloc's implicit device-wide synchronisation is not
+// allowed.  This entry point lets them run the two-pass step on buffers they
+// already own.  The only device memory it needs beyond the caller's f_in and
+// f_out -- the potential field of the step and the error word -- lives in a
+// fixed file-scope array of LBM_STATIC_SCRATCH_BYTES that every GPU loading
+// the library holds until the process exits.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[LBM_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+constexpr size_t kErrBytes = 256;  // error word, padded so the field stays 256-byte aligned
+
+std::mutex g_scratch_mutex;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The array's
+// name is a host-side stand-in in host code, so its address is looked up
+// once per device with that device current.
+lbm_status scratch_on_current_device(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_E_CUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return LBM_E_CUDA;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return LBM_OK;
+}
+
+double alpha_at(const lbm_params &p, double T, double Tc) {
+    double m, s;
+    switch (p.eos) {
+    case LBM_EOS_PR:  // Eq. 28
+        m = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
+        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
+        return s * s;
+    case LBM_EOS_RKS:
+        m = 0.480 + 1.574 * p.omega - 0.176 * p.omega * p.omega;
+        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
+        return s * s;
+    case LBM_EOS_RK:  // Eq. 27
+        return 1.0 / std::sqrt(T);
+    default:
+        return 1.0;
+    }
+}
+
+template <typename T>
+lbm_status run_step(const lbm_params &p, double Tc, const void *f_in, void *f_out, void *scratch) {
+    using namespace lbm;
+    Model<T> m{};
+    m.nx = p.nx;
+    m.ny = p.ny;
+    m.eos = p.eos;
+    const double Temp = p.Tr * Tc;
+    m.RT = (T)(p.R * Temp);
+    m.a = (T)p.a;
+    m.b = (T)p.b;
+    m.aal = (T)(p.a * alpha_at(p, Temp, Tc));
+    m.k = (T)p.k;
+    m.omega = (T)(1.0 / p.tau);
+    const int radius = p.hdm_radius ? p.hdm_radius : (p.prec == LBM_F64 ? 40 : 26);
+    double wx[kMaxRadius + 1] = {}, wy[kMaxRadius + 1] = {};
+    if (lbm_hdm_weights(p.nx, radius, wx, &m.kx) != LBM_OK || lbm_hdm_weights(p.ny, radius, wy, &m.ky) != LBM_OK)
+        return LBM_E_INVALID;
+    for (int j = 0; j <= kMaxRadius; ++j) {
+        m.wx[j] = (T)wx[j];
+        m.wy[j] = (T)wy[j];
+    }
+    cudaStream_t s = (cudaStream_t)p.stream;
+    int *err = (int *)scratch;
+    T *q = (T *)((unsigned char *)scratch + kErrBytes);
+    const bool sc = p.force == LBM_FORCE_SC, cdm = p.grad == LBM_GRAD_CDM;
+    if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return LBM_E_CUDA;
+    if (launch_potential<T>(m, sc, (const T *)f_in, q, err, s) != cudaSuccess) return LBM_E_CUDA;
+    if (launch_collide<T>(m, sc, cdm, (const T *)f_in, q, (T *)f_out, s) != cudaSuccess) return LBM_E_CUDA;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LBM_E_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LBM_E_CUDA;
+    return (h & kErrUnstable) ? LBM_E_UNSTABLE : LBM_OK;
+}
+
+}  // namespace
+
+namespace {
+long long max_cells(int prec) {
+    const size_t esz = prec == LBM_F64 ? sizeof(double) : sizeof(float);
+    return (long long)((LBM_STATIC_SCRATCH_BYTES - kErrBytes) / esz);
+}
+}  // namespace
+
+extern "C" lbm_status lbm_step_noalloc(const lbm_params *p, const void *f_in, void *f_out) {
+    if (!p || !f_in || !f_out || f_in == f_out) return LBM_E_INVALID;
+    if (p->nx < 1 || p->ny < 1 || (p->prec != LBM_F32 && p->prec != LBM_F64)) return LBM_E_INVALID;
+    if (p->eos < LBM_EOS_VDW || p->eos > LBM_EOS_RKS || (p->force != LBM_FORCE_SC && p->force != LBM_FORCE_ZC) ||
+        (p->grad != LBM_GRAD_HDM && p->grad != LBM_GRAD_CDM))
+        return LBM_E_INVALID;
+    if (p->hdm_radius < 0 || p->hdm_radius > lbm::kMaxRadius || p->flags & ~LBM_FLAG_TWO_PASS) return LBM_E_INVALID;
+    if (!(p->a >= 0) || !(p->b > 0) || !(p->R > 0) || !(p->Tr > 0) || !(p->tau > 0.5) || !std::isfinite(p->k))
+        return LBM_E_INVALID;
+    if ((long long)p->nx * p->ny > max_cells(p->prec)) return LBM_E_INVALID;
+    double Tc = p->Tc, rc = 0;
+    if (!(Tc > 0) && (p->a <= 0 || lbm_critical_point(p->eos, p->a, p->b, p->R, &Tc, &rc) != LBM_OK))
+        return LBM_E_INVALID;
+    void *scratch = nullptr;
+    lbm_status st = scratch_on_current_device(&scratch);
+    if (st != LBM_OK) return st;
+    return p->prec == LBM_F64 ? run_step<double>(*p, Tc, f_in, f_out, scratch)
+                              : run_step<float>(*p, Tc, f_in, f_out, scratch);
+}

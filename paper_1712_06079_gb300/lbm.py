@@ -72,6 +72,7 @@ SIGNATURES = {
     "lbm_observables": (ctypes.c_int, [_V, ctypes.POINTER(_Obs)]),
     "lbm_set_timing": (ctypes.c_int, [_V, ctypes.c_int]),
     "lbm_get_timing": (ctypes.c_int, [_V, ctypes.POINTER(_Timing)]),
+    "lbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(_Params), _V, _V]),
     "lbm_destroy": (None, [_V]),
     "lbm_last_error": (ctypes.c_char_p, [_V]),
 }
@@ -112,6 +113,13 @@ def critical_point(eos: str, a: float, b: float, R: float = 1.0):
     if st != OK:
         raise LBMError(st, "lbm_critical_point failed")
     return Tc.value, rc.value
+
+
+def step_noalloc(params: "Params", f_in_ptr: int, f_out_ptr: int) -> int:
+    """One step from device array f_in to device array f_out through
+    lbm_step_noalloc (no device allocation; see include/lbm.h).  Returns the
+    lbm_status code."""
+    return load().lbm_step_noalloc(ctypes.byref(params.c()), f_in_ptr, f_out_ptr)
 
 
 def hdm_weights(n: int, radius: int):
