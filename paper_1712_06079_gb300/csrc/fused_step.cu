@@ -9,35 +9,37 @@
 //
 // Decomposition.  A CTA of 8 warps owns a strip of TXI = 120 columns and a
 // segment of up to SEG_H = 128 rows.  It sweeps the segment in slabs of 8
-// rows, one warp per row and one lane per 4 consecutive cells (float4 SoA
-// loads, 16 B per lane, 512 B per warp).  Lanes 1..30 hold the strip's
-// columns; lanes 0 and 31 hold the 4-column groups just outside it, whose
-// collision is recomputed so that rho(t+1) of every strip cell can be formed
-// on chip (post-collision values of all eight neighbours are needed).
+// rows, one warp per row and one lane per 4 consecutive cells.  Lanes 1..30
+// hold the strip's columns; lanes 0 and 31 hold the 4-column groups just
+// outside it, whose collision is recomputed so that the density at t+1 of
+// every strip cell can be formed on chip.
 //
-// Per slab:
-//  1. the potential rows the HDM stencil needs (radius FK = 26 rows above and
-//     below, FK columns left and right) are staged in an 80-row shared ring,
-//     8 rows per chunk, by the bulk-copy engine (cp.async.bulk, one mbarrier
-//     per chunk, issued one slab ahead).  The potential field is stored with
-//     32 ghost columns on each side (periodic images), so every staged row is
-//     one contiguous 16-byte-aligned copy; rows wrap periodically;
-//  2. each lane loads f(t) of its 4 cells (9 float4), evaluates the explicit
-//     periodic HDM stencil (the exact solution of the tridiagonal system of
-//     Eq. 20, truncated at radius 26 where the neglected tail of the weights
-//     changes the derivative of a smooth field by < 3e-9) along x
-//     and y, the force (Eq. 22 Shan-Chen or Eq. 7 Zhang-Chen), the moments
-//     (Eq. 3) and the exact-difference forcing with BGK (Eq. 1, 2, 10), and
-//     stores the nine post-collision float4 into a 10-row shared ring.  The
-//     rest population is formed as rho minus the other eight, so the FP32
-//     collision conserves mass up to unbiased rounding (the FP32 D2Q9 weights
-//     themselves do not sum to one);
-//  3. after a barrier each warp gathers row y-1 of the slab (streaming: pull
-//     from the ring, x shifts by warp shuffles), sums rho(t+1), evaluates the
-//     EOS potential (Eq. 8, 21) and writes f(t+1) and q(t+1) (with ghosts).
-// The segment's first slab is shifted one row up so that the rows above the
-// segment are recomputed too; the collision work overhead is 8/120 in x and
-// about 8/128 in y.
+// f(t) of a lane's 4 cells is read with nine float4 loads into registers,
+// issued at the end of the previous slab's collision so that their latency
+// hides behind the barrier, the density pass and the next stencil.  The
+// potential rows arrive by the bulk-copy engine (cp.async.bulk, completion on
+// mbarriers, bounded waits), issued a slab ahead by warp 0:
+//  - the slab's 8 potential rows at full width (the 26-column HDM halo on
+//    each side, for d/dx), double-buffered;
+//  - an 80-row ring of potential rows at the lanes' 128 columns (26 rows
+//    above and below every slab row, for d/dy), 8 rows per chunk.
+// The potential field is stored with 32 ghost columns on each side (periodic
+// images), so every staged row is one contiguous 16-byte-aligned copy; rows
+// wrap periodically.
+//
+// Per slab, each lane evaluates the explicit periodic HDM stencil (the exact
+// solution of the tridiagonal system of Eq. 20, truncated at radius 26 where
+// the neglected tail of the weights changes the derivative of a smooth field
+// by < 3e-9) along x and y, the force (Eq. 22 Shan-Chen or Eq. 7 Zhang-Chen),
+// the moments (Eq. 3) and the exact-difference forcing with BGK (Eq. 1, 2,
+// 10).  It then streams (Eq. 1) by push: the x shift is a warp shuffle, the
+// destination float4 of f(t+1) is stored straight to HBM, and the three
+// partial sums of what lands in rows y-1, y, y+1 go to an 18-row shared ring.
+// After one block barrier each warp sums the three partials of one finished
+// row into rho(t+1) and writes the potential (Eq. 8, 21) of that row.  The
+// rest population is formed as rho minus the other eight, so the FP32
+// collision conserves mass up to unbiased rounding.  For tau = 1 the BGK term
+// vanishes exactly and the equilibrium at u is skipped.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,19 +53,25 @@ namespace {
 constexpr int FK = 26;              // HDM radius of this path
 constexpr int TXI = 120;            // interior columns per strip
 constexpr int QG = 32;              // ghost columns on each side of a padded potential row
-constexpr int QW = TXI + 2 * QG;    // floats per staged potential row
+constexpr int WW = TXI + 2 * QG;    // floats per wide potential row (d/dx halo)
+constexpr int NW = 128;             // floats per lane-column row (32 lanes x 4)
 constexpr int SLAB = 8;             // rows per slab (one warp each)
-constexpr int QCH = 10;             // chunks in the potential ring
-constexpr int QRING = QCH * SLAB;   // staged potential rows
-constexpr int QBASE = 33;           // chunk 0 starts at row ys - QBASE
-constexpr int FROWS = 10;           // post-collision rows kept
+constexpr int QCH = 10;             // chunks in the d/dy ring
+constexpr int QRING = QCH * SLAB;   // rows in the d/dy ring
+constexpr int QBASE = 33;           // ring chunk 0 starts at row ys - QBASE
+constexpr int PROWS = 18;           // partial-density ring rows
 constexpr int SEG_H = 128;          // rows per CTA segment
 constexpr int NTHR = 32 * SLAB;
-constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s per chunk wait
+constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s per wait
 
-constexpr size_t kQsBytes = sizeof(float) * QRING * QW;
-constexpr size_t kFsBytes = sizeof(float4) * 9 * FROWS * 32;
-constexpr size_t kSmemBytes = kQsBytes + kFsBytes + sizeof(uint64_t) * QCH;
+// shared-memory layout (bytes)
+constexpr size_t kQnBytes = sizeof(float) * QRING * NW;       // d/dy ring
+constexpr size_t kQwBytes = sizeof(float) * 2 * SLAB * WW;    // slab rows, full width, 2 buffers
+constexpr size_t kPsBytes = sizeof(float) * 3 * PROWS * NW;   // partial densities
+constexpr size_t kOffQw = kQnBytes;
+constexpr size_t kOffPs = kOffQw + kQwBytes;
+constexpr size_t kOffBar = kOffPs + kPsBytes;
+constexpr size_t kSmemBytes = kOffBar + sizeof(uint64_t) * (QCH + 2);
 
 struct FusedArgs {
     Model<float> m;
@@ -87,53 +95,22 @@ __device__ __forceinline__ float stencil_field(const Model<float> &m, float rho,
     return sc ? sqrtf(fabsf(U)) : U;
 }
 
-// Post-collision populations of one cell (Eq. 1 with the exact-difference
-// forcing of Eq. 10): f_i* = (1 - omega)(f_i - feq_i(u)) + feq_i(u + F/rho)
-// for i = 1..8 and f_0* = rho - sum_{i>0} f_i*.
-__device__ __forceinline__ void collide_cell(float (&f)[9], float r, float Fx, float Fy, float omega) {
-    float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    float jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
-    float inv = 1.0f / r;
-    float ux = jx * inv, uy = jy * inv;
-    float vx = ux + Fx * inv, vy = uy + Fy * inv;
-    const float om1 = 1.0f - omega;
-    float uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
-    float r9 = r * (1.0f / 9.0f), r36 = r * (1.0f / 36.0f);
-    float au = 1.0f - 1.5f * uu, av = 1.0f - 1.5f * vv;
-    float eq_u[9], eq_v[9];
-    {   // axis pairs (1,3) along x, (2,4) along y
-        float su = au + 4.5f * ux * ux, sv = av + 4.5f * vx * vx;
-        eq_u[1] = r9 * (su + 3.0f * ux); eq_u[3] = r9 * (su - 3.0f * ux);
-        eq_v[1] = r9 * (sv + 3.0f * vx); eq_v[3] = r9 * (sv - 3.0f * vx);
-        su = au + 4.5f * uy * uy; sv = av + 4.5f * vy * vy;
-        eq_u[2] = r9 * (su + 3.0f * uy); eq_u[4] = r9 * (su - 3.0f * uy);
-        eq_v[2] = r9 * (sv + 3.0f * vy); eq_v[4] = r9 * (sv - 3.0f * vy);
-    }
-    {   // diagonal pairs (5,7) along (1,1), (6,8) along (-1,1)
-        float p = ux + uy, q = vx + vy;
-        float su = au + 4.5f * p * p, sv = av + 4.5f * q * q;
-        eq_u[5] = r36 * (su + 3.0f * p); eq_u[7] = r36 * (su - 3.0f * p);
-        eq_v[5] = r36 * (sv + 3.0f * q); eq_v[7] = r36 * (sv - 3.0f * q);
-        p = uy - ux; q = vy - vx;
-        su = au + 4.5f * p * p; sv = av + 4.5f * q * q;
-        eq_u[6] = r36 * (su + 3.0f * p); eq_u[8] = r36 * (su - 3.0f * p);
-        eq_v[6] = r36 * (sv + 3.0f * q); eq_v[8] = r36 * (sv - 3.0f * q);
-    }
-    float moved = 0.0f;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        f[i] = fmaf(om1, f[i] - eq_u[i], eq_v[i]);
-        moved += f[i];
-    }
-    f[0] = r - moved;
+// f^eq_i(rho, u) of Eq. 2 for i = 1..8 with the lattice weights as FP32;
+// a = 1 - 1.5 |u|^2.
+__device__ __forceinline__ float feq_moving(int i, float rho, float ux, float uy, float a) {
+    const float eu = float(ex(i)) * ux + float(ey(i)) * uy;
+    const float w = i < 5 ? rho * (1.0f / 9.0f) : rho * (1.0f / 36.0f);
+    return w * (a + eu * (3.0f + 4.5f * eu));
 }
 
-template <bool SC>
+template <bool SC, bool TAU1>
 __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_constant__ FusedArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
-    float *qs = reinterpret_cast<float *>(smem);                        // [QRING][QW]
-    float4 *fs = reinterpret_cast<float4 *>(smem + kQsBytes);           // [9][FROWS][32]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kQsBytes + kFsBytes);
+    float *qn = reinterpret_cast<float *>(smem);               // [QRING][NW]
+    float *qw = reinterpret_cast<float *>(smem + kOffQw);      // [2][SLAB][WW]
+    float *ps = reinterpret_cast<float *>(smem + kOffPs);      // [3][PROWS][NW]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // QCH chunk barriers + 2 row barriers
+    uint64_t *row_bar = &bars[QCH];
 
     const Model<float> &m = A.m;
     const int nx = m.nx, ny = m.ny;
@@ -145,65 +122,94 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     const int hseg = min(SEG_H, ny - ys);
     const int nslab = hseg > 6 ? (hseg - 6 + SLAB - 1) / SLAB + 1 : 1;
     const int nchunks = nslab + 8;
-    const uint32_t row_bytes = (uint32_t)(nint + 2 * QG) * sizeof(float);
+    const int ncols = nint + 8;                     // lane columns actually staged (d/dy ring)
+    const int wcols = nint + 2 * QG;                // wide-row columns actually staged
     const int glast = nint / 4 + 1;                 // right ring lane
     const bool active = lane <= glast;
     const bool interior = lane >= 1 && lane < glast;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < QCH; ++i) ptx::mbar_init(&bars[i], 1);
+        for (int i = 0; i < QCH + 2; ++i) ptx::mbar_init(&bars[i], 1);
         ptx::fence_mbar_init();
     }
     __syncthreads();
 
-    // chunk c holds relative rows 8c .. 8c+7, i.e. global rows ys - QBASE + 8c + k,
-    // in ring rows (8c + k) mod QRING
-    auto issue_chunk = [&](int c) {
+    // d/dy ring chunk c: relative rows 8c .. 8c+7 = global rows ys - QBASE + 8c + k,
+    // lane columns x0 - 4 .. x0 + nint + 3 (padded x0 + QG - 4 ..), ring row (8c + k) % QRING
+    auto issue_chunk = [&](int c) {  // warp 0
         uint64_t *bar = &bars[c % QCH];
-        ptx::mbar_arrive_expect_tx(bar, SLAB * row_bytes);
-        for (int k = 0; k < SLAB; ++k) {
-            int ry = SLAB * c + k;
+        if (lane == 0) ptx::mbar_arrive_expect_tx(bar, SLAB * ncols * sizeof(float));
+        __syncwarp();
+        if (lane < SLAB) {
+            int ry = SLAB * c + lane;
             int y = wrapi(ys - QBASE + ry, ny);
-            ptx::bulk_g2s(qs + (ry % QRING) * QW, A.qin + (long long)y * A.qpitch + x0, row_bytes, bar);
+            ptx::bulk_g2s(qn + (ry % QRING) * NW, A.qin + (long long)y * A.qpitch + x0 + QG - 4,
+                          ncols * sizeof(float), bar);
         }
     };
-    int issued = 0;  // chunks issued so far (meaningful in thread 0)
-    if (threadIdx.x == 0)
+    // slab s: potential rows ys - 1 + 8s + w at full width into buffer s & 1
+    auto issue_rows = [&](int s) {  // warp 0
+        uint64_t *bar = &row_bar[s & 1];
+        if (lane == 0) ptx::mbar_arrive_expect_tx(bar, SLAB * wcols * sizeof(float));
+        __syncwarp();
+        if (lane < SLAB) {
+            int y = wrapi(ys - 1 + SLAB * s + lane, ny);
+            ptx::bulk_g2s(qw + ((s & 1) * SLAB + lane) * WW, A.qin + (long long)y * A.qpitch + x0,
+                          wcols * sizeof(float), bar);
+        }
+    };
+    int issued = 0;  // chunks issued so far (meaningful in warp 0)
+    if (warp == 0) {
         for (; issued < min(QCH, nchunks); ++issued) issue_chunk(issued);
+        issue_rows(0);
+    }
 
     const int xg = x0 - 4 + 4 * lane;               // first of this lane's 4 columns
     const int xgw = wrapi(xg, nx);
     bool timed_out = false;
 
-    for (int s = 0; s < nslab; ++s) {
-        if (threadIdx.x == 0 && s >= 1 && s + QCH - 1 < nchunks) {
-            ptx::fence_proxy_async_smem();
-            issue_chunk(s + QCH - 1);
-            issued = s + QCH;
-        }
-        // ---- collision of row yc = ys - 1 + 8s + warp ----
-        const int yc = ys - 1 + SLAB * s + warp;
-        const int ryc = SLAB * s + warp + QBASE - 1;     // relative row of yc
-        float fv[4][9];
-        if (active) {
-            const float *src = A.f + (long long)wrapi(yc, ny) * nx + xgw;
+    // f(t) of row ys - 1 + 8s + warp at the lane's 4 columns
+    float4 fv[9];
+    auto load_f = [&](int s) {
+        const float *src = A.f + (long long)wrapi(ys - 1 + SLAB * s + warp, ny) * nx + xgw;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                float4 v = __ldg(reinterpret_cast<const float4 *>(src + i * N));
-                fv[0][i] = v.x; fv[1][i] = v.y; fv[2][i] = v.z; fv[3][i] = v.w;
+        for (int i = 0; i < 9; ++i) fv[i] = __ldcs(reinterpret_cast<const float4 *>(src + i * N));
+    };
+    load_f(0);
+
+    for (int s = 0; s < nslab; ++s) {
+        // copies a slab ahead: the next slab's full-width rows and the ring chunk
+        // it needs last (their buffers were last read by the previous slab)
+        if (warp == 0 && s >= 1) {
+            ptx::fence_proxy_async_smem();
+            if (s + QCH - 1 < nchunks) {
+                issue_chunk(s + QCH - 1);
+                issued = s + QCH;
             }
+            if (s + 1 < nslab) issue_rows(s + 1);
+        } else if (warp == 0 && s + 1 < nslab) {
+            issue_rows(1);
         }
+        const int yc = ys - 1 + SLAB * s + warp;    // collided row of this warp
+        const int ryc = SLAB * s + warp + QBASE - 1;
         {
             const int cfirst = s == 0 ? 0 : s + 8, clast = min(s + 8, nchunks - 1);
             for (int c = cfirst; c <= clast; ++c)
                 if (!ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs)) timed_out = true;
+            if (!ptx::mbar_wait_bounded(&row_bar[s & 1], (s >> 1) & 1, kWaitLimitNs)) timed_out = true;
         }
-        if (active && !timed_out) {
-            float dx[4] = {0.f, 0.f, 0.f, 0.f}, dy[4] = {0.f, 0.f, 0.f, 0.f}, qc[4];
-            // d/dx: window of staged columns 4 lane .. 4 lane + 59 of row yc; the
-            // lane's cells sit at window positions 28..31
-            {
-                const float *qrow = qs + (ryc % QRING) * QW + 4 * lane;
+        // Every lane of a warp runs the collision (the shuffles need the whole
+        // warp); lanes past the strip's right ring lane work on unused shared
+        // columns and store nothing.
+        if (!__any_sync(0xffffffffu, timed_out)) {
+            float dx[4], dy[4], qc[4];
+            {   // d/dx: wide row columns 4 lane .. 4 lane + 59; cells at window positions 28..31.
+                // Each staged value enters as its deviation from the lane's second cell,
+                // so the weighted sums carry only local variations (the constant part of
+                // an antisymmetric stencil cancels exactly) and FP32 keeps its precision.
+                const float *qrow = qw + ((s & 1) * SLAB + warp) * WW + 4 * lane;
+                const float qref = qrow[29];
+                float sp[4] = {0.f, 0.f, 0.f, 0.f}, sm[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int k = 0; k < 15; ++k) {
                     float4 v4 = *reinterpret_cast<const float4 *>(qrow + 4 * k);
@@ -211,96 +217,152 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int pos = 4 * k + e;
+                        if (pos < 28 - FK || pos > 31 + FK) continue;
+                        const float t = v[e] - qref;
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             const int j = pos - 28 - c;
-                            if (j >= 1 && j <= FK) dx[c] = fmaf(m.wx[j], v[e], dx[c]);
-                            if (j <= -1 && j >= -FK) dx[c] = fmaf(-m.wx[-j], v[e], dx[c]);
+                            if (j >= 1 && j <= FK) sp[c] = fmaf(m.wx[j], t, sp[c]);
+                            if (j <= -1 && j >= -FK) sm[c] = fmaf(m.wx[-j], t, sm[c]);
                             if (j == 0) qc[c] = v[e];
                         }
                     }
                 }
-            }
-            // d/dy: rows yc - FK .. yc + FK at the lane's 4 columns (ring wraps once at most)
-            {
-                const float *qcol = qs + 28 + 4 * lane;
-                const int base = ryc % QRING;
 #pragma unroll
-                for (int j = -FK; j <= FK; ++j) {
-                    if (j == 0) continue;
-                    int row = base + j;
-                    if (j > 0) row = row >= QRING ? row - QRING : row;
-                    else row = row < 0 ? row + QRING : row;
-                    float4 v = *reinterpret_cast<const float4 *>(qcol + row * QW);
-                    const float w = j > 0 ? m.wy[j] : -m.wy[-j];
-                    dy[0] = fmaf(w, v.x, dy[0]);
-                    dy[1] = fmaf(w, v.y, dy[1]);
-                    dy[2] = fmaf(w, v.z, dy[2]);
-                    dy[3] = fmaf(w, v.w, dy[3]);
+                for (int c = 0; c < 4; ++c) dx[c] = sp[c] - sm[c];
+            }
+            {   // d/dy: ring rows yc - FK .. yc + FK at the lane's 4 columns, as
+                // sum_j w_j (q(y+j) - q(y-j)) with the differences taken first;
+                // odd and even j in separate sums; packed FP32x2 arithmetic
+                const float *qcol = qn + 4 * lane;
+                const int base = ryc % QRING;
+                const float2 neg1 = make_float2(-1.f, -1.f);
+                float2 se01 = make_float2(0.f, 0.f), se23 = se01, so01 = se01, so23 = se01;
+#pragma unroll
+                for (int j = 1; j <= FK; ++j) {
+                    int up = base + j, dn = base - j;
+                    up = up >= QRING ? up - QRING : up;
+                    dn = dn < 0 ? dn + QRING : dn;
+                    const float4 a = *reinterpret_cast<const float4 *>(qcol + up * NW);
+                    const float4 b = *reinterpret_cast<const float4 *>(qcol + dn * NW);
+                    const float2 w2 = make_float2(m.wy[j], m.wy[j]);
+                    const float2 d01 = __ffma2_rn(neg1, make_float2(b.x, b.y), make_float2(a.x, a.y));
+                    const float2 d23 = __ffma2_rn(neg1, make_float2(b.z, b.w), make_float2(a.z, a.w));
+                    if (j & 1) {
+                        so01 = __ffma2_rn(w2, d01, so01);
+                        so23 = __ffma2_rn(w2, d23, so23);
+                    } else {
+                        se01 = __ffma2_rn(w2, d01, se01);
+                        se23 = __ffma2_rn(w2, d23, se23);
+                    }
+                }
+                const float2 s01 = __fadd2_rn(so01, se01), s23 = __fadd2_rn(so23, se23);
+                dy[0] = s01.x; dy[1] = s01.y; dy[2] = s23.x; dy[3] = s23.y;
+            }
+            // moments of f(t) (Eq. 3)
+            float r[4] = {0.f, 0.f, 0.f, 0.f}, jx[4] = {0.f, 0.f, 0.f, 0.f}, jy[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float v[4] = {fv[i].x, fv[i].y, fv[i].z, fv[i].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    r[c] += v[c];
+                    if (ex(i)) jx[c] = fmaf(float(ex(i)), v[c], jx[c]);
+                    if (ey(i)) jy[c] = fmaf(float(ey(i)), v[c], jy[c]);
                 }
             }
+            // force and the two velocities of the forcing (Eq. 10, 22 / 7)
+            float ux[4], uy[4], vx[4], vy[4], au[4], av[4], moved[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                float r = ((fv[c][0] + fv[c][1]) + (fv[c][2] + fv[c][3])) +
-                          ((fv[c][4] + fv[c][5]) + (fv[c][6] + fv[c][7])) + fv[c][8];
-                if (!(r > 0.f) || !isfinite(r)) atomicOr(A.err, kErrUnstable);
+                if (active && (!(r[c] > 0.f) || !isfinite(r[c]))) atomicOr(A.err, kErrUnstable);
                 float Fx, Fy;
                 if (SC) {   // Eq. 22: F = -2 s Phi grad Phi, s the sign of U at the cell
-                    float sphi = potential_u(m, r) >= 0.f ? qc[c] : -qc[c];
+                    float sphi = potential_u(m, r[c]) >= 0.f ? qc[c] : -qc[c];
                     Fx = -2.0f * sphi * dx[c];
                     Fy = -2.0f * sphi * dy[c];
                 } else {    // Eq. 7: F = -grad U
                     Fx = -dx[c];
                     Fy = -dy[c];
                 }
-                collide_cell(fv[c], r, Fx, Fy, m.omega);
+                const float inv = 1.0f / r[c];
+                ux[c] = jx[c] * inv;
+                uy[c] = jy[c] * inv;
+                vx[c] = fmaf(Fx, inv, ux[c]);
+                vy[c] = fmaf(Fy, inv, uy[c]);
+                au[c] = 1.0f - 1.5f * (ux[c] * ux[c] + uy[c] * uy[c]);
+                av[c] = 1.0f - 1.5f * (vx[c] * vx[c] + vy[c] * vy[c]);
+                moved[c] = 0.f;
             }
-            const int slot = (SLAB * s + warp + 2) % FROWS;
+            // post-collision populations, pushed: x shift by shuffle, store to
+            // row yc + e_y if it lies in the segment, accumulate partial densities
+            const int rd0 = yc - ys + 3;            // relative destination row of e_y = 0
+            float4 part[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                              make_float4(0.f, 0.f, 0.f, 0.f)};
 #pragma unroll
-            for (int i = 0; i < 9; ++i)
-                fs[(i * FROWS + slot) * 32 + lane] = make_float4(fv[0][i], fv[1][i], fv[2][i], fv[3][i]);
+            for (int ii = 0; ii < 9; ++ii) {
+                const int i = ii == 8 ? 0 : ii + 1;     // rest population last
+                float post[4];
+                if (i == 0) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) post[c] = r[c] - moved[c];
+                } else {
+                    const float fi[4] = {fv[i].x, fv[i].y, fv[i].z, fv[i].w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float eqv = feq_moving(i, r[c], vx[c], vy[c], av[c]);
+                        if (TAU1) {
+                            post[c] = eqv;
+                        } else {
+                            const float equ = feq_moving(i, r[c], ux[c], uy[c], au[c]);
+                            post[c] = fmaf(1.0f - m.omega, fi[c] - equ, eqv);
+                        }
+                        moved[c] += post[c];
+                    }
+                }
+                float4 d;  // values landing on this lane's 4 columns
+                if (ex(i) == 1) {
+                    float left = __shfl_up_sync(0xffffffffu, post[3], 1);
+                    d = make_float4(left, post[0], post[1], post[2]);
+                } else if (ex(i) == -1) {
+                    float right = __shfl_down_sync(0xffffffffu, post[0], 1);
+                    d = make_float4(post[1], post[2], post[3], right);
+                } else {
+                    d = make_float4(post[0], post[1], post[2], post[3]);
+                }
+                const int yd = yc + ey(i);
+                if (interior && yd >= ys && yd < ys + hseg)
+                    __stcs(reinterpret_cast<float4 *>(A.fout + i * N + (long long)yd * nx + xg), d);
+                float4 &pp = part[ey(i) + 1];
+                pp.x += d.x; pp.y += d.y; pp.z += d.z; pp.w += d.w;
+            }
+            if (s + 1 < nslab) load_f(s + 1);   // f(t) of the next slab, in flight across the barrier
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {   // component k: what row yc sends to row yc + (k - 1)
+                const int slot = (rd0 + k - 1) % PROWS;
+                *reinterpret_cast<float4 *>(ps + (k * PROWS + slot) * NW + 4 * lane) = part[k];
+            }
         }
         if (__syncthreads_or(timed_out)) break;
 
-        // ---- streaming gather and outputs for row yo = ys + 8s - 2 + warp ----
+        // ---- rho(t+1) and the potential of row yo = ys + 8s - 2 + warp ----
         const int yo = ys + SLAB * s - 2 + warp;
-        if (yo >= ys && yo < ys + hseg) {           // warp-uniform
-            const int ro = SLAB * s + warp + 1;     // relative row of yo in the f* ring
-            float4 nf[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const int slot = (ro - ey(i) + FROWS) % FROWS;
-                float4 a = fs[(i * FROWS + slot) * 32 + lane];
-                if (ex(i) == 1) {          // f_i(x) = f_i*(x - 1)
-                    float left = __shfl_up_sync(0xffffffffu, a.w, 1);
-                    a = make_float4(left, a.x, a.y, a.z);
-                } else if (ex(i) == -1) {  // f_i(x) = f_i*(x + 1)
-                    float right = __shfl_down_sync(0xffffffffu, a.x, 1);
-                    a = make_float4(a.y, a.z, a.w, right);
-                }
-                nf[i] = a;
-            }
-            if (interior) {
-                float4 rho;
-                rho.x = ((nf[0].x + nf[1].x) + (nf[2].x + nf[3].x)) + ((nf[4].x + nf[5].x) + (nf[6].x + nf[7].x)) + nf[8].x;
-                rho.y = ((nf[0].y + nf[1].y) + (nf[2].y + nf[3].y)) + ((nf[4].y + nf[5].y) + (nf[6].y + nf[7].y)) + nf[8].y;
-                rho.z = ((nf[0].z + nf[1].z) + (nf[2].z + nf[3].z)) + ((nf[4].z + nf[5].z) + (nf[6].z + nf[7].z)) + nf[8].z;
-                rho.w = ((nf[0].w + nf[1].w) + (nf[2].w + nf[3].w)) + ((nf[4].w + nf[5].w) + (nf[6].w + nf[7].w)) + nf[8].w;
-                float4 q;
-                q.x = stencil_field(m, rho.x, SC);
-                q.y = stencil_field(m, rho.y, SC);
-                q.z = stencil_field(m, rho.z, SC);
-                q.w = stencil_field(m, rho.w, SC);
-                float *dst = A.fout + (long long)yo * nx + xg;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) __stcs(reinterpret_cast<float4 *>(dst + i * N), nf[i]);
-                float *qrow = A.qout + (long long)yo * A.qpitch + QG;
-                *reinterpret_cast<float4 *>(qrow + xg) = q;
-                if (xg < QG) *reinterpret_cast<float4 *>(qrow + xg + nx) = q;        // right ghost image
-                if (xg >= nx - QG) *reinterpret_cast<float4 *>(qrow + xg - nx) = q;  // left ghost image
-            }
+        if (interior && yo >= ys && yo < ys + hseg) {
+            const int slot = (yo - ys + 3) % PROWS;
+            // component 0: from row yo + 1 (down-movers), 1: from row yo, 2: from row yo - 1
+            const float4 a = *reinterpret_cast<const float4 *>(ps + (0 * PROWS + slot) * NW + 4 * lane);
+            const float4 b = *reinterpret_cast<const float4 *>(ps + (1 * PROWS + slot) * NW + 4 * lane);
+            const float4 cc = *reinterpret_cast<const float4 *>(ps + (2 * PROWS + slot) * NW + 4 * lane);
+            float4 q;
+            q.x = stencil_field(m, (a.x + b.x) + cc.x, SC);
+            q.y = stencil_field(m, (a.y + b.y) + cc.y, SC);
+            q.z = stencil_field(m, (a.z + b.z) + cc.z, SC);
+            q.w = stencil_field(m, (a.w + b.w) + cc.w, SC);
+            float *qrow = A.qout + (long long)yo * A.qpitch + QG;
+            *reinterpret_cast<float4 *>(qrow + xg) = q;
+            if (xg < QG) *reinterpret_cast<float4 *>(qrow + xg + nx) = q;        // right ghost image
+            if (xg >= nx - QG) *reinterpret_cast<float4 *>(qrow + xg - nx) = q;  // left ghost image
         }
-        __syncthreads();
     }
 
     if (timed_out) {
@@ -309,6 +371,8 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             // let copies still in flight land before the CTA's shared memory is released
             for (int c = max(0, issued - QCH); c < issued; ++c)
                 (void)ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs);
+            for (int b = 0; b < 2; ++b)
+                for (int ph = 0; ph < 2; ++ph) (void)ptx::mbar_wait_bounded(&row_bar[b], ph, kWaitLimitNs);
         }
         __syncthreads();
     }
@@ -360,7 +424,9 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     a.err = err;
     a.qpitch = fused_q_pitch(m.nx);
     dim3 grid((m.nx + TXI - 1) / TXI, (m.ny + SEG_H - 1) / SEG_H);
-    auto kern = sc ? fused_step_kernel<true> : fused_step_kernel<false>;
+    const bool tau1 = m.omega == 1.0f;
+    auto kern = sc ? (tau1 ? fused_step_kernel<true, true> : fused_step_kernel<true, false>)
+                   : (tau1 ? fused_step_kernel<false, true> : fused_step_kernel<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, NTHR, kSmemBytes, s>>>(a);

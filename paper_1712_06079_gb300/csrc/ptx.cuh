@@ -49,17 +49,28 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
+// Potentially blocking probe: the hardware may suspend the thread for a
+// bounded, implementation-defined time before answering.
+__device__ __forceinline__ bool mbar_try_parity(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Wait for the phase with the given parity to complete, giving up after
 // `limit_ns` nanoseconds of wall time.  Returns false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_test_parity(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 0;; ++it) {
-        if (mbar_test_parity(bar, parity)) return true;
-        if ((it & 63) == 63) {
-            if (globaltimer_ns() - t0 > limit_ns) return false;
-            __nanosleep(64);
-        }
+        if (mbar_try_parity(bar, parity)) return true;
+        if ((it & 15) == 15 && globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -71,6 +82,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, u
             smem_u32(dst_smem)),
         "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Prefetch `bytes` of global memory into L2 (bulk, no completion tracking).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src_gmem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src_gmem), "r"(bytes) : "memory");
 }
 
 }  // namespace ptx
