@@ -81,6 +81,7 @@ struct FusedArgs {
     float *qout;        // padded field of f(t+1)
     int *err;
     int qpitch;         // nx + 2 * QG
+    float2 wy2[FK + 1]; // (w_j, w_j) pairs of the d/dy weights for packed FP32x2 FMAs
 };
 
 __device__ __forceinline__ int wrapi(int i, int n) {
@@ -95,6 +96,31 @@ __device__ __forceinline__ float stencil_field(const Model<float> &m, float rho,
     return sc ? sqrtf(fabsf(U)) : U;
 }
 
+// U = k p_EOS - rho/3 (Eq. 8) with the equation of state fixed at compile time
+// (VdW Eq. 24, CS Eq. 29, PR Eq. 28, RK/RKS Eq. 27); quotients by the fast
+// FP32 reciprocal (2 ulp), the denominators being positive and well scaled.
+template <int EOS>
+__device__ __forceinline__ float potential_u_t(const Model<float> &m, float rho) {
+    float p;
+    if (EOS == LBM_EOS_CS) {
+        const float e = m.b * rho * 0.25f;
+        const float om = 1.0f - e;
+        p = __fdividef(rho * m.RT * (1.0f + e * (1.0f + e * (1.0f - e))), om * om * om) - m.a * rho * rho;
+    } else {
+        const float rep = __fdividef(rho * m.RT, 1.0f - m.b * rho);
+        if (EOS == LBM_EOS_VDW) p = rep - m.a * rho * rho;
+        else if (EOS == LBM_EOS_PR) p = rep - __fdividef(m.aal * rho * rho, 1.0f + m.b * rho * (2.0f - m.b * rho));
+        else p = rep - __fdividef(m.aal * rho * rho, 1.0f + m.b * rho);
+    }
+    return m.k * p - rho * (1.0f / 3.0f);
+}
+
+template <int EOS>
+__device__ __forceinline__ float stencil_field_t(const Model<float> &m, float rho, bool sc) {
+    const float U = potential_u_t<EOS>(m, rho);
+    return sc ? sqrtf(fabsf(U)) : U;
+}
+
 // f^eq_i(rho, u) of Eq. 2 for i = 1..8 with the lattice weights as FP32;
 // a = 1 - 1.5 |u|^2.
 __device__ __forceinline__ float feq_moving(int i, float rho, float ux, float uy, float a) {
@@ -103,7 +129,7 @@ __device__ __forceinline__ float feq_moving(int i, float rho, float ux, float uy
     return w * (a + eu * (3.0f + 4.5f * eu));
 }
 
-template <bool SC, bool TAU1>
+template <bool SC, bool TAU1, int EOS>
 __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_constant__ FusedArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     float *qn = reinterpret_cast<float *>(smem);               // [QRING][NW]
@@ -245,7 +271,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                     dn = dn < 0 ? dn + QRING : dn;
                     const float4 a = *reinterpret_cast<const float4 *>(qcol + up * NW);
                     const float4 b = *reinterpret_cast<const float4 *>(qcol + dn * NW);
-                    const float2 w2 = make_float2(m.wy[j], m.wy[j]);
+                    const float2 w2 = A.wy2[j];
                     const float2 d01 = __ffma2_rn(neg1, make_float2(b.x, b.y), make_float2(a.x, a.y));
                     const float2 d23 = __ffma2_rn(neg1, make_float2(b.z, b.w), make_float2(a.z, a.w));
                     if (j & 1) {
@@ -278,14 +304,14 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 if (active && (!(r[c] > 0.f) || !isfinite(r[c]))) atomicOr(A.err, kErrUnstable);
                 float Fx, Fy;
                 if (SC) {   // Eq. 22: F = -2 s Phi grad Phi, s the sign of U at the cell
-                    float sphi = potential_u(m, r[c]) >= 0.f ? qc[c] : -qc[c];
+                    float sphi = potential_u_t<EOS>(m, r[c]) >= 0.f ? qc[c] : -qc[c];
                     Fx = -2.0f * sphi * dx[c];
                     Fy = -2.0f * sphi * dy[c];
                 } else {    // Eq. 7: F = -grad U
                     Fx = -dx[c];
                     Fy = -dy[c];
                 }
-                const float inv = 1.0f / r[c];
+                const float inv = __fdividef(1.0f, r[c]);
                 ux[c] = jx[c] * inv;
                 uy[c] = jy[c] * inv;
                 vx[c] = fmaf(Fx, inv, ux[c]);
@@ -354,10 +380,10 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             const float4 b = *reinterpret_cast<const float4 *>(ps + (1 * PROWS + slot) * NW + 4 * lane);
             const float4 cc = *reinterpret_cast<const float4 *>(ps + (2 * PROWS + slot) * NW + 4 * lane);
             float4 q;
-            q.x = stencil_field(m, (a.x + b.x) + cc.x, SC);
-            q.y = stencil_field(m, (a.y + b.y) + cc.y, SC);
-            q.z = stencil_field(m, (a.z + b.z) + cc.z, SC);
-            q.w = stencil_field(m, (a.w + b.w) + cc.w, SC);
+            q.x = stencil_field_t<EOS>(m, (a.x + b.x) + cc.x, SC);
+            q.y = stencil_field_t<EOS>(m, (a.y + b.y) + cc.y, SC);
+            q.z = stencil_field_t<EOS>(m, (a.z + b.z) + cc.z, SC);
+            q.w = stencil_field_t<EOS>(m, (a.w + b.w) + cc.w, SC);
             float *qrow = A.qout + (long long)yo * A.qpitch + QG;
             *reinterpret_cast<float4 *>(qrow + xg) = q;
             if (xg < QG) *reinterpret_cast<float4 *>(qrow + xg + nx) = q;        // right ghost image
@@ -424,9 +450,20 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     a.err = err;
     a.qpitch = fused_q_pitch(m.nx);
     dim3 grid((m.nx + TXI - 1) / TXI, (m.ny + SEG_H - 1) / SEG_H);
+    for (int j = 0; j <= FK; ++j) a.wy2[j] = make_float2(m.wy[j], m.wy[j]);
     const bool tau1 = m.omega == 1.0f;
-    auto kern = sc ? (tau1 ? fused_step_kernel<true, true> : fused_step_kernel<true, false>)
-                   : (tau1 ? fused_step_kernel<false, true> : fused_step_kernel<false, false>);
+    void (*kern)(const FusedArgs) = nullptr;
+#define LBM_PICK(E)                                                                                        \
+    kern = sc ? (tau1 ? fused_step_kernel<true, true, E> : fused_step_kernel<true, false, E>)             \
+              : (tau1 ? fused_step_kernel<false, true, E> : fused_step_kernel<false, false, E>)
+    switch (m.eos) {
+    case LBM_EOS_VDW: LBM_PICK(LBM_EOS_VDW); break;
+    case LBM_EOS_CS: LBM_PICK(LBM_EOS_CS); break;
+    case LBM_EOS_PR: LBM_PICK(LBM_EOS_PR); break;
+    case LBM_EOS_RK: LBM_PICK(LBM_EOS_RK); break;
+    default: LBM_PICK(LBM_EOS_RKS); break;
+    }
+#undef LBM_PICK
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, NTHR, kSmemBytes, s>>>(a);
