@@ -287,6 +287,96 @@ def run_ours(args):
     return 0
 
 
+def run_sweep(args):
+    """Batched temperature/EOS sweep (64 uneven flat-interface lattices, Nx in
+    [256, 2048], Ny = 8, SC + HDM, FP32) in one persistent graph launch per
+    call, against 64 sequential single-lattice contexts on the same GPU."""
+    import numpy as np
+    import torch
+
+    from paper_1712_06079_gb300 import inputs, lbm
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    table = inputs.sweep_instances(64)
+    params, rho0, maxw = [], [], []
+    for d in table:
+        gp = lbm.Params(nx=d["nx"], ny=d["ny"], eos=d["eos"], a=d["a"], b=d["b"], omega=d["omega"], Tr=d["Tr"],
+                        k=d["k"], tau=d["tau"], force="sc", grad="hdm", prec="f32", stream=stream.cuda_stream)
+        g, l = lbm.maxwell(gp)
+        params.append(gp)
+        rho0.append(inputs.slab(d["nx"], d["ny"], g, l))
+        maxw.append((g, l))
+    cells = sum(p.nx * p.ny for p in params)
+    steps, seq_steps = args.steps, args.seq_steps
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # ---- batched ----
+    b = lbm.Batch(params)
+    b.init_density(rho0)
+    shape = b.tune(trial_steps=50)
+    b.init_density(rho0)
+    b.step(seq_steps)           # warm-up and the equal-accuracy comparison point
+    rho_b_short = b.density()
+    b.init_density(rho0)
+    b.step(2)
+    b.sync()
+    t0, t1 = ev(), ev()
+    t0.record(stream)
+    b.step(steps)
+    t1.record(stream)
+    t1.synchronize()
+    b.sync()
+    ms_batch = t0.elapsed_time(t1)
+    rho_b = b.density()
+    b.close()
+    # ---- sequential: one context per instance, stepped one after another ----
+    lats = [lbm.Lattice(p) for p in params]
+    for lat, r in zip(lats, rho0):
+        lat.init_density(r)
+        lat.step(2)
+    torch.cuda.synchronize()
+    t0, t1 = ev(), ev()
+    t0.record(stream)
+    for lat in lats:
+        lat.step(seq_steps)
+    t1.record(stream)
+    t1.synchronize()
+    ms_seq = t0.elapsed_time(t1)
+    for lat, r in zip(lats, rho0):
+        lat.init_density(r)
+        lat.step(seq_steps)
+    rho_s_short = [lat.moments()[0] for lat in lats]
+    for lat in lats:
+        lat.close()
+    diff = max(float(np.max(np.abs(x - y) / y)) for x, y in zip(rho_b_short, rho_s_short))
+    coex = []
+    for p, r, (g, l) in zip(params, rho_b, maxw):
+        prof = r.mean(0)
+        nx = p.nx
+        liq = float(prof[nx // 2 - nx // 16: nx // 2 + nx // 16 + 1].mean())
+        gas = float(np.r_[prof[: nx // 16 + 1], prof[-nx // 16:]].mean())
+        coex.append({"eos": p.eos, "Tr": round(p.Tr, 4), "nx": nx, "rho_g": gas, "rho_l": liq,
+                     "maxwell_g": g, "maxwell_l": l})
+    per_step_batch = ms_batch / steps
+    per_step_seq = ms_seq / seq_steps
+    line = {
+        "metric": "batched sweep: wall time per step of all 64 lattices", "unit": "ms",
+        "value": per_step_batch, "higher_is_better": False, "n_gpus": 1, "steps": steps,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "64 flat-interface lattices, Nx U[256,2048], Ny 8, EOS from {VdW, CS, PR, RK}, "
+                               "Tr linspace(0.5, 0.95), tau U[0.8, 1.2], SC + HDM", "cells": cells,
+                   "launch": {"block_threads": shape[0], "grid_blocks": shape[1]}},
+        "batched_ms_per_step": per_step_batch, "sequential_ms_per_step": per_step_seq,
+        "speedup": per_step_seq / per_step_batch,
+        "batched_mlups": cells * steps / (ms_batch * 1e-3) / 1e6,
+        "sequential_mlups": cells * seq_steps / (ms_seq * 1e-3) / 1e6,
+        "equal_accuracy_max_rel_diff": diff, "sequential_steps_timed": seq_steps,
+        "coexistence": coex,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global NX, NY
     ap = argparse.ArgumentParser()
@@ -297,12 +387,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=NX, help="lattice size (default: the 4096 x 4096 workload)")
     ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--workload", choices=["spinodal", "sweep"], default="spinodal",
+                    help="spinodal: the throughput line; sweep: batched vs sequential 64-lattice sweep")
+    ap.add_argument("--seq-steps", type=int, default=200, help="steps timed per lattice in the sequential arm")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     NX, NY = args.nx, args.ny
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 

@@ -116,6 +116,12 @@ typedef struct {
  * non-positive constants. */
 lbm_status lbm_critical_point(int eos, double a, double b, double R, double *Tc, double *rho_c);
 
+/* Coexistence densities of the Maxwell equal-area construction (Sec. 5.2) of
+ * the unscaled EOS at T = p->Tr * Tc (Tc = p->Tc, or computed when 0), using
+ * p->eos, a, b, R, omega; p_EOS(rho_g) = p_EOS(rho_l) and the p-v areas are
+ * equal.  Host-only FP64.  LBM_E_INVALID when Tr >= 1 or there is no loop. */
+lbm_status lbm_maxwell(const lbm_params *p, double *rho_g, double *rho_l);
+
 /* Weights of the explicit form of the periodic HDM operator (Eq. 20): on a
  * periodic line of n points the solution of the tridiagonal system is
  *   d_i = sum_{j=1..K} w[j] (u_{i+j} - u_{i-j}),
@@ -166,6 +172,58 @@ lbm_status lbm_set_timing(lbm_ctx *c, int enable);
 /* Read the accounting (synchronising).  Kernels launched while timing was
  * disabled are not counted. */
 lbm_status lbm_get_timing(lbm_ctx *c, lbm_timing *out);
+
+/* ---------------------------------------------------------------------------
+ * Batched sweep: n independent periodic lattices of uneven size, each with its
+ * own EOS, constants, T/Tc, tau, k, force form and gradient (the temperature
+ * and EOS sweeps behind the coexistence curves of Sec. 5.2, Fig. 5), advanced
+ * together by one persistent cooperative launch per lbm_batch_step call,
+ * replayed from a CUDA graph.  All instances share p[0].prec and p[0].stream.
+ * Host fields are concatenated instance after instance: a density field has
+ * nx_i*ny_i entries per instance, a distribution array 9*nx_i*ny_i (SoA within
+ * the instance).  Grid-wide waits inside the launch are bounded (2 s); a wait
+ * that gives up makes the launch return early and the next synchronising call
+ * answer LBM_E_TIMEOUT.
+ * ------------------------------------------------------------------------- */
+
+/* Validate p[0..n-1] and allocate the batch on the current device. */
+lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out);
+
+/* f = f^eq(rho, 0) (Eq. 2) for every instance from concatenated host FP64 rho. */
+lbm_status lbm_batch_init_density(lbm_batch *b, const double *rho);
+
+/* Set / read the full state (concatenated host FP64, 9*nx_i*ny_i per instance).
+ * lbm_batch_get_f synchronises. */
+lbm_status lbm_batch_set_f(lbm_batch *b, const double *f);
+lbm_status lbm_batch_get_f(lbm_batch *b, double *f);
+
+/* Advance every instance nsteps steps (Eq. 1): one persistent launch,
+ * asynchronous on the batch's stream. */
+lbm_status lbm_batch_step(lbm_batch *b, int nsteps);
+
+/* Wait for the batch's stream and check its error word. */
+lbm_status lbm_batch_sync(lbm_batch *b);
+
+/* Density (Eq. 3) of every instance into concatenated host FP64 rho.  Synchronising. */
+lbm_status lbm_batch_density(lbm_batch *b, double *rho);
+
+/* Launch shape of the persistent kernel: threads per block (128, 256 or 512)
+ * and co-resident blocks per SM (1 .. the occupancy limit). */
+lbm_status lbm_batch_set_launch(lbm_batch *b, int block_threads, int blocks_per_sm);
+lbm_status lbm_batch_get_launch(lbm_batch *b, int *block_threads, int *grid_blocks);
+
+/* Autotuner: time trial_steps steps for every candidate launch shape on a copy
+ * of the current state, keep the fastest (written to the out pointers, which
+ * may be NULL) and restore the state.  Synchronising. */
+lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int *grid_blocks);
+
+/* Test hook for the bounded grid barrier: block `block` (or none when -1)
+ * skips its first arrival, so the other blocks give up after limit_seconds
+ * (at most 60) and the next synchronising call answers LBM_E_TIMEOUT. */
+lbm_status lbm_batch_debug_skip_barrier(lbm_batch *b, int block, double limit_seconds);
+
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
 
 /* Size of the fixed device scratch array used by lbm_step_noalloc. */
 #define LBM_STATIC_SCRATCH_BYTES (4u << 20)

@@ -1,0 +1,747 @@
+// Batched sweep: many independent periodic lattices of uneven size, each with
+// its own equation of state, temperature and relaxation time, advanced by one
+// persistent cooperative launch (captured in a CUDA graph) instead of two
+// launches per instance per step.
+//
+// Layout.  The instances' cells are concatenated; instance i owns cells
+// [off_i, off_i + nx_i ny_i) of every array, with off_i a multiple of 512 so
+// that any chunk of 128..512 consecutive cells belongs to one instance.  f is
+// SoA over the whole batch: f[q * ntot + cell].
+//
+// One step = phase A (rho = sum f, potential field of Eq. 8/21 for every cell)
+// + grid barrier + phase B (HDM/CDM gradient of the potential, force Eq. 22 /
+// Eq. 7, exact-difference forcing + BGK of Eq. 1, 2, 10, periodic push
+// streaming within the instance) + grid barrier.  Blocks take 'chunks' of
+// blockDim cells of one instance (its parameters are uniform in the block).
+// The grid barrier is a counter/generation pair in global memory; every wait
+// is bounded by %globaltimer and sets LBM_E_TIMEOUT and an abort flag that
+// all blocks check, so no block can spin forever.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr int kAlign = 512;       // instance offsets are multiples of this many cells
+constexpr int kTableGrain = 128;  // cells per entry of the chunk -> instance table
+
+template <typename T>
+struct Inst {
+    Model<T> m;
+    int off;  // first cell of the instance in the concatenated arrays
+    int sc;   // Shan-Chen (Eq. 22) or Zhang-Chen (Eq. 7) form
+    int cdm;  // CDM (Eq. 15) instead of HDM (Eq. 20)
+};
+
+struct BarrierState {
+    unsigned int count;
+    unsigned int gen;
+    int abort;
+};
+
+template <typename T>
+struct BatchArgs {
+    const Inst<T> *inst;
+    const int *table;      // instance of each kTableGrain-cell group (-1 = padding)
+    T *f[2];               // the two distribution buffers (ping-pong by step parity)
+    T *q;                  // potential field
+    long long ntot;        // cells in the concatenated arrays (padded)
+    int nsteps;
+    int parity0;           // buffer holding the state at the first step
+    int *err;
+    BarrierState *bar;
+    unsigned long long limit_ns;
+    int skip_block;        // test hook: this block never arrives at the first barrier (-1: none)
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier with a wall-time bound.  Returns false if the batch was
+// aborted (by a timeout here or elsewhere).
+__device__ bool grid_sync(BarrierState *b, unsigned int nblocks, int *err, unsigned long long limit_ns) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &b->gen;
+        volatile int *vabort = &b->abort;
+        const unsigned int g = *vgen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == nblocks - 1) {
+            b->count = 0;
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            const unsigned long long t0 = gtimer();
+            unsigned int it = 0;
+            while (*vgen == g && !*vabort) {
+                if ((++it & 255) == 0 && gtimer() - t0 > limit_ns) {
+                    atomicOr(err, kErrTimeout);
+                    atomicExch(&b->abort, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        ok = !*vabort;
+    }
+    __syncthreads();
+    return ok;
+}
+
+template <typename T>
+__device__ __forceinline__ T qabs(T v, bool sc) {
+    return sc ? fabs(v) : v;
+}
+
+template <typename T>
+__global__ void batch_kernel(const BatchArgs<T> a) {
+    const unsigned int nblocks = gridDim.x;
+    const int B = blockDim.x;
+    const long long nchunks = a.ntot / B;
+    for (int step = 0; step < a.nsteps; ++step) {
+        const bool odd = ((a.parity0 + step) & 1) != 0;  // (a select, not a dynamic index into the parameters)
+        const T *__restrict__ f = odd ? a.f[1] : a.f[0];
+        T *__restrict__ fo = odd ? a.f[0] : a.f[1];
+        // ---- phase A: density and potential field ----
+        for (long long ch = blockIdx.x; ch < nchunks; ch += nblocks) {
+            const long long cell = ch * B + threadIdx.x;
+            const int ii = a.table[(ch * B) / kTableGrain];
+            if (ii < 0) continue;
+            const Inst<T> &I = a.inst[ii];
+            const long long local = cell - I.off;
+            if (local >= (long long)I.m.nx * I.m.ny) continue;
+            T r = T(0);
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) r += f[i * a.ntot + cell];
+            if (!(r > T(0)) || !isfinite(r)) atomicOr(a.err, kErrUnstable);
+            a.q[cell] = potential_field(I.m, r, I.sc != 0);
+        }
+        if (step == 0 && (int)blockIdx.x == a.skip_block) return;  // test hook: never arrive
+        if (!grid_sync(a.bar, nblocks, a.err, a.limit_ns)) return;
+        // ---- phase B: gradient, force, forcing + BGK, periodic push streaming ----
+        for (long long ch = blockIdx.x; ch < nchunks; ch += nblocks) {
+            const long long cell = ch * B + threadIdx.x;
+            const int ii = a.table[(ch * B) / kTableGrain];
+            if (ii < 0) continue;
+            const Inst<T> &I = a.inst[ii];
+            const Model<T> &m = I.m;
+            const int local = (int)(cell - I.off);
+            if (local >= m.nx * m.ny) continue;
+            const bool sc = I.sc != 0;
+            const int y = local / m.nx, x = local - y * m.nx;
+            const T *qi = a.q + I.off;
+            const T *qrow = qi + (long long)y * m.nx;
+            T dx = T(0), dy = T(0);
+            if (I.cdm) {
+                // Eq. 15 times 1/c_s^2 on the instance's periodic lattice
+                const int xp = x + 1 == m.nx ? 0 : x + 1, xm = x == 0 ? m.nx - 1 : x - 1;
+                const int yp = y + 1 == m.ny ? 0 : y + 1, ym = y == 0 ? m.ny - 1 : y - 1;
+                auto at = [&](int yy, int xx) { return qabs(__ldg(qi + (long long)yy * m.nx + xx), sc); };
+                const T e = at(y, xp), w = at(y, xm), nn = at(yp, x), s = at(ym, x);
+                const T ne = at(yp, xp), nw = at(yp, xm), se = at(ym, xp), sw = at(ym, xm);
+                dx = T(1.0 / 3.0) * (e - w) + T(1.0 / 12.0) * ((ne + se) - (nw + sw));
+                dy = T(1.0 / 3.0) * (nn - s) + T(1.0 / 12.0) * ((ne + nw) - (se + sw));
+            } else {
+                // explicit periodic form of Eq. 20 (folded weights for short lines)
+                for (int j = 1; j <= m.kx; ++j) {
+                    int xp = x + j, xm = x - j;
+                    if (xp >= m.nx) xp -= m.nx;
+                    if (xm < 0) xm += m.nx;
+                    dx += m.wx[j] * (qabs(__ldg(qrow + xp), sc) - qabs(__ldg(qrow + xm), sc));
+                }
+                for (int j = 1; j <= m.ky; ++j) {
+                    int yp = y + j, ym = y - j;
+                    if (yp >= m.ny) yp -= m.ny;
+                    if (ym < 0) ym += m.ny;
+                    dy += m.wy[j] * (qabs(__ldg(qi + (long long)yp * m.nx + x), sc) -
+                                     qabs(__ldg(qi + (long long)ym * m.nx + x), sc));
+                }
+            }
+            const T qc = a.q[cell];
+            T Fx, Fy;
+            if (sc) {  // Eq. 22: F = -2 s Phi grad Phi, q = s Phi
+                Fx = T(-2) * qc * dx;
+                Fy = T(-2) * qc * dy;
+            } else {   // Eq. 7
+                Fx = -dx;
+                Fy = -dy;
+            }
+            T fi[kQ];
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) fi[i] = f[i * a.ntot + cell];
+            T r = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                r += fi[i];
+                jx += T(ex(i)) * fi[i];
+                jy += T(ey(i)) * fi[i];
+            }
+            const T inv = T(1) / r;
+            const T ux = jx * inv, uy = jy * inv;
+            const T vx = ux + Fx * inv, vy = uy + Fy * inv;
+            const T uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
+            const int xp = x + 1 == m.nx ? 0 : x + 1, xm = x == 0 ? m.nx - 1 : x - 1;
+            const int yp = y + 1 == m.ny ? 0 : y + 1, ym = y == 0 ? m.ny - 1 : y - 1;
+            T moved = T(0);
+#pragma unroll
+            for (int i = 1; i < kQ; ++i) {
+                const T eu = T(ex(i)) * ux + T(ey(i)) * uy;
+                const T ev = T(ex(i)) * vx + T(ey(i)) * vy;
+                const T feq = r * wq<T>(i) * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
+                const T fsh = r * wq<T>(i) * (T(1) + T(3) * ev + T(4.5) * ev * ev - T(1.5) * vv);
+                const T post = fi[i] - (fi[i] - feq) * m.omega + (fsh - feq);
+                moved += post;
+                const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
+                const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
+                fo[i * a.ntot + I.off + (long long)dys * m.nx + dxs] = post;
+            }
+            fo[cell] = r - moved;
+        }
+        if (!grid_sync(a.bar, nblocks, a.err, a.limit_ns)) return;
+    }
+}
+
+template <typename T>
+__global__ void batch_init_kernel(const Inst<T> *inst, const int *table, const T *rho, T *f, long long ntot) {
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < ntot;
+         cell += (long long)gridDim.x * blockDim.x) {
+        const int ii = table[cell / kTableGrain];
+        const bool valid = ii >= 0 && cell - inst[ii].off < (long long)inst[ii].m.nx * inst[ii].m.ny;
+        const T r = valid ? rho[cell] : T(0);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) f[i * ntot + cell] = r * wq<T>(i);  // f^eq(rho, 0), Eq. 2
+    }
+}
+
+template <typename T>
+__global__ void batch_density_kernel(const Inst<T> *inst, const int *table, const T *f, T *rho, long long ntot) {
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < ntot;
+         cell += (long long)gridDim.x * blockDim.x) {
+        T r = T(0);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) r += f[i * ntot + cell];
+        rho[cell] = r;
+    }
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_batch {
+    int n = 0;
+    int prec = LBM_F32;
+    size_t esz = 4;
+    long long ntot = 0;
+    std::vector<lbm_params> params;
+    std::vector<long long> off;
+    void *inst_dev = nullptr;
+    int *table_dev = nullptr;
+    void *f[2] = {nullptr, nullptr};
+    void *q = nullptr;
+    void *stage_dev = nullptr;   // rho staging (ntot values of the precision)
+    void *stage_host = nullptr;  // pinned host staging
+    int *err = nullptr;
+    BarrierState *bar = nullptr;
+    int cur = 0;
+    cudaStream_t stream = nullptr;
+    int block_threads = 256;
+    int grid_blocks = 0;
+    unsigned long long limit_ns = 2000000000ull;  // 2 s per barrier wait
+    int skip_block = -1;
+    bool initialized = false;
+    bool unstable = false;
+    // graphs of the last step count, one per starting buffer parity
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+    int graph_steps[2] = {-1, -1}, graph_block[2] = {-1, -1}, graph_grid[2] = {-1, -1};
+    bool use_graph = true;
+    int graph_launches = 0;  // persistent launches issued through a graph
+    std::string msg;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch *b, lbm_status st, const std::string &m) {
+    if (b) b->msg = m;
+    return st;
+}
+
+#define BCK(b, expr, what)                                                                         \
+    do {                                                                                           \
+        cudaError_t e_ = (expr);                                                                   \
+        if (e_ != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+double alpha_b(const lbm_params &p, double T, double Tc) {
+    double m, s;
+    switch (p.eos) {
+    case LBM_EOS_PR:
+        m = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
+        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
+        return s * s;
+    case LBM_EOS_RKS:
+        m = 0.480 + 1.574 * p.omega - 0.176 * p.omega * p.omega;
+        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
+        return s * s;
+    case LBM_EOS_RK:
+        return 1.0 / std::sqrt(T);
+    default:
+        return 1.0;
+    }
+}
+
+template <typename T>
+lbm_status build_instances(lbm_batch *b, std::vector<Inst<T>> &out) {
+    out.resize(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        const lbm_params &p = b->params[i];
+        Inst<T> &I = out[i];
+        I = Inst<T>{};
+        double Tc = p.Tc, rc = 0;
+        if (!(Tc > 0) && lbm_critical_point(p.eos, p.a, p.b, p.R, &Tc, &rc) != LBM_OK)
+            return bfail(b, LBM_E_INVALID, "no critical point for instance " + std::to_string(i));
+        const double Temp = p.Tr * Tc;
+        I.m.nx = p.nx;
+        I.m.ny = p.ny;
+        I.m.eos = p.eos;
+        I.m.RT = (T)(p.R * Temp);
+        I.m.a = (T)p.a;
+        I.m.b = (T)p.b;
+        I.m.aal = (T)(p.a * alpha_b(p, Temp, Tc));
+        I.m.k = (T)p.k;
+        I.m.omega = (T)(1.0 / p.tau);
+        const int radius = p.hdm_radius ? p.hdm_radius : (b->prec == LBM_F64 ? 40 : 26);
+        double wx[kMaxRadius + 1] = {}, wy[kMaxRadius + 1] = {};
+        lbm_hdm_weights(p.nx, radius, wx, &I.m.kx);
+        lbm_hdm_weights(p.ny, radius, wy, &I.m.ky);
+        for (int j = 0; j <= kMaxRadius; ++j) {
+            I.m.wx[j] = (T)wx[j];
+            I.m.wy[j] = (T)wy[j];
+        }
+        I.off = (int)b->off[i];
+        I.sc = p.force == LBM_FORCE_SC;
+        I.cdm = p.grad == LBM_GRAD_CDM;
+    }
+    return LBM_OK;
+}
+
+template <typename T>
+BatchArgs<T> make_args(lbm_batch *b, int nsteps) {
+    BatchArgs<T> a{};
+    a.inst = (const Inst<T> *)b->inst_dev;
+    a.table = b->table_dev;
+    a.f[0] = (T *)b->f[0];
+    a.f[1] = (T *)b->f[1];
+    a.q = (T *)b->q;
+    a.ntot = b->ntot;
+    a.nsteps = nsteps;
+    a.parity0 = b->cur;
+    a.err = b->err;
+    a.bar = b->bar;
+    a.limit_ns = b->limit_ns;
+    a.skip_block = b->skip_block;
+    return a;
+}
+
+template <typename T>
+int max_blocks_per_sm(int threads) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<T>, threads, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+// Queue one persistent cooperative launch running nsteps steps.
+template <typename T>
+cudaError_t enqueue(lbm_batch *b, int nsteps) {
+    cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(BarrierState), b->stream);
+    if (e != cudaSuccess) return e;
+    BatchArgs<T> a = make_args<T>(b, nsteps);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(b->grid_blocks);
+    cfg.blockDim = dim3(b->block_threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_kernel<T>, a);
+}
+
+void drop_graph(lbm_batch *b, int k) {
+    if (b->graph_exec[k]) cudaGraphExecDestroy(b->graph_exec[k]);
+    if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+    b->graph_exec[k] = nullptr;
+    b->graph[k] = nullptr;
+    b->graph_steps[k] = -1;
+}
+
+// nsteps steps as one persistent launch, replayed from a CUDA graph captured
+// for this (step count, starting buffer, launch shape).
+template <typename T>
+lbm_status run_steps(lbm_batch *b, int nsteps) {
+    if (nsteps == 0) return LBM_OK;
+    const int k = b->cur;
+    if (b->use_graph && b->skip_block < 0) {
+        if (!b->graph_exec[k] || b->graph_steps[k] != nsteps || b->graph_block[k] != b->block_threads ||
+            b->graph_grid[k] != b->grid_blocks) {
+            drop_graph(b, k);
+            bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                cudaError_t e1 = enqueue<T>(b, nsteps);
+                cudaError_t e2 = cudaStreamEndCapture(b->stream, &b->graph[k]);
+                ok = e1 == cudaSuccess && e2 == cudaSuccess &&
+                     cudaGraphInstantiate(&b->graph_exec[k], b->graph[k], 0) == cudaSuccess;
+            }
+            if (!ok) {  // graphs unavailable for this launch: plain launches from now on
+                cudaGetLastError();
+                drop_graph(b, k);
+                b->use_graph = false;
+            } else {
+                b->graph_steps[k] = nsteps;
+                b->graph_block[k] = b->block_threads;
+                b->graph_grid[k] = b->grid_blocks;
+            }
+        }
+        if (b->graph_exec[k]) {
+            BCK(b, cudaGraphLaunch(b->graph_exec[k], b->stream), "cudaGraphLaunch");
+            b->graph_launches += 1;
+            b->cur = (b->cur + nsteps) & 1;
+            return LBM_OK;
+        }
+    }
+    BCK(b, enqueue<T>(b, nsteps), "cooperative launch");
+    b->cur = (b->cur + nsteps) & 1;
+    return LBM_OK;
+}
+
+lbm_status batch_sync(lbm_batch *b) {
+    int h = 0;
+    BCK(b, cudaMemcpyAsync(&h, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "read error word");
+    BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (h & kErrTimeout) return bfail(b, LBM_E_TIMEOUT, "a grid barrier wait timed out");
+    if (h & kErrUnstable) {
+        b->unstable = true;
+        return bfail(b, LBM_E_UNSTABLE, "unstable: NaN or non-positive density");
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out) {
+    if (!out) return LBM_E_INVALID;
+    *out = nullptr;
+    if (!p || n < 1) return LBM_E_INVALID;
+    const int prec = p[0].prec;
+    if (prec != LBM_F32 && prec != LBM_F64) return LBM_E_INVALID;
+    for (int i = 0; i < n; ++i) {
+        const lbm_params &q = p[i];
+        if (q.prec != prec || q.nx < 1 || q.ny < 1 || q.eos < LBM_EOS_VDW || q.eos > LBM_EOS_RKS ||
+            (q.force != LBM_FORCE_SC && q.force != LBM_FORCE_ZC) || (q.grad != LBM_GRAD_HDM && q.grad != LBM_GRAD_CDM) ||
+            q.hdm_radius < 0 || q.hdm_radius > kMaxRadius || !(q.a >= 0) || !(q.b > 0) || !(q.R > 0) || !(q.Tr > 0) ||
+            !(q.tau > 0.5) || (long long)q.nx * q.ny > (1LL << 30))
+            return LBM_E_INVALID;
+    }
+    lbm_batch *b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_E_NOMEM;
+    b->n = n;
+    b->prec = prec;
+    b->esz = prec == LBM_F64 ? sizeof(double) : sizeof(float);
+    b->params.assign(p, p + n);
+    b->stream = (cudaStream_t)p[0].stream;
+    long long o = 0;
+    for (int i = 0; i < n; ++i) {
+        b->off.push_back(o);
+        long long cells = (long long)p[i].nx * p[i].ny;
+        o += (cells + kAlign - 1) / kAlign * kAlign;
+    }
+    b->ntot = o;
+    auto bail = [&](lbm_status st) {
+        lbm_batch_destroy(b);
+        return st;
+    };
+    std::vector<int> table(b->ntot / kTableGrain, -1);
+    for (int i = 0; i < n; ++i) {
+        long long cells = (long long)p[i].nx * p[i].ny;
+        for (long long g = b->off[i] / kTableGrain; g < (b->off[i] + cells + kTableGrain - 1) / kTableGrain; ++g)
+            table[g] = i;
+    }
+    size_t inst_bytes;
+    std::vector<unsigned char> inst_host;
+    if (prec == LBM_F64) {
+        std::vector<Inst<double>> v;
+        if (build_instances<double>(b, v) != LBM_OK) return bail(LBM_E_INVALID);
+        inst_bytes = v.size() * sizeof(Inst<double>);
+        inst_host.assign((unsigned char *)v.data(), (unsigned char *)v.data() + inst_bytes);
+    } else {
+        std::vector<Inst<float>> v;
+        if (build_instances<float>(b, v) != LBM_OK) return bail(LBM_E_INVALID);
+        inst_bytes = v.size() * sizeof(Inst<float>);
+        inst_host.assign((unsigned char *)v.data(), (unsigned char *)v.data() + inst_bytes);
+    }
+    const size_t fbytes = (size_t)kQ * b->ntot * b->esz;
+    if (cudaMalloc(&b->inst_dev, inst_bytes) != cudaSuccess || cudaMalloc((void **)&b->table_dev, table.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->f[0], fbytes) != cudaSuccess || cudaMalloc(&b->f[1], fbytes) != cudaSuccess ||
+        cudaMalloc(&b->q, b->ntot * b->esz) != cudaSuccess || cudaMalloc(&b->stage_dev, b->ntot * b->esz) != cudaSuccess ||
+        cudaMalloc((void **)&b->err, sizeof(int)) != cudaSuccess || cudaMalloc((void **)&b->bar, sizeof(BarrierState)) != cudaSuccess ||
+        cudaHostAlloc(&b->stage_host, b->ntot * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+        return bail(LBM_E_NOMEM);
+    if (cudaMemcpy(b->inst_dev, inst_host.data(), inst_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->table_dev, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->f[0], 0, fbytes) != cudaSuccess || cudaMemset(b->f[1], 0, fbytes) != cudaSuccess ||
+        cudaMemset(b->err, 0, sizeof(int)) != cudaSuccess)
+        return bail(LBM_E_CUDA);
+    // default launch shape: 256 threads, as many co-resident blocks as occupancy allows
+    const int per_sm = prec == LBM_F64 ? max_blocks_per_sm<double>(256) : max_blocks_per_sm<float>(256);
+    if (per_sm < 1) return bail(LBM_E_CUDA);
+    b->block_threads = 256;
+    b->grid_blocks = per_sm * sm_count();
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_launch(lbm_batch *b, int block_threads, int blocks_per_sm) {
+    if (!b) return LBM_E_INVALID;
+    if (block_threads != 128 && block_threads != 256 && block_threads != 512)
+        return bfail(b, LBM_E_INVALID, "block_threads must be 128, 256 or 512");
+    const int maxb = b->prec == LBM_F64 ? max_blocks_per_sm<double>(block_threads) : max_blocks_per_sm<float>(block_threads);
+    if (blocks_per_sm < 1 || blocks_per_sm > maxb)
+        return bfail(b, LBM_E_INVALID, "blocks_per_sm must be in [1, " + std::to_string(maxb) + "]");
+    b->block_threads = block_threads;
+    b->grid_blocks = blocks_per_sm * sm_count();
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_launch(lbm_batch *b, int *block_threads, int *grid_blocks) {
+    if (!b || !block_threads || !grid_blocks) return LBM_E_INVALID;
+    *block_threads = b->block_threads;
+    *grid_blocks = b->grid_blocks;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_init_density(lbm_batch *b, const double *rho) {
+    if (!b || !rho) return LBM_E_INVALID;
+    // scatter the concatenated fields (instance after instance, nx*ny each) to the padded layout
+    std::vector<unsigned char> tmp;
+    const size_t esz = b->esz;
+    unsigned char *h = (unsigned char *)b->stage_host;
+    BCK(b, cudaStreamSynchronize(b->stream), "sync before staging");
+    std::fill(h, h + b->ntot * esz, 0);
+    long long src = 0;
+    for (int i = 0; i < b->n; ++i) {
+        long long cells = (long long)b->params[i].nx * b->params[i].ny;
+        for (long long c = 0; c < cells; ++c) {
+            double v = rho[src + c];
+            if (!(v > 0) || !std::isfinite(v)) return bfail(b, LBM_E_INVALID, "rho must be positive and finite");
+            if (esz == sizeof(double)) ((double *)h)[b->off[i] + c] = v;
+            else ((float *)h)[b->off[i] + c] = (float)v;
+        }
+        src += cells;
+    }
+    BCK(b, cudaMemcpyAsync(b->stage_dev, h, b->ntot * esz, cudaMemcpyHostToDevice, b->stream), "copy rho");
+    b->cur = 0;
+    const int blocks = (int)std::min<long long>((b->ntot + 255) / 256, 152 * 16);
+    if (b->prec == LBM_F64)
+        batch_init_kernel<double><<<blocks, 256, 0, b->stream>>>((const Inst<double> *)b->inst_dev, b->table_dev,
+                                                                 (const double *)b->stage_dev, (double *)b->f[0], b->ntot);
+    else
+        batch_init_kernel<float><<<blocks, 256, 0, b->stream>>>((const Inst<float> *)b->inst_dev, b->table_dev,
+                                                                (const float *)b->stage_dev, (float *)b->f[0], b->ntot);
+    BCK(b, cudaGetLastError(), "init kernel");
+    BCK(b, cudaMemsetAsync(b->err, 0, sizeof(int), b->stream), "clear error word");
+    b->initialized = true;
+    b->unstable = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, int nsteps) {
+    if (!b) return LBM_E_INVALID;
+    if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
+    if (b->unstable) return bfail(b, LBM_E_UNSTABLE, "batch is in the error state");
+    if (nsteps < 0) return bfail(b, LBM_E_INVALID, "nsteps must be >= 0");
+    return b->prec == LBM_F64 ? run_steps<double>(b, nsteps) : run_steps<float>(b, nsteps);
+}
+
+lbm_status lbm_batch_sync(lbm_batch *b) {
+    if (!b) return LBM_E_INVALID;
+    return batch_sync(b);
+}
+
+lbm_status lbm_batch_density(lbm_batch *b, double *rho) {
+    if (!b || !rho) return LBM_E_INVALID;
+    if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
+    const int blocks = (int)std::min<long long>((b->ntot + 255) / 256, 152 * 16);
+    if (b->prec == LBM_F64)
+        batch_density_kernel<double><<<blocks, 256, 0, b->stream>>>((const Inst<double> *)b->inst_dev, b->table_dev,
+                                                                    (const double *)b->f[b->cur], (double *)b->stage_dev, b->ntot);
+    else
+        batch_density_kernel<float><<<blocks, 256, 0, b->stream>>>((const Inst<float> *)b->inst_dev, b->table_dev,
+                                                                   (const float *)b->f[b->cur], (float *)b->stage_dev, b->ntot);
+    BCK(b, cudaGetLastError(), "density kernel");
+    BCK(b, cudaMemcpyAsync(b->stage_host, b->stage_dev, b->ntot * b->esz, cudaMemcpyDeviceToHost, b->stream), "copy rho");
+    lbm_status st = batch_sync(b);
+    if (st != LBM_OK && st != LBM_E_UNSTABLE) return st;
+    long long dst = 0;
+    for (int i = 0; i < b->n; ++i) {
+        long long cells = (long long)b->params[i].nx * b->params[i].ny;
+        for (long long c = 0; c < cells; ++c)
+            rho[dst + c] = b->esz == sizeof(double) ? ((double *)b->stage_host)[b->off[i] + c]
+                                                    : (double)((float *)b->stage_host)[b->off[i] + c];
+        dst += cells;
+    }
+    return st;
+}
+
+lbm_status lbm_batch_get_f(lbm_batch *b, double *f) {
+    if (!b || !f) return LBM_E_INVALID;
+    if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
+    long long total = 0;
+    for (int i = 0; i < b->n; ++i) total += (long long)b->params[i].nx * b->params[i].ny;
+    std::vector<unsigned char> all((size_t)kQ * b->ntot * b->esz);
+    BCK(b, cudaMemcpyAsync(all.data(), b->f[b->cur], all.size(), cudaMemcpyDeviceToHost, b->stream), "copy f");
+    lbm_status st = batch_sync(b);
+    if (st != LBM_OK && st != LBM_E_UNSTABLE) return st;
+    // output: instance after instance, each 9 x ny x nx (SoA within the instance)
+    long long dst = 0;
+    for (int i = 0; i < b->n; ++i) {
+        long long cells = (long long)b->params[i].nx * b->params[i].ny;
+        for (int k = 0; k < kQ; ++k)
+            for (long long c = 0; c < cells; ++c) {
+                size_t idx = (size_t)k * b->ntot + b->off[i] + c;
+                f[dst + k * cells + c] = b->esz == sizeof(double) ? ((double *)all.data())[idx]
+                                                                  : (double)((float *)all.data())[idx];
+            }
+        dst += kQ * cells;
+    }
+    return st;
+}
+
+lbm_status lbm_batch_set_f(lbm_batch *b, const double *f) {
+    if (!b || !f) return LBM_E_INVALID;
+    std::vector<unsigned char> all((size_t)kQ * b->ntot * b->esz, 0);
+    long long src = 0;
+    for (int i = 0; i < b->n; ++i) {
+        long long cells = (long long)b->params[i].nx * b->params[i].ny;
+        for (int k = 0; k < kQ; ++k)
+            for (long long c = 0; c < cells; ++c) {
+                size_t idx = (size_t)k * b->ntot + b->off[i] + c;
+                double v = f[src + k * cells + c];
+                if (b->esz == sizeof(double)) ((double *)all.data())[idx] = v;
+                else ((float *)all.data())[idx] = (float)v;
+            }
+        src += kQ * cells;
+    }
+    BCK(b, cudaMemcpyAsync(b->f[0], all.data(), all.size(), cudaMemcpyHostToDevice, b->stream), "copy f");
+    BCK(b, cudaStreamSynchronize(b->stream), "sync f copy");
+    BCK(b, cudaMemsetAsync(b->err, 0, sizeof(int), b->stream), "clear error word");
+    b->cur = 0;
+    b->initialized = true;
+    b->unstable = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int *grid_blocks) {
+    if (!b || trial_steps < 2) return LBM_E_INVALID;
+    if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
+    // work on a copy of the state: the trials advance it
+    const size_t fbytes = (size_t)kQ * b->ntot * b->esz;
+    void *save = nullptr;
+    BCK(b, cudaMalloc(&save, fbytes), "cudaMalloc(tune state)");
+    const int cur0 = b->cur;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_t = b->block_threads, best_g = b->grid_blocks;
+    const int threads[3] = {128, 256, 512};
+    lbm_status st = LBM_OK;
+    if (cudaMemcpyAsync(save, b->f[cur0], fbytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess) st = LBM_E_CUDA;
+    for (int ti = 0; ti < 3 && st == LBM_OK; ++ti) {
+        const int maxb = b->prec == LBM_F64 ? max_blocks_per_sm<double>(threads[ti]) : max_blocks_per_sm<float>(threads[ti]);
+        for (int per = 1; per <= maxb && st == LBM_OK; per = per < maxb && per * 2 > maxb ? maxb : per * 2) {
+            b->block_threads = threads[ti];
+            b->grid_blocks = per * sm_count();
+            // warm-up launch, then a timed one (plain launches: no graph per trial)
+            const bool g = b->use_graph;
+            b->use_graph = false;
+            lbm_status s1 = b->prec == LBM_F64 ? run_steps<double>(b, 2) : run_steps<float>(b, 2);
+            cudaEventRecord(e0, b->stream);
+            lbm_status s2 = b->prec == LBM_F64 ? run_steps<double>(b, trial_steps) : run_steps<float>(b, trial_steps);
+            cudaEventRecord(e1, b->stream);
+            b->use_graph = g;
+            if (s1 != LBM_OK || s2 != LBM_OK || cudaEventSynchronize(e1) != cudaSuccess) { st = LBM_E_CUDA; break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_t = b->block_threads; best_g = b->grid_blocks; }
+            if (per == maxb) break;
+        }
+    }
+    // restore the state and the error word
+    if (cudaMemcpyAsync(b->f[cur0], save, fbytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess) st = LBM_E_CUDA;
+    b->cur = cur0;
+    cudaMemsetAsync(b->err, 0, sizeof(int), b->stream);
+    cudaStreamSynchronize(b->stream);
+    cudaFree(save);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->block_threads = best_t;
+    b->grid_blocks = best_g;
+    if (block_threads) *block_threads = best_t;
+    if (grid_blocks) *grid_blocks = best_g;
+    return st == LBM_OK ? LBM_OK : bfail(b, st, "autotuning failed");
+}
+
+lbm_status lbm_batch_debug_skip_barrier(lbm_batch *b, int block, double limit_seconds) {
+    if (!b || !(limit_seconds > 0) || limit_seconds > 60) return LBM_E_INVALID;
+    b->skip_block = block;
+    b->limit_ns = (unsigned long long)(limit_seconds * 1e9);
+    return LBM_OK;
+}
+
+const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->msg.c_str() : "null batch"; }
+
+void lbm_batch_destroy(lbm_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    drop_graph(b, 0);
+    drop_graph(b, 1);
+    cudaFree(b->inst_dev);
+    cudaFree(b->table_dev);
+    cudaFree(b->f[0]);
+    cudaFree(b->f[1]);
+    cudaFree(b->q);
+    cudaFree(b->stage_dev);
+    cudaFree(b->err);
+    cudaFree(b->bar);
+    if (b->stage_host) cudaFreeHost(b->stage_host);
+    delete b;
+}
+
+}  // extern "C"

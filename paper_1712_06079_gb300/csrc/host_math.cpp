@@ -19,6 +19,7 @@
 // On a periodic line of n points the operator is the circulant with the
 // folded kernel sum_m c_{j + m n} (c_{-j} = -c_j), which is exactly the
 // periodic (cyclic) tridiagonal solve.
+#include <algorithm>
 #include <cmath>
 
 #include "lbm.h"
@@ -91,6 +92,114 @@ extern "C" lbm_status lbm_critical_point(int eos, double a, double b, double R, 
     double ratio = B.d / A.d;  // T / beta(T)
     *rho_c = rc;
     *Tc = (eos == LBM_EOS_RK) ? std::pow(ratio, 2.0 / 3.0) : ratio;
+    return LBM_OK;
+}
+
+namespace {
+
+// p_EOS(rho) and dp/drho at absolute temperature T with the given alpha.
+void eos_p(int eos, double a, double b, double R, double T, double alpha, double rho, double *p, double *dp) {
+    Dual2 A, B;
+    eos_parts(eos, a, b, R, {rho, 1.0, 0.0}, &A, &B);
+    *p = T * A.v - alpha * B.v;
+    *dp = T * A.d - alpha * B.d;
+}
+
+struct Isotherm {
+    int eos;
+    double a, b, R, T, alpha;
+    double p(double rho) const { double v, d; eos_p(eos, a, b, R, T, alpha, rho, &v, &d); return v; }
+    double dp(double rho) const { double v, d; eos_p(eos, a, b, R, T, alpha, rho, &v, &d); return d; }
+};
+
+// Root of dp/drho = 0 in [lo, hi] (dp changes sign there), by bisection.
+double dp_root(const Isotherm &I, double lo, double hi) {
+    bool lo_pos = I.dp(lo) > 0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if ((I.dp(mid) > 0) == lo_pos) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// rho in [lo, hi] with p(rho) = ps, p monotone increasing there (safeguarded Newton).
+double p_root(const Isotherm &I, double ps, double lo, double hi) {
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+        double v = I.p(x) - ps;
+        if (v > 0) hi = x; else lo = x;
+        double d = I.dp(x);
+        double xn = x - v / d;
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (std::fabs(xn - x) <= 1e-16 * x) { x = xn; break; }
+        x = xn;
+    }
+    return x;
+}
+
+// int_{rg}^{rl} (p - ps)/rho^2 drho, 16-point Gauss-Legendre on 64 panels in s = ln rho.
+double area(const Isotherm &I, double ps, double rg, double rl) {
+    static const double xg[8] = {0.0950125098376374, 0.2816035507792589, 0.4580167776572274, 0.6178762444026438,
+                                 0.7554044083550030, 0.8656312023878318, 0.9445750230732326, 0.9894009349916499};
+    static const double wg[8] = {0.1894506104550685, 0.1826034150449236, 0.1691565193950025, 0.1495959888165767,
+                                 0.1246289712555339, 0.0951585116824928, 0.0622535239386479, 0.0271524594117541};
+    const int panels = 64;
+    const double s0 = std::log(rg), s1 = std::log(rl), h = (s1 - s0) / panels;
+    double acc = 0.0;
+    for (int k = 0; k < panels; ++k) {
+        const double c = s0 + (k + 0.5) * h;
+        for (int i = 0; i < 8; ++i)
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                const double rho = std::exp(c + sgn * xg[i] * 0.5 * h);
+                acc += wg[i] * (I.p(rho) - ps) / rho;
+            }
+    }
+    return acc * 0.5 * h;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_maxwell(const lbm_params *p, double *rho_g, double *rho_l) {
+    if (!p || !rho_g || !rho_l || p->eos < LBM_EOS_VDW || p->eos > LBM_EOS_RKS || !(p->a > 0) || !(p->b > 0) ||
+        !(p->R > 0) || !(p->Tr > 0))
+        return LBM_E_INVALID;
+    double Tc = p->Tc, rc = 0;
+    if (!(Tc > 0) && lbm_critical_point(p->eos, p->a, p->b, p->R, &Tc, &rc) != LBM_OK) return LBM_E_INVALID;
+    if (!(p->Tr < 1.0)) return LBM_E_INVALID;
+    Isotherm I{p->eos, p->a, p->b, p->R, p->Tr * Tc, 1.0};
+    if (p->eos == LBM_EOS_RK) I.alpha = 1.0 / std::sqrt(I.T);
+    else if (p->eos == LBM_EOS_PR || p->eos == LBM_EOS_RKS) {
+        const double w = p->omega;
+        const double m = p->eos == LBM_EOS_PR ? 0.37464 + 1.54226 * w - 0.26992 * w * w : 0.480 + 1.574 * w - 0.176 * w * w;
+        const double s = 1.0 + m * (1.0 - std::sqrt(p->Tr));
+        I.alpha = s * s;
+    }
+    const double pole = (p->eos == LBM_EOS_CS) ? 4.0 / p->b : 1.0 / p->b;
+    // the isotherm's local maximum and minimum: sign changes of dp/drho on a log grid
+    const int N = 4000;
+    double prev = I.dp(pole * 1e-12), lo_prev = pole * 1e-12, smax = -1, smin = -1;
+    for (int i = 1; i <= N; ++i) {
+        const double rho = pole * std::exp(std::log(1e-12) * (1.0 - double(i) / N)) * (1.0 - 1e-9);
+        const double d = I.dp(rho);
+        if (prev > 0 && d <= 0 && smax < 0) smax = dp_root(I, lo_prev, rho);
+        else if (prev <= 0 && d > 0 && smax > 0) { smin = dp_root(I, lo_prev, rho); break; }
+        prev = d;
+        lo_prev = rho;
+    }
+    if (smax < 0 || smin < 0) return LBM_E_INVALID;  // no van der Waals loop
+    double plo = std::max(I.p(smin), 0.0), phi = I.p(smax);
+    double rg = 0, rl = 0;
+    for (int it = 0; it < 200; ++it) {  // bisection on p_sat: the area decreases as p_sat rises
+        const double ps = 0.5 * (plo + phi);
+        if (ps <= plo || ps >= phi) break;
+        rg = p_root(I, ps, 0.0, smax);
+        rl = p_root(I, ps, smin, pole);
+        if (area(I, ps, rg, rl) > 0) plo = ps; else phi = ps;
+    }
+    const double ps = 0.5 * (plo + phi);
+    *rho_g = p_root(I, ps, 0.0, smax);
+    *rho_l = p_root(I, ps, smin, pole);
     return LBM_OK;
 }
 

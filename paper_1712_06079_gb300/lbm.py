@@ -73,6 +73,20 @@ SIGNATURES = {
     "lbm_set_timing": (ctypes.c_int, [_V, ctypes.c_int]),
     "lbm_get_timing": (ctypes.c_int, [_V, ctypes.POINTER(_Timing)]),
     "lbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(_Params), _V, _V]),
+    "lbm_maxwell": (ctypes.c_int, [ctypes.POINTER(_Params), _D, _D]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.c_int, ctypes.POINTER(_V)]),
+    "lbm_batch_init_density": (ctypes.c_int, [_V, _D]),
+    "lbm_batch_set_f": (ctypes.c_int, [_V, _D]),
+    "lbm_batch_get_f": (ctypes.c_int, [_V, _D]),
+    "lbm_batch_step": (ctypes.c_int, [_V, ctypes.c_int]),
+    "lbm_batch_sync": (ctypes.c_int, [_V]),
+    "lbm_batch_density": (ctypes.c_int, [_V, _D]),
+    "lbm_batch_set_launch": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_get_launch": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_tune": (ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_debug_skip_barrier": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_V]),
+    "lbm_batch_destroy": (None, [_V]),
     "lbm_destroy": (None, [_V]),
     "lbm_last_error": (ctypes.c_char_p, [_V]),
 }
@@ -120,6 +134,15 @@ def step_noalloc(params: "Params", f_in_ptr: int, f_out_ptr: int) -> int:
     lbm_step_noalloc (no device allocation; see include/lbm.h).  Returns the
     lbm_status code."""
     return load().lbm_step_noalloc(ctypes.byref(params.c()), f_in_ptr, f_out_ptr)
+
+
+def maxwell(params: "Params"):
+    """(rho_g, rho_l) of the Maxwell construction for params' EOS at params.Tr."""
+    g, l = ctypes.c_double(), ctypes.c_double()
+    st = load().lbm_maxwell(ctypes.byref(params.c()), ctypes.byref(g), ctypes.byref(l))
+    if st != OK:
+        raise LBMError(st, "lbm_maxwell failed (no van der Waals loop?)")
+    return g.value, l.value
 
 
 def hdm_weights(n: int, radius: int):
@@ -228,6 +251,91 @@ class Lattice:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.lbm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many independent lattices advanced together (``lbm_batch``): one
+    persistent launch per ``step`` call, replayed from a CUDA graph."""
+
+    def __init__(self, params: list):
+        self._lib = load()
+        self.params = list(params)
+        arr = (_Params * len(self.params))(*[p.c() for p in self.params])
+        h = ctypes.c_void_p()
+        st = self._lib.lbm_batch_create(arr, len(self.params), ctypes.byref(h))
+        if st != OK:
+            raise LBMError(st, "lbm_batch_create failed")
+        self._h = h
+        self.shapes = [(p.ny, p.nx) for p in self.params]
+        self.cells = [p.nx * p.ny for p in self.params]
+
+    def _check(self, st: int):
+        if st != OK:
+            raise LBMError(st, self._lib.lbm_batch_last_error(self._h).decode())
+
+    def _split(self, flat, per):
+        out, o = [], 0
+        for n, shp in zip(self.cells, self.shapes):
+            out.append(flat[o:o + per * n].reshape((per,) + shp if per > 1 else shp))
+            o += per * n
+        return out
+
+    def init_density(self, rhos: list):
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(r, dtype=np.float64).ravel() for r in rhos]))
+        self._check(self._lib.lbm_batch_init_density(self._h, _dp(flat)))
+
+    def set_f(self, fs: list):
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.float64).ravel() for f in fs]))
+        self._check(self._lib.lbm_batch_set_f(self._h, _dp(flat)))
+
+    def get_f(self) -> list:
+        flat = np.empty(9 * sum(self.cells))
+        self._check(self._lib.lbm_batch_get_f(self._h, _dp(flat)))
+        return self._split(flat, 9)
+
+    def step(self, n: int = 1):
+        self._check(self._lib.lbm_batch_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._lib.lbm_batch_sync(self._h))
+
+    def density(self) -> list:
+        flat = np.empty(sum(self.cells))
+        self._check(self._lib.lbm_batch_density(self._h, _dp(flat)))
+        return self._split(flat, 1)
+
+    def set_launch(self, block_threads: int, blocks_per_sm: int):
+        self._check(self._lib.lbm_batch_set_launch(self._h, block_threads, blocks_per_sm))
+
+    def launch(self):
+        t, g = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.lbm_batch_get_launch(self._h, ctypes.byref(t), ctypes.byref(g)))
+        return t.value, g.value
+
+    def tune(self, trial_steps: int = 50):
+        t, g = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.lbm_batch_tune(self._h, int(trial_steps), ctypes.byref(t), ctypes.byref(g)))
+        return t.value, g.value
+
+    def debug_skip_barrier(self, block: int, limit_seconds: float):
+        self._check(self._lib.lbm_batch_debug_skip_barrier(self._h, int(block), float(limit_seconds)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.lbm_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -99,3 +99,20 @@ def test_null_handles_are_safe(lib):
     assert lib.lbm_sync(None) == lbm.E_INVALID
     assert lib.lbm_create(None, None) == lbm.E_INVALID
     assert lib.lbm_last_error(None)
+
+
+@pytest.mark.parametrize("eos,Tr", [("vdw", 0.5), ("vdw", 0.95), ("cs", 0.7), ("cs", 0.8), ("pr", 0.55), ("pr", 0.9),
+                                    ("rk", 0.6), ("rks", 0.75)])
+def test_library_maxwell_matches_oracle(lib, eos, Tr):
+    from paper_1712_06079_gb300 import inputs
+    t = dict(inputs.EOS_TABLE.get(eos, dict(a=9 / 49, b=2 / 21, omega=0.344, k=0.01)))
+    g, l = lbm.maxwell(lbm.Params(nx=1, ny=1, eos=eos, a=t["a"], b=t["b"], omega=t["omega"], Tr=Tr))
+    op = oracle.params_at(1, 1, eos, t["a"], t["b"], Tr, omega=t["omega"])
+    go, lo, _ = oracle.maxwell(op)
+    assert g == pytest.approx(go, rel=1e-9)
+    assert l == pytest.approx(lo, rel=1e-10)
+
+
+def test_library_maxwell_rejects_supercritical(lib):
+    with pytest.raises(lbm.LBMError):
+        lbm.maxwell(lbm.Params(nx=1, ny=1, eos="vdw", a=9 / 49, b=2 / 21, Tr=1.02))

@@ -1,0 +1,155 @@
+"""GPU tests of the batched sweep (lbm_batch_*): one persistent launch over
+many uneven lattices, each with its own EOS, temperature, tau, force form and
+gradient.  Parity against the FP64 oracle per instance, agreement with the
+single-lattice contexts, graph replay, the autotuner, and the bounded grid
+barrier (a block that never arrives makes the launch give up with
+LBM_E_TIMEOUT, without hanging the GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_06079_gb300 import inputs, lbm
+
+pytestmark = pytest.mark.gpu
+
+EOS = dict(inputs.EOS_TABLE)
+EOS["rks"] = dict(a=9 / 49, b=2 / 21, omega=0.344, k=0.01)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1712_06079_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def instance(nx, ny, eos, Tr, tau, force="sc", grad="hdm", prec="f64"):
+    t = EOS[eos]
+    gp = lbm.Params(nx=nx, ny=ny, eos=eos, a=t["a"], b=t["b"], omega=t["omega"], Tr=Tr, k=t["k"], tau=tau,
+                    force=force, grad=grad, prec=prec)
+    op = oracle.params_at(nx, ny, eos, t["a"], t["b"], Tr, omega=t["omega"], k=t["k"], tau=tau,
+                          force=force, grad=grad)
+    return gp, op
+
+
+MIX = [  # uneven sizes, every EOS, both forces and gradients
+    (256, 8, "pr", 0.7, 1.0, "zc", "hdm"),
+    (328, 8, "cs", 0.8, 0.9, "sc", "hdm"),
+    (96, 40, "vdw", 0.85, 1.1, "sc", "cdm"),
+    (512, 8, "rk", 0.75, 1.2, "zc", "hdm"),
+    (40, 24, "rks", 0.8, 0.8, "sc", "hdm"),
+    (1000, 8, "vdw", 0.9, 1.0, "zc", "cdm"),   # ZC + CDM is unstable at low Tr (physics, not the kernel)
+]
+
+
+def slab_state(op, seed):
+    g, l, _ = oracle.maxwell(op)
+    rho = inputs.slab(op.nx, op.ny, g, l)
+    xi = inputs.uniform01(seed, 2 * op.nx * op.ny).reshape(2, op.ny, op.nx)
+    return oracle.init(op, rho, 0.01 * (xi[0] - 0.5), 0.01 * (xi[1] - 0.5))
+
+
+def test_batch_f64_matches_oracle_per_instance():
+    pairs = [instance(*m) for m in MIX]
+    f0 = [slab_state(op, k + 1) for k, (_, op) in enumerate(pairs)]
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        b.set_f(f0)
+        b.step(1)
+        f1 = b.get_f()
+        b.step(2)      # a second launch of 2 steps (graph replay from the other buffer)
+        f3 = b.get_f()
+    for (gp, op), a, g1, g3 in zip(pairs, f0, f1, f3):
+        o1 = oracle.step(op, a)
+        assert np.max(np.abs(g1 - o1) / np.abs(o1)) < 1e-12, (gp.eos, gp.nx)
+        o3 = oracle.run(op, a, 3)
+        assert np.max(np.abs(g3 - o3) / np.abs(o3)) < 1e-11, (gp.eos, gp.nx)
+
+
+def test_batch_f32_matches_single_lattice_contexts():
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f32") for m in MIX]
+    f0 = [slab_state(op, k + 11) for k, (_, op) in enumerate(pairs)]
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        b.set_f(f0)
+        b.step(100)
+        fb = b.get_f()
+    for (gp, _), a, got in zip(pairs, f0, fb):
+        gp.two_pass = True
+        with lbm.Lattice(gp) as lat:
+            lat.set_f(a)
+            lat.step(100)
+            ref = lat.get_f()
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-5, (gp.eos, gp.nx)
+
+
+def test_batch_graph_replay_and_launch_shapes_agree():
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f64") for m in MIX[:4]]
+    f0 = [slab_state(op, k + 21) for k, (_, op) in enumerate(pairs)]
+    outs = []
+    for shape, chunks in [((256, 1), [8]), ((128, 2), [4, 4]), ((512, 1), [2, 6])]:
+        with lbm.Batch([gp for gp, _ in pairs]) as b:
+            b.set_launch(*shape)
+            b.set_f(f0)
+            for n in chunks:
+                b.step(n)
+            outs.append(b.get_f())
+    for other in outs[1:]:
+        for a, c in zip(outs[0], other):
+            assert np.array_equal(a, c)
+
+
+def test_batch_autotuner_keeps_state_and_picks_a_valid_shape():
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f32") for m in MIX]
+    rho0 = [inputs.slab(op.nx, op.ny, *oracle.maxwell(op)[:2]) for _, op in pairs]
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        b.init_density(rho0)
+        before = b.density()
+        threads, grid = b.tune(trial_steps=20)
+        assert threads in (128, 256, 512) and grid > 0
+        assert (threads, grid) == b.launch()
+        after = b.density()
+        for x, y in zip(before, after):
+            assert np.array_equal(x, y)
+        b.step(10)
+        b.sync()
+
+
+def test_batch_barrier_timeout_is_reported_without_hanging():
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f32") for m in MIX[:3]]
+    rho0 = [inputs.slab(op.nx, op.ny, *oracle.maxwell(op)[:2]) for _, op in pairs]
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        b.init_density(rho0)
+        b.debug_skip_barrier(0, 0.2)   # block 0 never arrives: the others give up after 0.2 s
+        b.step(3)
+        with pytest.raises(lbm.LBMError) as ei:
+            b.sync()
+        assert ei.value.status == lbm.E_TIMEOUT
+        b.debug_skip_barrier(-1, 2.0)
+        b.init_density(rho0)
+        b.step(3)
+        b.sync()
+
+
+def test_batch_sweep_coexistence_close_to_maxwell():
+    # a reduced sweep (8 instances, 8000 steps, past the interface transient that
+    # the oracle shows on the same lattices): HDM coexistence vs Maxwell (Sec. 5.2)
+    table = inputs.sweep_instances(8, tr_lo=0.7, tr_hi=0.9)
+    params, rho0, ref = [], [], []
+    for d in table:
+        nx = max(256, min(d["nx"], 512))
+        gp = lbm.Params(nx=nx, ny=8, eos=d["eos"], a=d["a"], b=d["b"], omega=d["omega"], Tr=d["Tr"], k=d["k"],
+                        tau=d["tau"], force="sc", grad="hdm", prec="f32")
+        g, l = lbm.maxwell(gp)
+        params.append(gp)
+        rho0.append(inputs.slab(nx, 8, g, l))
+        ref.append((g, l))
+    with lbm.Batch(params) as b:
+        b.init_density(rho0)
+        b.step(8000)
+        rho = b.density()
+    for gp, r, (g, l) in zip(params, rho, ref):
+        prof = r.mean(0)
+        nx = gp.nx
+        liq = prof[nx // 2 - nx // 16: nx // 2 + nx // 16 + 1].mean()
+        gas = np.r_[prof[: nx // 16 + 1], prof[-nx // 16:]].mean()
+        assert abs(liq / l - 1) < 0.02, (gp.eos, gp.Tr, liq, l)
+        assert abs(gas / g - 1) < 0.10, (gp.eos, gp.Tr, gas, g)
