@@ -377,6 +377,104 @@ def run_sweep(args):
     return 0
 
 
+def run_adjoint(args):
+    """Reverse-mode cost on the droplet objective: 512 x 512, CS T/Tc = 0.75,
+    droplet R = 80 relaxed towards a target droplet R = 90 (centre offset
+    seeded), L = sum (rho_T - rho_target)^2, N steps with a checkpoint every
+    ceil(sqrt(N)) steps.  FP32 forward and adjoint, FP64 accumulation of dL/dT.
+    Reports plain-forward, taped-forward and backward times, the cost ratio,
+    dL/dTr against central differences of the FP64 path (h = 1e-4 Tr), and the
+    FP32 gradient's error against the FP64 adjoint."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_1712_06079_gb300 import inputs, lbm
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    nx = ny = 512
+    N = args.adj_steps
+    C = max(1, math.ceil(math.sqrt(N)))
+    Tr = 0.75
+
+    def params(prec, tr=Tr):
+        return lbm.Params(nx=nx, ny=ny, eos="cs", a=1.0, b=4.0, Tr=tr, k=K_HU, tau=1.0, force="sc", grad="hdm",
+                          prec=prec, stream=stream.cuda_stream)
+
+    g, l = lbm.maxwell(params("f64"))
+    xi = inputs.uniform01(inputs.DEFAULT_SEED + 5, 2)
+    rho0 = inputs.droplet(nx, ny, 80.0, g, l)
+    target = inputs.droplet(nx, ny, 90.0, g, l, cx=nx / 2 + 8 * (xi[0] - 0.5), cy=ny / 2 + 8 * (xi[1] - 0.5))
+    tgt = torch.tensor(target, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def run(prec, tr=Tr, r0=rho0, timed=False):
+        dt = torch.float64 if prec == "f64" else torch.float32
+        with torch.cuda.stream(stream), lbm.Lattice(params(prec, tr)) as lat:
+            x = torch.tensor(r0, dtype=dt, device="cuda")
+            rT = torch.empty_like(x)
+            out = {}
+            if timed:       # plain forward: N library steps
+                lat.init_density(np.asarray(r0))
+                lat.step(args.warmup)
+                lat.sync()
+                a, b = ev(), ev()
+                a.record(stream)
+                lat.step(N)
+                b.record(stream)
+                b.synchronize()
+                out["plain_ms"] = a.elapsed_time(b)
+            a, b, c = ev(), ev(), ev()
+            torch.cuda.synchronize()
+            a.record(stream)
+            lat.adjoint_forward(x.data_ptr(), N, C, rT.data_ptr())
+            b.record(stream)
+            lat.sync()
+            L = float(((rT.double() - tgt) ** 2).sum())
+            gr = (2 * (rT.double() - tgt)).to(dt).contiguous()
+            g0 = torch.empty_like(x)
+            torch.cuda.synchronize()
+            _, gtr = lat.adjoint_backward(gr.data_ptr(), g0.data_ptr())
+            c.record(stream)
+            c.synchronize()
+            out.update(L=L, dTr=gtr, drho0=g0.double().cpu().numpy(), fwd_ms=a.elapsed_time(b),
+                       bwd_ms=b.elapsed_time(c))
+            return out
+
+    r32 = run("f32", timed=True)
+    r64 = run("f64")
+    h = 1e-4 * Tr
+    Lp, Lm = run("f64", Tr + h)["L"], run("f64", Tr - h)["L"]
+    fd_tr = (Lp - Lm) / (2 * h)
+    d = inputs.uniform01(inputs.DEFAULT_SEED + 6, nx * ny).reshape(ny, nx) - 0.5
+    eps = 1e-6
+    fd_dir = (run("f64", r0=rho0 + eps * d)["L"] - run("f64", r0=rho0 - eps * d)["L"]) / (2 * eps)
+    adj_dir = float((r64["drho0"] * d).sum())
+    ratio = (r32["fwd_ms"] + r32["bwd_ms"]) / r32["plain_ms"]
+    line = {
+        "metric": "adjoint cost: (taped forward + backward) / plain forward", "unit": "x",
+        "value": ratio, "higher_is_better": False, "n_gpus": 1, "steps": N, "warmup": args.warmup,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"droplet R80 -> target R90, 512x512 periodic, CS a=1 b=4 T/Tc={Tr}, SC force, "
+                               f"HDM gradient, tau 1, L2 objective on rho_T", "checkpoint_interval": C},
+        "plain_forward_ms": r32["plain_ms"], "taped_forward_ms": r32["fwd_ms"], "backward_ms": r32["bwd_ms"],
+        "backward_over_plain": r32["bwd_ms"] / r32["plain_ms"],
+        "L_f32": r32["L"], "L_f64": r64["L"],
+        "dL_dTr": {"f32": r32["dTr"], "f64": r64["dTr"], "fd_f64": fd_tr,
+                   "rel_err_f64_vs_fd": abs(r64["dTr"] - fd_tr) / abs(fd_tr),
+                   "rel_err_f32_vs_f64": abs(r32["dTr"] - r64["dTr"]) / abs(r64["dTr"])},
+        "dL_dG": 0.0,
+        "dL_drho0": {"directional_f64": adj_dir, "fd_f64": fd_dir,
+                     "rel_err_f64_vs_fd": abs(adj_dir - fd_dir) / abs(fd_dir),
+                     "max_err_f32_vs_f64_rel_to_max": float(np.abs(r32["drho0"] - r64["drho0"]).max()
+                                                            / np.abs(r64["drho0"]).max())},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global NX, NY
     ap = argparse.ArgumentParser()
@@ -387,8 +485,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=NX, help="lattice size (default: the 4096 x 4096 workload)")
     ap.add_argument("--ny", type=int, default=NY)
-    ap.add_argument("--workload", choices=["spinodal", "sweep"], default="spinodal",
-                    help="spinodal: the throughput line; sweep: batched vs sequential 64-lattice sweep")
+    ap.add_argument("--workload", choices=["spinodal", "sweep", "adjoint"], default="spinodal",
+                    help="spinodal: the throughput line; sweep: batched vs sequential 64-lattice sweep; "
+                         "adjoint: reverse-mode cost and gradient checks on the 512 x 512 droplet")
+    ap.add_argument("--adj-steps", type=int, default=5000, help="forward steps of the adjoint workload")
     ap.add_argument("--seq-steps", type=int, default=200, help="steps timed per lattice in the sequential arm")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -398,6 +498,8 @@ def main():
         return run_reference(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -165,6 +165,24 @@ lbm_status lbm_moments_device(lbm_ctx *c, void *rho, void *vx, void *vy);
 /* FP64 lattice reductions of the current state.  Synchronising. */
 lbm_status lbm_observables(lbm_ctx *c, lbm_obs *out);
 
+/* Reverse mode through nsteps steps, for gradients of a function of the final
+ * density (e.g. the L2 distance to a target droplet) with respect to the
+ * initial density and the temperature.  Not a passage of the paper: the
+ * adjoint of its step (Eq. 1-3, 7/8, 10, 20-22).
+ * lbm_adjoint_forward: f = f^eq(rho0, 0) (Eq. 2) from the device array rho0,
+ *   nsteps steps (Eq. 1), density of the final state into the device array
+ *   rho_T; the state every checkpoint_interval steps is kept on the device
+ *   (checkpoint_interval = ceil(sqrt(nsteps)) gives sqrt(N) checkpointing, 1
+ *   keeps every state).  The context is left on the final state.
+ * lbm_adjoint_backward: from dL/drho_T (device array) writes dL/drho0 (device
+ *   array) and dL/dT, dL/d(T/Tc) (host doubles, may be NULL), recomputing the
+ *   states between checkpoints with the same kernels and running the adjoint
+ *   step backwards; dL/dT is accumulated in FP64.  Synchronising.
+ * All device arrays hold nx*ny values of the context precision.  The
+ * interaction strength G of Eq. 4/6 cancels from Eq. 22, so dL/dG = 0. */
+lbm_status lbm_adjoint_forward(lbm_ctx *c, const void *rho0, int nsteps, int checkpoint_interval, void *rho_T);
+lbm_status lbm_adjoint_backward(lbm_ctx *c, const void *grad_rho_T, void *grad_rho0, double *grad_T, double *grad_Tr);
+
 /* Enable (1) or disable (0) the event accounting of lbm_step; enabling
  * resets the counters.  Not synchronising. */
 lbm_status lbm_set_timing(lbm_ctx *c, int enable);

@@ -43,6 +43,11 @@ struct lbm_ctx {
     struct Pending { cudaEvent_t a, b; int slot; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
+    // reverse-mode tape (lbm_adjoint_forward / lbm_adjoint_backward)
+    std::vector<void *> ckpt;       // states at t = 0, C, 2C, ... (9 n values each)
+    void *tmp[2] = {nullptr, nullptr};
+    void *qpad_tape[2] = {nullptr, nullptr};
+    int tape_steps = -1, tape_C = 0;
 };
 
 namespace {
@@ -248,9 +253,181 @@ lbm_status ensure_stage(lbm_ctx *c, size_t bytes) {
     return LBM_OK;
 }
 
+void free_tape(lbm_ctx *c) {
+    for (void *p : c->ckpt) cudaFree(p);
+    c->ckpt.clear();
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->tmp[k]);
+        cudaFree(c->qpad_tape[k]);
+        c->tmp[k] = c->qpad_tape[k] = nullptr;
+    }
+    c->tape_steps = -1;
+}
+
+double dalpha_dT(const lbm_params &p, double T, double Tc) {
+    double m, s;
+    switch (p.eos) {
+    case LBM_EOS_PR:  // alpha = (1 + m (1 - sqrt(T/Tc)))^2, Eq. 28
+        m = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
+        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
+        return -s * m / std::sqrt(T * Tc);
+    case LBM_EOS_RKS:
+        m = 0.480 + 1.574 * p.omega - 0.176 * p.omega * p.omega;
+        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
+        return -s * m / std::sqrt(T * Tc);
+    case LBM_EOS_RK:  // alpha = T^-1/2, Eq. 27
+        return -0.5 / (T * std::sqrt(T));
+    default:
+        return 0.0;
+    }
+}
+
+// One forward step from state `src` to `dst` (explicit buffers); qsrc/qdst are
+// the padded potential fields of the single-pass path (qsrc valid on entry).
+template <typename T>
+cudaError_t tape_step(lbm_ctx *c, const Model<T> &m, const void *src, void *dst, int parity) {
+    if (c->fused) {
+        return launch_fused_step(*(const Model<float> *)&m, is_sc(c), (const float *)src,
+                                 (const float *)c->qpad_tape[parity], (float *)dst, (float *)c->qpad_tape[1 - parity],
+                                 c->err, c->stream);
+    }
+    cudaError_t e = launch_potential<T>(m, is_sc(c), (const T *)src, (T *)c->q, c->err, c->stream);
+    if (e != cudaSuccess) return e;
+    return launch_collide<T>(m, is_sc(c), is_cdm(c), (const T *)src, (const T *)c->q, (T *)dst, c->stream);
+}
+
+template <typename T>
+lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
+    free_tape(c);
+    const size_t fbytes = (size_t)kQ * c->n * sizeof(T);
+    const int nck = nsteps / C + 1;
+    for (int k = 0; k < nck; ++k) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, fbytes) != cudaSuccess) {
+            free_tape(c);
+            return fail(c, LBM_E_NOMEM, "not enough device memory for %d checkpoints", nck);
+        }
+        c->ckpt.push_back(p);
+    }
+    if (cudaMalloc(&c->tmp[0], fbytes) != cudaSuccess || cudaMalloc(&c->tmp[1], fbytes) != cudaSuccess) {
+        free_tape(c);
+        return fail(c, LBM_E_NOMEM, "tape scratch");
+    }
+    if (c->fused) {
+        size_t qb = sizeof(float) * (size_t)fused_q_pitch(c->p.nx) * c->p.ny;
+        if (cudaMalloc(&c->qpad_tape[0], qb) != cudaSuccess || cudaMalloc(&c->qpad_tape[1], qb) != cudaSuccess) {
+            free_tape(c);
+            return fail(c, LBM_E_NOMEM, "tape potential fields");
+        }
+    }
+    Model<T> m = model_of<T>(c);
+    CK(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");
+    CK(c, launch_init<T>(m, rho0, nullptr, nullptr, (T *)c->ckpt[0], c->stream), "init kernel");
+    if (c->fused)
+        CK(c, launch_potential_padded(*(const Model<float> *)&m, is_sc(c), (const float *)c->ckpt[0],
+                                      (float *)c->qpad_tape[0], c->err, c->stream), "potential");
+    const void *cur = c->ckpt[0];
+    for (int t = 0; t < nsteps; ++t) {
+        void *dst = ((t + 1) % C == 0) ? c->ckpt[(t + 1) / C] : c->tmp[(t + 1) & 1];
+        CK(c, tape_step<T>(c, m, cur, dst, t & 1), "tape forward step");
+        cur = dst;
+    }
+    CK(c, launch_density<T>(c->n, (const T *)cur, rhoT, c->stream), "density");
+    // leave the context on the final state too
+    CK(c, cudaMemcpyAsync(c->f[0], cur, fbytes, cudaMemcpyDeviceToDevice, c->stream), "copy final state");
+    c->cur = 0;
+    c->initialized = true;
+    c->unstable = false;
+    c->qpad_valid = false;
+    c->tape_steps = nsteps;
+    c->tape_C = C;
+    return LBM_OK;
+}
+
+template <typename T>
+lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *gT) {
+    const int N = c->tape_steps, C = c->tape_C;
+    const size_t fbytes = (size_t)kQ * c->n * sizeof(T);
+    Model<T> m = model_of<T>(c);
+    const T R = (T)c->p.R, aalp = (T)(c->p.a * dalpha_dT(c->p, c->T, c->Tc));
+    // segment states f^{kC+1} .. f^{kC+C-1}; lambda ping-pong; 6 aux fields; FP64 dL/dT
+    std::vector<void *> seg(C > 1 ? C - 1 : 0, nullptr);
+    void *lam[2] = {nullptr, nullptr}, *aux = nullptr;
+    double *Tbar = nullptr;
+    lbm_status st = LBM_OK;
+    auto release = [&]() {
+        for (void *p : seg) cudaFree(p);
+        cudaFree(lam[0]);
+        cudaFree(lam[1]);
+        cudaFree(aux);
+        cudaFree(Tbar);
+    };
+    for (auto &p : seg)
+        if (cudaMalloc(&p, fbytes) != cudaSuccess) st = LBM_E_NOMEM;
+    if (cudaMalloc(&lam[0], fbytes) != cudaSuccess || cudaMalloc(&lam[1], fbytes) != cudaSuccess ||
+        cudaMalloc(&aux, 6 * c->n * sizeof(T)) != cudaSuccess || cudaMalloc((void **)&Tbar, sizeof(double)) != cudaSuccess)
+        st = LBM_E_NOMEM;
+    if (st != LBM_OK) {
+        release();
+        return fail(c, st, "not enough device memory for the adjoint");
+    }
+    cudaError_t e = cudaMemsetAsync(Tbar, 0, sizeof(double), c->stream);
+    if (e == cudaSuccess) e = launch_adjoint_seed<T>(c->n, grad_rhoT, (T *)lam[0], c->stream);
+    int li = 0;
+    for (int k = (N - 1) / C; k >= 0 && e == cudaSuccess; --k) {
+        const int t0 = k * C, t1 = std::min(N, t0 + C);  // states t0 .. t1-1 are needed
+        // recompute f^{t0+1} .. f^{t1-1} from the checkpoint (the same forward kernels)
+        if (c->fused && t1 - t0 > 1)
+            e = launch_potential_padded(*(const Model<float> *)&m, is_sc(c), (const float *)c->ckpt[k],
+                                        (float *)c->qpad_tape[0], c->err, c->stream);
+        const void *cur = c->ckpt[k];
+        for (int t = t0; t < t1 - 1 && e == cudaSuccess; ++t) {
+            e = tape_step<T>(c, m, cur, seg[t - t0], (t - t0) & 1);
+            cur = seg[t - t0];
+        }
+        for (int t = t1 - 1; t >= t0 && e == cudaSuccess; --t) {
+            const T *ft = (const T *)(t == t0 ? c->ckpt[k] : seg[t - t0 - 1]);
+            e = launch_potential<T>(m, is_sc(c), ft, (T *)c->q, c->err, c->stream);
+            if (e == cudaSuccess)
+                e = launch_adjoint_step<T>(m, R, aalp, is_sc(c), is_cdm(c), ft, (const T *)c->q, (const T *)lam[li],
+                                           (T *)aux, (T *)lam[1 - li], Tbar, c->stream);
+            li = 1 - li;
+        }
+    }
+    if (e == cudaSuccess) e = launch_adjoint_initial<T>(c->n, (const T *)lam[li], grad_rho0, c->stream);
+    double h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, Tbar, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    release();
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint");
+    *gT = h;
+    return read_error_word(c);
+}
+
 }  // namespace
 
 extern "C" {
+
+lbm_status lbm_adjoint_forward(lbm_ctx *c, const void *rho0, int nsteps, int checkpoint_interval, void *rho_T) {
+    if (!c) return LBM_E_INVALID;
+    if (!rho0 || !rho_T) return fail(c, LBM_E_INVALID, "rho0 and rho_T must be device arrays");
+    if (nsteps < 1 || checkpoint_interval < 1) return fail(c, LBM_E_INVALID, "need nsteps >= 1, checkpoint_interval >= 1");
+    return is_f64(c) ? tape_forward<double>(c, (const double *)rho0, nsteps, checkpoint_interval, (double *)rho_T)
+                     : tape_forward<float>(c, (const float *)rho0, nsteps, checkpoint_interval, (float *)rho_T);
+}
+
+lbm_status lbm_adjoint_backward(lbm_ctx *c, const void *grad_rho_T, void *grad_rho0, double *grad_T, double *grad_Tr) {
+    if (!c) return LBM_E_INVALID;
+    if (c->tape_steps < 1) return fail(c, LBM_E_STATE, "no tape: call lbm_adjoint_forward first");
+    if (!grad_rho_T || !grad_rho0) return fail(c, LBM_E_INVALID, "grad arrays must be device arrays");
+    double gT = 0;
+    lbm_status st = is_f64(c) ? tape_backward<double>(c, (const double *)grad_rho_T, (double *)grad_rho0, &gT)
+                              : tape_backward<float>(c, (const float *)grad_rho_T, (float *)grad_rho0, &gT);
+    if (st != LBM_OK) return st;
+    if (grad_T) *grad_T = gT;
+    if (grad_Tr) *grad_Tr = gT * c->Tc;  // T = Tr Tc
+    return LBM_OK;
+}
 
 lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if (!out) return fail(nullptr, LBM_E_INVALID, "out is NULL");
@@ -503,6 +680,7 @@ void lbm_destroy(lbm_ctx *c) {
     cudaFree(c->partial);
     cudaFree(c->obs_dev);
     cudaFree(c->err);
+    free_tape(c);
     if (c->stage) cudaFreeHost(c->stage);
     for (auto &p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto ev : c->event_pool) cudaEventDestroy(ev);

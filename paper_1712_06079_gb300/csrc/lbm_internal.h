@@ -45,4 +45,20 @@ cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float 
 cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, const float *qin, float *fout,
                               float *qout, int *err, cudaStream_t s);
 
+// Adjoint (reverse-time) step (adjoint.cu): from lambda = dL/df at t+1 and the
+// state f at t (with its potential field q from launch_potential), writes
+// lambda at t into lam_out and adds dL/dT of this step to *Tbar (FP64).
+// aux holds 6 * n scratch values.  R is the gas constant, aalp = a dalpha/dT.
+template <typename T>
+cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cdm, const T *f, const T *q,
+                                const T *lam_next, T *aux, T *lam_out, double *Tbar, cudaStream_t s);
+// lambda_i = grad_rho for every i (the final density is sum_i f_i).
+template <typename T>
+cudaError_t launch_adjoint_seed(long long n, const T *grad_rho, T *lam, cudaStream_t s);
+// dL/drho0 = sum_i w_i lambda_i at t = 0 (f = f^eq(rho0, 0)).
+template <typename T>
+cudaError_t launch_adjoint_initial(long long n, const T *lam, T *grad_rho0, cudaStream_t s);
+template <typename T>
+cudaError_t launch_density(long long n, const T *f, T *rho, cudaStream_t s);
+
 }  // namespace lbm

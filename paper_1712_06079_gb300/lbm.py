@@ -74,6 +74,8 @@ SIGNATURES = {
     "lbm_get_timing": (ctypes.c_int, [_V, ctypes.POINTER(_Timing)]),
     "lbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(_Params), _V, _V]),
     "lbm_maxwell": (ctypes.c_int, [ctypes.POINTER(_Params), _D, _D]),
+    "lbm_adjoint_forward": (ctypes.c_int, [_V, _V, ctypes.c_int, ctypes.c_int, _V]),
+    "lbm_adjoint_backward": (ctypes.c_int, [_V, _V, _V, _D, _D]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.c_int, ctypes.POINTER(_V)]),
     "lbm_batch_init_density": (ctypes.c_int, [_V, _D]),
     "lbm_batch_set_f": (ctypes.c_int, [_V, _D]),
@@ -237,6 +239,15 @@ class Lattice:
         o = _Obs()
         self._check(self._lib.lbm_observables(self._h, ctypes.byref(o)))
         return {k: getattr(o, k) for k, _ in _Obs._fields_}
+
+    def adjoint_forward(self, rho0_ptr: int, nsteps: int, checkpoint_interval: int, rhoT_ptr: int):
+        self._check(self._lib.lbm_adjoint_forward(self._h, rho0_ptr, int(nsteps), int(checkpoint_interval), rhoT_ptr))
+
+    def adjoint_backward(self, grad_rhoT_ptr: int, grad_rho0_ptr: int):
+        gT, gTr = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.lbm_adjoint_backward(self._h, grad_rhoT_ptr, grad_rho0_ptr, ctypes.byref(gT),
+                                                   ctypes.byref(gTr)))
+        return gT.value, gTr.value
 
     def set_timing(self, enable: bool):
         self._check(self._lib.lbm_set_timing(self._h, 1 if enable else 0))
