@@ -183,6 +183,14 @@ lbm_status lbm_observables(lbm_ctx *c, lbm_obs *out);
 lbm_status lbm_adjoint_forward(lbm_ctx *c, const void *rho0, int nsteps, int checkpoint_interval, void *rho_T);
 lbm_status lbm_adjoint_backward(lbm_ctx *c, const void *grad_rho_T, void *grad_rho0, double *grad_T, double *grad_Tr);
 
+/* Launch shape of the single-pass FP32 step (not a passage of the paper): a
+ * CTA sweeps `rows` rows of a 120-column strip.  0 (the default) picks the
+ * height from the lattice and the device's SM count; 1..ny fixes it.  Results
+ * do not depend on it.  LBM_E_INVALID outside [0, ny].  lbm_get_segment_rows
+ * reports the height in use, 0 when the context runs the two-pass step. */
+lbm_status lbm_set_segment_rows(lbm_ctx *c, int rows);
+lbm_status lbm_get_segment_rows(lbm_ctx *c, int *rows);
+
 /* Enable (1) or disable (0) the event accounting of lbm_step; enabling
  * resets the counters.  Not synchronising. */
 lbm_status lbm_set_timing(lbm_ctx *c, int enable);

@@ -8,7 +8,9 @@
 // cell's own density, and U (Eq. 8) for the Zhang-Chen form.
 //
 // Decomposition.  A CTA of 8 warps owns a strip of TXI = 120 columns and a
-// segment of up to SEG_H = 128 rows.  It sweeps the segment in slabs of 8
+// segment of up to seg_h rows (a launch parameter; 126 on large lattices,
+// fewer on small ones so that the grid fills the GPU).  It sweeps the segment
+// in slabs of 8
 // rows, one warp per row and one lane per 4 consecutive cells.  Lanes 1..30
 // hold the strip's columns; lanes 0 and 31 hold the 4-column groups just
 // outside it, whose collision is recomputed so that the density at t+1 of
@@ -60,7 +62,6 @@ constexpr int QCH = 10;             // chunks in the d/dy ring
 constexpr int QRING = QCH * SLAB;   // rows in the d/dy ring
 constexpr int QBASE = 33;           // ring chunk 0 starts at row ys - QBASE
 constexpr int PROWS = 18;           // partial-density ring rows
-constexpr int SEG_H = 128;          // rows per CTA segment
 constexpr int NTHR = 32 * SLAB;
 constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s per wait
 
@@ -81,6 +82,7 @@ struct FusedArgs {
     float *qout;        // padded field of f(t+1)
     int *err;
     int qpitch;         // nx + 2 * QG
+    int seg_h;          // rows per CTA segment
     float2 wy2[FK + 1]; // (w_j, w_j) pairs of the d/dy weights for packed FP32x2 FMAs
 };
 
@@ -144,8 +146,8 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x0 = blockIdx.x * TXI;
     const int nint = min(TXI, nx - x0);             // interior columns (multiple of 4)
-    const int ys = blockIdx.y * SEG_H;
-    const int hseg = min(SEG_H, ny - ys);
+    const int ys = blockIdx.y * A.seg_h;
+    const int hseg = min(A.seg_h, ny - ys);
     const int nslab = hseg > 6 ? (hseg - 6 + SLAB - 1) / SLAB + 1 : 1;
     const int nchunks = nslab + 8;
     const int ncols = nint + 8;                     // lane columns actually staged (d/dy ring)
@@ -430,6 +432,19 @@ bool fused_step_supported(const Model<float> &m, bool cdm, int radius) {
 
 int fused_q_pitch(int nx) { return nx + 2 * QG; }
 
+// A segment of h rows collides 8 ceil((h + 2) / 8) rows (its own, the one above
+// and the one below, in whole slabs) and stages h + 66 potential rows for
+// d/dy, so h = 8k - 2 wastes no collided rows.  The tallest such segment that
+// still gives every SM a CTA keeps the halo overhead lowest (measured on 512^2
+// to 4096^2 lattices: 14, 62, 126, 126 rows); smaller grids leave SMs idle.
+int fused_auto_seg_rows(int nx, int ny, int num_sms) {
+    const long long strips = (nx + TXI - 1) / TXI;
+    const int cand[] = {126, 62, 30, 14, 6};
+    for (int h : cand)
+        if (strips * ((ny + h - 1) / h) >= num_sms) return h;
+    return 6;
+}
+
 cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float *f, float *qpad, int *err,
                                     cudaStream_t s) {
     const int pitch = fused_q_pitch(m.nx);
@@ -440,7 +455,7 @@ cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float 
 }
 
 cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, const float *qin, float *fout,
-                              float *qout, int *err, cudaStream_t s) {
+                              float *qout, int *err, int seg_rows, cudaStream_t s) {
     FusedArgs a;
     a.m = m;
     a.f = f;
@@ -449,7 +464,10 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     a.qout = qout;
     a.err = err;
     a.qpitch = fused_q_pitch(m.nx);
-    dim3 grid((m.nx + TXI - 1) / TXI, (m.ny + SEG_H - 1) / SEG_H);
+    a.seg_h = seg_rows;
+    if (seg_rows < 1) return cudaErrorInvalidValue;
+    dim3 grid((m.nx + TXI - 1) / TXI, (m.ny + seg_rows - 1) / seg_rows);
+    if (grid.y > 65535) return cudaErrorInvalidValue;
     for (int j = 0; j <= FK; ++j) a.wy2[j] = make_float2(m.wy[j], m.wy[j]);
     const bool tau1 = m.omega == 1.0f;
     void (*kern)(const FusedArgs) = nullptr;

@@ -26,6 +26,8 @@ struct lbm_ctx {
     bool fused = false;           // FP32 single-pass step in use
     void *qpad[2] = {nullptr, nullptr};  // padded potential of f[0] / f[1] (fused path)
     bool qpad_valid = false;      // qpad[cur] holds the potential of f[cur]
+    int seg_rows = 0;             // rows per CTA segment of the fused path (0: automatic)
+    int num_sms = 0;              // SMs of the context's device
     void *mom = nullptr;          // rho, vx, vy scratch (3 n values), lazily allocated
     double *partial = nullptr;    // reduction partials
     lbm_obs *obs_dev = nullptr;
@@ -178,6 +180,10 @@ cudaError_t step_once(lbm_ctx *c, const Model<T> &m) {
     return cudaSuccess;
 }
 
+int seg_rows_of(const lbm_ctx *c) {
+    return c->seg_rows > 0 ? c->seg_rows : fused_auto_seg_rows(c->p.nx, c->p.ny, c->num_sms);
+}
+
 // One time step by the single-pass FP32 kernel.
 cudaError_t step_fused(lbm_ctx *c, const Model<float> &m) {
     const float *f = (const float *)c->f[c->cur];
@@ -191,7 +197,7 @@ cudaError_t step_fused(lbm_ctx *c, const Model<float> &m) {
     }
     e = timed_launch(c, 2, [&] {
         return launch_fused_step(m, is_sc(c), f, (const float *)c->qpad[c->cur], (float *)c->f[1 - c->cur],
-                                 (float *)c->qpad[1 - c->cur], c->err, c->stream);
+                                 (float *)c->qpad[1 - c->cur], c->err, seg_rows_of(c), c->stream);
     });
     if (e != cudaSuccess) return e;
     if (c->timing) c->tm.steps += 1;
@@ -289,7 +295,7 @@ cudaError_t tape_step(lbm_ctx *c, const Model<T> &m, const void *src, void *dst,
     if (c->fused) {
         return launch_fused_step(*(const Model<float> *)&m, is_sc(c), (const float *)src,
                                  (const float *)c->qpad_tape[parity], (float *)dst, (float *)c->qpad_tape[1 - parity],
-                                 c->err, c->stream);
+                                 c->err, seg_rows_of(c), c->stream);
     }
     cudaError_t e = launch_potential<T>(m, is_sc(c), (const T *)src, (T *)c->q, c->err, c->stream);
     if (e != cudaSuccess) return e;
@@ -475,6 +481,10 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
         return st;
     };
     cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return bail(e, "cudaDeviceGetAttribute");
     size_t fbytes = (size_t)kQ * c->n * c->esz;
     if ((e = cudaMalloc(&c->f[0], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f0)");
     if ((e = cudaMalloc(&c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
@@ -492,6 +502,19 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if ((e = cudaMalloc(&c->err, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc(err)");
     if ((e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)) != cudaSuccess) return bail(e, "cudaMemset(err)");
     *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_segment_rows(lbm_ctx *c, int rows) {
+    if (!c) return LBM_E_INVALID;
+    if (rows < 0 || rows > c->p.ny) return fail(c, LBM_E_INVALID, "segment rows must be in [0, ny = %d]", c->p.ny);
+    c->seg_rows = rows;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_segment_rows(lbm_ctx *c, int *rows) {
+    if (!c || !rows) return LBM_E_INVALID;
+    *rows = c->fused ? seg_rows_of(c) : 0;
     return LBM_OK;
 }
 

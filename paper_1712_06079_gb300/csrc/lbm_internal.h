@@ -36,14 +36,17 @@ cudaError_t launch_observables(long long n, const T *rho, const T *vx, const T *
 
 // Single-pass FP32 step (fused_step.cu): reads f(t) and the padded potential
 // q(t), writes f(t+1) and the padded potential of f(t+1).  The padded
-// potential has fused_q_pitch(nx) floats per row, column x stored at x + 24,
-// with periodic images in the 24 ghost columns on each side.
+// potential has fused_q_pitch(nx) floats per row, column x stored at x + 32,
+// with periodic images in the 32 ghost columns on each side.  A CTA sweeps a
+// segment of seg_rows rows of a 120-column strip; fused_auto_seg_rows picks
+// the segment height for a lattice on a GPU with num_sms SMs.
 bool fused_step_supported(const Model<float> &m, bool cdm, int radius);
 int fused_q_pitch(int nx);
+int fused_auto_seg_rows(int nx, int ny, int num_sms);
 cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float *f, float *qpad, int *err,
                                     cudaStream_t s);
 cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, const float *qin, float *fout,
-                              float *qout, int *err, cudaStream_t s);
+                              float *qout, int *err, int seg_rows, cudaStream_t s);
 
 // Adjoint (reverse-time) step (adjoint.cu): from lambda = dL/df at t+1 and the
 // state f at t (with its potential field q from launch_potential), writes

@@ -75,6 +75,8 @@ SIGNATURES = {
     "lbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(_Params), _V, _V]),
     "lbm_maxwell": (ctypes.c_int, [ctypes.POINTER(_Params), _D, _D]),
     "lbm_adjoint_forward": (ctypes.c_int, [_V, _V, ctypes.c_int, ctypes.c_int, _V]),
+    "lbm_set_segment_rows": (ctypes.c_int, [_V, ctypes.c_int]),
+    "lbm_get_segment_rows": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int)]),
     "lbm_adjoint_backward": (ctypes.c_int, [_V, _V, _V, _D, _D]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.c_int, ctypes.POINTER(_V)]),
     "lbm_batch_init_density": (ctypes.c_int, [_V, _D]),
@@ -239,6 +241,15 @@ class Lattice:
         o = _Obs()
         self._check(self._lib.lbm_observables(self._h, ctypes.byref(o)))
         return {k: getattr(o, k) for k, _ in _Obs._fields_}
+
+    def set_segment_rows(self, rows: int):
+        """Rows per CTA segment of the single-pass FP32 step (0: automatic)."""
+        self._check(self._lib.lbm_set_segment_rows(self._h, int(rows)))
+
+    def segment_rows(self) -> int:
+        r = ctypes.c_int()
+        self._check(self._lib.lbm_get_segment_rows(self._h, ctypes.byref(r)))
+        return r.value
 
     def adjoint_forward(self, rho0_ptr: int, nsteps: int, checkpoint_interval: int, rhoT_ptr: int):
         self._check(self._lib.lbm_adjoint_forward(self._h, rho0_ptr, int(nsteps), int(checkpoint_interval), rhoT_ptr))

@@ -234,3 +234,31 @@ def test_f32_single_pass_kernel_parity(nx, ny, eos, Tr, force):
     fb, kinds_b = run_f32(gp, f0, 20, two_pass=True)
     assert "collide" in kinds_b and "fused_step" not in kinds_b
     assert np.max(np.abs(fa - fb) / np.abs(fb)) < 1e-5
+
+
+def test_f32_single_pass_segment_height_does_not_change_results():
+    # the CTA segment height is a launch shape only: every cell computes the
+    # same arithmetic whichever CTA owns it, so the states are bit-identical
+    nx, ny = 252, 200
+    gp, op = make(nx, ny, "cs", 0.8, "sc", "hdm", prec="f32")
+    g, l, _ = oracle.maxwell(op)
+    f0 = perturbed_state(op, inputs.droplet(nx, ny, 50, g, l), seed=3)
+    outs = {}
+    for rows in (0, 1, 6, 7, 9, 14, 62, 126, 128, 200):
+        with lbm.Lattice(gp) as lat:
+            lat.set_segment_rows(rows)
+            used = lat.segment_rows()
+            assert used == rows or (rows == 0 and used > 0)
+            lat.set_f(f0)
+            lat.step(12)
+            outs[rows] = lat.get_f()
+    for rows, fr in outs.items():
+        assert np.array_equal(fr, outs[0]), rows
+    with lbm.Lattice(gp) as lat:
+        for bad in (-1, ny + 1):
+            with pytest.raises(lbm.LBMError) as ei:
+                lat.set_segment_rows(bad)
+            assert ei.value.status == lbm.E_INVALID
+    gp.two_pass = True
+    with lbm.Lattice(gp) as lat:
+        assert lat.segment_rows() == 0
