@@ -17,144 +17,358 @@
 //   u_bar += v_bar, F_bar = v_bar / rho, rho_bar -= v_bar.F / rho^2
 //   j_bar = u_bar / rho, rho_bar -= u_bar.u / rho
 //   SC: D_bar = -2 s Phi F_bar, Phi_bar_centre = -2 s (F_bar.D);  ZC: D_bar = -F_bar
-// (pass 1), then, because the periodic derivative is an antisymmetric
-// circulant (its transpose is its negative),
+// and, because the periodic derivative is an antisymmetric circulant (its
+// transpose is its negative),
 //   Phi_bar = Phi_bar_centre - Dx[Dx_bar] - Dy[Dy_bar]
-//   U_bar = Phi_bar sign(U) / (2 Phi) (SC) or Phi_bar (ZC)
+//   U_bar = Phi_bar s / (2 Phi) (SC) or Phi_bar (ZC)
 //   rho_bar += U_bar (k dp/drho - 1/3),  T_bar += U_bar k dp/dT
-//   lambda_i(t) = (1 - omega) g_i + rho_bar + e_i . j_bar
-// (pass 2).  T_bar is accumulated in FP64 (block reduction, one atomic per block).
+//   lambda_i(t) = (1 - omega) g_i + rho_bar + e_i . j_bar.
+//
+// Two tiled kernels per step.  Kernel A stages the stencil field of the
+// tile with its halo in shared memory (asynchronous copies) and does
+// everything up to D_bar, with the centre term already folded into rho_bar
+// and T_bar; it writes D_bar, the partial rho_bar and rho.  Kernel B stages
+// D_bar with its halo and finishes rho_bar, T_bar and lambda(t).  For tau = 1
+// (omega = 1) every lambda_i(t) is rho_bar + e_i . j_bar, so lambda is kept as
+// the three fields (rho_bar, jx_bar, jy_bar) instead of nine, staged in
+// shared memory with a one-cell halo for the pull g_i = lambda_i(x + e_i).
+// The HDM stencils run at a compile-time radius (26 in FP32, 40 in FP64)
+// over weights that are zero past the folded radius of the lattice.  T_bar
+// terms are summed over each warp in the working precision (32 terms), then
+// in FP64 over the warps of a CTA into one slot per CTA (no atomics, so the
+// sum is reproducible), over the steps in the same slots, and over the slots
+// in a fixed order at the end.
 #include <cuda_runtime.h>
 
 #include "lbm_internal.h"
+#include "ptx.cuh"
 
 namespace lbm {
 namespace {
 
-// dp_EOS/drho and dp_EOS/dT at the model temperature (Eq. 24, 27-29);
-// m.RT = R T, m.aal = a alpha(T), aalp = a dalpha/dT, R the gas constant.
 template <typename T>
-__device__ __forceinline__ void p_derivs(const Model<T> &m, T R, T aalp, T rho, T &dpdr, T &dpdT) {
+struct AdjTile;
+template <>
+struct AdjTile<float> {   // one cell per thread, 1024 threads
+    static constexpr int TX = 64, TY = 16, TYT = 16;
+};
+template <>
+struct AdjTile<double> {  // two cells per thread (register budget)
+    static constexpr int TX = 32, TY = 16, TYT = 8;
+};
+
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rsqrt_fast(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_fast(double x) { return 1.0 / sqrt(x); }
+
+// U = k p_EOS - rho/3 (Eq. 8) with dp_EOS/drho and dp_EOS/dT at the model
+// temperature (Eq. 24, 27-29); m.RT = R T, m.aal = a alpha(T), aalp =
+// a dalpha/dT, R the gas constant.  Reciprocals by the fast FP32 form (the
+// denominators are positive and well scaled).
+template <typename T>
+__device__ __forceinline__ void eos_derivs(const Model<T> &m, T R, T aalp, T rho, T &U, T &dpdr, T &dpdT) {
+    T p;
     if (m.eos == LBM_EOS_CS) {
         const T e = m.b * rho * T(0.25);
         const T om = T(1) - e;
+        const T inv = rcp_fast(om);
+        const T inv3 = inv * inv * inv;
         const T num = T(1) + e + e * e - e * e * e;
-        const T Z = num / (om * om * om);
-        const T dZ = ((T(1) + T(2) * e - T(3) * e * e) * om + T(3) * num) / (om * om * om * om);
+        const T Z = num * inv3;
+        const T dZ = ((T(1) + T(2) * e - T(3) * e * e) * om + T(3) * num) * inv3 * inv;
+        p = rho * m.RT * Z - m.a * rho * rho;
         dpdr = m.RT * (Z + e * dZ) - T(2) * m.a * rho;
         dpdT = R * rho * Z;
-        return;
+    } else {
+        const T inv = rcp_fast(T(1) - m.b * rho);
+        const T rep = rho * m.RT * inv;
+        const T drep_dr = m.RT * inv * inv, drep_dT = R * rho * inv;
+        if (m.eos == LBM_EOS_VDW) {
+            p = rep - m.a * rho * rho;
+            dpdr = drep_dr - T(2) * m.a * rho;
+            dpdT = drep_dT;
+        } else if (m.eos == LBM_EOS_PR) {
+            const T id = rcp_fast(T(1) + T(2) * m.b * rho - m.b * m.b * rho * rho);
+            p = rep - m.aal * rho * rho * id;
+            dpdr = drep_dr - m.aal * T(2) * rho * (T(1) + m.b * rho) * id * id;
+            dpdT = drep_dT - aalp * rho * rho * id;
+        } else {  // RK, RKS
+            const T id = rcp_fast(T(1) + m.b * rho);
+            p = rep - m.aal * rho * rho * id;
+            dpdr = drep_dr - m.aal * rho * (T(2) + m.b * rho) * id * id;
+            dpdT = drep_dT - aalp * rho * rho * id;
+        }
     }
-    const T om = T(1) - m.b * rho;
-    const T drep_dr = m.RT / (om * om), drep_dT = R * rho / om;
-    if (m.eos == LBM_EOS_VDW) {
-        dpdr = drep_dr - T(2) * m.a * rho;
-        dpdT = drep_dT;
-    } else if (m.eos == LBM_EOS_PR) {
-        const T den = T(1) + T(2) * m.b * rho - m.b * m.b * rho * rho;
-        dpdr = drep_dr - m.aal * T(2) * rho * (T(1) + m.b * rho) / (den * den);
-        dpdT = drep_dT - aalp * rho * rho / den;
-    } else {  // RK, RKS
-        const T den = T(1) + m.b * rho;
-        dpdr = drep_dr - m.aal * rho * (T(2) + m.b * rho) / (den * den);
-        dpdT = drep_dT - aalp * rho * rho / den;
+    U = m.k * p - rho * T(1.0 / 3.0);
+}
+
+// kappa = dPhi/dU (k dp/drho - 1/3) and theta = dPhi/dU k dp/dT at density
+// rho, with dPhi/dU = s / (2 Phi) for the Shan-Chen field and 1 for
+// Zhang-Chen; sgn = s.
+template <typename T, bool SC>
+__device__ __forceinline__ void eos_coeffs(const Model<T> &m, T R, T aalp, T rho, T &kappa, T &theta, T &sgn) {
+    T U, dpdr, dpdT;
+    eos_derivs(m, R, aalp, rho, U, dpdr, dpdT);
+    T d = T(1);
+    sgn = U >= T(0) ? T(1) : T(-1);
+    if (SC) {
+        const T aU = fabs(U);
+        d = aU > T(0) ? T(0.5) * sgn * rsqrt_fast(aU) : T(0);
     }
+    kappa = d * (m.k * dpdr - T(1.0 / 3.0));
+    theta = d * m.k * dpdT;
 }
 
 template <typename T>
 struct AdjArgs {
     Model<T> m;
-    T R;          // gas constant
-    T aalp;       // a dalpha/dT
-    const T *f;   // state at t
-    const T *q;   // potential field of f: s Phi (SC) or U (ZC)
-    const T *lam; // adjoint at t+1
-    T *aux;       // 6 fields: rho_bar, jx_bar, jy_bar, Dx_bar, Dy_bar, Phi_bar_centre
-    T *lam_out;   // adjoint at t
-    double *Tbar; // FP64 accumulator of dL/dT
+    T R;            // gas constant
+    T aalp;         // a dalpha/dT
+    const T *f;     // state at t (nine unpadded fields)
+    // Every other field is addressed as base[k * stride + y * pitch + off + x].
+    const T *q;     // stencil field of f; |q| = Phi (SC) or U (ZC)
+    int qpitch, qoff;
+    const T *lam;   // adjoint at t+1 (nine fields, or three for tau = 1)
+    T *lam_out;     // adjoint at t
+    long long lstride;
+    int lpitch, loff;
+    T *aux;         // D_bar_x, D_bar_y, partial rho_bar, rho[, j_bar_x, j_bar_y]
+    long long dstride;
+    int dpitch, doff;
+    double *Tpart;  // one FP64 slot per CTA of A, then per CTA of B
+    int *err;       // error word (a bounded wait that gave up)
 };
 
-template <typename T, bool SC>
-__device__ __forceinline__ T st(T v) {
-    return SC ? fabs(v) : v;
+// Sum of v over the CTA (over each warp in T, then in FP64), added to *slot.
+template <typename T>
+__device__ __forceinline__ void block_sum_into(T v, double *slot) {
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nwarps = (blockDim.x * blockDim.y + 31) / 32;
+    if ((tid & 31) == 0) red[tid >> 5] = (double)v;
+    __syncthreads();
+    if (tid < 32) {
+        double s = tid < nwarps ? red[tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (tid == 0) *slot += s;
+    }
 }
 
-// Periodic derivative of a field at (x, y) of an nx x ny lattice.
-template <typename T, bool SC, bool CDM>
-__device__ __forceinline__ void deriv(const Model<T> &m, const T *__restrict__ q, int x, int y, T &dx, T &dy) {
-    const int nx = m.nx, ny = m.ny;
-    if (CDM) {
-        const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
-        const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
-        auto at = [&](int yy, int xx) { return st<T, SC>(q[(long long)yy * nx + xx]); };
-        const T e = at(y, xp), w = at(y, xm), nn = at(yp, x), s = at(ym, x);
-        const T ne = at(yp, xp), nw = at(yp, xm), se = at(ym, xp), sw = at(ym, xm);
-        dx = T(1.0 / 3.0) * (e - w) + T(1.0 / 12.0) * ((ne + se) - (nw + sw));
-        dy = T(1.0 / 3.0) * (nn - s) + T(1.0 / 12.0) * ((ne + nw) - (se + sw));
-        return;
+// Copies the rectangle [lx0, lx1) x [ly0, ly1) of a shared array of pitch P
+// from the periodic field src (row pitch spitch, column offset soff), whose
+// element (gx0 + lx, gy0 + ly) lands at dst[ly * P + lx].  Asynchronous,
+// element by element (cp.async).
+template <typename T, int TX, int TYT>
+__device__ __forceinline__ void stage_rect(T *dst, int P, const T *src, int spitch, int soff, int nx, int ny, int gx0,
+                                           int gy0, int lx0, int lx1, int ly0, int ly1) {
+    for (int lx = lx0 + (int)threadIdx.x; lx < lx1; lx += TX) {
+        const int gx = wrap_index(gx0 + lx, nx) + soff;
+        for (int ly = ly0 + (int)threadIdx.y; ly < ly1; ly += TYT) {
+            const int gy = wrap_index(gy0 + ly, ny);
+            ptx::cp_async<sizeof(T)>(dst + ly * P + lx, src + (long long)gy * spitch + gx);
+        }
     }
-    const T *row = q + (long long)y * nx;
-    T ax = T(0), ay = T(0);
-    for (int j = 1; j <= m.kx; ++j) {
-        int xp = x + j, xm = x - j;
-        if (xp >= nx) xp -= nx;
-        if (xm < 0) xm += nx;
-        ax += m.wx[j] * (st<T, SC>(row[xp]) - st<T, SC>(row[xm]));
-    }
-    for (int j = 1; j <= m.ky; ++j) {
-        int yp = y + j, ym = y - j;
-        if (yp >= ny) yp -= ny;
-        if (ym < 0) ym += ny;
-        ay += m.wy[j] * (st<T, SC>(q[(long long)yp * nx + x]) - st<T, SC>(q[(long long)ym * nx + x]));
-    }
-    dx = ax;
-    dy = ay;
 }
 
-template <typename T, bool SC, bool CDM>
-__global__ void adj_local_kernel(const AdjArgs<T> a) {
+// Antisymmetric stencil sum_j w_j (v[j s] - v[-j s]) with the x (YAX false)
+// or y weights of the model, at compile-time radius KC (weights zero past the
+// folded radius) or at the runtime radius (KC = 0).
+template <typename T, int KC, bool ABS, bool YAX>
+__device__ __forceinline__ T stencil(const T *v, int s, const Model<T> &m) {
+    auto val = [&](int o) { return ABS ? fabs(v[o]) : v[o]; };
+    T acc = T(0);
+    if (KC > 0) {
+#pragma unroll
+        for (int j = 1; j <= KC; ++j) acc += (YAX ? m.wy[j] : m.wx[j]) * (val(j * s) - val(-j * s));
+    } else {
+        const int k = YAX ? m.ky : m.kx;
+        for (int j = 1; j <= k; ++j) acc += (YAX ? m.wy[j] : m.wx[j]) * (val(j * s) - val(-j * s));
+    }
+    return acc;
+}
+
+// Store of a padded field value at column x of row `row`, with its periodic
+// image in the ghost columns (PAD) when x lies within kGhost of an edge.
+constexpr int kGhost = 32;
+__device__ __forceinline__ int yp_of(int y, int ny) { return y + 1 == ny ? 0 : y + 1; }
+__device__ __forceinline__ int ym_of(int y, int ny) { return y == 0 ? ny - 1 : y - 1; }
+template <typename T, bool PAD>
+__device__ __forceinline__ void store_field(T *row, int x, int nx, T v) {
+    row[x] = v;
+    if (PAD) {
+        if (x < kGhost) row[x + nx] = v;
+        if (x >= nx - kGhost) row[x - nx] = v;
+    }
+}
+
+// Padded staging geometry (FP32 single-pass layout, HDM radius KC <= 28):
+// a staged row keeps the tile's column 0 at XO, so a row with the x halo is
+// one 16-byte-aligned copy of TX + 2 XO values starting at tile column -XO.
+constexpr int XO = 28;   // x halo columns staged (>= radius, XO * 4 bytes a multiple of 16)
+constexpr int LO = 4;    // lambda halo columns staged (>= 1)
+
+// Bounded wait of the whole CTA for the bulk copies on bars[k]; on timeout
+// flags the error word, lets the copies in flight on all nbar barriers land
+// and returns false.
+__device__ __forceinline__ bool cta_wait_copies(uint64_t *bars, int nbar, int k, int *err) {
+    constexpr uint64_t kLimitNs = 200ull * 1000 * 1000;
+    const bool ok = ptx::mbar_wait_bounded(&bars[k], 0, kLimitNs);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            atomicOr(err, kErrTimeout);
+            for (int b = 0; b < nbar; ++b) (void)ptx::mbar_wait_bounded(&bars[b], 0, kLimitNs);
+        }
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+template <typename T, bool SC, bool CDM, bool TAU1, int KC, bool PAD>
+__global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(const AdjArgs<T> a) {
+    constexpr int TX = AdjTile<T>::TX, TY = AdjTile<T>::TY, TYT = AdjTile<T>::TYT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const Model<T> &m = a.m;
-    const long long n = (long long)m.nx * m.ny;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(c / m.nx), x = (int)(c - (long long)y * m.nx);
-        T fi[kQ], g[kQ];
+    const int nx = m.nx, ny = m.ny;
+    const long long n = (long long)nx * ny;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int hx = CDM ? 1 : (KC ? KC : m.kx), hy = CDM ? 1 : (KC ? KC : m.ky);
+    // staged field: S[ly * W + XS + lx] = q(x0 + lx, y0 - hy + ly); lambda tile
+    // L[(k * LH + ly) * LW + LS + lx] = lambda_k(x0 + lx, y0 - 1 + ly)
+    const int W = PAD ? TX + 2 * XO : TX + 2 * hx, H = TY + 2 * hy;
+    const int XS = PAD ? XO : hx;
+    constexpr int LW = PAD ? TX + 2 * LO : TX + 2, LH = TY + 2, LS = PAD ? LO : 1;
+    T *S = reinterpret_cast<T *>(smem_raw);
+    T *L = S + W * H;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(L + (TAU1 ? 3 * LW * LH : 0));  // PAD: field, lambda
+    if constexpr (PAD) {
+        const int tid = threadIdx.x + TX * threadIdx.y;
+        if (tid == 0) {
+            ptx::mbar_init(&bars[0], 1);
+            ptx::mbar_init(&bars[1], 1);
+            ptx::fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid < 32) {  // warp 0 issues one bulk copy per staged row
+            const int ncore = min(TX, nx - x0);                 // a multiple of 4
+            const uint32_t wide = (ncore + 2 * XO) * sizeof(T), core = ncore * sizeof(T);
+            const uint32_t lrow = (ncore + 2 * LO) * sizeof(T);
+            if (tid == 0) {
+                ptx::mbar_arrive_expect_tx(&bars[0], TY * wide + 2 * hy * core);
+                ptx::mbar_arrive_expect_tx(&bars[1], TAU1 ? 3 * LH * lrow : 0);
+            }
+            __syncwarp();
+            for (int ly = tid; ly < H; ly += 32) {
+                const T *src = a.q + (long long)wrap_index(y0 - hy + ly, ny) * a.qpitch + a.qoff + x0;
+                if (ly >= hy && ly < hy + TY) ptx::bulk_g2s(S + ly * W, src - XO, wide, &bars[0]);
+                else ptx::bulk_g2s(S + ly * W + XO, src, core, &bars[0]);
+            }
+            if (TAU1)
+                for (int r = tid; r < 3 * LH; r += 32) {
+                    const int k = r / LH, ly = r - k * LH;
+                    const T *src = a.lam + k * a.lstride + (long long)wrap_index(y0 - 1 + ly, ny) * a.lpitch + a.loff + x0;
+                    ptx::bulk_g2s(L + r * LW, src - LO, lrow, &bars[1]);
+                }
+        }
+    } else {
+        // element-wise: a cross for the separable HDM, the full box for the CDM
+        if (CDM) {
+            stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, 0, W, 0, H);
+        } else {
+            stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, 0, W, hy, hy + TY);
+            stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, hx, hx + TX, 0, hy);
+            stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, hx, hx + TX, hy + TY, H);
+        }
+        if (TAU1)
+            for (int k = 0; k < 3; ++k)
+                stage_rect<T, TX, TYT>(L + k * LW * LH, LW, a.lam + k * a.lstride, a.lpitch, a.loff, nx, ny, x0 - 1,
+                                       y0 - 1, 0, LW, 0, LH);
+        ptx::cp_async_wait_all();
+        __syncthreads();
+    }
+
+    // Every thread runs the cell loop (the waits are CTA-wide); cells outside
+    // the lattice compute on a clamped index and store nothing.  With the bulk
+    // copies in flight, the cell's own loads and the EOS terms come first.
+    T tacc = T(0);
+    const int lx = threadIdx.x, x = x0 + lx;
+    const int xc = min(x, nx - 1);
+    const int xp = xc + 1 == nx ? 0 : xc + 1, xm = xc == 0 ? nx - 1 : xc - 1;
+#pragma unroll
+    for (int k = 0; k < TY / TYT; ++k) {
+        const int ly = threadIdx.y + k * TYT, y = y0 + ly;
+        const bool valid = x < nx && y < ny;
+        const int yc = min(y, ny - 1);
+        const long long c = (long long)yc * nx + xc;
+        const int yp = yc + 1 == ny ? 0 : yc + 1, ym = yc == 0 ? ny - 1 : yc - 1;
         T r = T(0), jx = T(0), jy = T(0);
-        const int xp = x + 1 == m.nx ? 0 : x + 1, xm = x == 0 ? m.nx - 1 : x - 1;
-        const int yp = y + 1 == m.ny ? 0 : y + 1, ym = y == 0 ? m.ny - 1 : y - 1;
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
-            fi[i] = a.f[i * n + c];
-            r += fi[i];
-            jx += T(ex(i)) * fi[i];
-            jy += T(ey(i)) * fi[i];
-            const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
-            const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
-            g[i] = a.lam[i * n + (long long)dys * m.nx + dxs];  // lambda_i(x + e_i)
+            const T fi = a.f[i * n + c];
+            r += fi;
+            jx += T(ex(i)) * fi;
+            jy += T(ey(i)) * fi;
         }
-        T Dx, Dy;
-        deriv<T, SC, CDM>(m, a.q, x, y, Dx, Dy);
-        const T qc = a.q[c];
-        T Fx, Fy;
-        if (SC) { Fx = T(-2) * qc * Dx; Fy = T(-2) * qc * Dy; }
-        else { Fx = -Dx; Fy = -Dy; }
+        T kappa, theta, sgn;
+        eos_coeffs<T, SC>(m, a.R, a.aalp, r, kappa, theta, sgn);
         const T inv = T(1) / r;
-        const T ux = jx * inv, uy = jy * inv, vx = ux + Fx * inv, vy = uy + Fy * inv;
+        const T ux = jx * inv, uy = jy * inv;
+        if (PAD && k == 0 && !cta_wait_copies(bars, 2, 0, a.err)) return;
+        // D of the field at the cell (Eq. 15 / 20) from the staged tile
+        const T *row = S + (ly + hy) * W + (XS + lx);
+        auto fld = [&](int o) { return SC ? fabs(row[o]) : row[o]; };
+        T Dx, Dy;
+        if (CDM) {
+            const T e = fld(1), w = fld(-1), nn = fld(W), s = fld(-W);
+            const T ne = fld(W + 1), nw = fld(W - 1), se = fld(-W + 1), sw = fld(-W - 1);
+            Dx = T(1.0 / 3.0) * (e - w) + T(1.0 / 12.0) * ((ne + se) - (nw + sw));
+            Dy = T(1.0 / 3.0) * (nn - s) + T(1.0 / 12.0) * ((ne + nw) - (se + sw));
+        } else {
+            Dx = stencil<T, KC, SC, false>(row, 1, m);
+            Dy = stencil<T, KC, SC, true>(row, W, m);
+        }
+        const T phi = fld(0);  // Phi (SC) or U (ZC)
+        T Fx, Fy;
+        if (SC) { Fx = T(-2) * sgn * phi * Dx; Fy = T(-2) * sgn * phi * Dy; }
+        else { Fx = -Dx; Fy = -Dy; }
+        const T vx = ux + Fx * inv, vy = uy + Fy * inv;
         const T uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
+        if (PAD && TAU1 && k == 0 && !cta_wait_copies(bars, 2, 1, a.err)) return;
+        T g[kQ];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {  // g_i = lambda_i(x + e_i)
+            if (TAU1) {
+                const int o = (ly + 1 + ey(i)) * LW + (LS + lx + ex(i));
+                g[i] = L[o] + T(ex(i)) * L[LW * LH + o] + T(ey(i)) * L[2 * LW * LH + o];
+            } else {
+                const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : xc);
+                const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : yc);
+                g[i] = __ldg(a.lam + i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs);
+            }
+        }
         const T om1 = T(1) - m.omega;
         T rb = T(0), ubx = T(0), uby = T(0), vbx = T(0), vby = T(0);
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
             const T exi = T(ex(i)), eyi = T(ey(i)), w = wq<T>(i);
-            const T eu = exi * ux + eyi * uy, ev = exi * vx + eyi * vy;
-            const T feq_u = r * w * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
+            const T ev = exi * vx + eyi * vy;
             const T feq_v = r * w * (T(1) + T(3) * ev + T(4.5) * ev * ev - T(1.5) * vv);
-            const T ai = -om1 * g[i], bi = g[i];
-            rb += (ai * feq_u + bi * feq_v) * inv;
-            const T cu = ai * r * w, cv = bi * r * w;
-            ubx += cu * (T(3) * exi + T(9) * eu * exi - T(3) * ux);
-            uby += cu * (T(3) * eyi + T(9) * eu * eyi - T(3) * uy);
+            const T cv = g[i] * r * w;
+            rb += g[i] * feq_v * inv;
             vbx += cv * (T(3) * exi + T(9) * ev * exi - T(3) * vx);
             vby += cv * (T(3) * eyi + T(9) * ev * eyi - T(3) * vy);
+            if (!TAU1) {
+                const T eu = exi * ux + eyi * uy;
+                const T feq_u = r * w * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
+                const T ai = -om1 * g[i], cu = ai * r * w;
+                rb += ai * feq_u * inv;
+                ubx += cu * (T(3) * exi + T(9) * eu * exi - T(3) * ux);
+                uby += cu * (T(3) * eyi + T(9) * eu * eyi - T(3) * uy);
+            }
         }
         ubx += vbx;
         uby += vby;
@@ -162,96 +376,178 @@ __global__ void adj_local_kernel(const AdjArgs<T> a) {
         rb -= (vbx * Fx + vby * Fy) * inv * inv;
         const T jbx = ubx * inv, jby = uby * inv;
         rb -= (ubx * ux + uby * uy) * inv;
-        T Dbx, Dby, Pc;
+        T Dbx, Dby;
         if (SC) {
-            Dbx = T(-2) * qc * Fbx;
-            Dby = T(-2) * qc * Fby;
-            const T s = qc >= T(0) ? T(1) : T(-1);
-            Pc = T(-2) * s * (Fbx * Dx + Fby * Dy);
+            Dbx = T(-2) * sgn * phi * Fbx;
+            Dby = T(-2) * sgn * phi * Fby;
+            const T pc = T(-2) * sgn * (Fbx * Dx + Fby * Dy);  // centre part of Phi_bar
+            rb += pc * kappa;
+            if (valid) tacc += pc * theta;
         } else {
             Dbx = -Fbx;
             Dby = -Fby;
-            Pc = T(0);
         }
-        a.aux[0 * n + c] = rb;
-        a.aux[1 * n + c] = jbx;
-        a.aux[2 * n + c] = jby;
-        a.aux[3 * n + c] = Dbx;
-        a.aux[4 * n + c] = Dby;
-        a.aux[5 * n + c] = Pc;
+        if (valid) {
+            T *drow = a.aux + (long long)y * a.dpitch + a.doff;
+            store_field<T, PAD>(drow, x, nx, Dbx);
+            store_field<T, PAD>(drow + a.dstride, x, nx, Dby);
+            drow[2 * a.dstride + x] = rb;
+            drow[3 * a.dstride + x] = r;
+            if (TAU1) {
+                T *lrow = a.lam_out + (long long)y * a.lpitch + a.loff;
+                store_field<T, PAD>(lrow + a.lstride, x, nx, jbx);
+                store_field<T, PAD>(lrow + 2 * a.lstride, x, nx, jby);
+            } else {
+                drow[4 * a.dstride + x] = jbx;
+                drow[5 * a.dstride + x] = jby;
+            }
+        }
     }
+    if (SC) block_sum_into(tacc, a.Tpart + blockIdx.x + gridDim.x * blockIdx.y);
 }
 
-template <typename T, bool SC, bool CDM>
-__global__ void adj_finish_kernel(const AdjArgs<T> a) {
+template <typename T, bool SC, bool CDM, bool TAU1, int KC, bool PAD>
+__global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(const AdjArgs<T> a) {
+    constexpr int TX = AdjTile<T>::TX, TY = AdjTile<T>::TY, TYT = AdjTile<T>::TYT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const Model<T> &m = a.m;
-    const long long n = (long long)m.nx * m.ny;
-    double tb = 0.0;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(c / m.nx), x = (int)(c - (long long)y * m.nx);
-        // Phi_bar = centre term - Dx[Dx_bar] - Dy[Dy_bar]  (transpose of the antisymmetric derivative)
-        T ddx, ddy, tmp;
-        deriv<T, false, CDM>(m, a.aux + 3 * n, x, y, ddx, tmp);
-        deriv<T, false, CDM>(m, a.aux + 4 * n, x, y, tmp, ddy);
-        const T pbar = a.aux[5 * n + c] - ddx - ddy;
-        T r = T(0);
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) r += a.f[i * n + c];
-        const T qc = a.q[c];
-        T Ubar;
-        if (SC) {
-            const T phi = fabs(qc);
-            const T s = qc >= T(0) ? T(1) : T(-1);
-            Ubar = phi > T(0) ? pbar * s / (T(2) * phi) : T(0);
-        } else {
-            Ubar = pbar;
+    const int nx = m.nx, ny = m.ny;
+    const int hx = CDM ? 1 : (KC ? KC : m.kx), hy = CDM ? 1 : (KC ? KC : m.ky);
+    // D_bar_x over the tile's rows with the x halo, D_bar_y over its columns
+    // with the y halo; the CDM takes the full box of halo 1 for both
+    const int XS = PAD ? XO : hx;
+    const int WX = TX + 2 * XS, HX = CDM ? TY + 2 : TY;
+    const int WY = CDM ? TX + 2 : TX, HY = TY + 2 * hy;
+    const int ox = CDM ? 1 : 0;  // column offset of the tile in the D_bar_y array
+    const int oy = CDM ? 1 : 0;  // row offset of the tile in the D_bar_x array
+    T *SX = reinterpret_cast<T *>(smem_raw);
+    T *SY = SX + WX * HX;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(SY + WY * HY);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    if constexpr (PAD) {
+        const int tid = threadIdx.x + TX * threadIdx.y;
+        if (tid == 0) {
+            ptx::mbar_init(&bars[0], 1);
+            ptx::fence_mbar_init();
         }
-        T dpdr, dpdT;
-        p_derivs(m, a.R, a.aalp, r, dpdr, dpdT);
-        const T rb = a.aux[0 * n + c] + Ubar * (m.k * dpdr - T(1.0 / 3.0));
-        tb += (double)Ubar * (double)m.k * (double)dpdT;
-        const T jbx = a.aux[1 * n + c], jby = a.aux[2 * n + c];
-        const T om1 = T(1) - m.omega;
-        const int xp = x + 1 == m.nx ? 0 : x + 1, xm = x == 0 ? m.nx - 1 : x - 1;
-        const int yp = y + 1 == m.ny ? 0 : y + 1, ym = y == 0 ? m.ny - 1 : y - 1;
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-            T direct = T(0);
-            if (om1 != T(0)) {
-                const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
-                const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
-                direct = om1 * a.lam[i * n + (long long)dys * m.nx + dxs];
+        __syncthreads();
+        if (tid < 32) {
+            const int ncore = min(TX, nx - x0);
+            const uint32_t wide = (ncore + 2 * XO) * sizeof(T), core = ncore * sizeof(T);
+            if (tid == 0) ptx::mbar_arrive_expect_tx(&bars[0], HX * wide + HY * core);
+            __syncwarp();
+            for (int ly = tid; ly < HX; ly += 32) {
+                const T *src = a.aux + (long long)wrap_index(y0 + ly, ny) * a.dpitch + a.doff + x0;
+                ptx::bulk_g2s(SX + ly * WX, src - XO, wide, &bars[0]);
             }
-            a.lam_out[i * n + c] = direct + rb + T(ex(i)) * jbx + T(ey(i)) * jby;
+            for (int ly = tid; ly < HY; ly += 32) {
+                const T *src = a.aux + a.dstride + (long long)wrap_index(y0 - hy + ly, ny) * a.dpitch + a.doff + x0;
+                ptx::bulk_g2s(SY + ly * WY, src, core, &bars[0]);
+            }
         }
-    }
-    // FP64 block reduction of dL/dT
-    __shared__ double sh[256];
-    sh[threadIdx.x] = tb;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    } else {
+        stage_rect<T, TX, TYT>(SX, WX, a.aux, a.dpitch, a.doff, nx, ny, x0 - hx, y0 - oy, 0, WX, 0, HX);
+        stage_rect<T, TX, TYT>(SY, WY, a.aux + a.dstride, a.dpitch, a.doff, nx, ny, x0 - ox, y0 - hy, 0, WY, 0, HY);
+        ptx::cp_async_wait_all();
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(a.Tbar, sh[0]);
+
+    T tacc = T(0);
+    const int lx = threadIdx.x, x = x0 + lx;
+    const int xc = min(x, nx - 1);
+    const int xp = xc + 1 == nx ? 0 : xc + 1, xm = xc == 0 ? nx - 1 : xc - 1;
+#pragma unroll
+    for (int k = 0; k < TY / TYT; ++k) {
+        const int ly = threadIdx.y + k * TYT, y = y0 + ly;
+        const bool valid = x < nx && y < ny;
+        const int yc = min(y, ny - 1);
+        const T *drow = a.aux + (long long)yc * a.dpitch + a.doff;
+        const T r = drow[3 * a.dstride + xc];
+        const T rb0 = drow[2 * a.dstride + xc];
+        T kappa, theta, sgn;
+        eos_coeffs<T, SC>(m, a.R, a.aalp, r, kappa, theta, sgn);
+        if (PAD && k == 0 && !cta_wait_copies(bars, 1, 0, a.err)) return;
+        // the transposed derivative: Dx^T = -Dx, Dy^T = -Dy
+        const T *rx = SX + (ly + oy) * WX + (lx + XS);
+        const T *ry = SY + (ly + hy) * WY + (lx + ox);
+        T ddx, ddy;
+        if (CDM) {
+            ddx = T(1.0 / 3.0) * (rx[1] - rx[-1]) +
+                  T(1.0 / 12.0) * ((rx[WX + 1] + rx[-WX + 1]) - (rx[WX - 1] + rx[-WX - 1]));
+            ddy = T(1.0 / 3.0) * (ry[WY] - ry[-WY]) +
+                  T(1.0 / 12.0) * ((ry[WY + 1] + ry[WY - 1]) - (ry[-WY + 1] + ry[-WY - 1]));
+        } else {
+            ddx = stencil<T, KC, false, false>(rx, 1, m);
+            ddy = stencil<T, KC, false, true>(ry, WY, m);
+        }
+        const T pbar = -ddx - ddy;
+        const T rb = rb0 + kappa * pbar;
+        if (!valid) continue;
+        tacc += theta * pbar;
+        T *lrow = a.lam_out + (long long)y * a.lpitch + a.loff;
+        if (TAU1) {
+            store_field<T, PAD>(lrow, x, nx, rb);
+        } else {
+            const T jbx = drow[4 * a.dstride + x], jby = drow[5 * a.dstride + x];
+            const T om1 = T(1) - m.omega;
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
+                const int dys = ey(i) == 1 ? yp_of(y, ny) : (ey(i) == -1 ? ym_of(y, ny) : y);
+                const T gi = a.lam[i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs];
+                lrow[i * a.lstride + x] = om1 * gi + rb + T(ex(i)) * jbx + T(ey(i)) * jby;
+            }
+        }
+    }
+    block_sum_into(tacc, a.Tpart + blockIdx.x + gridDim.x * blockIdx.y);
 }
 
-template <typename T>
-__global__ void adj_seed_kernel(long long n, const T *grad_rho, T *lam) {
+// lambda at the final step from dL/drho_T (rho_T = sum_i f_i): lambda_i = g
+// for all i, i.e. (g, 0, 0) in the three-field form.
+template <typename T, bool PAD>
+__global__ void adj_seed_kernel(int nx, int ny, int nlam, const T *grad_rho, T *lam, long long lstride, int lpitch,
+                                int loff) {
+    const long long n = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(c / nx), x = (int)(c - (long long)y * nx);
         const T g = grad_rho[c];
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) lam[i * n + c] = g;  // rho = sum_i f_i
+        T *row = lam + (long long)y * lpitch + loff;
+        if (nlam == 3) {
+            store_field<T, PAD>(row, x, nx, g);
+            store_field<T, PAD>(row + lstride, x, nx, T(0));
+            store_field<T, PAD>(row + 2 * lstride, x, nx, T(0));
+        } else {
+            for (int i = 0; i < kQ; ++i) row[i * lstride + x] = g;
+        }
     }
 }
 
+// f_i = w_i rho0 at rest (Eq. 2): dL/drho0 = sum_i w_i lambda_i, which for
+// lambda_i = rho_bar + e_i . j_bar is rho_bar (sum w_i = 1, sum w_i e_i = 0).
 template <typename T>
-__global__ void adj_initial_kernel(long long n, const T *lam, T *grad_rho0) {
+__global__ void adj_initial_kernel(int nx, int ny, int nlam, const T *lam, long long lstride, int lpitch, int loff,
+                                   T *grad_rho0) {
+    const long long n = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        T s = T(0);
+        const int y = (int)(c / nx), x = (int)(c - (long long)y * nx);
+        const T *row = lam + (long long)y * lpitch + loff + x;
+        if (nlam == 3) {
+            grad_rho0[c] = row[0];
+        } else {
+            T s = T(0);
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) s += wq<T>(i) * lam[i * n + c];  // f_i = w_i rho0 at rest (Eq. 2)
-        grad_rho0[c] = s;
+            for (int i = 0; i < kQ; ++i) s += wq<T>(i) * row[i * lstride];
+            grad_rho0[c] = s;
+        }
+    }
+}
+
+__global__ void sum_slots_kernel(const double *slots, int nslots, double *out) {
+    // one thread, fixed order: reproducible
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nslots; ++i) s += slots[i];
+        *out = s;
     }
 }
 
@@ -270,42 +566,128 @@ int blocks_for(long long n) {
     return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
 }
 
+template <typename T>
+dim3 adj_grid(int nx, int ny) {
+    return dim3((nx + AdjTile<T>::TX - 1) / AdjTile<T>::TX, (ny + AdjTile<T>::TY - 1) / AdjTile<T>::TY);
+}
+
+template <typename T, bool SC, bool CDM, bool TAU1, int KC, bool PAD>
+cudaError_t launch_adj_t(const AdjArgs<T> &a, cudaStream_t s) {
+    constexpr int TX = AdjTile<T>::TX, TY = AdjTile<T>::TY, TYT = AdjTile<T>::TYT;
+    const int hx = CDM ? 1 : (KC ? KC : a.m.kx), hy = CDM ? 1 : (KC ? KC : a.m.ky);
+    const int XS = PAD ? XO : hx;
+    const int LW = PAD ? TX + 2 * LO : TX + 2;
+    const size_t smem_a = sizeof(T) * ((size_t)(TX + 2 * XS) * (TY + 2 * hy) + (TAU1 ? 3 * LW * (TY + 2) : 0)) +
+                          (PAD ? 2 * sizeof(uint64_t) : 0);
+    const size_t smem_b = (CDM ? sizeof(T) * 2 * (size_t)(TX + 2) * (TY + 2)
+                               : sizeof(T) * ((size_t)(TX + 2 * XS) * TY + (size_t)TX * (TY + 2 * hy))) +
+                          (PAD ? sizeof(uint64_t) : 0);
+    auto ka = adj_a_kernel<T, SC, CDM, TAU1, KC, PAD>;
+    auto kb = adj_b_kernel<T, SC, CDM, TAU1, KC, PAD>;
+    cudaError_t e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+    if (e != cudaSuccess) return e;
+    const dim3 grid = adj_grid<T>(a.m.nx, a.m.ny), block(TX, TYT);
+    ka<<<grid, block, smem_a, s>>>(a);
+    AdjArgs<T> b = a;
+    b.Tpart = a.Tpart + grid.x * grid.y;
+    kb<<<grid, block, smem_b, s>>>(b);
+    return cudaGetLastError();
+}
+
+// compile-time HDM radius of the fast variants
+template <typename T>
+constexpr int adj_kc() { return sizeof(T) == 4 ? 26 : 40; }
+
+template <typename T, bool SC, bool CDM, bool TAU1>
+cudaError_t launch_adj_k(const AdjArgs<T> &a, bool padded, cudaStream_t s) {
+    if constexpr (CDM) {
+        return launch_adj_t<T, SC, CDM, TAU1, 0, false>(a, s);
+    } else {
+        if constexpr (sizeof(T) == 4)
+            if (padded) return launch_adj_t<T, SC, CDM, TAU1, adj_kc<T>(), true>(a, s);
+        if (a.m.kx <= adj_kc<T>() && a.m.ky <= adj_kc<T>())
+            return launch_adj_t<T, SC, CDM, TAU1, adj_kc<T>(), false>(a, s);
+        return launch_adj_t<T, SC, CDM, TAU1, 0, false>(a, s);
+    }
+}
+
 }  // namespace
 
 template <typename T>
-cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cdm, const T *f, const T *q,
-                                const T *lam_next, T *aux, T *lam_out, double *Tbar, cudaStream_t s) {
+int adjoint_slots(int nx, int ny) {
+    const dim3 g = adj_grid<T>(nx, ny);
+    return 2 * (int)(g.x * g.y);
+}
+
+AdjLayout adjoint_layout(int nx, int ny, bool padded, bool tau1) {
+    AdjLayout l;
+    const int pp = nx + 2 * kGhost;
+    l.dpitch = padded ? pp : nx;
+    l.doff = padded ? kGhost : 0;
+    l.dstride = (long long)l.dpitch * ny;
+    l.naux = tau1 ? 4 : 6;
+    l.lpitch = padded && tau1 ? pp : nx;
+    l.loff = padded && tau1 ? kGhost : 0;
+    l.lstride = (long long)l.lpitch * ny;
+    l.nlam = tau1 ? 3 : 9;
+    return l;
+}
+
+template <typename T>
+cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cdm, bool tau1, bool padded,
+                                const AdjLayout &l, const T *f, const T *q, int qpitch, int qoff, const T *lam_next,
+                                T *aux, T *lam_out, double *Tpart, int *err, cudaStream_t s) {
     AdjArgs<T> a;
     a.m = m;
     a.R = R;
     a.aalp = aalp;
     a.f = f;
     a.q = q;
+    a.qpitch = qpitch;
+    a.qoff = qoff;
     a.lam = lam_next;
-    a.aux = aux;
     a.lam_out = lam_out;
-    a.Tbar = Tbar;
-    const long long n = (long long)m.nx * m.ny;
-    const int nb = blocks_for(n);
+    a.lstride = l.lstride;
+    a.lpitch = l.lpitch;
+    a.loff = l.loff;
+    a.aux = aux;
+    a.dstride = l.dstride;
+    a.dpitch = l.dpitch;
+    a.doff = l.doff;
+    a.Tpart = Tpart;
+    a.err = err;
+#define LBM_ADJ_PICK(SC, CDM)                                                                             \
+    return tau1 ? launch_adj_k<T, SC, CDM, true>(a, padded, s) : launch_adj_k<T, SC, CDM, false>(a, padded, s)
     if (sc) {
-        if (cdm) { adj_local_kernel<T, true, true><<<nb, 256, 0, s>>>(a); adj_finish_kernel<T, true, true><<<nb, 256, 0, s>>>(a); }
-        else { adj_local_kernel<T, true, false><<<nb, 256, 0, s>>>(a); adj_finish_kernel<T, true, false><<<nb, 256, 0, s>>>(a); }
-    } else {
-        if (cdm) { adj_local_kernel<T, false, true><<<nb, 256, 0, s>>>(a); adj_finish_kernel<T, false, true><<<nb, 256, 0, s>>>(a); }
-        else { adj_local_kernel<T, false, false><<<nb, 256, 0, s>>>(a); adj_finish_kernel<T, false, false><<<nb, 256, 0, s>>>(a); }
+        if (cdm) LBM_ADJ_PICK(true, true);
+        LBM_ADJ_PICK(true, false);
     }
+    if (cdm) LBM_ADJ_PICK(false, true);
+    LBM_ADJ_PICK(false, false);
+#undef LBM_ADJ_PICK
+}
+
+template <typename T>
+cudaError_t launch_adjoint_seed(int nx, int ny, bool padded, const AdjLayout &l, const T *grad_rho, T *lam,
+                                cudaStream_t s) {
+    const long long n = (long long)nx * ny;
+    if (padded)
+        adj_seed_kernel<T, true><<<blocks_for(n), 256, 0, s>>>(nx, ny, l.nlam, grad_rho, lam, l.lstride, l.lpitch, l.loff);
+    else
+        adj_seed_kernel<T, false><<<blocks_for(n), 256, 0, s>>>(nx, ny, l.nlam, grad_rho, lam, l.lstride, l.lpitch, l.loff);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_adjoint_seed(long long n, const T *grad_rho, T *lam, cudaStream_t s) {
-    adj_seed_kernel<T><<<blocks_for(n), 256, 0, s>>>(n, grad_rho, lam);
+cudaError_t launch_adjoint_initial(int nx, int ny, const AdjLayout &l, const T *lam, T *grad_rho0, cudaStream_t s) {
+    const long long n = (long long)nx * ny;
+    adj_initial_kernel<T><<<blocks_for(n), 256, 0, s>>>(nx, ny, l.nlam, lam, l.lstride, l.lpitch, l.loff, grad_rho0);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_adjoint_initial(long long n, const T *lam, T *grad_rho0, cudaStream_t s) {
-    adj_initial_kernel<T><<<blocks_for(n), 256, 0, s>>>(n, lam, grad_rho0);
+cudaError_t launch_sum_slots(const double *slots, int nslots, double *out, cudaStream_t s) {
+    sum_slots_kernel<<<1, 32, 0, s>>>(slots, nslots, out);
     return cudaGetLastError();
 }
 
@@ -315,11 +697,13 @@ cudaError_t launch_density(long long n, const T *f, T *rho, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-#define LBM_ADJ_INST(T)                                                                                     \
-    template cudaError_t launch_adjoint_step<T>(const Model<T> &, T, T, bool, bool, const T *, const T *,    \
-                                                const T *, T *, T *, double *, cudaStream_t);                \
-    template cudaError_t launch_adjoint_seed<T>(long long, const T *, T *, cudaStream_t);                  \
-    template cudaError_t launch_adjoint_initial<T>(long long, const T *, T *, cudaStream_t);               \
+#define LBM_ADJ_INST(T)                                                                                      \
+    template int adjoint_slots<T>(int, int);                                                                \
+    template cudaError_t launch_adjoint_step<T>(const Model<T> &, T, T, bool, bool, bool, bool, const AdjLayout &, \
+                                                const T *, const T *, int, int, const T *, T *, T *, double *, int *, \
+                                                cudaStream_t);                                              \
+    template cudaError_t launch_adjoint_seed<T>(int, int, bool, const AdjLayout &, const T *, T *, cudaStream_t); \
+    template cudaError_t launch_adjoint_initial<T>(int, int, const AdjLayout &, const T *, T *, cudaStream_t);   \
     template cudaError_t launch_density<T>(long long, const T *, T *, cudaStream_t);
 LBM_ADJ_INST(float)
 LBM_ADJ_INST(double)

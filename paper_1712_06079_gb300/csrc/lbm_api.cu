@@ -50,6 +50,13 @@ struct lbm_ctx {
     void *tmp[2] = {nullptr, nullptr};
     void *qpad_tape[2] = {nullptr, nullptr};
     int tape_steps = -1, tape_C = 0;
+    // reverse sweep buffers, allocated with the tape: the states recomputed
+    // inside a segment, the stencil field of every state of a segment, the
+    // adjoint ping-pong, kernel scratch and the FP64 dL/dT slots
+    std::vector<void *> seg, segq;
+    void *lam[2] = {nullptr, nullptr};
+    void *aux = nullptr;
+    double *slots = nullptr;
 };
 
 namespace {
@@ -262,6 +269,18 @@ lbm_status ensure_stage(lbm_ctx *c, size_t bytes) {
 void free_tape(lbm_ctx *c) {
     for (void *p : c->ckpt) cudaFree(p);
     c->ckpt.clear();
+    for (void *p : c->seg) cudaFree(p);
+    for (void *p : c->segq) cudaFree(p);
+    c->seg.clear();
+    c->segq.clear();
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->lam[k]);
+        c->lam[k] = nullptr;
+    }
+    cudaFree(c->aux);
+    cudaFree(c->slots);
+    c->aux = nullptr;
+    c->slots = nullptr;
     for (int k = 0; k < 2; ++k) {
         cudaFree(c->tmp[k]);
         cudaFree(c->qpad_tape[k]);
@@ -304,27 +323,52 @@ cudaError_t tape_step(lbm_ctx *c, const Model<T> &m, const void *src, void *dst,
 
 template <typename T>
 lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
-    free_tape(c);
     const size_t fbytes = (size_t)kQ * c->n * sizeof(T);
     const int nck = nsteps / C + 1;
-    for (int k = 0; k < nck; ++k) {
-        void *p = nullptr;
-        if (cudaMalloc(&p, fbytes) != cudaSuccess) {
-            free_tape(c);
-            return fail(c, LBM_E_NOMEM, "not enough device memory for %d checkpoints", nck);
-        }
-        c->ckpt.push_back(p);
-    }
-    if (cudaMalloc(&c->tmp[0], fbytes) != cudaSuccess || cudaMalloc(&c->tmp[1], fbytes) != cudaSuccess) {
+    c->tape_steps = -1;
+    // a tape of the same shape (checkpoint count and interval) is reused
+    const bool reuse = c->slots && c->tape_C == C && c->ckpt.size() == (size_t)nck;
+    if (!reuse) {
         free_tape(c);
-        return fail(c, LBM_E_NOMEM, "tape scratch");
-    }
-    if (c->fused) {
-        size_t qb = sizeof(float) * (size_t)fused_q_pitch(c->p.nx) * c->p.ny;
-        if (cudaMalloc(&c->qpad_tape[0], qb) != cudaSuccess || cudaMalloc(&c->qpad_tape[1], qb) != cudaSuccess) {
-            free_tape(c);
-            return fail(c, LBM_E_NOMEM, "tape potential fields");
+        for (int k = 0; k < nck; ++k) {
+            void *p = nullptr;
+            if (cudaMalloc(&p, fbytes) != cudaSuccess) {
+                free_tape(c);
+                return fail(c, LBM_E_NOMEM, "not enough device memory for %d checkpoints", nck);
+            }
+            c->ckpt.push_back(p);
         }
+        if (cudaMalloc(&c->tmp[0], fbytes) != cudaSuccess || cudaMalloc(&c->tmp[1], fbytes) != cudaSuccess) {
+            free_tape(c);
+            return fail(c, LBM_E_NOMEM, "tape scratch");
+        }
+        if (c->fused) {
+            size_t qb = sizeof(float) * (size_t)fused_q_pitch(c->p.nx) * c->p.ny;
+            if (cudaMalloc(&c->qpad_tape[0], qb) != cudaSuccess || cudaMalloc(&c->qpad_tape[1], qb) != cudaSuccess) {
+                free_tape(c);
+                return fail(c, LBM_E_NOMEM, "tape potential fields");
+            }
+        }
+        {   // buffers of the reverse sweep
+            const bool tau1 = model_of<T>(c).omega == T(1);
+            const int qpitch = c->fused ? fused_q_pitch(c->p.nx) : c->p.nx;
+            const size_t qbytes = sizeof(T) * (size_t)qpitch * c->p.ny;
+            const AdjLayout lay = adjoint_layout(c->p.nx, c->p.ny, c->fused, tau1);
+            const size_t lbytes = (size_t)lay.nlam * lay.lstride * sizeof(T);
+            bool ok = true;
+            c->seg.assign(C > 1 ? C - 1 : 0, nullptr);
+            c->segq.assign(C, nullptr);
+            for (auto &p : c->seg) ok = ok && cudaMalloc(&p, fbytes) == cudaSuccess;
+            for (auto &p : c->segq) ok = ok && cudaMalloc(&p, qbytes) == cudaSuccess;
+            ok = ok && cudaMalloc(&c->lam[0], lbytes) == cudaSuccess && cudaMalloc(&c->lam[1], lbytes) == cudaSuccess &&
+                 cudaMalloc(&c->aux, (size_t)lay.naux * lay.dstride * sizeof(T)) == cudaSuccess &&
+                 cudaMalloc((void **)&c->slots, sizeof(double) * (adjoint_slots<T>(c->p.nx, c->p.ny) + 1)) == cudaSuccess;
+            if (!ok) {
+                free_tape(c);
+                return fail(c, LBM_E_NOMEM, "not enough device memory for the reverse sweep buffers");
+            }
+        }
+        c->tape_C = C;
     }
     Model<T> m = model_of<T>(c);
     CK(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");
@@ -353,58 +397,59 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
 template <typename T>
 lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *gT) {
     const int N = c->tape_steps, C = c->tape_C;
-    const size_t fbytes = (size_t)kQ * c->n * sizeof(T);
+    const int nx = c->p.nx, ny = c->p.ny;
     Model<T> m = model_of<T>(c);
     const T R = (T)c->p.R, aalp = (T)(c->p.a * dalpha_dT(c->p, c->T, c->Tc));
-    // segment states f^{kC+1} .. f^{kC+C-1}; lambda ping-pong; 6 aux fields; FP64 dL/dT
-    std::vector<void *> seg(C > 1 ? C - 1 : 0, nullptr);
-    void *lam[2] = {nullptr, nullptr}, *aux = nullptr;
-    double *Tbar = nullptr;
-    lbm_status st = LBM_OK;
-    auto release = [&]() {
-        for (void *p : seg) cudaFree(p);
-        cudaFree(lam[0]);
-        cudaFree(lam[1]);
-        cudaFree(aux);
-        cudaFree(Tbar);
-    };
-    for (auto &p : seg)
-        if (cudaMalloc(&p, fbytes) != cudaSuccess) st = LBM_E_NOMEM;
-    if (cudaMalloc(&lam[0], fbytes) != cudaSuccess || cudaMalloc(&lam[1], fbytes) != cudaSuccess ||
-        cudaMalloc(&aux, 6 * c->n * sizeof(T)) != cudaSuccess || cudaMalloc((void **)&Tbar, sizeof(double)) != cudaSuccess)
-        st = LBM_E_NOMEM;
-    if (st != LBM_OK) {
-        release();
-        return fail(c, st, "not enough device memory for the adjoint");
-    }
-    cudaError_t e = cudaMemsetAsync(Tbar, 0, sizeof(double), c->stream);
-    if (e == cudaSuccess) e = launch_adjoint_seed<T>(c->n, grad_rhoT, (T *)lam[0], c->stream);
+    const bool tau1 = m.omega == T(1);
+    const AdjLayout lay = adjoint_layout(nx, ny, c->fused, tau1);
+    // stencil fields: the single-pass layout (padded rows) or the plain one
+    const int qpitch = c->fused ? fused_q_pitch(nx) : nx;
+    const int qoff = (qpitch - nx) / 2;
+    const int nslots = adjoint_slots<T>(nx, ny);
+    std::vector<void *> &seg = c->seg, &segq = c->segq;
+    void **lam = c->lam, *aux = c->aux;
+    double *slots = c->slots;
+    const int rows = c->fused ? seg_rows_of(c) : 0;
+    cudaError_t e = cudaMemsetAsync(slots, 0, sizeof(double) * (nslots + 1), c->stream);
+    if (e == cudaSuccess) e = launch_adjoint_seed<T>(nx, ny, c->fused, lay, grad_rhoT, (T *)lam[0], c->stream);
     int li = 0;
     for (int k = (N - 1) / C; k >= 0 && e == cudaSuccess; --k) {
         const int t0 = k * C, t1 = std::min(N, t0 + C);  // states t0 .. t1-1 are needed
-        // recompute f^{t0+1} .. f^{t1-1} from the checkpoint (the same forward kernels)
-        if (c->fused && t1 - t0 > 1)
-            e = launch_potential_padded(*(const Model<float> *)&m, is_sc(c), (const float *)c->ckpt[k],
-                                        (float *)c->qpad_tape[0], c->err, c->stream);
-        const void *cur = c->ckpt[k];
-        for (int t = t0; t < t1 - 1 && e == cudaSuccess; ++t) {
-            e = tape_step<T>(c, m, cur, seg[t - t0], (t - t0) & 1);
-            cur = seg[t - t0];
+        // recompute f^{t0+1} .. f^{t1-1} from the checkpoint with the forward
+        // kernels, keeping the stencil field of every state t0 .. t1-1
+        if (c->fused) {
+            const Model<float> &mf = *(const Model<float> *)&m;
+            e = launch_potential_padded(mf, is_sc(c), (const float *)c->ckpt[k], (float *)segq[0], c->err, c->stream);
+            const void *cur = c->ckpt[k];
+            for (int t = t0; t < t1 - 1 && e == cudaSuccess; ++t) {
+                e = launch_fused_step(mf, is_sc(c), (const float *)cur, (const float *)segq[t - t0],
+                                      (float *)seg[t - t0], (float *)segq[t - t0 + 1], c->err, rows, c->stream);
+                cur = seg[t - t0];
+            }
+        } else {
+            const void *cur = c->ckpt[k];
+            for (int t = t0; t < t1 && e == cudaSuccess; ++t) {
+                e = launch_potential<T>(m, is_sc(c), (const T *)cur, (T *)segq[t - t0], c->err, c->stream);
+                if (e == cudaSuccess && t < t1 - 1) {
+                    e = launch_collide<T>(m, is_sc(c), is_cdm(c), (const T *)cur, (const T *)segq[t - t0],
+                                          (T *)seg[t - t0], c->stream);
+                    cur = seg[t - t0];
+                }
+            }
         }
         for (int t = t1 - 1; t >= t0 && e == cudaSuccess; --t) {
             const T *ft = (const T *)(t == t0 ? c->ckpt[k] : seg[t - t0 - 1]);
-            e = launch_potential<T>(m, is_sc(c), ft, (T *)c->q, c->err, c->stream);
-            if (e == cudaSuccess)
-                e = launch_adjoint_step<T>(m, R, aalp, is_sc(c), is_cdm(c), ft, (const T *)c->q, (const T *)lam[li],
-                                           (T *)aux, (T *)lam[1 - li], Tbar, c->stream);
+            e = launch_adjoint_step<T>(m, R, aalp, is_sc(c), is_cdm(c), tau1, c->fused, lay, ft,
+                                       (const T *)segq[t - t0], qpitch, qoff, (const T *)lam[li], (T *)aux,
+                                       (T *)lam[1 - li], slots, c->err, c->stream);
             li = 1 - li;
         }
     }
-    if (e == cudaSuccess) e = launch_adjoint_initial<T>(c->n, (const T *)lam[li], grad_rho0, c->stream);
+    if (e == cudaSuccess) e = launch_adjoint_initial<T>(nx, ny, lay, (const T *)lam[li], grad_rho0, c->stream);
+    if (e == cudaSuccess) e = launch_sum_slots(slots, nslots, slots + nslots, c->stream);
     double h = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, Tbar, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, slots + nslots, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    release();
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint");
     *gT = h;
     return read_error_word(c);

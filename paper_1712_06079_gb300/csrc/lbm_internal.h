@@ -49,18 +49,39 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
                               float *qout, int *err, int seg_rows, cudaStream_t s);
 
 // Adjoint (reverse-time) step (adjoint.cu): from lambda = dL/df at t+1 and the
-// state f at t (with its potential field q from launch_potential), writes
-// lambda at t into lam_out and adds dL/dT of this step to *Tbar (FP64).
-// aux holds 6 * n scratch values.  R is the gas constant, aalp = a dalpha/dT.
+// state f at t with its stencil field q (row y, column x at
+// q[y * qpitch + qoff + x]; |q| = Phi for the Shan-Chen form, U for
+// Zhang-Chen), writes lambda at t into lam_out and adds the step's dL/dT to
+// the FP64 slots Tpart[0 .. adjoint_slots).  lambda has nine fields, or three
+// (rho_bar, jx_bar, jy_bar with lambda_i = rho_bar + e_i . j_bar) when tau1;
+// aux holds naux scratch fields.  Field k, row y, column x of lambda / aux
+// sits at [k * stride + y * pitch + off + x] as adjoint_layout gives: padded
+// rows with 32 periodic ghost columns on each side for the FP32 single-pass
+// layout (padded = true: q in that layout, nx % 4 == 0, nx >= 64, HDM radius
+// 26), plain rows otherwise.  R is the gas constant, aalp = a dalpha/dT; err
+// receives kErrTimeout if a bounded wait on a copy gives up.
+struct AdjLayout {
+    int dpitch, doff, naux;
+    long long dstride;
+    int lpitch, loff, nlam;
+    long long lstride;
+};
+AdjLayout adjoint_layout(int nx, int ny, bool padded, bool tau1);
 template <typename T>
-cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cdm, const T *f, const T *q,
-                                const T *lam_next, T *aux, T *lam_out, double *Tbar, cudaStream_t s);
-// lambda_i = grad_rho for every i (the final density is sum_i f_i).
+int adjoint_slots(int nx, int ny);
 template <typename T>
-cudaError_t launch_adjoint_seed(long long n, const T *grad_rho, T *lam, cudaStream_t s);
+cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cdm, bool tau1, bool padded,
+                                const AdjLayout &l, const T *f, const T *q, int qpitch, int qoff, const T *lam_next,
+                                T *aux, T *lam_out, double *Tpart, int *err, cudaStream_t s);
+// lambda at the final step from dL/drho_T (rho_T = sum_i f_i).
+template <typename T>
+cudaError_t launch_adjoint_seed(int nx, int ny, bool padded, const AdjLayout &l, const T *grad_rho, T *lam,
+                                cudaStream_t s);
 // dL/drho0 = sum_i w_i lambda_i at t = 0 (f = f^eq(rho0, 0)).
 template <typename T>
-cudaError_t launch_adjoint_initial(long long n, const T *lam, T *grad_rho0, cudaStream_t s);
+cudaError_t launch_adjoint_initial(int nx, int ny, const AdjLayout &l, const T *lam, T *grad_rho0, cudaStream_t s);
+// *out = sum of nslots doubles in index order (one thread).
+cudaError_t launch_sum_slots(const double *slots, int nslots, double *out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_density(long long n, const T *f, T *rho, cudaStream_t s);
 

@@ -130,3 +130,25 @@ def test_adjoint_fp32_close_to_fp64():
     assert L32 == pytest.approx(L64, rel=1e-4)
     assert t32 == pytest.approx(t64, rel=1e-3)
     assert np.abs(g32 - g64).max() < 1e-3 * np.abs(g64).max()
+
+
+FP32_CASES = [
+    # (eos, Tr, force, grad, tau, nx, ny): the single-pass layout with tau != 1
+    # (nine-field lambda), ragged 64 x 16 adjoint tiles, and the plain-layout
+    # FP32 path (CDM)
+    ("cs", 0.8, "sc", "hdm", 0.8, 100, 70),
+    ("pr", 0.9, "zc", "hdm", 1.0, 132, 58),
+    ("vdw", 0.85, "sc", "cdm", 1.2, 48, 40),
+]
+
+
+@pytest.mark.parametrize("eos,Tr,force,grad,tau,nx,ny", FP32_CASES)
+def test_adjoint_fp32_paths_close_to_fp64(eos, Tr, force, grad, tau, nx, ny):
+    p64, rho0, target = setup(nx, ny, eos, Tr, force, grad, tau)
+    p32 = lbm.Params(**{**p64.__dict__, "prec": "f32"})
+    n = 30
+    L64, g64, t64, _ = adjoint(p64, rho0, target, n, 6)
+    L32, g32, t32, _ = adjoint(p32, rho0, target, n, 6)
+    assert L32 == pytest.approx(L64, rel=1e-4)
+    assert t32 == pytest.approx(t64, rel=2e-3)
+    assert np.abs(g32 - g64).max() < 1e-3 * np.abs(g64).max()
