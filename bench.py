@@ -126,10 +126,15 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def source_digest() -> str:
+# sources that define each timed kernel: a committed DRAM-traffic figure is
+# used only while these files are unchanged
+KERNEL_SOURCES = {"fused_step": ["fused_step.cu", "lbm_device.cuh", "ptx.cuh"]}
+
+
+def source_digest(kernel: str) -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1712_06079_gb300", "csrc", "*"))):
-        h.update(open(p, "rb").read())
+    for name in KERNEL_SOURCES.get(kernel, []):
+        h.update(open(os.path.join(ROOT, "paper_1712_06079_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -137,14 +142,14 @@ def ncu_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
     try:
         d = json.load(open(path))
     except ValueError:
         return None
     e = d.get(kernel)
-    if not e or e.get("source_digest") != source_digest():
+    if not e or e.get("source_digest") != source_digest(kernel):
         return None
     return e.get("bytes_per_launch_full_size")
 
