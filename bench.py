@@ -485,6 +485,55 @@ def run_adjoint(args):
     return 0
 
 
+def run_coexistence(args):
+    """Flat-interface coexistence: PR (a=2/49, b=2/21, omega=0.344) on 1024 x 8,
+    liquid slab in the middle half, ZC force, HDM and CDM, T/Tc in {0.9, 0.7,
+    0.55}, tau = 1, 20000 steps, in FP32 and FP64 on the GPU; bulk densities
+    against the library's Maxwell construction (Sec. 5.2) and FP32 against FP64."""
+    import numpy as np
+    import torch
+
+    from paper_1712_06079_gb300 import inputs, lbm
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    t = inputs.EOS_TABLE["pr"]
+    nx, ny, steps = 1024, 8, args.coex_steps
+
+    def bulk(rho):
+        prof = rho.mean(0)
+        liq = float(prof[nx // 2 - nx // 16: nx // 2 + nx // 16 + 1].mean())
+        gas = float(np.r_[prof[: nx // 16 + 1], prof[-nx // 16:]].mean())
+        return liq, gas
+
+    cases = []
+    for Tr in (0.9, 0.7, 0.55):
+        for grad in ("hdm", "cdm"):
+            row = {"Tr": Tr, "grad": grad}
+            for prec in ("f32", "f64"):
+                gp = lbm.Params(nx=nx, ny=ny, eos="pr", a=t["a"], b=t["b"], omega=t["omega"], Tr=Tr, k=t["k"],
+                                tau=1.0, force="zc", grad=grad, prec=prec, stream=stream.cuda_stream)
+                g, l = lbm.maxwell(gp)
+                row.update(maxwell_g=g, maxwell_l=l)
+                with lbm.Lattice(gp) as lat:
+                    lat.init_density(inputs.slab(nx, ny, g, l))
+                    try:
+                        lat.step(steps)
+                        lat.sync()
+                        liq, gas = bulk(lat.moments()[0])
+                        row[prec] = {"rho_l": liq, "rho_g": gas, "err_l": liq / l - 1, "err_g": gas / g - 1}
+                    except lbm.LBMError as e:
+                        row[prec] = {"unstable": str(e)}
+            if "rho_l" in row["f32"] and "rho_l" in row["f64"]:
+                row["f32_vs_f64"] = {"rho_l": row["f32"]["rho_l"] / row["f64"]["rho_l"] - 1,
+                                     "rho_g": row["f32"]["rho_g"] / row["f64"]["rho_g"] - 1}
+            cases.append(row)
+    print(json.dumps({"metric": "flat-interface coexistence vs Maxwell (PR, ZC, HDM vs CDM)", "unit": "relative error",
+                      "steps": steps, "dtype": "f32 and f64", "data": "synthetic",
+                      "config": {"workload": "PR slab 1024x8, tau 1, k 0.04, liquid in the middle half, tanh W=2"},
+                      "cases": cases}), flush=True)
+    return 0
+
 def main():
     global NX, NY
     ap = argparse.ArgumentParser()
@@ -495,9 +544,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=NX, help="lattice size (default: the 4096 x 4096 workload)")
     ap.add_argument("--ny", type=int, default=NY)
-    ap.add_argument("--workload", choices=["spinodal", "sweep", "adjoint"], default="spinodal",
+    ap.add_argument("--workload", choices=["spinodal", "sweep", "adjoint", "coexistence"], default="spinodal",
                     help="spinodal: the throughput line; sweep: batched vs sequential 64-lattice sweep; "
-                         "adjoint: reverse-mode cost and gradient checks on the 512 x 512 droplet")
+                         "adjoint: reverse-mode cost and gradient checks on the 512 x 512 droplet; "
+                         "coexistence: PR flat interface, HDM vs CDM, FP32 and FP64 vs Maxwell")
+    ap.add_argument("--coex-steps", type=int, default=20000, help="steps of the coexistence workload")
     ap.add_argument("--adj-steps", type=int, default=5000, help="forward steps of the adjoint workload")
     ap.add_argument("--seq-steps", type=int, default=200, help="steps timed per lattice in the sequential arm")
     args = ap.parse_args()
@@ -510,6 +561,8 @@ def main():
         return run_sweep(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "coexistence":
+        return run_coexistence(args)
     return run_ours(args)
 
 
