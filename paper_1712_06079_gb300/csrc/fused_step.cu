@@ -86,6 +86,16 @@ struct FusedArgs {
     float2 wy2[FK + 1]; // (w_j, w_j) pairs of the d/dy weights for packed FP32x2 FMAs
 };
 
+// f(t) is read once per step: a 16-byte load that takes no L1 line (L1 holds
+// what the other loads in flight need; measured +1.5 % at 4096^2, +4 % at 2048^2)
+__device__ __forceinline__ float4 ld_stream(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ int wrapi(int i, int n) {
     while (i < 0) i += n;
     while (i >= n) i -= n;
@@ -201,7 +211,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     auto load_f = [&](int s) {
         const float *src = A.f + (long long)wrapi(ys - 1 + SLAB * s + warp, ny) * nx + xgw;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fv[i] = __ldcs(reinterpret_cast<const float4 *>(src + i * N));
+        for (int i = 0; i < 9; ++i) fv[i] = ld_stream(reinterpret_cast<const float4 *>(src + i * N));
     };
     load_f(0);
 
