@@ -272,17 +272,20 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             {   // d/dy: ring rows yc - FK .. yc + FK at the lane's 4 columns, as
                 // sum_j w_j (q(y+j) - q(y-j)) with the differences taken first;
                 // odd and even j in separate sums; packed FP32x2 arithmetic
+                // the window of ring rows base - FK .. base + FK wraps at most once
+                // on each side: two base offsets, one select per tap, the tap
+                // itself an immediate offset of the shared load
                 const float *qcol = qn + 4 * lane;
                 const int base = ryc % QRING;
+                const int b0 = base * NW, bu = (base - QRING) * NW, bd = (base + QRING) * NW;
                 const float2 neg1 = make_float2(-1.f, -1.f);
                 float2 se01 = make_float2(0.f, 0.f), se23 = se01, so01 = se01, so23 = se01;
 #pragma unroll
                 for (int j = 1; j <= FK; ++j) {
-                    int up = base + j, dn = base - j;
-                    up = up >= QRING ? up - QRING : up;
-                    dn = dn < 0 ? dn + QRING : dn;
-                    const float4 a = *reinterpret_cast<const float4 *>(qcol + up * NW);
-                    const float4 b = *reinterpret_cast<const float4 *>(qcol + dn * NW);
+                    const int ou = (j >= QRING - base ? bu : b0) + j * NW;
+                    const int od = (j > base ? bd : b0) - j * NW;
+                    const float4 a = *reinterpret_cast<const float4 *>(qcol + ou);
+                    const float4 b = *reinterpret_cast<const float4 *>(qcol + od);
                     const float2 w2 = A.wy2[j];
                     const float2 d01 = __ffma2_rn(neg1, make_float2(b.x, b.y), make_float2(a.x, a.y));
                     const float2 d23 = __ffma2_rn(neg1, make_float2(b.z, b.w), make_float2(a.z, a.w));
