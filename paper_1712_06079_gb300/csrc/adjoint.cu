@@ -542,13 +542,14 @@ __global__ void adj_initial_kernel(int nx, int ny, int nlam, const T *lam, long 
     }
 }
 
+// Sum of the slots in a fixed order (lane k takes slots k, k + 32, ... in
+// turn, then a fixed shuffle tree): one warp, reproducible.
 __global__ void sum_slots_kernel(const double *slots, int nslots, double *out) {
-    // one thread, fixed order: reproducible
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < nslots; ++i) s += slots[i];
-        *out = s;
-    }
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nslots; i += 32) s += slots[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *out = s;
 }
 
 template <typename T>
