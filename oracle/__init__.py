@@ -26,7 +26,7 @@ _SO = os.path.join(_BUILD, "liblbm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-EOS = {"vdw": 0, "cs": 1, "pr": 2, "rk": 3, "rks": 4}
+EOS = {"vdw": 0, "cs": 1, "pr": 2, "rk": 3, "rks": 4, "psi": 5}
 FORCE = {"sc": 0, "zc": 1}
 GRAD = {"hdm": 0, "cdm": 1}
 
@@ -54,7 +54,8 @@ class _Params(ctypes.Structure):
                 ("force", ctypes.c_int), ("grad", ctypes.c_int), ("pad", ctypes.c_int),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double),
                 ("omega", ctypes.c_double), ("T", ctypes.c_double), ("Tc", ctypes.c_double),
-                ("k", ctypes.c_double), ("tau", ctypes.c_double)]
+                ("k", ctypes.c_double), ("tau", ctypes.c_double), ("G", ctypes.c_double),
+                ("rho0", ctypes.c_double)]
 
 
 def _load():
@@ -115,10 +116,12 @@ class Params:
     tau: float = 1.0
     force: str = "sc"
     grad: str = "hdm"
+    G: float = 0.0       # eos "psi": interaction strength of Eq. 4
+    rho0: float = 1.0    # eos "psi": reference density of the effective mass
 
     def c(self) -> _Params:
         return _Params(self.nx, self.ny, EOS[self.eos], FORCE[self.force], GRAD[self.grad], 0,
-                       self.a, self.b, self.R, self.omega, self.T, self.Tc, self.k, self.tau)
+                       self.a, self.b, self.R, self.omega, self.T, self.Tc, self.k, self.tau, self.G, self.rho0)
 
 
 def critical_point(eos: str, a: float, b: float, R: float = 1.0):
@@ -135,6 +138,12 @@ def params_at(nx, ny, eos, a, b, Tr, *, R=1.0, omega=0.0, k=1.0, tau=1.0,
               force="sc", grad="hdm") -> Params:
     Tc, _ = critical_point(eos, a, b, R)
     return Params(nx, ny, eos, a, b, R, omega, Tr * Tc, Tc, k, tau, force, grad)
+
+
+def params_psi(nx, ny, G, *, rho0=1.0, tau=1.0, force="sc", grad="hdm") -> Params:
+    """The original Shan-Chen model (Eq. 4-5): effective mass psi = 1 - exp(-rho/rho0),
+    interaction strength G; no equation of state, temperature or Hu factor."""
+    return Params(nx, ny, "psi", tau=tau, force=force, grad=grad, G=G, rho0=rho0)
 
 
 def maxwell(p: Params):

@@ -34,13 +34,13 @@
 #include <omp.h>
 #endif
 
-enum { ORC_VDW = 0, ORC_CS = 1, ORC_PR = 2, ORC_RK = 3, ORC_RKS = 4 };
+enum { ORC_VDW = 0, ORC_CS = 1, ORC_PR = 2, ORC_RK = 3, ORC_RKS = 4, ORC_PSI = 5 };
 enum { ORC_SC = 0, ORC_ZC = 1 };
 enum { ORC_HDM = 0, ORC_CDM = 1 };
 
 typedef struct {
     int nx, ny;
-    int eos;      /* ORC_VDW .. ORC_RKS */
+    int eos;      /* ORC_VDW .. ORC_RKS, or ORC_PSI: the effective mass of Eq. 4 */
     int force;    /* ORC_SC (Eq. 22) or ORC_ZC (Eq. 7) */
     int grad;     /* ORC_HDM (Eq. 20) or ORC_CDM (Eq. 15) */
     int pad;
@@ -49,6 +49,8 @@ typedef struct {
     double Tc;    /* critical temperature (used by the alpha(T) of PR and RKS) */
     double k;     /* Hu scaling of the EOS, Sec. 5 */
     double tau;   /* BGK relaxation time, Eq. 1 */
+    double G;     /* ORC_PSI: interaction strength of Eq. 4 */
+    double rho0;  /* ORC_PSI: reference density of psi = 1 - exp(-rho/rho0) */
 } orc_params;
 
 /* D2Q9 velocity set and weights (Eq. 2 "D2Q9 model"; the paper does not print
@@ -144,6 +146,12 @@ static void eos_eval(int eos, double a, double b, double R, double T,
 }
 
 static void eos_at(const orc_params *q, double rho, double *p, double *dp) {
+    if (q->eos == ORC_PSI) {  /* Eq. 5: p = rho c_s^2 + (G/2) psi^2 */
+        double e = exp(-rho / q->rho0), psi = 1.0 - e;
+        if (p) *p = rho * CS2 + 0.5 * q->G * psi * psi;
+        if (dp) *dp = CS2 + q->G * psi * e / q->rho0;
+        return;
+    }
     double al = orc_alpha(q->eos, q->omega, q->T, q->Tc);
     eos_eval(q->eos, q->a, q->b, q->R, q->T, al, rho, p, dp);
 }
@@ -263,7 +271,8 @@ static double golden_extremum(const orc_params *q, double lo, double hi, int sig
 
 /* Returns 0 on success, 1 if the isotherm has no van der Waals loop. */
 int orc_maxwell(const orc_params *q, double *rho_g, double *rho_l, double *p_sat) {
-    double pole = rho_pole(q->eos, q->b);
+    /* Eq. 5 has no pole: p grows as rho/3 once psi saturates */
+    double pole = q->eos == ORC_PSI ? 50.0 * q->rho0 : rho_pole(q->eos, q->b);
     /* locate the spinodal maximum and minimum on a log grid */
     int N = 20000;
     double lmin = log(pole * 1e-14), lmax = log(pole * (1.0 - 1e-9));
@@ -415,22 +424,35 @@ void orc_cdm_grad(const double *q, double *gx, double *gy, int nx, int ny) {
 /*   SC (Eq. 22): Phi = sqrt|U| (Eq. 21), F = -2 s Phi grad Phi, s = sign of U */
 /*                at the cell (s = +1 for U >= 0)                             */
 /*   ZC (Eq. 7):  F = -grad U                                                  */
+/* With the effective mass psi = 1 - exp(-rho/rho0) (ORC_PSI):                */
+/*   SC (Eq. 4):  F = -G psi grad psi                                          */
+/*   ZC (Eq. 7):  F = -grad U, U = p - rho c_s^2 = (G/2) psi^2 (Eq. 5)         */
 /* ------------------------------------------------------------------------ */
 
 void orc_force(const orc_params *q, const double *rho, double *Fx, double *Fy) {
     size_t n = (size_t)q->nx * q->ny;
     double *U = (double *)malloc(sizeof(double) * n * 4);
     double *fld = U + n, *gx = fld + n, *gy = gx + n;
+    const int psi_mode = q->eos == ORC_PSI;
     for (size_t c = 0; c < n; ++c) {
-        double p;
-        eos_at(q, rho[c], &p, NULL);
-        U[c] = q->k * p - rho[c] * CS2;
-        fld[c] = (q->force == ORC_SC) ? sqrt(fabs(U[c])) : U[c];
+        if (psi_mode) {
+            double psi = 1.0 - exp(-rho[c] / q->rho0);
+            U[c] = 0.5 * q->G * psi * psi;
+            fld[c] = (q->force == ORC_SC) ? psi : U[c];
+        } else {
+            double p;
+            eos_at(q, rho[c], &p, NULL);
+            U[c] = q->k * p - rho[c] * CS2;
+            fld[c] = (q->force == ORC_SC) ? sqrt(fabs(U[c])) : U[c];
+        }
     }
     if (q->grad == ORC_HDM) orc_hdm_grad(fld, gx, gy, q->nx, q->ny);
     else orc_cdm_grad(fld, gx, gy, q->nx, q->ny);
     for (size_t c = 0; c < n; ++c) {
-        if (q->force == ORC_SC) {
+        if (q->force == ORC_SC && psi_mode) {
+            Fx[c] = -q->G * fld[c] * gx[c];
+            Fy[c] = -q->G * fld[c] * gy[c];
+        } else if (q->force == ORC_SC) {
             double s = U[c] >= 0.0 ? 1.0 : -1.0;
             Fx[c] = -2.0 * s * fld[c] * gx[c];
             Fy[c] = -2.0 * s * fld[c] * gy[c];
