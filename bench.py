@@ -446,7 +446,7 @@ def run_adjoint(args):
             torch.cuda.synchronize()
             a, b = ev(), ev()
             a.record(stream)
-            _, gtr = lat.adjoint_backward(gr.data_ptr(), g0.data_ptr())
+            _, gtr, _ = lat.adjoint_backward(gr.data_ptr(), g0.data_ptr())
             b.record(stream)
             b.synchronize()
             bwd_ms = a.elapsed_time(b)

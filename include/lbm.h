@@ -56,8 +56,18 @@ typedef enum {
 /* Equations of state (Sec. 5.2): van der Waals (Eq. 24), Carnahan-Starling
  * (Eq. 29, with the standard (1 - b rho/4)^3 denominator), Peng-Robinson
  * (Eq. 28), Redlich-Kwong with alpha = 1/sqrt(T) (Eq. 27) and its Soave form
- * (alpha(T) given after Eq. 27). */
-typedef enum { LBM_EOS_VDW = 0, LBM_EOS_CS = 1, LBM_EOS_PR = 2, LBM_EOS_RK = 3, LBM_EOS_RKS = 4 } lbm_eos;
+ * (alpha(T) given after Eq. 27).  LBM_EOS_PSI_EXP is the original Shan-Chen
+ * model instead (Eq. 4-5): effective mass psi = 1 - exp(-rho/rho0), force
+ * F = -G psi grad psi, pressure p = rho/3 + (G/2) psi^2; it has no
+ * temperature, critical point or Hu factor (Tr, Tc, a, b, R, omega, k unused). */
+typedef enum {
+    LBM_EOS_VDW = 0,
+    LBM_EOS_CS = 1,
+    LBM_EOS_PR = 2,
+    LBM_EOS_RK = 3,
+    LBM_EOS_RKS = 4,
+    LBM_EOS_PSI_EXP = 5
+} lbm_eos;
 /* Interaction form: Shan-Chen effective mass (Eq. 4 rewritten as Eq. 22) or
  * Zhang-Chen potential (Eq. 7 with U of Eq. 8). */
 typedef enum { LBM_FORCE_SC = 0, LBM_FORCE_ZC = 1 } lbm_force;
@@ -85,6 +95,9 @@ typedef struct {
     double k;        /* Hu scaling p = k p_EOS (Sec. 5; 0.01 VdW, 0.02 RK,
                         0.04 PR and CS in Sec. 5.2) */
     double tau;      /* BGK relaxation time (Eq. 1), > 0.5 */
+    double G;        /* LBM_EOS_PSI_EXP: interaction strength of Eq. 4, < 0
+                        (phase separation below G = -4 rho0 / 3) */
+    double rho0;     /* LBM_EOS_PSI_EXP: reference density of psi, > 0 */
     void *stream;    /* cudaStream_t for all work of this context, or NULL */
 } lbm_params;
 
@@ -119,7 +132,9 @@ lbm_status lbm_critical_point(int eos, double a, double b, double R, double *Tc,
 /* Coexistence densities of the Maxwell equal-area construction (Sec. 5.2) of
  * the unscaled EOS at T = p->Tr * Tc (Tc = p->Tc, or computed when 0), using
  * p->eos, a, b, R, omega; p_EOS(rho_g) = p_EOS(rho_l) and the p-v areas are
- * equal.  Host-only FP64.  LBM_E_INVALID when Tr >= 1 or there is no loop. */
+ * equal.  For LBM_EOS_PSI_EXP the same construction on the pressure of Eq. 5
+ * (p->G, p->rho0).  Host-only FP64.  LBM_E_INVALID when Tr >= 1 or there is
+ * no loop. */
 lbm_status lbm_maxwell(const lbm_params *p, double *rho_g, double *rho_l);
 
 /* Weights of the explicit form of the periodic HDM operator (Eq. 20): on a
@@ -167,7 +182,8 @@ lbm_status lbm_observables(lbm_ctx *c, lbm_obs *out);
 
 /* Reverse mode through nsteps steps, for gradients of a function of the final
  * density (e.g. the L2 distance to a target droplet) with respect to the
- * initial density and the temperature.  Not a passage of the paper: the
+ * initial density and the model's scalar parameter: the temperature, or the
+ * interaction strength G of LBM_EOS_PSI_EXP.  Not a passage of the paper: the
  * adjoint of its step (Eq. 1-3, 7/8, 10, 20-22).
  * lbm_adjoint_forward: f = f^eq(rho0, 0) (Eq. 2) from the device array rho0,
  *   nsteps steps (Eq. 1), density of the final state into the device array
@@ -175,13 +191,17 @@ lbm_status lbm_observables(lbm_ctx *c, lbm_obs *out);
  *   (checkpoint_interval = ceil(sqrt(nsteps)) gives sqrt(N) checkpointing, 1
  *   keeps every state).  The context is left on the final state.
  * lbm_adjoint_backward: from dL/drho_T (device array) writes dL/drho0 (device
- *   array) and dL/dT, dL/d(T/Tc) (host doubles, may be NULL), recomputing the
- *   states between checkpoints with the same kernels and running the adjoint
- *   step backwards; dL/dT is accumulated in FP64.  Synchronising.
- * All device arrays hold nx*ny values of the context precision.  The
- * interaction strength G of Eq. 4/6 cancels from Eq. 22, so dL/dG = 0. */
+ *   array) and dL/dT, dL/d(T/Tc), dL/dG (host doubles, each may be NULL),
+ *   recomputing the states between checkpoints with the same kernels and
+ *   running the adjoint step backwards; the scalar gradient is accumulated in
+ *   FP64.  Synchronising.
+ * All device arrays hold nx*ny values of the context precision.  With an
+ * equation of state the interaction strength G of Eq. 4/6 cancels from
+ * Eq. 22, so dL/dG = 0; with LBM_EOS_PSI_EXP there is no temperature, so
+ * dL/dT = dL/d(T/Tc) = 0 and dL/dG is live. */
 lbm_status lbm_adjoint_forward(lbm_ctx *c, const void *rho0, int nsteps, int checkpoint_interval, void *rho_T);
-lbm_status lbm_adjoint_backward(lbm_ctx *c, const void *grad_rho_T, void *grad_rho0, double *grad_T, double *grad_Tr);
+lbm_status lbm_adjoint_backward(lbm_ctx *c, const void *grad_rho_T, void *grad_rho0, double *grad_T, double *grad_Tr,
+                                double *grad_G);
 
 /* Launch shape of the single-pass FP32 step (not a passage of the paper): a
  * CTA sweeps `rows` rows of a 120-column strip.  0 (the default) picks the

@@ -21,7 +21,9 @@
 // transpose is its negative),
 //   Phi_bar = Phi_bar_centre - Dx[Dx_bar] - Dy[Dy_bar]
 //   U_bar = Phi_bar s / (2 Phi) (SC) or Phi_bar (ZC)
-//   rho_bar += U_bar (k dp/drho - 1/3),  T_bar += U_bar k dp/dT
+//   rho_bar += U_bar dU/drho,  T_bar += U_bar dU/dtheta
+// with theta = T for an equation of state (dU/dT = k dp/dT) and theta = G for
+// the effective mass of Eq. 4 (dU/dG = psi^2 / 2).
 //   lambda_i(t) = (1 - omega) g_i + rho_bar + e_i . j_bar.
 //
 // Two tiled kernels per step.  Kernel A stages the stencil field of the
@@ -62,13 +64,22 @@ __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rsqrt_fast(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_fast(double x) { return 1.0 / sqrt(x); }
 
-// U = k p_EOS - rho/3 (Eq. 8) with dp_EOS/drho and dp_EOS/dT at the model
-// temperature (Eq. 24, 27-29); m.RT = R T, m.aal = a alpha(T), aalp =
-// a dalpha/dT, R the gas constant.  Reciprocals by the fast FP32 form (the
+// U (Eq. 8) with its derivatives in rho and in the model's scalar parameter
+// theta: with an equation of state U = k p_EOS - rho/3 and theta = T (Eq. 24,
+// 27-29; m.RT = R T, m.aal = a alpha(T), aalp = a dalpha/dT, R the gas
+// constant); with the effective mass of Eq. 4 U = (G/2) psi^2 (Eq. 5, m.a =
+// G/2, m.b = 1/rho0) and theta = G.  Reciprocals by the fast FP32 form (the
 // denominators are positive and well scaled).
 template <typename T>
-__device__ __forceinline__ void eos_derivs(const Model<T> &m, T R, T aalp, T rho, T &U, T &dpdr, T &dpdT) {
-    T p;
+__device__ __forceinline__ void eos_derivs(const Model<T> &m, T R, T aalp, T rho, T &U, T &dUdr, T &dUdth) {
+    if (m.eos == LBM_EOS_PSI_EXP) {
+        const T e = exp(-rho * m.b), psi = T(1) - e;
+        U = m.a * psi * psi;
+        dUdr = T(2) * m.a * psi * e * m.b;
+        dUdth = T(0.5) * psi * psi;
+        return;
+    }
+    T p, dpdr, dpdT;
     if (m.eos == LBM_EOS_CS) {
         const T e = m.b * rho * T(0.25);
         const T om = T(1) - e;
@@ -101,23 +112,25 @@ __device__ __forceinline__ void eos_derivs(const Model<T> &m, T R, T aalp, T rho
         }
     }
     U = m.k * p - rho * T(1.0 / 3.0);
+    dUdr = m.k * dpdr - T(1.0 / 3.0);
+    dUdth = m.k * dpdT;
 }
 
-// kappa = dPhi/dU (k dp/drho - 1/3) and theta = dPhi/dU k dp/dT at density
-// rho, with dPhi/dU = s / (2 Phi) for the Shan-Chen field and 1 for
-// Zhang-Chen; sgn = s.
+// kappa = dPhi/dU dU/drho and theta = dPhi/dU dU/dtheta at density rho, with
+// dPhi/dU = s / (2 Phi) for the Shan-Chen field and 1 for Zhang-Chen;
+// sgn = s.
 template <typename T, bool SC>
 __device__ __forceinline__ void eos_coeffs(const Model<T> &m, T R, T aalp, T rho, T &kappa, T &theta, T &sgn) {
-    T U, dpdr, dpdT;
-    eos_derivs(m, R, aalp, rho, U, dpdr, dpdT);
+    T U, dUdr, dUdth;
+    eos_derivs(m, R, aalp, rho, U, dUdr, dUdth);
     T d = T(1);
     sgn = U >= T(0) ? T(1) : T(-1);
     if (SC) {
         const T aU = fabs(U);
         d = aU > T(0) ? T(0.5) * sgn * rsqrt_fast(aU) : T(0);
     }
-    kappa = d * (m.k * dpdr - T(1.0 / 3.0));
-    theta = d * m.k * dpdT;
+    kappa = d * dUdr;
+    theta = d * dUdth;
 }
 
 template <typename T>

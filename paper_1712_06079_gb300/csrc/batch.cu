@@ -287,24 +287,6 @@ lbm_status bfail(lbm_batch *b, lbm_status st, const std::string &m) {
         if (e_ != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-double alpha_b(const lbm_params &p, double T, double Tc) {
-    double m, s;
-    switch (p.eos) {
-    case LBM_EOS_PR:
-        m = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
-        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
-        return s * s;
-    case LBM_EOS_RKS:
-        m = 0.480 + 1.574 * p.omega - 0.176 * p.omega * p.omega;
-        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
-        return s * s;
-    case LBM_EOS_RK:
-        return 1.0 / std::sqrt(T);
-    default:
-        return 1.0;
-    }
-}
-
 template <typename T>
 lbm_status build_instances(lbm_batch *b, std::vector<Inst<T>> &out) {
     out.resize(b->n);
@@ -312,18 +294,17 @@ lbm_status build_instances(lbm_batch *b, std::vector<Inst<T>> &out) {
         const lbm_params &p = b->params[i];
         Inst<T> &I = out[i];
         I = Inst<T>{};
-        double Tc = p.Tc, rc = 0;
-        if (!(Tc > 0) && lbm_critical_point(p.eos, p.a, p.b, p.R, &Tc, &rc) != LBM_OK)
+        ModelScalars ms;
+        if (model_scalars(p, &ms) != LBM_OK)
             return bfail(b, LBM_E_INVALID, "no critical point for instance " + std::to_string(i));
-        const double Temp = p.Tr * Tc;
         I.m.nx = p.nx;
         I.m.ny = p.ny;
         I.m.eos = p.eos;
-        I.m.RT = (T)(p.R * Temp);
-        I.m.a = (T)p.a;
-        I.m.b = (T)p.b;
-        I.m.aal = (T)(p.a * alpha_b(p, Temp, Tc));
-        I.m.k = (T)p.k;
+        I.m.RT = (T)ms.RT;
+        I.m.a = (T)ms.a;
+        I.m.b = (T)ms.b;
+        I.m.aal = (T)ms.aal;
+        I.m.k = (T)ms.k;
         I.m.omega = (T)(1.0 / p.tau);
         const int radius = p.hdm_radius ? p.hdm_radius : (b->prec == LBM_F64 ? 40 : 26);
         double wx[kMaxRadius + 1] = {}, wy[kMaxRadius + 1] = {};
@@ -462,10 +443,8 @@ lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out) {
     if (prec != LBM_F32 && prec != LBM_F64) return LBM_E_INVALID;
     for (int i = 0; i < n; ++i) {
         const lbm_params &q = p[i];
-        if (q.prec != prec || q.nx < 1 || q.ny < 1 || q.eos < LBM_EOS_VDW || q.eos > LBM_EOS_RKS ||
-            (q.force != LBM_FORCE_SC && q.force != LBM_FORCE_ZC) || (q.grad != LBM_GRAD_HDM && q.grad != LBM_GRAD_CDM) ||
-            q.hdm_radius < 0 || q.hdm_radius > kMaxRadius || !(q.a >= 0) || !(q.b > 0) || !(q.R > 0) || !(q.Tr > 0) ||
-            !(q.tau > 0.5) || (long long)q.nx * q.ny > (1LL << 30))
+        const char *why = "";
+        if (q.prec != prec || check_params(q, &why) != LBM_OK || (long long)q.nx * q.ny > (1LL << 30))
             return LBM_E_INVALID;
     }
     lbm_batch *b = new (std::nothrow) lbm_batch();

@@ -109,10 +109,15 @@ __device__ __forceinline__ float stencil_field(const Model<float> &m, float rho,
 }
 
 // U = k p_EOS - rho/3 (Eq. 8) with the equation of state fixed at compile time
-// (VdW Eq. 24, CS Eq. 29, PR Eq. 28, RK/RKS Eq. 27); quotients by the fast
-// FP32 reciprocal (2 ulp), the denominators being positive and well scaled.
+// (VdW Eq. 24, CS Eq. 29, PR Eq. 28, RK/RKS Eq. 27), or (G/2) psi^2 for the
+// effective mass of Eq. 4; quotients by the fast FP32 reciprocal (2 ulp), the
+// denominators being positive and well scaled.
 template <int EOS>
 __device__ __forceinline__ float potential_u_t(const Model<float> &m, float rho) {
+    if (EOS == LBM_EOS_PSI_EXP) {  // U = (G/2) psi^2, psi = 1 - exp(-rho/rho0) (Eq. 4-5)
+        const float psi = 1.0f - expf(-rho * m.b);
+        return m.a * psi * psi;
+    }
     float p;
     if (EOS == LBM_EOS_CS) {
         const float e = m.b * rho * 0.25f;
@@ -492,6 +497,7 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     case LBM_EOS_CS: LBM_PICK(LBM_EOS_CS); break;
     case LBM_EOS_PR: LBM_PICK(LBM_EOS_PR); break;
     case LBM_EOS_RK: LBM_PICK(LBM_EOS_RK); break;
+    case LBM_EOS_PSI_EXP: LBM_PICK(LBM_EOS_PSI_EXP); break;
     default: LBM_PICK(LBM_EOS_RKS); break;
     }
 #undef LBM_PICK

@@ -108,8 +108,18 @@ void eos_p(int eos, double a, double b, double R, double T, double alpha, double
 struct Isotherm {
     int eos;
     double a, b, R, T, alpha;
-    double p(double rho) const { double v, d; eos_p(eos, a, b, R, T, alpha, rho, &v, &d); return v; }
-    double dp(double rho) const { double v, d; eos_p(eos, a, b, R, T, alpha, rho, &v, &d); return d; }
+    double G = 0, rho0 = 1;  // LBM_EOS_PSI_EXP: p = rho/3 + (G/2) psi^2, psi = 1 - exp(-rho/rho0) (Eq. 5)
+    void eval(double rho, double *v, double *d) const {
+        if (eos == LBM_EOS_PSI_EXP) {
+            const double e = std::exp(-rho / rho0), psi = 1.0 - e;
+            *v = rho / 3.0 + 0.5 * G * psi * psi;
+            *d = 1.0 / 3.0 + G * psi * e / rho0;
+            return;
+        }
+        eos_p(eos, a, b, R, T, alpha, rho, v, d);
+    }
+    double p(double rho) const { double v, d; eval(rho, &v, &d); return v; }
+    double dp(double rho) const { double v, d; eval(rho, &v, &d); return d; }
 };
 
 // Root of dp/drho = 0 in [lo, hi] (dp changes sign there), by bisection.
@@ -161,13 +171,24 @@ double area(const Isotherm &I, double ps, double rg, double rl) {
 }  // namespace
 
 extern "C" lbm_status lbm_maxwell(const lbm_params *p, double *rho_g, double *rho_l) {
-    if (!p || !rho_g || !rho_l || p->eos < LBM_EOS_VDW || p->eos > LBM_EOS_RKS || !(p->a > 0) || !(p->b > 0) ||
-        !(p->R > 0) || !(p->Tr > 0))
-        return LBM_E_INVALID;
-    double Tc = p->Tc, rc = 0;
-    if (!(Tc > 0) && lbm_critical_point(p->eos, p->a, p->b, p->R, &Tc, &rc) != LBM_OK) return LBM_E_INVALID;
-    if (!(p->Tr < 1.0)) return LBM_E_INVALID;
-    Isotherm I{p->eos, p->a, p->b, p->R, p->Tr * Tc, 1.0};
+    if (!p || !rho_g || !rho_l) return LBM_E_INVALID;
+    Isotherm I{p->eos, p->a, p->b, p->R, 0.0, 1.0};
+    double pole;
+    if (p->eos == LBM_EOS_PSI_EXP) {
+        if (!(p->G < 0) || !(p->rho0 > 0) || !std::isfinite(p->G)) return LBM_E_INVALID;
+        I.G = p->G;
+        I.rho0 = p->rho0;
+        pole = 50.0 * p->rho0;  // no pole: psi saturates and p grows as rho/3
+    } else {
+        if (p->eos < LBM_EOS_VDW || p->eos > LBM_EOS_RKS || !(p->a > 0) || !(p->b > 0) || !(p->R > 0) ||
+            !(p->Tr > 0))
+            return LBM_E_INVALID;
+        double Tc = p->Tc, rc = 0;
+        if (!(Tc > 0) && lbm_critical_point(p->eos, p->a, p->b, p->R, &Tc, &rc) != LBM_OK) return LBM_E_INVALID;
+        if (!(p->Tr < 1.0)) return LBM_E_INVALID;
+        I.T = p->Tr * Tc;
+        pole = (p->eos == LBM_EOS_CS) ? 4.0 / p->b : 1.0 / p->b;
+    }
     if (p->eos == LBM_EOS_RK) I.alpha = 1.0 / std::sqrt(I.T);
     else if (p->eos == LBM_EOS_PR || p->eos == LBM_EOS_RKS) {
         const double w = p->omega;
@@ -175,7 +196,6 @@ extern "C" lbm_status lbm_maxwell(const lbm_params *p, double *rho_g, double *rh
         const double s = 1.0 + m * (1.0 - std::sqrt(p->Tr));
         I.alpha = s * s;
     }
-    const double pole = (p->eos == LBM_EOS_CS) ? 4.0 / p->b : 1.0 / p->b;
     // the isotherm's local maximum and minimum: sign changes of dp/drho on a log grid
     const int N = 4000;
     double prev = I.dp(pole * 1e-12), lo_prev = pole * 1e-12, smax = -1, smin = -1;

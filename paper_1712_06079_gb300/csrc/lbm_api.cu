@@ -13,9 +13,78 @@
 
 using namespace lbm;
 
+namespace lbm {
+
+lbm_status check_params(const lbm_params &p, const char **why) {
+    auto bad = [&](const char *w) {
+        *why = w;
+        return LBM_E_INVALID;
+    };
+    if (p.nx < 1 || p.ny < 1) return bad("nx, ny must be >= 1");
+    if ((long long)p.nx * p.ny > (1LL << 31)) return bad("lattice larger than 2^31 cells");
+    if (p.prec != LBM_F32 && p.prec != LBM_F64) return bad("prec must be LBM_F32 or LBM_F64");
+    if (p.eos < LBM_EOS_VDW || p.eos > LBM_EOS_PSI_EXP) return bad("unknown eos");
+    if (p.force != LBM_FORCE_SC && p.force != LBM_FORCE_ZC) return bad("unknown force form");
+    if (p.grad != LBM_GRAD_HDM && p.grad != LBM_GRAD_CDM) return bad("unknown gradient");
+    if (p.hdm_radius < 0 || p.hdm_radius > kMaxRadius) return bad("hdm_radius must be in [0, 48]");
+    if (p.flags & ~LBM_FLAG_TWO_PASS) return bad("unknown flags");
+    if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return bad("tau must be > 0.5");
+    if (p.eos == LBM_EOS_PSI_EXP) {
+        if (!std::isfinite(p.G) || p.G == 0.0) return bad("G must be finite and non-zero");
+        if (!(p.rho0 > 0) || !std::isfinite(p.rho0)) return bad("rho0 must be > 0");
+        return LBM_OK;
+    }
+    if (!(p.a >= 0) || !(p.b > 0) || !(p.R > 0)) return bad("need a >= 0, b > 0, R > 0");
+    if (!(p.Tr > 0) || !std::isfinite(p.Tr)) return bad("Tr must be > 0");
+    if (!std::isfinite(p.k) || !std::isfinite(p.omega)) return bad("k, omega must be finite");
+    return LBM_OK;
+}
+
+lbm_status model_scalars(const lbm_params &p, ModelScalars *s) {
+    *s = ModelScalars{};
+    if (p.eos == LBM_EOS_PSI_EXP) {  // Eq. 4-5
+        s->a = 0.5 * p.G;
+        s->b = 1.0 / p.rho0;
+        s->k = 1.0;
+        return LBM_OK;
+    }
+    double Tc = p.Tc, rc = 0;
+    if (!(Tc > 0) && (p.a <= 0 || lbm_critical_point(p.eos, p.a, p.b, p.R, &Tc, &rc) != LBM_OK))
+        return LBM_E_INVALID;
+    const double T = p.Tr * Tc;
+    double alpha = 1.0, dalpha = 0.0, m, q;
+    switch (p.eos) {
+    case LBM_EOS_PR:   // alpha = (1 + m (1 - sqrt(T/Tc)))^2, Eq. 28
+    case LBM_EOS_RKS:  // the Soave form after Eq. 27
+        m = p.eos == LBM_EOS_PR ? 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega
+                                : 0.480 + 1.574 * p.omega - 0.176 * p.omega * p.omega;
+        q = 1.0 + m * (1.0 - std::sqrt(T / Tc));
+        alpha = q * q;
+        dalpha = -q * m / std::sqrt(T * Tc);
+        break;
+    case LBM_EOS_RK:  // alpha = T^-1/2, Eq. 27
+        alpha = 1.0 / std::sqrt(T);
+        dalpha = -0.5 / (T * std::sqrt(T));
+        break;
+    default:
+        break;
+    }
+    s->T = T;
+    s->Tc = Tc;
+    s->a = p.a;
+    s->b = p.b;
+    s->aal = p.a * alpha;
+    s->aalp = p.a * dalpha;
+    s->k = p.k;
+    s->RT = p.R * T;
+    return LBM_OK;
+}
+
+}  // namespace lbm
+
 struct lbm_ctx {
     lbm_params p{};
-    double T = 0, Tc = 0, alpha = 1;
+    ModelScalars ms{};              // host scalars of p (temperature, EOS constants)
     int kx = 0, ky = 0;
     double wx[kMaxRadius + 1] = {}, wy[kMaxRadius + 1] = {};
     size_t esz = 4;               // bytes per value (float or double)
@@ -83,24 +152,6 @@ lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
-double alpha_of(const lbm_params &p, double T, double Tc) {
-    double m, s;
-    switch (p.eos) {
-    case LBM_EOS_PR:  // Eq. 28
-        m = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
-        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
-        return s * s;
-    case LBM_EOS_RKS:  // Soave form after Eq. 27
-        m = 0.480 + 1.574 * p.omega - 0.176 * p.omega * p.omega;
-        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
-        return s * s;
-    case LBM_EOS_RK:  // Eq. 27
-        return 1.0 / std::sqrt(T);
-    default:
-        return 1.0;
-    }
-}
-
 template <typename T>
 Model<T> model_of(const lbm_ctx *c) {
     Model<T> m{};
@@ -109,11 +160,11 @@ Model<T> model_of(const lbm_ctx *c) {
     m.eos = c->p.eos;
     m.kx = c->kx;
     m.ky = c->ky;
-    m.RT = (T)(c->p.R * c->T);
-    m.a = (T)c->p.a;
-    m.b = (T)c->p.b;
-    m.aal = (T)(c->p.a * c->alpha);
-    m.k = (T)c->p.k;
+    m.RT = (T)c->ms.RT;
+    m.a = (T)c->ms.a;
+    m.b = (T)c->ms.b;
+    m.aal = (T)c->ms.aal;
+    m.k = (T)c->ms.k;
     m.omega = (T)(1.0 / c->p.tau);
     for (int j = 0; j <= kMaxRadius; ++j) {
         m.wx[j] = (T)c->wx[j];
@@ -289,24 +340,6 @@ void free_tape(lbm_ctx *c) {
     c->tape_steps = -1;
 }
 
-double dalpha_dT(const lbm_params &p, double T, double Tc) {
-    double m, s;
-    switch (p.eos) {
-    case LBM_EOS_PR:  // alpha = (1 + m (1 - sqrt(T/Tc)))^2, Eq. 28
-        m = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
-        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
-        return -s * m / std::sqrt(T * Tc);
-    case LBM_EOS_RKS:
-        m = 0.480 + 1.574 * p.omega - 0.176 * p.omega * p.omega;
-        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
-        return -s * m / std::sqrt(T * Tc);
-    case LBM_EOS_RK:  // alpha = T^-1/2, Eq. 27
-        return -0.5 / (T * std::sqrt(T));
-    default:
-        return 0.0;
-    }
-}
-
 // One forward step from state `src` to `dst` (explicit buffers); qsrc/qdst are
 // the padded potential fields of the single-pass path (qsrc valid on entry).
 template <typename T>
@@ -399,7 +432,7 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     const int N = c->tape_steps, C = c->tape_C;
     const int nx = c->p.nx, ny = c->p.ny;
     Model<T> m = model_of<T>(c);
-    const T R = (T)c->p.R, aalp = (T)(c->p.a * dalpha_dT(c->p, c->T, c->Tc));
+    const T R = (T)c->p.R, aalp = (T)c->ms.aalp;
     const bool tau1 = m.omega == T(1);
     const AdjLayout lay = adjoint_layout(nx, ny, c->fused, tau1);
     // stencil fields: the single-pass layout (padded rows) or the plain one
@@ -467,7 +500,8 @@ lbm_status lbm_adjoint_forward(lbm_ctx *c, const void *rho0, int nsteps, int che
                      : tape_forward<float>(c, (const float *)rho0, nsteps, checkpoint_interval, (float *)rho_T);
 }
 
-lbm_status lbm_adjoint_backward(lbm_ctx *c, const void *grad_rho_T, void *grad_rho0, double *grad_T, double *grad_Tr) {
+lbm_status lbm_adjoint_backward(lbm_ctx *c, const void *grad_rho_T, void *grad_rho0, double *grad_T, double *grad_Tr,
+                                double *grad_G) {
     if (!c) return LBM_E_INVALID;
     if (c->tape_steps < 1) return fail(c, LBM_E_STATE, "no tape: call lbm_adjoint_forward first");
     if (!grad_rho_T || !grad_rho0) return fail(c, LBM_E_INVALID, "grad arrays must be device arrays");
@@ -475,8 +509,11 @@ lbm_status lbm_adjoint_backward(lbm_ctx *c, const void *grad_rho_T, void *grad_r
     lbm_status st = is_f64(c) ? tape_backward<double>(c, (const double *)grad_rho_T, (double *)grad_rho0, &gT)
                               : tape_backward<float>(c, (const float *)grad_rho_T, (float *)grad_rho0, &gT);
     if (st != LBM_OK) return st;
-    if (grad_T) *grad_T = gT;
-    if (grad_Tr) *grad_Tr = gT * c->Tc;  // T = Tr Tc
+    // the accumulated scalar is dL/dG for the effective mass of Eq. 4, else dL/dT
+    const bool psi = c->p.eos == LBM_EOS_PSI_EXP;
+    if (grad_T) *grad_T = psi ? 0.0 : gT;
+    if (grad_Tr) *grad_Tr = psi ? 0.0 : gT * c->ms.Tc;  // T = Tr Tc
+    if (grad_G) *grad_G = psi ? gT : 0.0;
     return LBM_OK;
 }
 
@@ -484,19 +521,11 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if (!out) return fail(nullptr, LBM_E_INVALID, "out is NULL");
     *out = nullptr;
     if (!p) return fail(nullptr, LBM_E_INVALID, "params is NULL");
-    if (p->nx < 1 || p->ny < 1) return fail(nullptr, LBM_E_INVALID, "nx, ny must be >= 1 (got %d, %d)", p->nx, p->ny);
-    if ((long long)p->nx * p->ny > (1LL << 31)) return fail(nullptr, LBM_E_INVALID, "lattice larger than 2^31 cells");
-    if (p->prec != LBM_F32 && p->prec != LBM_F64) return fail(nullptr, LBM_E_INVALID, "prec must be LBM_F32 or LBM_F64");
-    if (p->eos < LBM_EOS_VDW || p->eos > LBM_EOS_RKS) return fail(nullptr, LBM_E_INVALID, "unknown eos %d", p->eos);
-    if (p->force != LBM_FORCE_SC && p->force != LBM_FORCE_ZC) return fail(nullptr, LBM_E_INVALID, "unknown force form");
-    if (p->grad != LBM_GRAD_HDM && p->grad != LBM_GRAD_CDM) return fail(nullptr, LBM_E_INVALID, "unknown gradient");
-    if (p->hdm_radius < 0 || p->hdm_radius > kMaxRadius)
-        return fail(nullptr, LBM_E_INVALID, "hdm_radius must be in [0, %d]", kMaxRadius);
-    if (p->flags & ~LBM_FLAG_TWO_PASS) return fail(nullptr, LBM_E_INVALID, "unknown flags 0x%x", p->flags);
-    if (!(p->a >= 0) || !(p->b > 0) || !(p->R > 0)) return fail(nullptr, LBM_E_INVALID, "need a >= 0, b > 0, R > 0");
-    if (!(p->Tr > 0) || !std::isfinite(p->Tr)) return fail(nullptr, LBM_E_INVALID, "Tr must be > 0");
-    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(nullptr, LBM_E_INVALID, "tau must be > 0.5");
-    if (!std::isfinite(p->k) || !std::isfinite(p->omega)) return fail(nullptr, LBM_E_INVALID, "k, omega must be finite");
+    const char *why = "";
+    if (check_params(*p, &why) != LBM_OK) return fail(nullptr, LBM_E_INVALID, "%s", why);
+    ModelScalars ms;
+    if (model_scalars(*p, &ms) != LBM_OK)
+        return fail(nullptr, LBM_E_INVALID, "no critical point for these EOS constants; pass Tc explicitly");
 
     lbm_ctx *c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(nullptr, LBM_E_NOMEM, "host allocation failed");
@@ -504,17 +533,7 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     c->stream = (cudaStream_t)p->stream;
     c->esz = p->prec == LBM_F64 ? sizeof(double) : sizeof(float);
     c->n = (long long)p->nx * p->ny;
-    if (p->Tc > 0) {
-        c->Tc = p->Tc;
-    } else {
-        double rc;
-        if (p->a <= 0 || lbm_critical_point(p->eos, p->a, p->b, p->R, &c->Tc, &rc) != LBM_OK) {
-            delete c;
-            return fail(nullptr, LBM_E_INVALID, "no critical point for these EOS constants; pass Tc explicitly");
-        }
-    }
-    c->T = p->Tr * c->Tc;
-    c->alpha = alpha_of(*p, c->T, c->Tc);
+    c->ms = ms;
     int radius = p->hdm_radius ? p->hdm_radius : (p->prec == LBM_F64 ? 40 : 26);
     lbm_hdm_weights(p->nx, radius, c->wx, &c->kx);
     lbm_hdm_weights(p->ny, radius, c->wy, &c->ky);

@@ -39,7 +39,7 @@ struct Model {
     int eos;       // lbm_eos
     int kx, ky;    // HDM stencil radius along x and y (already folded to the period)
     T RT;          // R * T
-    T a, b;
+    T a, b;        // EOS constants; for LBM_EOS_PSI_EXP a = G/2, b = 1/rho0 (Eq. 4-5)
     T aal;         // a * alpha(T) (PR, RK, RKS)
     T k;           // Hu scaling
     T omega;       // 1 / tau
@@ -61,9 +61,16 @@ __device__ __forceinline__ T p_eos(const Model<T> &m, T rho) {
     return rep - m.aal * rho * rho / (T(1) + m.b * rho);  // RK, RKS
 }
 
-// Interaction potential U = k p_EOS - rho c_s^2 (Eq. 8 with Hu scaling).
+// Interaction potential U = k p_EOS - rho c_s^2 (Eq. 8 with Hu scaling); for
+// the effective mass of Eq. 4 (a = G/2, b = 1/rho0) U = p - rho c_s^2 =
+// (G/2) psi^2 (Eq. 5), so the Eq. 22 form -2 s Phi grad Phi with
+// Phi = sqrt|U| is the force -G psi grad psi of Eq. 4.
 template <typename T>
 __device__ __forceinline__ T potential_u(const Model<T> &m, T rho) {
+    if (m.eos == LBM_EOS_PSI_EXP) {
+        const T psi = T(1) - exp(-rho * m.b);
+        return m.a * psi * psi;
+    }
     return m.k * p_eos(m, rho) - rho * T(1.0 / 3.0);
 }
 

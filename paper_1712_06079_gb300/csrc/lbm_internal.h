@@ -7,6 +7,19 @@
 
 namespace lbm {
 
+// Host-side scalars of a parameter set.  With an equation of state: T = Tr Tc
+// (Tc = p.Tc, or from lbm_critical_point), a, b, a alpha(T) and its
+// T-derivative (Eq. 27, 28), k, R T.  With the effective mass of Eq. 4
+// (LBM_EOS_PSI_EXP): a = G/2, b = 1/rho0, k = 1, the rest 0 -- the device
+// potential is then U = a (1 - exp(-b rho))^2 (Eq. 5 minus rho c_s^2).
+struct ModelScalars {
+    double T, Tc, a, b, aal, aalp, k, RT;
+};
+// Range checks of a parameter set shared by every entry point; returns
+// LBM_E_INVALID with a reason in *why.
+lbm_status check_params(const lbm_params &p, const char **why);
+lbm_status model_scalars(const lbm_params &p, ModelScalars *s);
+
 // f = f^eq(rho, u) (Eq. 2); ux/uy may be null (zero velocity).
 template <typename T>
 cudaError_t launch_init(const Model<T> &m, const T *rho, const T *ux, const T *uy, T *f, cudaStream_t s);

@@ -42,37 +42,18 @@ lbm_status scratch_on_current_device(void **out) {
     return LBM_OK;
 }
 
-double alpha_at(const lbm_params &p, double T, double Tc) {
-    double m, s;
-    switch (p.eos) {
-    case LBM_EOS_PR:  // Eq. 28
-        m = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
-        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
-        return s * s;
-    case LBM_EOS_RKS:
-        m = 0.480 + 1.574 * p.omega - 0.176 * p.omega * p.omega;
-        s = 1.0 + m * (1.0 - std::sqrt(T / Tc));
-        return s * s;
-    case LBM_EOS_RK:  // Eq. 27
-        return 1.0 / std::sqrt(T);
-    default:
-        return 1.0;
-    }
-}
-
 template <typename T>
-lbm_status run_step(const lbm_params &p, double Tc, const void *f_in, void *f_out, void *scratch) {
+lbm_status run_step(const lbm_params &p, const lbm::ModelScalars &ms, const void *f_in, void *f_out, void *scratch) {
     using namespace lbm;
     Model<T> m{};
     m.nx = p.nx;
     m.ny = p.ny;
     m.eos = p.eos;
-    const double Temp = p.Tr * Tc;
-    m.RT = (T)(p.R * Temp);
-    m.a = (T)p.a;
-    m.b = (T)p.b;
-    m.aal = (T)(p.a * alpha_at(p, Temp, Tc));
-    m.k = (T)p.k;
+    m.RT = (T)ms.RT;
+    m.a = (T)ms.a;
+    m.b = (T)ms.b;
+    m.aal = (T)ms.aal;
+    m.k = (T)ms.k;
     m.omega = (T)(1.0 / p.tau);
     const int radius = p.hdm_radius ? p.hdm_radius : (p.prec == LBM_F64 ? 40 : 26);
     double wx[kMaxRadius + 1] = {}, wy[kMaxRadius + 1] = {};
@@ -106,20 +87,14 @@ long long max_cells(int prec) {
 
 extern "C" lbm_status lbm_step_noalloc(const lbm_params *p, const void *f_in, void *f_out) {
     if (!p || !f_in || !f_out || f_in == f_out) return LBM_E_INVALID;
-    if (p->nx < 1 || p->ny < 1 || (p->prec != LBM_F32 && p->prec != LBM_F64)) return LBM_E_INVALID;
-    if (p->eos < LBM_EOS_VDW || p->eos > LBM_EOS_RKS || (p->force != LBM_FORCE_SC && p->force != LBM_FORCE_ZC) ||
-        (p->grad != LBM_GRAD_HDM && p->grad != LBM_GRAD_CDM))
-        return LBM_E_INVALID;
-    if (p->hdm_radius < 0 || p->hdm_radius > lbm::kMaxRadius || p->flags & ~LBM_FLAG_TWO_PASS) return LBM_E_INVALID;
-    if (!(p->a >= 0) || !(p->b > 0) || !(p->R > 0) || !(p->Tr > 0) || !(p->tau > 0.5) || !std::isfinite(p->k))
-        return LBM_E_INVALID;
+    const char *why = "";
+    if (lbm::check_params(*p, &why) != LBM_OK) return LBM_E_INVALID;
     if ((long long)p->nx * p->ny > max_cells(p->prec)) return LBM_E_INVALID;
-    double Tc = p->Tc, rc = 0;
-    if (!(Tc > 0) && (p->a <= 0 || lbm_critical_point(p->eos, p->a, p->b, p->R, &Tc, &rc) != LBM_OK))
-        return LBM_E_INVALID;
+    lbm::ModelScalars ms;
+    if (lbm::model_scalars(*p, &ms) != LBM_OK) return LBM_E_INVALID;
     void *scratch = nullptr;
     lbm_status st = scratch_on_current_device(&scratch);
     if (st != LBM_OK) return st;
-    return p->prec == LBM_F64 ? run_step<double>(*p, Tc, f_in, f_out, scratch)
-                              : run_step<float>(*p, Tc, f_in, f_out, scratch);
+    return p->prec == LBM_F64 ? run_step<double>(*p, ms, f_in, f_out, scratch)
+                              : run_step<float>(*p, ms, f_in, f_out, scratch);
 }

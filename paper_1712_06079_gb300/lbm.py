@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 OK, E_INVALID, E_NOMEM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE = range(7)
-EOS = {"vdw": 0, "cs": 1, "pr": 2, "rk": 3, "rks": 4}
+EOS = {"vdw": 0, "cs": 1, "pr": 2, "rk": 3, "rks": 4, "psi_exp": 5}
 FORCE = {"sc": 0, "zc": 1}
 GRAD = {"hdm": 0, "cdm": 1}
 PREC = {"f32": 0, "f64": 1}
@@ -38,7 +38,7 @@ class _Params(ctypes.Structure):
                 ("flags", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double),
                 ("R", ctypes.c_double), ("omega", ctypes.c_double), ("Tr", ctypes.c_double),
                 ("Tc", ctypes.c_double), ("k", ctypes.c_double), ("tau", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("G", ctypes.c_double), ("rho0", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class _Obs(ctypes.Structure):
@@ -77,7 +77,7 @@ SIGNATURES = {
     "lbm_adjoint_forward": (ctypes.c_int, [_V, _V, ctypes.c_int, ctypes.c_int, _V]),
     "lbm_set_segment_rows": (ctypes.c_int, [_V, ctypes.c_int]),
     "lbm_get_segment_rows": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int)]),
-    "lbm_adjoint_backward": (ctypes.c_int, [_V, _V, _V, _D, _D]),
+    "lbm_adjoint_backward": (ctypes.c_int, [_V, _V, _V, _D, _D, _D]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.c_int, ctypes.POINTER(_V)]),
     "lbm_batch_init_density": (ctypes.c_int, [_V, _D]),
     "lbm_batch_set_f": (ctypes.c_int, [_V, _D]),
@@ -176,12 +176,14 @@ class Params:
     prec: str = "f32"
     hdm_radius: int = 0
     two_pass: bool = False  # LBM_FLAG_TWO_PASS: never use the single-pass FP32 kernel
+    G: float = 0.0     # eos "psi_exp": interaction strength of Eq. 4
+    rho0: float = 1.0  # eos "psi_exp": reference density of psi = 1 - exp(-rho/rho0)
     stream: int = 0  # cudaStream_t as an integer (torch.cuda.Stream.cuda_stream), 0 = default
 
     def c(self) -> _Params:
         return _Params(self.nx, self.ny, PREC[self.prec], EOS[self.eos], FORCE[self.force], GRAD[self.grad],
                        self.hdm_radius, FLAG_TWO_PASS if self.two_pass else 0, self.a, self.b, self.R, self.omega, self.Tr, self.Tc, self.k,
-                       self.tau, ctypes.c_void_p(self.stream or None))
+                       self.tau, self.G, self.rho0, ctypes.c_void_p(self.stream or None))
 
 
 class Lattice:
@@ -255,10 +257,11 @@ class Lattice:
         self._check(self._lib.lbm_adjoint_forward(self._h, rho0_ptr, int(nsteps), int(checkpoint_interval), rhoT_ptr))
 
     def adjoint_backward(self, grad_rhoT_ptr: int, grad_rho0_ptr: int):
-        gT, gTr = ctypes.c_double(), ctypes.c_double()
+        """Writes dL/drho0 and returns (dL/dT, dL/d(T/Tc), dL/dG)."""
+        gT, gTr, gG = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         self._check(self._lib.lbm_adjoint_backward(self._h, grad_rhoT_ptr, grad_rho0_ptr, ctypes.byref(gT),
-                                                   ctypes.byref(gTr)))
-        return gT.value, gTr.value
+                                                   ctypes.byref(gTr), ctypes.byref(gG)))
+        return gT.value, gTr.value, gG.value
 
     def set_timing(self, enable: bool):
         self._check(self._lib.lbm_set_timing(self._h, 1 if enable else 0))

@@ -116,3 +116,30 @@ def test_library_maxwell_matches_oracle(lib, eos, Tr):
 def test_library_maxwell_rejects_supercritical(lib):
     with pytest.raises(lbm.LBMError):
         lbm.maxwell(lbm.Params(nx=1, ny=1, eos="vdw", a=9 / 49, b=2 / 21, Tr=1.02))
+
+
+@pytest.mark.parametrize("G,rho0", [(-1.6, 1.0), (-2.0, 1.0), (-3.0, 0.5)])
+def test_library_maxwell_psi_exp_matches_oracle(lib, G, rho0):
+    # the equal-area pair of the pressure of Eq. 5 (original effective mass)
+    g, l = lbm.maxwell(lbm.Params(nx=1, ny=1, eos="psi_exp", G=G, rho0=rho0))
+    go, lo, _ = oracle.maxwell(oracle.params_psi(1, 1, G, rho0=rho0))
+    assert g == pytest.approx(go, rel=1e-9)
+    assert l == pytest.approx(lo, rel=1e-10)
+
+
+@pytest.mark.parametrize("bad", [dict(G=0.0), dict(G=float("nan")), dict(rho0=0.0), dict(rho0=-1.0)])
+def test_create_rejects_bad_psi_exp_params(lib, bad):
+    import ctypes
+    p = lbm.Params(nx=16, ny=16, eos="psi_exp", G=-2.0, rho0=1.0)
+    for k, v in bad.items():
+        setattr(p, k, v)
+    c = p.c()
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(ctypes.byref(c), ctypes.byref(h)) == lbm.E_INVALID
+    assert h.value is None
+
+
+def test_psi_exp_above_critical_strength_has_no_loop(lib):
+    # G_c = -4 rho0 / 3 for Eq. 5
+    with pytest.raises(lbm.LBMError):
+        lbm.maxwell(lbm.Params(nx=1, ny=1, eos="psi_exp", G=-1.3, rho0=1.0))
