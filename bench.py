@@ -455,9 +455,12 @@ def run_adjoint(args):
 
     r32 = run("f32", timed=True)
     r64 = run("f64")
+    # central differences at h = 1e-4 Tr and h/2; the Richardson combination
+    # (4 FD(h/2) - FD(h)) / 3 removes the h^2 term of the truncation error
     h = 1e-4 * Tr
-    Lp, Lm = run("f64", Tr + h)["L"], run("f64", Tr - h)["L"]
-    fd_tr = (Lp - Lm) / (2 * h)
+    fd_tr = (run("f64", Tr + h)["L"] - run("f64", Tr - h)["L"]) / (2 * h)
+    fd_tr2 = (run("f64", Tr + h / 2)["L"] - run("f64", Tr - h / 2)["L"]) / h
+    fd_tr_rich = (4 * fd_tr2 - fd_tr) / 3
     d = inputs.uniform01(inputs.DEFAULT_SEED + 6, nx * ny).reshape(ny, nx) - 0.5
     eps = 1e-6
     fd_dir = (run("f64", r0=rho0 + eps * d)["L"] - run("f64", r0=rho0 - eps * d)["L"]) / (2 * eps)
@@ -489,6 +492,8 @@ def run_adjoint(args):
 
     hG = 1e-4 * 1.7
     fdG = (psi_run("f64", -1.7 + hG)[0] - psi_run("f64", -1.7 - hG)[0]) / (2 * hG)
+    fdG2 = (psi_run("f64", -1.7 + hG / 2)[0] - psi_run("f64", -1.7 - hG / 2)[0]) / hG
+    fdG_rich = (4 * fdG2 - fdG) / 3
     g64 = psi_run("f64", -1.7)[1]
     g32 = psi_run("f32", -1.7)[1]
     line = {
@@ -500,13 +505,16 @@ def run_adjoint(args):
         "plain_forward_ms": r32["plain_ms"], "taped_forward_ms": r32["fwd_ms"], "backward_ms": r32["bwd_ms"],
         "backward_over_plain": r32["bwd_ms"] / r32["plain_ms"],
         "L_f32": r32["L"], "L_f64": r64["L"],
-        "dL_dTr": {"f32": r32["dTr"], "f64": r64["dTr"], "fd_f64": fd_tr,
+        "dL_dTr": {"f32": r32["dTr"], "f64": r64["dTr"], "fd_f64": fd_tr, "fd_f64_richardson": fd_tr_rich,
                    "rel_err_f64_vs_fd": abs(r64["dTr"] - fd_tr) / abs(fd_tr),
+                   "rel_err_f64_vs_fd_richardson": abs(r64["dTr"] - fd_tr_rich) / abs(fd_tr_rich),
                    "rel_err_f32_vs_f64": abs(r32["dTr"] - r64["dTr"]) / abs(r64["dTr"])},
         "dL_dG": 0.0,
         "psi_exp_dL_dG": {"workload": "original effective mass (Eq. 4) G = -1.7, 256x256 droplet R50 -> R56, "
                                       "2000 steps, checkpoint interval 45",
                           "f64": g64, "f32": g32, "fd_f64": fdG, "rel_err_f64_vs_fd": abs(g64 - fdG) / abs(fdG),
+                          "fd_f64_richardson": fdG_rich,
+                          "rel_err_f64_vs_fd_richardson": abs(g64 - fdG_rich) / abs(fdG_rich),
                           "rel_err_f32_vs_f64": abs(g32 - g64) / abs(g64)},
         "dL_drho0": {"directional_f64": adj_dir, "fd_f64": fd_dir,
                      "rel_err_f64_vs_fd": abs(adj_dir - fd_dir) / abs(fd_dir),
