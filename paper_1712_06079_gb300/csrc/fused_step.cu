@@ -23,8 +23,9 @@
 // mbarriers, bounded waits), issued a slab ahead by warp 0:
 //  - the slab's 8 potential rows at full width (the 26-column HDM halo on
 //    each side, for d/dx), double-buffered;
-//  - an 80-row ring of potential rows at the lanes' 128 columns (26 rows
-//    above and below every slab row, for d/dy), 8 rows per chunk.
+//  - a 48-row ring of potential rows at the lanes' 128 columns (the slab's
+//    rows, the row above and the 26 rows below it, for the d/dy recurrences),
+//    8 rows per chunk.
 // The potential field is stored with 32 ghost columns on each side (periodic
 // images), so every staged row is one contiguous 16-byte-aligned copy; rows
 // wrap periodically.
@@ -45,6 +46,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "lbm_internal.h"
 #include "ptx.cuh"
@@ -58,9 +60,10 @@ constexpr int QG = 32;              // ghost columns on each side of a padded po
 constexpr int WW = TXI + 2 * QG;    // floats per wide potential row (d/dx halo)
 constexpr int NW = 128;             // floats per lane-column row (32 lanes x 4)
 constexpr int SLAB = 8;             // rows per slab (one warp each)
-constexpr int QCH = 10;             // chunks in the d/dy ring
+constexpr int QCH = 6;              // chunks in the d/dy ring: slab s reads chunks s .. s+4, s+5 in flight
 constexpr int QRING = QCH * SLAB;   // rows in the d/dy ring
-constexpr int QBASE = 33;           // ring chunk 0 starts at row ys - QBASE
+constexpr int QBASE = 2;            // ring chunk 0 starts at row ys - QBASE
+constexpr int QAHEAD = 4;           // slab s reads ring chunks s .. s + QAHEAD
 constexpr int PROWS = 18;           // partial-density ring rows
 constexpr int NTHR = 32 * SLAB;
 constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s per wait
@@ -70,8 +73,10 @@ constexpr size_t kQnBytes = sizeof(float) * QRING * NW;       // d/dy ring
 constexpr size_t kQwBytes = sizeof(float) * 2 * SLAB * WW;    // slab rows, full width, 2 buffers
 constexpr size_t kPsBytes = sizeof(float) * 3 * PROWS * NW;   // partial densities
 constexpr size_t kOffQw = kQnBytes;
+constexpr size_t kAbBytes = sizeof(float) * 2 * SLAB * NW;    // column recurrences P, Q of the slab rows
 constexpr size_t kOffPs = kOffQw + kQwBytes;
-constexpr size_t kOffBar = kOffPs + kPsBytes;
+constexpr size_t kOffAb = kOffPs + kPsBytes;
+constexpr size_t kOffBar = kOffAb + kAbBytes;
 constexpr size_t kSmemBytes = kOffBar + sizeof(uint64_t) * (QCH + 2);
 
 struct FusedArgs {
@@ -83,7 +88,8 @@ struct FusedArgs {
     int *err;
     int qpitch;         // nx + 2 * QG
     int seg_h;          // rows per CTA segment
-    float2 wy2[FK + 1]; // (w_j, w_j) pairs of the d/dy weights for packed FP32x2 FMAs
+    float w1y, w2y;     // d/dy weights w_1, w_2 (w_j = w_2 r^(j-2) for j >= 2)
+    float ry, ry12;     // r = (sqrt 5 - 3)/2 of Eq. 20's tridiagonal operator, and r^12
 };
 
 // f(t) is read once per step: a 16-byte load that takes no L1 line (L1 holds
@@ -152,6 +158,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     float *qn = reinterpret_cast<float *>(smem);               // [QRING][NW]
     float *qw = reinterpret_cast<float *>(smem + kOffQw);      // [2][SLAB][WW]
     float *ps = reinterpret_cast<float *>(smem + kOffPs);      // [3][PROWS][NW]
+    float *ab = reinterpret_cast<float *>(smem + kOffAb);      // [2][SLAB][NW]: P_{y-1}, Q_{y+1}
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // QCH chunk barriers + 2 row barriers
     uint64_t *row_bar = &bars[QCH];
 
@@ -164,7 +171,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     const int ys = blockIdx.y * A.seg_h;
     const int hseg = min(A.seg_h, ny - ys);
     const int nslab = hseg > 6 ? (hseg - 6 + SLAB - 1) / SLAB + 1 : 1;
-    const int nchunks = nslab + 8;
+    const int nchunks = nslab + QAHEAD;
     const int ncols = nint + 8;                     // lane columns actually staged (d/dy ring)
     const int wcols = nint + 2 * QG;                // wide-row columns actually staged
     const int glast = nint / 4 + 1;                 // right ring lane
@@ -218,6 +225,30 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
 #pragma unroll
         for (int i = 0; i < 9; ++i) fv[i] = ld_stream(reinterpret_cast<const float4 *>(src + i * N));
     };
+    // d/dy column recurrences: thread (warp, lane) follows ring column
+    // 16 warp + lane % 16 (padded column x0 + QG - 4 + cl); lanes < 16 carry the
+    // forward sum P down the segment.  Its start P_(ys-2), over rows ys - 27 ..
+    // ys - 3 above the ring, and the column's reference value q(ys - 1) come from
+    // the padded field, with all loads in flight while the first copies land.
+    const int cl = 16 * warp + (lane & 15);
+    const bool fwdl = lane < 16;
+    float colref = 0.f, pcarry = 0.f;
+    if (cl < ncols) {
+        const float *g = A.qin + x0 + QG - 4 + cl;
+        const int yr = ys - 1 < 0 ? ys - 1 + ny : ys - 1;
+        colref = __ldg(g + (long long)yr * A.qpitch);
+        if (fwdl) {
+            float v[25];
+#pragma unroll
+            for (int k = 0; k < 25; ++k) {
+                const int y = ys - 27 + k;                  // ny >= 2 FK + 2 > 27: one wrap at most
+                v[k] = __ldg(g + (long long)(y < 0 ? y + ny : y) * A.qpitch);
+            }
+#pragma unroll
+            for (int k = 0; k < 25; ++k) pcarry = fmaf(A.ry, pcarry, v[k] - colref);
+        }
+    }
+
     load_f(0);
 
     for (int s = 0; s < nslab; ++s) {
@@ -236,15 +267,49 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         const int yc = ys - 1 + SLAB * s + warp;    // collided row of this warp
         const int ryc = SLAB * s + warp + QBASE - 1;
         {
-            const int cfirst = s == 0 ? 0 : s + 8, clast = min(s + 8, nchunks - 1);
+            const int cfirst = s == 0 ? 0 : s + QAHEAD, clast = min(s + QAHEAD, nchunks - 1);
             for (int c = cfirst; c <= clast; ++c)
                 if (!ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs)) timed_out = true;
             if (!ptx::mbar_wait_bounded(&row_bar[s & 1], (s >> 1) & 1, kWaitLimitNs)) timed_out = true;
         }
+        // d/dy of the slab's rows in recurrence form.  The explicit periodic
+        // HDM weights are w_j = w_2 r^(j-2) for j >= 2, so with t = q - q_ref along
+        // a column, P_y = t_(y-1) + r P_(y-1) and Q_y = t_(y+1) + r Q_(y+1),
+        //   D_y = w_1 (q_(y+1) - q_(y-1)) + w_2 (Q_(y+1) - P_(y-1)).
+        // Q_(y+1) of the slab's last row sums the 25 rows below it (the same
+        // truncation as the stencil): lanes >= 16 take the 12 nearest, lanes < 16
+        // the 13 farthest (one shuffle joins them); then lanes < 16 step P down
+        // the slab (carried across slabs) and lanes >= 16 step Q up it.  Every
+        // lane runs the same instructions on its own rows; all rows read lie in
+        // ring chunks s .. s + 4.  A timed-out wait leaves stale rows here; the
+        // barrier below then ends the sweep before anything is stored.
+        {
+            const float *col = qn + cl;
+            const int y0r = SLAB * s + QBASE - 1;   // ring-relative row of the slab's first row
+            float x = 0.f;
+            int ri = (y0r + (fwdl ? 33 : 20)) % QRING;   // far part Y0+33 .. Y0+21, near part Y0+20 .. Y0+9
+#pragma unroll
+            for (int k = 0; k < 13; ++k) {
+                if (fwdl || k < 12) x = fmaf(A.ry, x, col[ri * NW] - colref);
+                ri = ri == 0 ? QRING - 1 : ri - 1;
+            }
+            const float far = __shfl_sync(0xffffffffu, x, lane & 15);
+            float v = fwdl ? pcarry : fmaf(A.ry12, far, x);   // P_(Y0-1) or Q_(Y0+8)
+            ri = fwdl ? (y0r - 1) % QRING : (y0r + SLAB) % QRING;
+            float *dst = ab + (fwdl ? 0 : SLAB * NW) + cl;
+#pragma unroll
+            for (int k = 0; k < SLAB; ++k) {
+                dst[(fwdl ? k : SLAB - 1 - k) * NW] = v;     // P_(Y0+k-1) / Q_(Y0+8-k)
+                v = fmaf(A.ry, v, col[ri * NW] - colref);   // rows Y0-1+k / Y0+8-k
+                ri = fwdl ? (ri + 1 == QRING ? 0 : ri + 1) : (ri == 0 ? QRING - 1 : ri - 1);
+            }
+            if (fwdl) pcarry = v;   // P_(Y0+7) = P of the next slab's first row minus one
+        }
+        if (__syncthreads_or(timed_out)) break;
         // Every lane of a warp runs the collision (the shuffles need the whole
         // warp); lanes past the strip's right ring lane work on unused shared
         // columns and store nothing.
-        if (!__any_sync(0xffffffffu, timed_out)) {
+        {
             float dx[4], dy[4], qc[4];
             {   // d/dx: wide row columns 4 lane .. 4 lane + 59; cells at window positions 28..31.
                 // Each staged value enters as its deviation from the lane's second cell,
@@ -274,36 +339,15 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
 #pragma unroll
                 for (int c = 0; c < 4; ++c) dx[c] = sp[c] - sm[c];
             }
-            {   // d/dy: ring rows yc - FK .. yc + FK at the lane's 4 columns, as
-                // sum_j w_j (q(y+j) - q(y-j)) with the differences taken first;
-                // odd and even j in separate sums; packed FP32x2 arithmetic
-                // the window of ring rows base - FK .. base + FK wraps at most once
-                // on each side: two base offsets, one select per tap, the tap
-                // itself an immediate offset of the shared load
-                const float *qcol = qn + 4 * lane;
-                const int base = ryc % QRING;
-                const int b0 = base * NW, bu = (base - QRING) * NW, bd = (base + QRING) * NW;
-                const float2 neg1 = make_float2(-1.f, -1.f);
-                float2 se01 = make_float2(0.f, 0.f), se23 = se01, so01 = se01, so23 = se01;
-#pragma unroll
-                for (int j = 1; j <= FK; ++j) {
-                    const int ou = (j >= QRING - base ? bu : b0) + j * NW;
-                    const int od = (j > base ? bd : b0) - j * NW;
-                    const float4 a = *reinterpret_cast<const float4 *>(qcol + ou);
-                    const float4 b = *reinterpret_cast<const float4 *>(qcol + od);
-                    const float2 w2 = A.wy2[j];
-                    const float2 d01 = __ffma2_rn(neg1, make_float2(b.x, b.y), make_float2(a.x, a.y));
-                    const float2 d23 = __ffma2_rn(neg1, make_float2(b.z, b.w), make_float2(a.z, a.w));
-                    if (j & 1) {
-                        so01 = __ffma2_rn(w2, d01, so01);
-                        so23 = __ffma2_rn(w2, d23, so23);
-                    } else {
-                        se01 = __ffma2_rn(w2, d01, se01);
-                        se23 = __ffma2_rn(w2, d23, se23);
-                    }
-                }
-                const float2 s01 = __fadd2_rn(so01, se01), s23 = __fadd2_rn(so23, se23);
-                dy[0] = s01.x; dy[1] = s01.y; dy[2] = s23.x; dy[3] = s23.y;
+            {   // d/dy from the column recurrences of this row
+                const float4 qa = *reinterpret_cast<const float4 *>(qn + ((ryc + 1) % QRING) * NW + 4 * lane);
+                const float4 qb = *reinterpret_cast<const float4 *>(qn + ((ryc - 1) % QRING) * NW + 4 * lane);
+                const float4 P = *reinterpret_cast<const float4 *>(ab + warp * NW + 4 * lane);
+                const float4 Q = *reinterpret_cast<const float4 *>(ab + (SLAB + warp) * NW + 4 * lane);
+                dy[0] = fmaf(A.w1y, qa.x - qb.x, A.w2y * (Q.x - P.x));
+                dy[1] = fmaf(A.w1y, qa.y - qb.y, A.w2y * (Q.y - P.y));
+                dy[2] = fmaf(A.w1y, qa.z - qb.z, A.w2y * (Q.z - P.z));
+                dy[3] = fmaf(A.w1y, qa.w - qb.w, A.w2y * (Q.w - P.w));
             }
             // moments of f(t) (Eq. 3)
             float r[4] = {0.f, 0.f, 0.f, 0.f}, jx[4] = {0.f, 0.f, 0.f, 0.f}, jy[4] = {0.f, 0.f, 0.f, 0.f};
@@ -389,7 +433,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 *reinterpret_cast<float4 *>(ps + (k * PROWS + slot) * NW + 4 * lane) = part[k];
             }
         }
-        if (__syncthreads_or(timed_out)) break;
+        __syncthreads();
 
         // ---- rho(t+1) and the potential of row yo = ys + 8s - 2 + warp ----
         const int yo = ys + SLAB * s - 2 + warp;
@@ -486,7 +530,11 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     if (seg_rows < 1) return cudaErrorInvalidValue;
     dim3 grid((m.nx + TXI - 1) / TXI, (m.ny + seg_rows - 1) / seg_rows);
     if (grid.y > 65535) return cudaErrorInvalidValue;
-    for (int j = 0; j <= FK; ++j) a.wy2[j] = make_float2(m.wy[j], m.wy[j]);
+    a.w1y = m.wy[1];
+    a.w2y = m.wy[2];
+    const double r = 0.5 * (std::sqrt(5.0) - 3.0);   // root of r^2/3 + r + 1/3 = 0 (Eq. 20's operator)
+    a.ry = (float)r;
+    a.ry12 = (float)std::pow(r, 12);
     const bool tau1 = m.omega == 1.0f;
     void (*kern)(const FusedArgs) = nullptr;
 #define LBM_PICK(E)                                                                                        \

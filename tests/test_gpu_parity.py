@@ -237,8 +237,11 @@ def test_f32_single_pass_kernel_parity(nx, ny, eos, Tr, force):
 
 
 def test_f32_single_pass_segment_height_does_not_change_results():
-    # the CTA segment height is a launch shape only: every cell computes the
-    # same arithmetic whichever CTA owns it, so the states are bit-identical
+    # the CTA segment height is a launch shape: every cell takes the same
+    # arithmetic except the d/dy forward recurrence, which carries its sum
+    # from the segment's first row (terms beyond the 26-row stencil radius,
+    # weight r^26 ~ 1e-11) and so rounds along a different path; the states
+    # agree to the bar the single-pass and two-pass FP32 paths are held to
     nx, ny = 252, 200
     gp, op = make(nx, ny, "cs", 0.8, "sc", "hdm", prec="f32")
     g, l, _ = oracle.maxwell(op)
@@ -253,7 +256,7 @@ def test_f32_single_pass_segment_height_does_not_change_results():
             lat.step(12)
             outs[rows] = lat.get_f()
     for rows, fr in outs.items():
-        assert np.array_equal(fr, outs[0]), rows
+        assert np.max(np.abs(fr - outs[0]) / np.abs(outs[0])) < 1e-5, rows
     with lbm.Lattice(gp) as lat:
         for bad in (-1, ny + 1):
             with pytest.raises(lbm.LBMError) as ei:
