@@ -17,8 +17,9 @@
 // every strip cell can be formed on chip.
 //
 // f(t) of a lane's 4 cells is read with nine float4 loads into registers,
-// issued at the end of the previous slab's collision so that their latency
-// hides behind the barrier, the density pass and the next stencil.  The
+// issued during the previous slab (for tau = 1 right after its moments, which
+// are the last use of f(t); otherwise after its collision) so that their
+// latency hides behind the barrier, the density pass and the next stencil.  The
 // potential rows arrive by the bulk-copy engine (cp.async.bulk, completion on
 // mbarriers, bounded waits), issued a slab ahead by warp 0:
 //  - the slab's 8 potential rows at full width (the 26-column HDM halo on
@@ -366,6 +367,9 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                     if (ey(i)) jy[c] = fmaf(float(ey(i)), v[c], jy[c]);
                 }
             }
+            // for tau = 1 the collision reads no f(t) after the moments, so f(t) of
+            // the next slab goes in flight here, across the whole collision
+            if (TAU1 && s + 1 < nslab) load_f(s + 1);
             // force and the two velocities of the forcing (Eq. 10, 22 / 7)
             float ux[4], uy[4], vx[4], vy[4], au[4], av[4], moved[4];
 #pragma unroll
@@ -431,7 +435,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 float4 &pp = part[ey(i) + 1];
                 pp.x += d.x; pp.y += d.y; pp.z += d.z; pp.w += d.w;
             }
-            if (s + 1 < nslab) load_f(s + 1);   // f(t) of the next slab, in flight across the barrier
+            if (!TAU1 && s + 1 < nslab) load_f(s + 1);   // in flight across the barrier
 #pragma unroll
             for (int k = 0; k < 3; ++k) {   // component k: what row yc sends to row yc + (k - 1)
                 const int slot = (rd0 + k - 1) % PROWS;
