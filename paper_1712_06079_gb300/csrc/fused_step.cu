@@ -79,7 +79,7 @@ constexpr size_t kQnBytes = sizeof(float) * QRING * NW;       // d/dy ring
 constexpr size_t kQwBytes = sizeof(float) * 2 * SLAB * WW;    // slab rows, full width, 2 buffers
 constexpr size_t kPsBytes = sizeof(float) * 3 * PROWS * NW;   // partial densities
 constexpr size_t kOffQw = kQnBytes;
-constexpr size_t kAbBytes = sizeof(float) * 2 * SLAB * NW;    // column recurrences P, Q of the slab rows
+constexpr size_t kAbBytes = sizeof(float) * 2 * 2 * SLAB * NW;  // P, Q of the slab rows, two slabs
 constexpr size_t kOffPs = kOffQw + kQwBytes;
 constexpr size_t kOffAb = kOffPs + kPsBytes;
 constexpr size_t kOffBar = kOffAb + kAbBytes;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     float *qn = reinterpret_cast<float *>(smem);               // [QRING][NW]
     float *qw = reinterpret_cast<float *>(smem + kOffQw);      // [2][SLAB][WW]
     float *ps = reinterpret_cast<float *>(smem + kOffPs);      // [3][PROWS][NW]
-    float *ab = reinterpret_cast<float *>(smem + kOffAb);      // [2][SLAB][NW]: P_{y-1}, Q_{y+1}
+    float *ab = reinterpret_cast<float *>(smem + kOffAb);      // [2 slabs][2][SLAB][NW]: P_{y-1}, Q_{y+1}
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // QCH chunk barriers + 2 row barriers
     uint64_t *row_bar = &bars[QCH];
 
@@ -255,9 +255,49 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         }
     }
 
+    // d/dy of the slab's rows in recurrence form.  The explicit periodic
+    // HDM weights are w_j = w_2 r^(j-2) for j >= 2, so with t = q - q_ref along
+    // a column, P_y = t_(y-1) + r P_(y-1) and Q_y = t_(y+1) + r Q_(y+1),
+    //   D_y = w_1 (q_(y+1) - q_(y-1)) + w_2 (Q_(y+1) - P_(y-1)).
+    // Q_(y+1) of the slab's last row sums the 25 rows below it (the same
+    // truncation as the stencil): lanes >= 16 take the 12 nearest, lanes < 16
+    // the 13 farthest (one shuffle joins them); then lanes < 16 step P down
+    // the slab (carried across slabs) and lanes >= 16 step Q up it.  Every
+    // lane runs the same instructions on its own rows; all rows read lie in
+    // ring chunks s .. s + 4.  Slab s + 1's recurrences run at the end of slab
+    // s, so one barrier per slab serves them and the partial densities.
+    auto column_phase = [&](int s) {
+        const float *col = qn + cl;
+        const int y0r = SLAB * s + QBASE - 1;   // ring-relative row of the slab's first row
+        float x = 0.f;
+        int ri = (y0r + (fwdl ? 33 : 20)) % QRING;   // far part Y0+33 .. Y0+21, near part Y0+20 .. Y0+9
+#pragma unroll
+        for (int k = 0; k < 13; ++k) {
+            if (fwdl || k < 12) x = fmaf(A.ry, x, col[ri * NW] - colref);
+            ri = ri == 0 ? QRING - 1 : ri - 1;
+        }
+        const float far = __shfl_sync(0xffffffffu, x, lane & 15);
+        float v = fwdl ? pcarry : fmaf(A.ry12, far, x);   // P_(Y0-1) or Q_(Y0+8)
+        ri = fwdl ? (y0r - 1) % QRING : (y0r + SLAB) % QRING;
+        float *dst = ab + (s & 1) * 2 * SLAB * NW + (fwdl ? 0 : SLAB * NW) + cl;
+#pragma unroll
+        for (int k = 0; k < SLAB; ++k) {
+            dst[(fwdl ? k : SLAB - 1 - k) * NW] = v;     // P_(Y0+k-1) / Q_(Y0+8-k)
+            v = fmaf(A.ry, v, col[ri * NW] - colref);   // rows Y0-1+k / Y0+8-k
+            ri = fwdl ? (ri + 1 == QRING ? 0 : ri + 1) : (ri == 0 ? QRING - 1 : ri - 1);
+        }
+        if (fwdl) pcarry = v;   // P_(Y0+7) = P of the next slab's first row minus one
+    };
+
     load_f(0);
 
-    for (int s = 0; s < nslab; ++s) {
+    // slab 0's recurrences before the sweep (ring chunks 0 .. QAHEAD)
+    for (int c = 0; c <= min(QAHEAD, nchunks - 1); ++c)
+        if (!ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs)) timed_out = true;
+    column_phase(0);
+    const bool stop0 = __syncthreads_or(timed_out);
+
+    for (int s = 0; s < nslab && !stop0; ++s) {
         // copies a slab ahead: the next slab's full-width rows and the ring chunk
         // it needs last (their buffers were last read by the previous slab)
         if (warp == 0 && s >= 1) {
@@ -272,46 +312,10 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         }
         const int yc = ys - 1 + SLAB * s + warp;    // collided row of this warp
         const int ryc = SLAB * s + warp + QBASE - 1;
-        {
-            const int cfirst = s == 0 ? 0 : s + QAHEAD, clast = min(s + QAHEAD, nchunks - 1);
-            for (int c = cfirst; c <= clast; ++c)
-                if (!ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs)) timed_out = true;
-            if (!ptx::mbar_wait_bounded(&row_bar[s & 1], (s >> 1) & 1, kWaitLimitNs)) timed_out = true;
-        }
-        // d/dy of the slab's rows in recurrence form.  The explicit periodic
-        // HDM weights are w_j = w_2 r^(j-2) for j >= 2, so with t = q - q_ref along
-        // a column, P_y = t_(y-1) + r P_(y-1) and Q_y = t_(y+1) + r Q_(y+1),
-        //   D_y = w_1 (q_(y+1) - q_(y-1)) + w_2 (Q_(y+1) - P_(y-1)).
-        // Q_(y+1) of the slab's last row sums the 25 rows below it (the same
-        // truncation as the stencil): lanes >= 16 take the 12 nearest, lanes < 16
-        // the 13 farthest (one shuffle joins them); then lanes < 16 step P down
-        // the slab (carried across slabs) and lanes >= 16 step Q up it.  Every
-        // lane runs the same instructions on its own rows; all rows read lie in
-        // ring chunks s .. s + 4.  A timed-out wait leaves stale rows here; the
-        // barrier below then ends the sweep before anything is stored.
-        {
-            const float *col = qn + cl;
-            const int y0r = SLAB * s + QBASE - 1;   // ring-relative row of the slab's first row
-            float x = 0.f;
-            int ri = (y0r + (fwdl ? 33 : 20)) % QRING;   // far part Y0+33 .. Y0+21, near part Y0+20 .. Y0+9
-#pragma unroll
-            for (int k = 0; k < 13; ++k) {
-                if (fwdl || k < 12) x = fmaf(A.ry, x, col[ri * NW] - colref);
-                ri = ri == 0 ? QRING - 1 : ri - 1;
-            }
-            const float far = __shfl_sync(0xffffffffu, x, lane & 15);
-            float v = fwdl ? pcarry : fmaf(A.ry12, far, x);   // P_(Y0-1) or Q_(Y0+8)
-            ri = fwdl ? (y0r - 1) % QRING : (y0r + SLAB) % QRING;
-            float *dst = ab + (fwdl ? 0 : SLAB * NW) + cl;
-#pragma unroll
-            for (int k = 0; k < SLAB; ++k) {
-                dst[(fwdl ? k : SLAB - 1 - k) * NW] = v;     // P_(Y0+k-1) / Q_(Y0+8-k)
-                v = fmaf(A.ry, v, col[ri * NW] - colref);   // rows Y0-1+k / Y0+8-k
-                ri = fwdl ? (ri + 1 == QRING ? 0 : ri + 1) : (ri == 0 ? QRING - 1 : ri - 1);
-            }
-            if (fwdl) pcarry = v;   // P_(Y0+7) = P of the next slab's first row minus one
-        }
-        if (__syncthreads_or(timed_out)) break;
+        if (!ptx::mbar_wait_bounded(&row_bar[s & 1], (s >> 1) & 1, kWaitLimitNs)) timed_out = true;
+        // A timed-out wait leaves stale shared rows: the slab then computes and
+        // stores values of no use (in bounds), the barrier below ends the sweep
+        // and the error word reports the timeout.
         // Every lane of a warp runs the collision (the shuffles need the whole
         // warp); lanes past the strip's right ring lane work on unused shared
         // columns and store nothing.
@@ -348,8 +352,9 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             {   // d/dy from the column recurrences of this row
                 const float4 qa = *reinterpret_cast<const float4 *>(qn + ((ryc + 1) % QRING) * NW + 4 * lane);
                 const float4 qb = *reinterpret_cast<const float4 *>(qn + ((ryc - 1) % QRING) * NW + 4 * lane);
-                const float4 P = *reinterpret_cast<const float4 *>(ab + warp * NW + 4 * lane);
-                const float4 Q = *reinterpret_cast<const float4 *>(ab + (SLAB + warp) * NW + 4 * lane);
+                const float *abs_ = ab + (s & 1) * 2 * SLAB * NW;
+                const float4 P = *reinterpret_cast<const float4 *>(abs_ + warp * NW + 4 * lane);
+                const float4 Q = *reinterpret_cast<const float4 *>(abs_ + (SLAB + warp) * NW + 4 * lane);
                 dy[0] = fmaf(A.w1y, qa.x - qb.x, A.w2y * (Q.x - P.x));
                 dy[1] = fmaf(A.w1y, qa.y - qb.y, A.w2y * (Q.y - P.y));
                 dy[2] = fmaf(A.w1y, qa.z - qb.z, A.w2y * (Q.z - P.z));
@@ -442,7 +447,12 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 *reinterpret_cast<float4 *>(ps + (k * PROWS + slot) * NW + 4 * lane) = part[k];
             }
         }
-        __syncthreads();
+        if (s + 1 < nslab) {   // slab s + 1's recurrences: its last ring chunk, then the column phase
+            const int c = s + 1 + QAHEAD;
+            if (c < nchunks && !ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs)) timed_out = true;
+            column_phase(s + 1);
+        }
+        if (__syncthreads_or(timed_out)) break;
 
         // ---- rho(t+1) and the potential of row yo = ys + 8s - 2 + warp ----
         const int yo = ys + SLAB * s - 2 + warp;
