@@ -38,13 +38,14 @@
 // the same operator runs in recurrence form: its weights are geometric past
 // the first (w_j = w_2 r^(j-2)), so per slab every ring column carries a
 // forward sum down the segment and a 25-row backward sum, and each row reads
-// two values per cell.  Per slab, after the recurrences and one barrier, each
-// lane forms the force (Eq. 22 Shan-Chen or Eq. 7 Zhang-Chen), the moments
-// (Eq. 3) and the exact-difference forcing with BGK (Eq. 1, 2, 10).  It then
-// streams (Eq. 1) by push: the x shift is a warp shuffle, the destination
-// float4 of f(t+1) is stored straight to HBM, and the three partial sums of
-// what lands in rows y-1, y, y+1 go to an 18-row shared ring.  After a second
-// barrier each warp sums the three partials of one finished row into
+// two values per cell; the sums of slab s+1 are formed at the end of slab s.
+// Per slab each lane forms the force (Eq. 22 Shan-Chen or Eq. 7 Zhang-Chen),
+// the moments (Eq. 3) and the exact-difference forcing with BGK (Eq. 1, 2,
+// 10).  It then streams (Eq. 1) by push: the x shift is a warp shuffle, the
+// destination float4 of f(t+1) is stored straight to HBM, and the three
+// partial sums of what lands in rows y-1, y, y+1 go to an 18-row shared ring.
+// After the slab's one barrier each warp sums the three partials of one
+// finished row into
 // rho(t+1) and writes the potential (Eq. 8, 21) of that row.  The
 // rest population is formed as rho minus the other eight, so the FP32
 // collision conserves mass up to unbiased rounding.  For tau = 1 the BGK term
