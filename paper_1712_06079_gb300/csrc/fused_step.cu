@@ -34,22 +34,23 @@
 // The derivative is the explicit periodic HDM operator (the exact solution of
 // the tridiagonal system of Eq. 20, truncated at radius 26 where the
 // neglected tail of the weights changes the derivative of a smooth field by
-// < 3e-9).  Along x each lane applies its 52 taps to the staged row.  Along y
-// the same operator runs in recurrence form: its weights are geometric past
-// the first (w_j = w_2 r^(j-2)), so per slab every ring column carries a
-// forward sum down the segment and a 25-row backward sum, and each row reads
-// two values per cell; the sums of slab s+1 are formed at the end of slab s.
-// Per slab each lane forms the force (Eq. 22 Shan-Chen or Eq. 7 Zhang-Chen),
-// the moments (Eq. 3) and the exact-difference forcing with BGK (Eq. 1, 2,
-// 10).  It then streams (Eq. 1) by push: the x shift is a warp shuffle, the
-// destination float4 of f(t+1) is stored straight to HBM, and the three
-// partial sums of what lands in rows y-1, y, y+1 go to an 18-row shared ring.
-// After the slab's one barrier each warp sums the three partials of one
-// finished row into
-// rho(t+1) and writes the potential (Eq. 8, 21) of that row.  The
-// rest population is formed as rho minus the other eight, so the FP32
-// collision conserves mass up to unbiased rounding.  For tau = 1 the BGK term
-// vanishes exactly and the equilibrium at u is skipped.
+// < 3e-9).  Its weights are geometric past the first (w_j = w_2 r^(j-2)), so
+// both directions run in recurrence form.  Along x each lane forms the two
+// 25-term sums of its first and last cell from the staged row (five short
+// Horner groups each) and steps them to its other cells.  Along y every ring
+// column carries a forward sum down the segment and a 25-row backward sum per
+// slab, and each row reads two values per cell; the sums of slab s+1 are
+// formed at the end of slab s.  Per slab each lane forms the force (Eq. 22
+// Shan-Chen or Eq. 7 Zhang-Chen), the moments (Eq. 3) and the
+// exact-difference forcing with BGK (Eq. 1, 2, 10).  It then streams (Eq. 1)
+// by push: the x shift is a warp shuffle, the destination float4 of f(t+1) is
+// stored straight to HBM, and the three partial sums of what lands in rows
+// y-1, y, y+1 go to an 18-row shared ring.  After the slab's one barrier each
+// warp sums the three partials of one finished row into rho(t+1) and writes
+// the potential (Eq. 8, 21) of that row.  The rest population is formed as
+// rho minus the other eight, so the FP32 collision conserves mass up to
+// unbiased rounding.  For tau = 1 the BGK term vanishes exactly and the
+// equilibrium at u is skipped.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -95,8 +96,9 @@ struct FusedArgs {
     int *err;
     int qpitch;         // nx + 2 * QG
     int seg_h;          // rows per CTA segment
-    float w1y, w2y;     // d/dy weights w_1, w_2 (w_j = w_2 r^(j-2) for j >= 2)
-    float ry, ry12;     // r = (sqrt 5 - 3)/2 of Eq. 20's tridiagonal operator, and r^12
+    float w1x, w2x;     // d/dx weights w_1, w_2 (w_j = w_2 r^(j-2) for j >= 2)
+    float w1y, w2y;     // d/dy weights
+    float ry, ry5, ry12, ry25;  // r = (sqrt 5 - 3)/2 of Eq. 20's tridiagonal operator, and r^5, r^12, r^25
 };
 
 // f(t) is read once per step: a 16-byte load that takes no L1 line (L1 holds
@@ -205,8 +207,10 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         }
     };
     // slab s: potential rows ys - 1 + 8s + w at full width into buffer s & 1
+    int rows_issued = 0;  // slab row sets issued so far (meaningful in warp 0)
     auto issue_rows = [&](int s) {  // warp 0
         uint64_t *bar = &row_bar[s & 1];
+        rows_issued = s + 1;
         if (lane == 0) ptx::mbar_arrive_expect_tx(bar, SLAB * wcols * sizeof(float));
         __syncwarp();
         if (lane < SLAB) {
@@ -296,9 +300,9 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     for (int c = 0; c <= min(QAHEAD, nchunks - 1); ++c)
         if (!ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs)) timed_out = true;
     column_phase(0);
-    const bool stop0 = __syncthreads_or(timed_out);
+    bool stop = __syncthreads_or(timed_out);   // CTA-uniform
 
-    for (int s = 0; s < nslab && !stop0; ++s) {
+    for (int s = 0; s < nslab && !stop; ++s) {
         // copies a slab ahead: the next slab's full-width rows and the ring chunk
         // it needs last (their buffers were last read by the previous slab)
         if (warp == 0 && s >= 1) {
@@ -323,32 +327,47 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         {
             float dx[4], dy[4], qc[4];
             {   // d/dx: wide row columns 4 lane .. 4 lane + 59; cells at window positions 28..31.
-                // Each staged value enters as its deviation from the lane's second cell,
-                // so the weighted sums carry only local variations (the constant part of
-                // an antisymmetric stencil cancels exactly) and FP32 keeps its precision.
+                // Recurrence form of the same radius-26 operator: for the lane's cell c,
+                //   P_c = sum_{j=2..26} r^(j-2) t_(28+c-j),  Q_c = sum_{j=2..26} r^(j-2) t_(28+c+j),
+                //   d/dx = w_1 (t_(29+c) - t_(27+c)) + w_2 (Q_c - P_c),
+                // P_0 and Q_3 as five 5-term Horner groups joined by r^5, the other
+                // cells by one step each (P_c = t_(26+c) + r P_(c-1) - r^25 t_(1+c), Q
+                // mirrored).  Each staged value enters as its deviation t from the
+                // lane's second cell, so the sums carry only local variations.
                 const float *qrow = qw + ((s & 1) * SLAB + warp) * WW + 4 * lane;
-                const float qref = qrow[29];
-                float sp[4] = {0.f, 0.f, 0.f, 0.f}, sm[4] = {0.f, 0.f, 0.f, 0.f};
+                float t[60];
 #pragma unroll
                 for (int k = 0; k < 15; ++k) {
-                    float4 v4 = *reinterpret_cast<const float4 *>(qrow + 4 * k);
-                    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int pos = 4 * k + e;
-                        if (pos < 28 - FK || pos > 31 + FK) continue;
-                        const float t = v[e] - qref;
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int j = pos - 28 - c;
-                            if (j >= 1 && j <= FK) sp[c] = fmaf(m.wx[j], t, sp[c]);
-                            if (j <= -1 && j >= -FK) sm[c] = fmaf(m.wx[-j], t, sm[c]);
-                            if (j == 0) qc[c] = v[e];
-                        }
-                    }
+                    const float4 v4 = *reinterpret_cast<const float4 *>(qrow + 4 * k);
+                    t[4 * k] = v4.x; t[4 * k + 1] = v4.y; t[4 * k + 2] = v4.z; t[4 * k + 3] = v4.w;
                 }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) dx[c] = sp[c] - sm[c];
+                for (int c = 0; c < 4; ++c) qc[c] = t[28 + c];
+                const float qref = t[29];
+#pragma unroll
+                for (int p = 2; p <= 57; ++p) t[p] -= qref;
+                const float r = A.ry, r5 = A.ry5, r25 = A.ry25;
+                float gp[5], gq[5];
+#pragma unroll
+                for (int g = 0; g < 5; ++g) {
+                    float x = t[2 + 5 * g];                 // P_0: positions 2 + 5g .. 6 + 5g, far to near
+#pragma unroll
+                    for (int i = 1; i < 5; ++i) x = fmaf(r, x, t[2 + 5 * g + i]);
+                    gp[g] = x;
+                    float y = t[37 + 5 * g];                // Q_3: positions 37 + 5g .. 33 + 5g, far to near
+#pragma unroll
+                    for (int i = 1; i < 5; ++i) y = fmaf(r, y, t[37 + 5 * g - i]);
+                    gq[g] = y;
+                }
+                float P[4], Q[4];
+                P[0] = fmaf(fmaf(fmaf(fmaf(gp[0], r5, gp[1]), r5, gp[2]), r5, gp[3]), r5, gp[4]);
+                Q[3] = fmaf(fmaf(fmaf(fmaf(gq[4], r5, gq[3]), r5, gq[2]), r5, gq[1]), r5, gq[0]);
+#pragma unroll
+                for (int c = 1; c < 4; ++c) P[c] = fmaf(-r25, t[1 + c], fmaf(r, P[c - 1], t[26 + c]));
+#pragma unroll
+                for (int c = 2; c >= 0; --c) Q[c] = fmaf(-r25, t[55 + c], fmaf(r, Q[c + 1], t[30 + c]));
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dx[c] = fmaf(A.w1x, t[29 + c] - t[27 + c], A.w2x * (Q[c] - P[c]));
             }
             {   // d/dy from the column recurrences of this row
                 const float4 qa = *reinterpret_cast<const float4 *>(qn + ((ryc + 1) % QRING) * NW + 4 * lane);
@@ -453,7 +472,10 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             if (c < nchunks && !ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs)) timed_out = true;
             column_phase(s + 1);
         }
-        if (__syncthreads_or(timed_out)) break;
+        if (__syncthreads_or(timed_out)) {
+            stop = true;
+            break;
+        }
 
         // ---- rho(t+1) and the potential of row yo = ys + 8s - 2 + warp ----
         const int yo = ys + SLAB * s - 2 + warp;
@@ -475,14 +497,15 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         }
     }
 
-    if (timed_out) {
+    if (stop) {   // CTA-uniform: some thread's wait timed out
         if (threadIdx.x == 0) {
             atomicOr(A.err, kErrTimeout);
-            // let copies still in flight land before the CTA's shared memory is released
+            // thread 0 issued every copy: let those still in flight land before
+            // the CTA's shared memory is released
             for (int c = max(0, issued - QCH); c < issued; ++c)
                 (void)ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs);
-            for (int b = 0; b < 2; ++b)
-                for (int ph = 0; ph < 2; ++ph) (void)ptx::mbar_wait_bounded(&row_bar[b], ph, kWaitLimitNs);
+            for (int r = max(0, rows_issued - 2); r < rows_issued; ++r)
+                (void)ptx::mbar_wait_bounded(&row_bar[r & 1], (r >> 1) & 1, kWaitLimitNs);
         }
         __syncthreads();
     }
@@ -553,8 +576,12 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     a.w1y = m.wy[1];
     a.w2y = m.wy[2];
     const double r = 0.5 * (std::sqrt(5.0) - 3.0);   // root of r^2/3 + r + 1/3 = 0 (Eq. 20's operator)
+    a.w1x = m.wx[1];
+    a.w2x = m.wx[2];
     a.ry = (float)r;
+    a.ry5 = (float)std::pow(r, 5);
     a.ry12 = (float)std::pow(r, 12);
+    a.ry25 = (float)std::pow(r, 25);
     const bool tau1 = m.omega == 1.0f;
     void (*kern)(const FusedArgs) = nullptr;
 #define LBM_PICK(E)                                                                                        \
