@@ -3,9 +3,10 @@
 // One launch per time step reads f(t) and the potential field q(t) and
 // writes f(t+1) and q(t+1) = potential of f(t+1), so a step moves 9 floats
 // in + 9 floats out + 1 float in + 1 float out per cell (80 B) instead of
-// the 116 B of the two-pass form.  The field is Phi = sqrt|U| (Eq. 21) for
-// the Shan-Chen form, whose sign s at the cell itself is re-derived from the
-// cell's own density, and U (Eq. 8) for the Zhang-Chen form.
+// the 116 B of the two-pass form.  The field is the signed root s Phi,
+// Phi = sqrt|U| (Eq. 21), s the sign of U, for the Shan-Chen form (the
+// stencils read |q| = Phi, the cell's force takes s Phi as stored) and U
+// (Eq. 8) for the Zhang-Chen form.
 //
 // Decomposition.  A CTA of 8 warps owns a strip of TXI = 120 columns and a
 // segment of up to seg_h rows (a launch parameter; 126 on large lattices,
@@ -19,7 +20,10 @@
 // f(t) of a lane's 4 cells is read with nine float4 loads into registers,
 // issued during the previous slab (for tau = 1 right after its moments, which
 // are the last use of f(t); otherwise after its collision) so that their
-// latency hides behind the barrier, the density pass and the next stencil.  The
+// latency hides behind the barrier and the density pass.  A slab takes the
+// moments first, so f(t) is out of the registers before the derivatives
+// stage their rows (the kernel runs at the 128-register limit of two CTAs
+// per SM).  The
 // potential rows arrive by the bulk-copy engine (cp.async.bulk, completion on
 // mbarriers, bounded waits), issued a slab ahead by warp 0:
 //  - the slab's 8 potential rows at full width (the 26-column HDM halo on
@@ -96,6 +100,7 @@ struct FusedArgs {
     int *err;
     int qpitch;         // nx + 2 * QG
     int seg_h;          // rows per CTA segment
+    int n4;             // float4s per population plane (nx ny / 4)
     float w1x, w2x;     // d/dx weights w_1, w_2 (w_j = w_2 r^(j-2) for j >= 2)
     float w1y, w2y;     // d/dy weights
     float ry, ry5, ry12, ry25;  // r = (sqrt 5 - 3)/2 of Eq. 20's tridiagonal operator, and r^5, r^12, r^25
@@ -117,10 +122,12 @@ __device__ __forceinline__ int wrapi(int i, int n) {
     return i;
 }
 
-// Field staged for the stencil: Phi = sqrt|U| (SC, Eq. 21) or U (ZC, Eq. 8).
+// Field staged for the stencil: the signed root s Phi = s sqrt|U|, s the sign
+// of U (SC, Eq. 21), or U (ZC, Eq. 8).  The SC stencil reads |q| = Phi and the
+// cell's own force takes s Phi as stored.
 __device__ __forceinline__ float stencil_field(const Model<float> &m, float rho, bool sc) {
     float U = potential_u(m, rho);
-    return sc ? sqrtf(fabsf(U)) : U;
+    return sc ? (U >= 0.f ? sqrtf(U) : -sqrtf(-U)) : U;
 }
 
 // U = k p_EOS - rho/3 (Eq. 8) with the equation of state fixed at compile time
@@ -150,7 +157,7 @@ __device__ __forceinline__ float potential_u_t(const Model<float> &m, float rho)
 template <int EOS>
 __device__ __forceinline__ float stencil_field_t(const Model<float> &m, float rho, bool sc) {
     const float U = potential_u_t<EOS>(m, rho);
-    return sc ? sqrtf(fabsf(U)) : U;
+    return sc ? (U >= 0.f ? sqrtf(U) : -sqrtf(-U)) : U;
 }
 
 // f^eq_i(rho, u) of Eq. 2 for i = 1..8 with the lattice weights as FP32;
@@ -228,13 +235,15 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     const int xg = x0 - 4 + 4 * lane;               // first of this lane's 4 columns
     const int xgw = wrapi(xg, nx);
     bool timed_out = false;
+    bool unstable = false;                          // a non-positive or non-finite density
 
     // f(t) of row ys - 1 + 8s + warp at the lane's 4 columns
     float4 fv[9];
     auto load_f = [&](int s) {
         const float *src = A.f + (long long)wrapi(ys - 1 + SLAB * s + warp, ny) * nx + xgw;
+        const float4 *p = reinterpret_cast<const float4 *>(src);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fv[i] = ld_stream(reinterpret_cast<const float4 *>(src + i * N));
+        for (int i = 0; i < 9; ++i, p += A.n4) fv[i] = ld_stream(p);   // one pointer stepped plane by plane
     };
     // d/dy column recurrences: thread (warp, lane) follows ring column
     // 16 warp + lane % 16 (padded column x0 + QG - 4 + cl); lanes < 16 carry the
@@ -243,11 +252,12 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     // the padded field, with all loads in flight while the first copies land.
     const int cl = 16 * warp + (lane & 15);
     const bool fwdl = lane < 16;
+    auto mag = [](float v) { return SC ? fabsf(v) : v; };   // the stencil's field value
     float colref = 0.f, pcarry = 0.f;
     if (cl < ncols) {
         const float *g = A.qin + x0 + QG - 4 + cl;
         const int yr = ys - 1 < 0 ? ys - 1 + ny : ys - 1;
-        colref = __ldg(g + (long long)yr * A.qpitch);
+        colref = mag(__ldg(g + (long long)yr * A.qpitch));
         if (fwdl) {
             float v[25];
 #pragma unroll
@@ -256,7 +266,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 v[k] = __ldg(g + (long long)(y < 0 ? y + ny : y) * A.qpitch);
             }
 #pragma unroll
-            for (int k = 0; k < 25; ++k) pcarry = fmaf(A.ry, pcarry, v[k] - colref);
+            for (int k = 0; k < 25; ++k) pcarry = fmaf(A.ry, pcarry, mag(v[k]) - colref);
         }
     }
 
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         int ri = (y0r + (fwdl ? 33 : 20)) % QRING;   // far part Y0+33 .. Y0+21, near part Y0+20 .. Y0+9
 #pragma unroll
         for (int k = 0; k < 13; ++k) {
-            if (fwdl || k < 12) x = fmaf(A.ry, x, col[ri * NW] - colref);
+            if (fwdl || k < 12) x = fmaf(A.ry, x, mag(col[ri * NW]) - colref);
             ri = ri == 0 ? QRING - 1 : ri - 1;
         }
         const float far = __shfl_sync(0xffffffffu, x, lane & 15);
@@ -288,7 +298,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
 #pragma unroll
         for (int k = 0; k < SLAB; ++k) {
             dst[(fwdl ? k : SLAB - 1 - k) * NW] = v;     // P_(Y0+k-1) / Q_(Y0+8-k)
-            v = fmaf(A.ry, v, col[ri * NW] - colref);   // rows Y0-1+k / Y0+8-k
+            v = fmaf(A.ry, v, mag(col[ri * NW]) - colref);   // rows Y0-1+k / Y0+8-k
             ri = fwdl ? (ri + 1 == QRING ? 0 : ri + 1) : (ri == 0 ? QRING - 1 : ri - 1);
         }
         if (fwdl) pcarry = v;   // P_(Y0+7) = P of the next slab's first row minus one
@@ -326,6 +336,21 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         // columns and store nothing.
         {
             float dx[4], dy[4], qc[4];
+            // moments of f(t) (Eq. 3)
+            float r[4] = {0.f, 0.f, 0.f, 0.f}, jx[4] = {0.f, 0.f, 0.f, 0.f}, jy[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float v[4] = {fv[i].x, fv[i].y, fv[i].z, fv[i].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    r[c] += v[c];
+                    if (ex(i)) jx[c] = fmaf(float(ex(i)), v[c], jx[c]);
+                    if (ey(i)) jy[c] = fmaf(float(ey(i)), v[c], jy[c]);
+                }
+            }
+            // for tau = 1 nothing after the moments reads f(t), so f(t) of the next
+            // slab goes in flight here, across the derivatives and the collision
+            if (TAU1 && s + 1 < nslab) load_f(s + 1);
             {   // d/dx: wide row columns 4 lane .. 4 lane + 59; cells at window positions 28..31.
                 // Recurrence form of the same radius-26 operator: for the lane's cell c,
                 //   P_c = sum_{j=2..26} r^(j-2) t_(28+c-j),  Q_c = sum_{j=2..26} r^(j-2) t_(28+c+j),
@@ -343,9 +368,9 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) qc[c] = t[28 + c];
-                const float qref = t[29];
+                const float qref = mag(t[29]);
 #pragma unroll
-                for (int p = 2; p <= 57; ++p) t[p] -= qref;
+                for (int p = 2; p <= 57; ++p) t[p] = mag(t[p]) - qref;
                 const float r = A.ry, r5 = A.ry5, r25 = A.ry25;
                 float gp[5], gq[5];
 #pragma unroll
@@ -375,36 +400,20 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 const float *abs_ = ab + (s & 1) * 2 * SLAB * NW;
                 const float4 P = *reinterpret_cast<const float4 *>(abs_ + warp * NW + 4 * lane);
                 const float4 Q = *reinterpret_cast<const float4 *>(abs_ + (SLAB + warp) * NW + 4 * lane);
-                dy[0] = fmaf(A.w1y, qa.x - qb.x, A.w2y * (Q.x - P.x));
-                dy[1] = fmaf(A.w1y, qa.y - qb.y, A.w2y * (Q.y - P.y));
-                dy[2] = fmaf(A.w1y, qa.z - qb.z, A.w2y * (Q.z - P.z));
-                dy[3] = fmaf(A.w1y, qa.w - qb.w, A.w2y * (Q.w - P.w));
+                dy[0] = fmaf(A.w1y, mag(qa.x) - mag(qb.x), A.w2y * (Q.x - P.x));
+                dy[1] = fmaf(A.w1y, mag(qa.y) - mag(qb.y), A.w2y * (Q.y - P.y));
+                dy[2] = fmaf(A.w1y, mag(qa.z) - mag(qb.z), A.w2y * (Q.z - P.z));
+                dy[3] = fmaf(A.w1y, mag(qa.w) - mag(qb.w), A.w2y * (Q.w - P.w));
             }
-            // moments of f(t) (Eq. 3)
-            float r[4] = {0.f, 0.f, 0.f, 0.f}, jx[4] = {0.f, 0.f, 0.f, 0.f}, jy[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const float v[4] = {fv[i].x, fv[i].y, fv[i].z, fv[i].w};
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    r[c] += v[c];
-                    if (ex(i)) jx[c] = fmaf(float(ex(i)), v[c], jx[c]);
-                    if (ey(i)) jy[c] = fmaf(float(ey(i)), v[c], jy[c]);
-                }
-            }
-            // for tau = 1 the collision reads no f(t) after the moments, so f(t) of
-            // the next slab goes in flight here, across the whole collision
-            if (TAU1 && s + 1 < nslab) load_f(s + 1);
             // force and the two velocities of the forcing (Eq. 10, 22 / 7)
             float ux[4], uy[4], vx[4], vy[4], au[4], av[4], moved[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                if (active && (!(r[c] > 0.f) || !isfinite(r[c]))) atomicOr(A.err, kErrUnstable);
+                unstable |= active && !(r[c] > 0.f && r[c] < INFINITY);   // NaN fails both
                 float Fx, Fy;
-                if (SC) {   // Eq. 22: F = -2 s Phi grad Phi, s the sign of U at the cell
-                    float sphi = potential_u_t<EOS>(m, r[c]) >= 0.f ? qc[c] : -qc[c];
-                    Fx = -2.0f * sphi * dx[c];
-                    Fy = -2.0f * sphi * dy[c];
+                if (SC) {   // Eq. 22: F = -2 s Phi grad Phi, s Phi the stored field at the cell
+                    Fx = -2.0f * qc[c] * dx[c];
+                    Fy = -2.0f * qc[c] * dy[c];
                 } else {    // Eq. 7: F = -grad U
                     Fx = -dx[c];
                     Fy = -dy[c];
@@ -421,6 +430,11 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             // post-collision populations, pushed: x shift by shuffle, store to
             // row yc + e_y if it lies in the segment, accumulate partial densities
             const int rd0 = yc - ys + 3;            // relative destination row of e_y = 0
+            bool rowok[3];                          // destination row yc + k - 1 lies in the segment
+#pragma unroll
+            for (int k = 0; k < 3; ++k) rowok[k] = interior && yc + k - 1 >= ys && yc + k - 1 < ys + hseg;
+            float4 *const dst0 = reinterpret_cast<float4 *>(A.fout + (long long)yc * nx + xg);   // plane 0, row yc
+            float4 *dst = dst0;
             float4 part[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
                               make_float4(0.f, 0.f, 0.f, 0.f)};
 #pragma unroll
@@ -454,9 +468,8 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 } else {
                     d = make_float4(post[0], post[1], post[2], post[3]);
                 }
-                const int yd = yc + ey(i);
-                if (interior && yd >= ys && yd < ys + hseg)
-                    __stcs(reinterpret_cast<float4 *>(A.fout + i * N + (long long)yd * nx + xg), d);
+                if (i != 0) dst += A.n4;                // plane i, stepped from plane i - 1
+                if (rowok[ey(i) + 1]) __stcs((i == 0 ? dst0 : dst) + ey(i) * (nx >> 2), d);
                 float4 &pp = part[ey(i) + 1];
                 pp.x += d.x; pp.y += d.y; pp.z += d.z; pp.w += d.w;
             }
@@ -497,6 +510,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         }
     }
 
+    if (unstable) atomicOr(A.err, kErrUnstable);
     if (stop) {   // CTA-uniform: some thread's wait timed out
         if (threadIdx.x == 0) {
             atomicOr(A.err, kErrTimeout);
@@ -570,6 +584,7 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     a.err = err;
     a.qpitch = fused_q_pitch(m.nx);
     a.seg_h = seg_rows;
+    a.n4 = (int)((long long)m.nx * m.ny / 4);
     if (seg_rows < 1) return cudaErrorInvalidValue;
     dim3 grid((m.nx + TXI - 1) / TXI, (m.ny + seg_rows - 1) / seg_rows);
     if (grid.y > 65535) return cudaErrorInvalidValue;
