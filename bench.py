@@ -211,6 +211,10 @@ def run_ours(args):
 
     lat = lbm.Lattice(params)
     lat.init_density(rho0)
+    if args.segment_rows:
+        lat.set_segment_rows(args.segment_rows)
+    tuned = not args.no_tune and not args.segment_rows
+    seg_rows = lat.tune_segment_rows(3) if tuned else lat.segment_rows()
     lat.step(args.warmup)
     lat.sync()
     # --- device-timed region: inputs resident in HBM ---
@@ -272,6 +276,7 @@ def run_ours(args):
                      "step_frac_of_min_bytes": STEP_MIN_BYTES * value * 1e6 / world / (peak * 1e9)},
         "kernels_ms_per_launch": {k: v["ms"] / v["count"] for k, v in kern.items()},
         "gpu_launches": timing["launches"],
+        "launch": {"segment_rows": seg_rows, "tuned": tuned},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": cells * 4 / args.steps,
                 "d2h_bytes_per_step": (3 * cells * 4 + 4) / args.steps,
                 "note": "init_density from host FP64 rho (converted to FP32 in pinned staging), "
@@ -709,6 +714,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the automatic segment height instead of timing the candidates before warm-up")
+    ap.add_argument("--segment-rows", type=int, default=0,
+                    help="fix the segment height of the single-pass step (no tuning); 0: tune")
     ap.add_argument("--nx", type=int, default=NX, help="lattice size (default: the 4096 x 4096 workload)")
     ap.add_argument("--ny", type=int, default=NY)
     ap.add_argument("--workload", choices=["spinodal", "sweep", "adjoint", "coexistence", "droplet", "laplace"],

@@ -206,10 +206,22 @@ lbm_status lbm_adjoint_backward(lbm_ctx *c, const void *grad_rho_T, void *grad_r
 /* Launch shape of the single-pass FP32 step (not a passage of the paper): a
  * CTA sweeps `rows` rows of a 120-column strip.  0 (the default) picks the
  * height from the lattice and the device's SM count; 1..ny fixes it.  Results
- * do not depend on it.  LBM_E_INVALID outside [0, ny].  lbm_get_segment_rows
- * reports the height in use, 0 when the context runs the two-pass step. */
+ * depend on it only through FP32 rounding (the d/dy sums restart at every
+ * segment; the same height gives bit-identical results).  LBM_E_INVALID
+ * outside [0, ny].  lbm_get_segment_rows reports the height in use, 0 when
+ * the context runs the two-pass step. */
 lbm_status lbm_set_segment_rows(lbm_ctx *c, int rows);
 lbm_status lbm_get_segment_rows(lbm_ctx *c, int *rows);
+
+/* Autotuner for the segment height (not a passage of the paper): times
+ * `trials` (1..1000) launches of the single-pass step for every height
+ * 8k - 2 <= min(ny, 1022), on the current state, keeps the fastest for the
+ * context and returns it in *rows.  The state is kept: each trial reads f
+ * and writes only the buffers that the next step overwrites.  *rows = 0 and
+ * nothing timed when the context runs the two-pass step.  LBM_E_STATE before
+ * initialisation, LBM_E_INVALID for a bad argument, LBM_E_UNSTABLE if the
+ * trial steps flag a non-positive density.  Synchronising. */
+lbm_status lbm_tune_segment_rows(lbm_ctx *c, int trials, int *rows);
 
 /* Enable (1) or disable (0) the event accounting of lbm_step; enabling
  * resets the counters.  Not synchronising. */

@@ -582,6 +582,58 @@ lbm_status lbm_get_segment_rows(lbm_ctx *c, int *rows) {
     return LBM_OK;
 }
 
+lbm_status lbm_tune_segment_rows(lbm_ctx *c, int trials, int *rows) {
+    lbm_status st = check_ready(c);
+    if (st != LBM_OK) return st;
+    if (!rows) return fail(c, LBM_E_INVALID, "rows must be non-NULL");
+    if (trials < 1 || trials > 1000) return fail(c, LBM_E_INVALID, "trials must be in [1, 1000]");
+    if (!c->fused) {
+        *rows = 0;
+        return LBM_OK;
+    }
+    // Every trial launch reads the current state (f and its padded potential)
+    // and writes the buffers the next step overwrites, so the state is kept.
+    const Model<float> m = model_of<float>(c);
+    const float *f = (const float *)c->f[c->cur];
+    if (!c->qpad_valid) {
+        CK(c, launch_potential_padded(m, is_sc(c), f, (float *)c->qpad[c->cur], c->err, c->stream), "potential");
+        c->qpad_valid = true;
+    }
+    auto launch = [&](int h) {
+        return launch_fused_step(m, is_sc(c), f, (const float *)c->qpad[c->cur], (float *)c->f[1 - c->cur],
+                                 (float *)c->qpad[1 - c->cur], c->err, h, c->stream);
+    };
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    int best = 0;
+    float best_ms = 0.f;
+    // heights 8k - 2 (whole slabs, no wasted collided rows) up to the lattice or 1022 rows
+    const int hmax = std::min(c->p.ny, 1022);
+    for (int h = 6; h <= hmax && e == cudaSuccess; h += 8) {
+        if ((c->p.ny + h - 1) / h > 65535) continue;
+        e = launch(h);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
+        for (int t = 0; t < trials && e == cudaSuccess; ++t) e = launch(h);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e == cudaSuccess && (best == 0 || ms < best_ms)) {
+            best = h;
+            best_ms = ms;
+        }
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    CK(c, e, "segment-height trials");
+    st = read_error_word(c);
+    if (st != LBM_OK) return st;
+    c->seg_rows = best;
+    *rows = best;
+    return LBM_OK;
+}
+
 lbm_status lbm_init_density_device(lbm_ctx *c, const void *rho, const void *ux, const void *uy) {
     if (!c) return LBM_E_INVALID;
     if (!rho) return fail(c, LBM_E_INVALID, "rho is NULL");

@@ -77,6 +77,7 @@ SIGNATURES = {
     "lbm_adjoint_forward": (ctypes.c_int, [_V, _V, ctypes.c_int, ctypes.c_int, _V]),
     "lbm_set_segment_rows": (ctypes.c_int, [_V, ctypes.c_int]),
     "lbm_get_segment_rows": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_tune_segment_rows": (ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "lbm_adjoint_backward": (ctypes.c_int, [_V, _V, _V, _D, _D, _D]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.c_int, ctypes.POINTER(_V)]),
     "lbm_batch_init_density": (ctypes.c_int, [_V, _D]),
@@ -251,6 +252,13 @@ class Lattice:
     def segment_rows(self) -> int:
         r = ctypes.c_int()
         self._check(self._lib.lbm_get_segment_rows(self._h, ctypes.byref(r)))
+        return r.value
+
+    def tune_segment_rows(self, trials: int = 3) -> int:
+        """Time the single-pass step at every segment height 8k - 2 on the current
+        state (which is kept), keep the fastest and return it (0: two-pass step)."""
+        r = ctypes.c_int()
+        self._check(self._lib.lbm_tune_segment_rows(self._h, int(trials), ctypes.byref(r)))
         return r.value
 
     def adjoint_forward(self, rho0_ptr: int, nsteps: int, checkpoint_interval: int, rhoT_ptr: int):

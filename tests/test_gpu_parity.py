@@ -267,6 +267,45 @@ def test_f32_single_pass_segment_height_does_not_change_results():
         assert lat.segment_rows() == 0
 
 
+def test_f32_segment_height_tuner_keeps_state():
+    # the tuner times trial launches on the current state: it leaves the
+    # state it found, keeps a whole-slab height 8k - 2 <= ny, and the steps
+    # after it are bit-identical to steps with that height set by hand
+    nx, ny = 252, 200
+    gp, op = make(nx, ny, "cs", 0.8, "sc", "hdm", prec="f32")
+    g, l, _ = oracle.maxwell(op)
+    f0 = perturbed_state(op, inputs.droplet(nx, ny, 50, g, l), seed=3)
+    with lbm.Lattice(gp) as lat:
+        lat.set_f(f0)
+        lat.step(3)
+        before = lat.get_f()
+        rows = lat.tune_segment_rows(2)
+        assert rows % 8 == 6 and 6 <= rows <= ny
+        assert lat.segment_rows() == rows
+        assert np.array_equal(lat.get_f(), before)
+        lat.step(5)
+        tuned = lat.get_f()
+    with lbm.Lattice(gp) as lat:
+        lat.set_f(f0)
+        lat.step(3)
+        lat.set_segment_rows(rows)
+        lat.step(5)
+        assert np.array_equal(lat.get_f(), tuned)
+    with lbm.Lattice(gp) as lat:
+        with pytest.raises(lbm.LBMError) as ei:
+            lat.tune_segment_rows(2)
+        assert ei.value.status == lbm.E_STATE
+        lat.set_f(f0)
+        for bad in (0, 1001):
+            with pytest.raises(lbm.LBMError) as ei:
+                lat.tune_segment_rows(bad)
+            assert ei.value.status == lbm.E_INVALID
+    gp.two_pass = True
+    with lbm.Lattice(gp) as lat:
+        lat.set_f(f0)
+        assert lat.tune_segment_rows(2) == 0
+
+
 def test_f32_single_pass_is_deterministic():
     # the same input stepped twice in fresh contexts gives bit-identical
     # states: every value the kernel reads from shared memory has landed (the
