@@ -459,6 +459,17 @@ def run_adjoint(args):
             return out
 
     r32 = run("f32", timed=True)
+    ratio = (r32["fwd_ms"] + r32["bwd_ms"]) / r32["plain_ms"]
+    if args.adj_cost_only:
+        print(json.dumps({
+            "metric": "adjoint cost: (taped forward + backward) / plain forward", "unit": "x", "value": ratio,
+            "higher_is_better": False, "n_gpus": 1, "steps": N, "warmup": args.warmup, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": f"droplet R80 -> target R90, {nx}x{ny} periodic, CS a=1 "
+                                                        f"b=4 T/Tc={Tr}, SC force, HDM gradient, tau 1 (cost only)",
+                                            "checkpoint_interval": C},
+            "plain_forward_ms": r32["plain_ms"], "taped_forward_ms": r32["fwd_ms"], "backward_ms": r32["bwd_ms"],
+            "backward_over_plain": r32["bwd_ms"] / r32["plain_ms"]}), flush=True)
+        return 0
     r64 = run("f64")
     # central differences at h = 1e-4 Tr and h/2; the Richardson combination
     # (4 FD(h/2) - FD(h)) / 3 removes the h^2 term of the truncation error
@@ -470,7 +481,6 @@ def run_adjoint(args):
     eps = 1e-6
     fd_dir = (run("f64", r0=rho0 + eps * d)["L"] - run("f64", r0=rho0 - eps * d)["L"]) / (2 * eps)
     adj_dir = float((r64["drho0"] * d).sum())
-    ratio = (r32["fwd_ms"] + r32["bwd_ms"]) / r32["plain_ms"]
 
     # a live interaction-strength gradient: the original effective mass of
     # Eq. 4 (psi = 1 - exp(-rho), G = -1.7), 256 x 256 droplet R 50 -> 56,
@@ -731,6 +741,8 @@ def main():
     ap.add_argument("--droplet-steps", type=int, default=2000, help="steps of the droplet workload")
     ap.add_argument("--coex-steps", type=int, default=20000, help="steps of the coexistence workload")
     ap.add_argument("--adj-steps", type=int, default=5000, help="forward steps of the adjoint workload")
+    ap.add_argument("--adj-cost-only", action="store_true",
+                    help="adjoint workload: time the FP32 forward and reverse sweeps only (no gradient checks)")
     ap.add_argument("--seq-steps", type=int, default=200, help="steps timed per lattice in the sequential arm")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -42,6 +42,8 @@
 // in a fixed order at the end.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "lbm_internal.h"
 #include "ptx.cuh"
 
@@ -51,8 +53,8 @@ namespace {
 template <typename T>
 struct AdjTile;
 template <>
-struct AdjTile<float> {   // one cell per thread, 1024 threads
-    static constexpr int TX = 64, TY = 16, TYT = 16;
+struct AdjTile<float> {   // two cells per thread, 512 threads (the padded tile phase needs ~50 registers)
+    static constexpr int TX = 64, TY = 16, TYT = 8;
 };
 template <>
 struct AdjTile<double> {  // two cells per thread (register budget)
@@ -151,6 +153,7 @@ struct AdjArgs {
     int dpitch, doff;
     double *Tpart;  // one FP64 slot per CTA of A, then per CTA of B
     int *err;       // error word (a bounded wait that gave up)
+    T r, r5, r25;   // r = (sqrt 5 - 3)/2 of Eq. 20's operator and its powers (padded FP32 tiles)
 };
 
 // Sum of v over the CTA (over each warp in T, then in FP64), added to *slot.
@@ -224,6 +227,52 @@ __device__ __forceinline__ void store_field(T *row, int x, int nx, T v) {
 constexpr int XO = 28;   // x halo columns staged (>= radius, XO * 4 bytes a multiple of 16)
 constexpr int LO = 4;    // lambda halo columns staged (>= 1)
 
+// HDM derivatives of a padded FP32 tile (64 x 16 cells) of a staged field,
+// written to D[ly * 64 + lx] (along x) and D[1024 + ly * 64 + lx] (along y),
+// both radius-26 operators in recurrence form (hdm_window4).
+// Along x, tile row ly is staged at X + ly * XP with tile column c at X + ly *
+// XP + 28 + c; work items 0..255 take four cells of a row each from one
+// 60-value window of 16-byte loads.  Along y, tile cell (lx, ly) is staged at
+// Y + (26 + ly) * YP + yc0 + lx (26 halo rows on each side); items 256..511
+// take four cells of a column each from one 56-row window.  Thread k of the
+// CTA (at least 512 threads) takes item k; the caller synchronises the CTA
+// before and after.  ABS: the field enters as its magnitude.
+template <bool ABS>
+__device__ __forceinline__ void tile_hdm(const float *X, int XP, const float *Y, int YP, int yc0, float *D,
+                                         const Model<float> &m, float r, float r5, float r25) {
+    auto mag = [](float v) { return ABS ? fabsf(v) : v; };
+    const int item = threadIdx.x + blockDim.x * threadIdx.y;
+    if (item >= 512) return;
+    float t[60], d[4];
+#pragma unroll
+    for (int p = 0; p < 60; ++p) t[p] = 0.f;
+    if (item < 256) {
+        const int ly = item >> 4, g = item & 15;
+        const float *w = X + ly * XP + 4 * g;    // window position p = tile column 4g - 28 + p
+#pragma unroll
+        for (int k = 0; k < 15; ++k) {
+            const float4 v4 = *reinterpret_cast<const float4 *>(w + 4 * k);
+            t[4 * k] = v4.x; t[4 * k + 1] = v4.y; t[4 * k + 2] = v4.z; t[4 * k + 3] = v4.w;
+        }
+        const float ref = mag(t[29]);
+#pragma unroll
+        for (int p = 2; p <= 57; ++p) t[p] = mag(t[p]) - ref;
+        hdm_window4(t, m.wx[1], m.wx[2], r, r5, r25, d);
+        *reinterpret_cast<float4 *>(D + ly * 64 + 4 * g) = make_float4(d[0], d[1], d[2], d[3]);
+    } else {
+        const int i = item - 256, cx = i & 63, h = i >> 6;
+        const float *col = Y + 4 * h * YP + yc0 + cx;   // window position p = staged row 4h - 2 + p
+#pragma unroll
+        for (int p = 2; p <= 57; ++p) t[p] = col[(p - 2) * YP];
+        const float ref = mag(t[29]);
+#pragma unroll
+        for (int p = 2; p <= 57; ++p) t[p] = mag(t[p]) - ref;
+        hdm_window4(t, m.wy[1], m.wy[2], r, r5, r25, d);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) D[1024 + (4 * h + c) * 64 + cx] = d[c];
+    }
+}
+
 // Bounded wait of the whole CTA for the bulk copies on bars[k]; on timeout
 // flags the error word, lets the copies in flight on all nbar barriers land
 // and returns false.
@@ -258,6 +307,10 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
     T *S = reinterpret_cast<T *>(smem_raw);
     T *L = S + W * H;
     uint64_t *bars = reinterpret_cast<uint64_t *>(L + (TAU1 ? 3 * LW * LH : 0));  // PAD: field, lambda
+    // padded FP32 tiles: the field's derivatives over the tile, formed once
+    constexpr bool RECUR = PAD && KC == 26 && !CDM;
+    static_assert(!RECUR || TX * TYT >= 512, "the tile phase takes one work item per thread");
+    T *DT = reinterpret_cast<T *>(bars + 2);
     if constexpr (PAD) {
         const int tid = threadIdx.x + TX * threadIdx.y;
         if (tid == 0) {
@@ -340,6 +393,13 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
             const T ne = fld(W + 1), nw = fld(W - 1), se = fld(-W + 1), sw = fld(-W - 1);
             Dx = T(1.0 / 3.0) * (e - w) + T(1.0 / 12.0) * ((ne + se) - (nw + sw));
             Dy = T(1.0 / 3.0) * (nn - s) + T(1.0 / 12.0) * ((ne + nw) - (se + sw));
+        } else if constexpr (RECUR) {
+            if (k == 0) {
+                tile_hdm<SC>(S + hy * W, W, S, W, XO, DT, m, a.r, a.r5, a.r25);
+                __syncthreads();
+            }
+            Dx = DT[ly * TX + lx];
+            Dy = DT[TX * TY + ly * TX + lx];
         } else {
             Dx = stencil<T, KC, SC, false>(row, 1, m);
             Dy = stencil<T, KC, SC, true>(row, W, m);
@@ -436,6 +496,9 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
     T *SX = reinterpret_cast<T *>(smem_raw);
     T *SY = SX + WX * HX;
     uint64_t *bars = reinterpret_cast<uint64_t *>(SY + WY * HY);
+    constexpr bool RECUR = PAD && KC == 26 && !CDM;
+    static_assert(!RECUR || TX * TYT >= 512, "the tile phase takes one work item per thread");
+    T *DT = reinterpret_cast<T *>(bars + 2);   // padded FP32 tiles: D_bar's derivatives over the tile
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     if constexpr (PAD) {
         const int tid = threadIdx.x + TX * threadIdx.y;
@@ -489,6 +552,13 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
                   T(1.0 / 12.0) * ((rx[WX + 1] + rx[-WX + 1]) - (rx[WX - 1] + rx[-WX - 1]));
             ddy = T(1.0 / 3.0) * (ry[WY] - ry[-WY]) +
                   T(1.0 / 12.0) * ((ry[WY + 1] + ry[WY - 1]) - (ry[-WY + 1] + ry[-WY - 1]));
+        } else if constexpr (RECUR) {
+            if (k == 0) {
+                tile_hdm<false>(SX + oy * WX, WX, SY, WY, ox, DT, m, a.r, a.r5, a.r25);
+                __syncthreads();
+            }
+            ddx = DT[ly * TX + lx];
+            ddy = DT[TX * TY + ly * TX + lx];
         } else {
             ddx = stencil<T, KC, false, false>(rx, 1, m);
             ddy = stencil<T, KC, false, true>(ry, WY, m);
@@ -591,11 +661,13 @@ cudaError_t launch_adj_t(const AdjArgs<T> &a, cudaStream_t s) {
     const int hx = CDM ? 1 : (KC ? KC : a.m.kx), hy = CDM ? 1 : (KC ? KC : a.m.ky);
     const int XS = PAD ? XO : hx;
     const int LW = PAD ? TX + 2 * LO : TX + 2;
+    constexpr bool RECUR = PAD && KC == 26 && !CDM;   // tile derivatives after the barriers
+    const size_t dt = RECUR ? 2 * sizeof(T) * TX * TY : 0;
     const size_t smem_a = sizeof(T) * ((size_t)(TX + 2 * XS) * (TY + 2 * hy) + (TAU1 ? 3 * LW * (TY + 2) : 0)) +
-                          (PAD ? 2 * sizeof(uint64_t) : 0);
+                          (PAD ? 2 * sizeof(uint64_t) : 0) + dt;
     const size_t smem_b = (CDM ? sizeof(T) * 2 * (size_t)(TX + 2) * (TY + 2)
                                : sizeof(T) * ((size_t)(TX + 2 * XS) * TY + (size_t)TX * (TY + 2 * hy))) +
-                          (PAD ? sizeof(uint64_t) : 0);
+                          (PAD ? 2 * sizeof(uint64_t) : 0) + dt;
     auto ka = adj_a_kernel<T, SC, CDM, TAU1, KC, PAD>;
     auto kb = adj_b_kernel<T, SC, CDM, TAU1, KC, PAD>;
     cudaError_t e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
@@ -671,6 +743,10 @@ cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cd
     a.doff = l.doff;
     a.Tpart = Tpart;
     a.err = err;
+    const double r = 0.5 * (std::sqrt(5.0) - 3.0);   // root of r^2/3 + r + 1/3 = 0 (Eq. 20's operator)
+    a.r = (T)r;
+    a.r5 = (T)std::pow(r, 5);
+    a.r25 = (T)std::pow(r, 25);
 #define LBM_ADJ_PICK(SC, CDM)                                                                             \
     return tau1 ? launch_adj_k<T, SC, CDM, true>(a, padded, s) : launch_adj_k<T, SC, CDM, false>(a, padded, s)
     if (sc) {

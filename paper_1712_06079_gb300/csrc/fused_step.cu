@@ -352,13 +352,8 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             // slab goes in flight here, across the derivatives and the collision
             if (TAU1 && s + 1 < nslab) load_f(s + 1);
             {   // d/dx: wide row columns 4 lane .. 4 lane + 59; cells at window positions 28..31.
-                // Recurrence form of the same radius-26 operator: for the lane's cell c,
-                //   P_c = sum_{j=2..26} r^(j-2) t_(28+c-j),  Q_c = sum_{j=2..26} r^(j-2) t_(28+c+j),
-                //   d/dx = w_1 (t_(29+c) - t_(27+c)) + w_2 (Q_c - P_c),
-                // P_0 and Q_3 as five 5-term Horner groups joined by r^5, the other
-                // cells by one step each (P_c = t_(26+c) + r P_(c-1) - r^25 t_(1+c), Q
-                // mirrored).  Each staged value enters as its deviation t from the
-                // lane's second cell, so the sums carry only local variations.
+                // The radius-26 operator in recurrence form (hdm_window4); each staged
+                // value enters as its deviation t from the lane's second cell.
                 const float *qrow = qw + ((s & 1) * SLAB + warp) * WW + 4 * lane;
                 float t[60];
 #pragma unroll
@@ -371,28 +366,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 const float qref = mag(t[29]);
 #pragma unroll
                 for (int p = 2; p <= 57; ++p) t[p] = mag(t[p]) - qref;
-                const float r = A.ry, r5 = A.ry5, r25 = A.ry25;
-                float gp[5], gq[5];
-#pragma unroll
-                for (int g = 0; g < 5; ++g) {
-                    float x = t[2 + 5 * g];                 // P_0: positions 2 + 5g .. 6 + 5g, far to near
-#pragma unroll
-                    for (int i = 1; i < 5; ++i) x = fmaf(r, x, t[2 + 5 * g + i]);
-                    gp[g] = x;
-                    float y = t[37 + 5 * g];                // Q_3: positions 37 + 5g .. 33 + 5g, far to near
-#pragma unroll
-                    for (int i = 1; i < 5; ++i) y = fmaf(r, y, t[37 + 5 * g - i]);
-                    gq[g] = y;
-                }
-                float P[4], Q[4];
-                P[0] = fmaf(fmaf(fmaf(fmaf(gp[0], r5, gp[1]), r5, gp[2]), r5, gp[3]), r5, gp[4]);
-                Q[3] = fmaf(fmaf(fmaf(fmaf(gq[4], r5, gq[3]), r5, gq[2]), r5, gq[1]), r5, gq[0]);
-#pragma unroll
-                for (int c = 1; c < 4; ++c) P[c] = fmaf(-r25, t[1 + c], fmaf(r, P[c - 1], t[26 + c]));
-#pragma unroll
-                for (int c = 2; c >= 0; --c) Q[c] = fmaf(-r25, t[55 + c], fmaf(r, Q[c + 1], t[30 + c]));
-#pragma unroll
-                for (int c = 0; c < 4; ++c) dx[c] = fmaf(A.w1x, t[29 + c] - t[27 + c], A.w2x * (Q[c] - P[c]));
+                hdm_window4(t, A.w1x, A.w2x, A.ry, A.ry5, A.ry25, dx);
             }
             {   // d/dy from the column recurrences of this row
                 const float4 qa = *reinterpret_cast<const float4 *>(qn + ((ryc + 1) % QRING) * NW + 4 * lane);

@@ -91,4 +91,41 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
     return i;
 }
 
+// HDM derivative of four consecutive cells from a window of 60 staged values
+// t[0..59], the cells at positions 28..31 (positions 2..57 are read): the
+// explicit periodic operator of Eq. 20 truncated at radius 26, whose weights
+// are geometric past the first, w_j = w_2 r^(j-2), run in recurrence form:
+//   P_c = sum_{j=2..26} r^(j-2) t_(28+c-j),   Q_c = sum_{j=2..26} r^(j-2) t_(28+c+j),
+//   D_c = w_1 (t_(29+c) - t_(27+c)) + w_2 (Q_c - P_c).
+// P_0 and Q_3 are five independent 5-term Horner groups joined by r^5; the
+// other cells follow by one step each (P_c = t_(26+c) + r P_(c-1) - r^25
+// t_(1+c), Q mirrored), dropping the term that leaves the radius, so the
+// truncation is the stencil's.  t should hold deviations from a nearby value:
+// the constant part cancels between P and Q, and the sums then carry only
+// local variations.
+__device__ __forceinline__ void hdm_window4(const float (&t)[60], float w1, float w2, float r, float r5, float r25,
+                                            float (&d)[4]) {
+    float gp[5], gq[5];
+#pragma unroll
+    for (int g = 0; g < 5; ++g) {
+        float x = t[2 + 5 * g];                 // P_0: positions 2 + 5g .. 6 + 5g, far to near
+#pragma unroll
+        for (int i = 1; i < 5; ++i) x = fmaf(r, x, t[2 + 5 * g + i]);
+        gp[g] = x;
+        float y = t[37 + 5 * g];                // Q_3: positions 37 + 5g .. 33 + 5g, far to near
+#pragma unroll
+        for (int i = 1; i < 5; ++i) y = fmaf(r, y, t[37 + 5 * g - i]);
+        gq[g] = y;
+    }
+    float P[4], Q[4];
+    P[0] = fmaf(fmaf(fmaf(fmaf(gp[0], r5, gp[1]), r5, gp[2]), r5, gp[3]), r5, gp[4]);
+    Q[3] = fmaf(fmaf(fmaf(fmaf(gq[4], r5, gq[3]), r5, gq[2]), r5, gq[1]), r5, gq[0]);
+#pragma unroll
+    for (int c = 1; c < 4; ++c) P[c] = fmaf(-r25, t[1 + c], fmaf(r, P[c - 1], t[26 + c]));
+#pragma unroll
+    for (int c = 2; c >= 0; --c) Q[c] = fmaf(-r25, t[55 + c], fmaf(r, Q[c + 1], t[30 + c]));
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d[c] = fmaf(w1, t[29 + c] - t[27 + c], w2 * (Q[c] - P[c]));
+}
+
 }  // namespace lbm
