@@ -589,6 +589,50 @@ def run_coexistence(args):
                       "cases": cases}), flush=True)
     return 0
 
+def run_profile(args):
+    """Sec. 5.1 / Fig. 4: derivatives of the exact equilibrium profile across a
+    flat interface (VdW a=9/49 b=2/21, T/Tc = 0.9, kappa = 0.05, h = 0.5; the
+    stored fixture tests/golden/flat_profile_vdw_tr09.txt, written from the
+    FP64 oracle by tests/golden/make_flat_profile.py) by the library's HDM and
+    CDM operators (lbm_gradient), FP64 and FP32, against the exact slope.  The
+    line is made periodic by its mirror image (two interfaces 256 apart)."""
+    import numpy as np
+    import torch
+
+    from paper_1712_06079_gb300 import lbm
+
+    torch.cuda.set_device(0)
+    rows = np.loadtxt(os.path.join(ROOT, "tests", "golden", "flat_profile_vdw_tr09.txt"))
+    y, rho, drho = rows[:, 0], rows[:, 1], rows[:, 2]
+    line, exact = np.concatenate([rho, rho[::-1]]), np.concatenate([drho, -drho[::-1]])
+    h, n = 0.5, line.size
+    q = np.tile(line[:, None], (1, 4))
+    out = {}
+    i0 = len(y) // 2
+    win = slice(i0 - 20, i0 + 21)   # the interface, +-10 length units
+    for prec in ("f64", "f32"):
+        for grad in ("hdm", "cdm"):
+            with lbm.Lattice(lbm.Params(nx=4, ny=n, eos="vdw", a=9 / 49, b=2 / 21, Tr=0.9, force="sc", grad=grad,
+                                        prec=prec)) as lat:
+                _, gy = lat.gradient(q, h)
+            err = gy[:, 0] - exact
+            out[f"{grad}_{prec}"] = {"max_rel_err": float(np.abs(err).max() / np.abs(exact).max()),
+                                     "rms_rel_err_interface": float(np.sqrt(np.mean(err[win] ** 2)) / np.abs(exact).max()),
+                                     "err_at_y": {f"{y[i]:+.1f}": float(err[i]) for i in range(i0 - 4, i0 + 5, 2)}}
+    line_out = {
+        "metric": "max |D rho - exact| / max |exact| on the exact flat-interface profile (Fig. 4)", "unit": "relative",
+        "value": out["hdm_f32"]["max_rel_err"], "higher_is_better": False, "n_gpus": 1, "dtype": "f32 (f64 beside it)",
+        "data": "synthetic (exact profile from the FP64 oracle, stored fixture)",
+        "config": {"workload": "VdW a=9/49 b=2/21 T/Tc=0.9, kappa=0.05, h=0.5, 512-point profile mirrored to 1024"},
+        "cdm_over_hdm_f32": out["cdm_f32"]["max_rel_err"] / out["hdm_f32"]["max_rel_err"],
+        "cdm_over_hdm_f64": out["cdm_f64"]["max_rel_err"] / out["hdm_f64"]["max_rel_err"],
+        "exact_max_slope": float(np.abs(exact).max()), "rho_g": float(rho[0]), "rho_l": float(rho[-1]),
+        **out,
+    }
+    print(json.dumps(line_out), flush=True)
+    return 0
+
+
 def run_droplet(args):
     """Static droplet: 128 x 128, CS a=1 b=4, T/Tc = 0.8, droplet R = 30 (tanh
     W = 2 between the Maxwell densities), SC force, HDM gradient, tau = 1,
@@ -730,7 +774,8 @@ def main():
                     help="fix the segment height of the single-pass step (no tuning); 0: tune")
     ap.add_argument("--nx", type=int, default=NX, help="lattice size (default: the 4096 x 4096 workload)")
     ap.add_argument("--ny", type=int, default=NY)
-    ap.add_argument("--workload", choices=["spinodal", "sweep", "adjoint", "coexistence", "droplet", "laplace"],
+    ap.add_argument("--workload", choices=["spinodal", "sweep", "adjoint", "coexistence", "droplet", "laplace",
+                                           "profile"],
                     default="spinodal",
                     help="spinodal: the throughput line; sweep: batched vs sequential 64-lattice sweep; "
                          "adjoint: reverse-mode cost and gradient checks on the 512 x 512 droplet; "
@@ -758,6 +803,8 @@ def main():
         return run_coexistence(args)
     if args.workload == "droplet":
         return run_droplet(args)
+    if args.workload == "profile":
+        return run_profile(args)
     if args.workload == "laplace":
         return run_laplace(args)
     return run_ours(args)

@@ -180,6 +180,18 @@ lbm_status lbm_moments_device(lbm_ctx *c, void *rho, void *vx, void *vy);
 /* FP64 lattice reductions of the current state.  Synchronising. */
 lbm_status lbm_observables(lbm_ctx *c, lbm_obs *out);
 
+/* The context's gradient operator applied to a caller field, with the same
+ * device code as the step's interaction (the two-pass kernels' tile stencil):
+ * HDM, the periodic solution of Eq. 20 along every row (d/dx) and column
+ * (d/dy) as the folded explicit stencil of the context's radius, or CDM, Eq. 15
+ * times 1/c_s^2 = 3; both divided by the grid spacing h (the step uses h = 1).
+ * q, gx, gy: host FP64 arrays of nx*ny values, row-major (x fastest), q taken
+ * as given (no magnitude, unlike the Shan-Chen field); computed in the
+ * context precision (q rounded to FP32 for FP32 contexts).  The lattice state
+ * is not touched and need not be initialised.  LBM_E_INVALID for NULL arrays
+ * or h <= 0.  Synchronising. */
+lbm_status lbm_gradient(lbm_ctx *c, const double *q, double h, double *gx, double *gy);
+
 /* Reverse mode through nsteps steps, for gradients of a function of the final
  * density (e.g. the L2 distance to a target droplet) with respect to the
  * initial density and the model's scalar parameter: the temperature, or the

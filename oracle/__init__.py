@@ -78,6 +78,8 @@ def _load():
             lib.orc_step.argtypes = [P, D, D]
             lib.orc_run.argtypes = [P, D, ctypes.c_int]
             lib.orc_moments.argtypes = [P, D, D, D, D]
+            lib.orc_flat_profile.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, D, D]
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -153,6 +155,20 @@ def maxwell(p: Params):
     if _load().orc_maxwell(ctypes.byref(p.c()), ctypes.byref(g), ctypes.byref(l), ctypes.byref(s)):
         raise RuntimeError("no van der Waals loop at this temperature")
     return g.value, l.value, s.value
+
+
+def flat_profile(p: Params, kappa: float, h: float, n: int, i0: int | None = None, sub: int = 64):
+    """Equilibrium density profile across a flat interface (Sec. 5.1): Eq. 26
+    with the pressure tensor of Eq. 25 for the unscaled EOS at p.T, integrated
+    through its first integral (kappa/2) rho'^2 = W(rho).  Returns (y, rho,
+    drho/dy) at y_i = (i - i0) h, rising from rho_g to rho_l, y = 0 at the mean
+    of the two Maxwell densities (i0 = n // 2 by default)."""
+    i0 = n // 2 if i0 is None else int(i0)
+    rho, drho = np.empty(n), np.empty(n)
+    if _load().orc_flat_profile(ctypes.byref(p.c()), float(kappa), float(h), int(n), i0, int(sub),
+                                _ptr(rho), _ptr(drho)):
+        raise RuntimeError("no van der Waals loop at this temperature, or invalid arguments")
+    return (np.arange(n) - i0) * h, rho, drho
 
 
 def p_eos(p: Params, rho):

@@ -314,6 +314,140 @@ int orc_maxwell(const orc_params *q, double *rho_g, double *rho_l, double *p_sat
 }
 
 /* ------------------------------------------------------------------------ */
+/* Flat-interface equilibrium profile (Sec. 5.1, Eq. 25-26).  For a profile  */
+/* rho(y), Eq. 26 with the tensor of Eq. 25 keeps only                        */
+/*   d/dy [ p(rho) - kappa rho rho'' + (kappa/2) rho'^2 ] = 0,                */
+/* so the bracket equals its bulk value, the coexistence pressure p_s.        */
+/* A first integral is (kappa/2) rho'^2 = W(rho) with                          */
+/*   W(rho) = rho I(rho),  I(rho) = int_{rho_g}^{rho} (p(s) - p_s)/s^2 ds:     */
+/* differentiating, kappa rho'' = W'(rho) = I + (p - p_s)/rho, and then       */
+/* p - kappa rho rho'' + (kappa/2) rho'^2 = p - rho I - (p - p_s) + rho I =   */
+/* p_s.  W has double roots at rho_g and, by the equal-area rule, at rho_l,   */
+/* so the lower limit may be either bulk density; W is evaluated from the     */
+/* nearer one (no cancellation in the tails) by Gauss-Legendre quadrature.    */
+/* The profile rising from rho_g to rho_l is integrated in the logit          */
+/*   u = ln((rho - rho_g)/(rho_l - rho)),                                      */
+/*   du/dy = sqrt(2 W / kappa) (rho_l - rho_g) / ((rho - rho_g)(rho_l - rho)), */
+/* which keeps rho strictly between the bulk densities and is linear in y in  */
+/* the tails.  y = 0 at u = 0 (the mean density); classical Runge-Kutta (4th  */
+/* order), `sub` steps per grid spacing h, outward in both directions.        */
+/* ------------------------------------------------------------------------ */
+
+#define GL_N 24
+static double gl_x[GL_N], gl_w[GL_N];
+static int gl_ready = 0;
+
+/* Gauss-Legendre nodes and weights on [-1, 1]: roots of P_n by Newton's      */
+/* method from the guess cos(pi (i - 1/4)/(n + 1/2)), P_n and P_n' from the   */
+/* three-term recurrence; w_i = 2 / ((1 - x_i^2) P_n'(x_i)^2).                */
+static void gl_init(void) {
+    if (gl_ready) return;
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < GL_N; ++i) {
+        double x = cos(pi * (i + 0.75) / (GL_N + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= GL_N; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = GL_N * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        gl_x[i] = x;
+        gl_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    gl_ready = 1;
+}
+
+/* int_a^b (p(s) - ps)/s^2 ds, as int (p(e^t) - ps) e^-t dt over t = ln s,    */
+/* by composite Gauss-Legendre (the integrand is smooth in t)                  */
+static double area_gl(const orc_params *q, double ps, double a, double b, int panels) {
+    double t0 = log(a), w = (log(b) - t0) / panels, acc = 0.0;
+    for (int k = 0; k < panels; ++k) {
+        double c = t0 + (k + 0.5) * w, hw = 0.5 * w;
+        for (int i = 0; i < GL_N; ++i) {
+            double s = exp(c + hw * gl_x[i]);
+            acc += gl_w[i] * hw * (p_of(q, s) - ps) / s;
+        }
+    }
+    return acc;
+}
+
+/* W(rho) = rho int_{rb}^{rho} (p(s) - p_s)/s^2 ds, rb the nearer bulk density */
+static double profile_W(const orc_params *q, double ps, double rg, double rl, double rho) {
+    double rb = (rho - rg < rl - rho) ? rg : rl;
+    return rho * area_gl(q, ps, rb, rho, 4);
+}
+
+/* p(rho) = ps by Newton from rho (a stable branch, dp/drho > 0) */
+static double newton_p(const orc_params *q, double ps, double rho) {
+    for (int it = 0; it < 60; ++it) {
+        double p, dp;
+        eos_at(q, rho, &p, &dp);
+        double d = (p - ps) / dp;
+        rho -= d;
+        if (fabs(d) <= 1e-17 * rho) break;
+    }
+    return rho;
+}
+
+typedef struct { const orc_params *q; double ps, rg, rl, kappa; } profile_ctx;
+
+static void profile_at(const profile_ctx *c, double u, double *rho, double *drho, double *dudy) {
+    double D = c->rl - c->rg;
+    double g = D / (1.0 + exp(-u)), l = D / (1.0 + exp(u));  /* rho - rho_g, rho_l - rho */
+    double r = g < l ? c->rg + g : c->rl - l;
+    double W = profile_W(c->q, c->ps, c->rg, c->rl, r);
+    double v = W > 0.0 ? sqrt(2.0 * W / c->kappa) : 0.0;
+    *rho = r;
+    *drho = v;
+    *dudy = v * D / (g * l);
+}
+
+/* rho[i], drho[i] = rho'(y_i) at y_i = (i - i0) h, i = 0 .. n-1, for the     */
+/* unscaled EOS of q at q->T (the Hu factor k plays no part).  Returns 0, or  */
+/* 1 if the isotherm has no van der Waals loop or the arguments are invalid.  */
+int orc_flat_profile(const orc_params *q, double kappa, double h, int n, int i0, int sub, double *rho, double *drho) {
+    profile_ctx c;
+    if (!(kappa > 0.0) || !(h > 0.0) || n < 1 || i0 < 0 || i0 >= n || sub < 1) return 1;
+    if (orc_maxwell(q, &c.rg, &c.rl, &c.ps)) return 1;
+    c.q = q;
+    c.kappa = kappa;
+    gl_init();
+    /* The two branches of W meet only if the equal-area integral vanishes to  */
+    /* rounding: refine p_s by Newton on A(p_s) = int_{rho_g}^{rho_l} (p -     */
+    /* p_s)/s^2 ds (dA/dp_s = 1/rho_l - 1/rho_g, the limits contributing       */
+    /* nothing), re-rooting the bulk densities each time.                      */
+    for (int it = 0; it < 6; ++it) {
+        double A = area_gl(q, c.ps, c.rg, c.rl, 32);
+        double dps = A / (1.0 / c.rg - 1.0 / c.rl);
+        c.ps += dps;
+        c.rg = newton_p(q, c.ps, c.rg);
+        c.rl = newton_p(q, c.ps, c.rl);
+        if (fabs(dps) <= 1e-16 * c.ps) break;
+    }
+    for (int dir = -1; dir <= 1; dir += 2) {
+        double u = 0.0, r, d, k1, k2, k3, k4, dy = dir * h / sub;
+        for (int i = i0; i >= 0 && i < n; i += dir) {
+            if (i != i0)
+                for (int k = 0; k < sub; ++k) {
+                    profile_at(&c, u, &r, &d, &k1);
+                    profile_at(&c, u + 0.5 * dy * k1, &r, &d, &k2);
+                    profile_at(&c, u + 0.5 * dy * k2, &r, &d, &k3);
+                    profile_at(&c, u + dy * k3, &r, &d, &k4);
+                    u += dy / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+                }
+            profile_at(&c, u, &rho[i], &drho[i], &k1);
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Equilibrium, Eq. 2.                                                        */
 /* ------------------------------------------------------------------------ */
 

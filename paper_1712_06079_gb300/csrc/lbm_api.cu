@@ -771,6 +771,39 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy) {
     return read_error_word(c);
 }
 
+lbm_status lbm_gradient(lbm_ctx *c, const double *q, double h, double *gx, double *gy) {
+    if (!c) return LBM_E_INVALID;
+    if (!q || !gx || !gy) return fail(c, LBM_E_INVALID, "q, gx and gy must be non-NULL host arrays");
+    if (!(h > 0) || !std::isfinite(h)) return fail(c, LBM_E_INVALID, "grid spacing h must be positive and finite");
+    lbm_status st = ensure_mom(c);
+    if (st != LBM_OK) return st;
+    char *dev = (char *)c->mom;
+    const size_t fb = c->n * c->esz;
+    if (is_f64(c)) {
+        CK(c, cudaMemcpyAsync(dev, q, fb, cudaMemcpyHostToDevice, c->stream), "copy field");
+        CK(c, launch_gradient<double>(model_of<double>(c), is_cdm(c), (const double *)dev, h, (double *)(dev + fb),
+                                      (double *)(dev + 2 * fb), c->stream), "gradient kernel");
+        CK(c, cudaMemcpyAsync(gx, dev + fb, fb, cudaMemcpyDeviceToHost, c->stream), "copy gradient");
+        CK(c, cudaMemcpyAsync(gy, dev + 2 * fb, fb, cudaMemcpyDeviceToHost, c->stream), "copy gradient");
+        CK(c, cudaStreamSynchronize(c->stream), "sync gradient");
+    } else {
+        if ((st = ensure_stage(c, 3 * fb)) != LBM_OK) return st;
+        CK(c, cudaStreamSynchronize(c->stream), "sync before staging");
+        float *hs = (float *)c->stage;
+        for (long long i = 0; i < c->n; ++i) hs[i] = (float)q[i];
+        CK(c, cudaMemcpyAsync(dev, hs, fb, cudaMemcpyHostToDevice, c->stream), "copy field");
+        CK(c, launch_gradient<float>(model_of<float>(c), is_cdm(c), (const float *)dev, (float)h, (float *)(dev + fb),
+                                     (float *)(dev + 2 * fb), c->stream), "gradient kernel");
+        CK(c, cudaMemcpyAsync(hs + c->n, dev + fb, 2 * fb, cudaMemcpyDeviceToHost, c->stream), "copy gradient");
+        CK(c, cudaStreamSynchronize(c->stream), "sync gradient");
+        for (long long i = 0; i < c->n; ++i) {
+            gx[i] = hs[c->n + i];
+            gy[i] = hs[2 * c->n + i];
+        }
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_observables(lbm_ctx *c, lbm_obs *out) {
     lbm_status st = check_ready(c);
     if (st != LBM_OK) return st;

@@ -40,6 +40,11 @@ template <typename T>
 cudaError_t launch_moments(const Model<T> &m, bool sc, bool cdm, const T *f, const T *q, T *rho, T *vx, T *vy,
                            cudaStream_t s);
 
+// HDM (Eq. 20) or CDM (Eq. 15 times 1/c_s^2) gradient of the periodic field
+// q (nx * ny, row-major) on a grid of spacing h into gx, gy.
+template <typename T>
+cudaError_t launch_gradient(const Model<T> &m, bool cdm, const T *q, T h, T *gx, T *gy, cudaStream_t s);
+
 // FP64 reductions of (rho, vx, vy) over n cells into *out (device memory).
 // partial must hold observables_partial_count() * 6 doubles.
 int observables_partial_count();

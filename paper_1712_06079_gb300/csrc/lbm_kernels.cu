@@ -176,6 +176,31 @@ __global__ void __launch_bounds__(TX *TYT) collide_kernel(Model<T> m, const T *_
     }
 }
 
+// Gradient of a plain field (no magnitude taken), divided by the grid spacing:
+// the same tile staging and operator as the collision pass.
+template <typename T, int TX, int TY, int TYT, bool CDM>
+__global__ void __launch_bounds__(TX *TYT) gradient_kernel(Model<T> m, const T *__restrict__ q, T inv_h,
+                                                           T *__restrict__ gx, T *__restrict__ gy) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *S = reinterpret_cast<T *>(smem_raw);
+    const int hx = CDM ? 1 : m.kx, hy = CDM ? 1 : m.ky;
+    const int W = TX + 2 * hx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    stage_tile<T, TX, TY, CDM>(m, q, S, hx, hy, x0, y0);
+    __syncthreads();
+    const int lx = threadIdx.x, x = x0 + lx;
+    if (x >= m.nx) return;
+    for (int k = 0; k < TY / TYT; ++k) {
+        const int ly = threadIdx.y + k * TYT, y = y0 + ly;
+        if (y >= m.ny) break;
+        T dx, dy;
+        gradient<T, false, CDM>(m, S + (ly + hy) * W + (lx + hx), W, dx, dy);
+        const long long c = (long long)y * m.nx + x;
+        gx[c] = dx * inv_h;
+        gy[c] = dy * inv_h;
+    }
+}
+
 template <typename T>
 dim3 grid_for(const Model<T> &m) {
     using Tl = Tile<T>;
@@ -290,6 +315,19 @@ cudaError_t launch_moments(const Model<T> &m, bool sc, bool cdm, const T *f, con
     return dispatch_collide<T, true>(m, sc, cdm, f, q, nullptr, rho, vx, vy, s);
 }
 
+template <typename T>
+cudaError_t launch_gradient(const Model<T> &m, bool cdm, const T *q, T h, T *gx, T *gy, cudaStream_t s) {
+    using Tl = Tile<T>;
+    auto kern = cdm ? gradient_kernel<T, Tl::TX, Tl::TY, Tl::TYT, true> : gradient_kernel<T, Tl::TX, Tl::TY, Tl::TYT, false>;
+    const size_t smem = smem_for(m, cdm);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid_for(m), dim3(Tl::TX, Tl::TYT), smem, s>>>(m, q, T(1) / h, gx, gy);
+    return cudaGetLastError();
+}
+
 int observables_partial_count() { return kObsBlocks; }
 
 template <typename T>
@@ -307,7 +345,8 @@ cudaError_t launch_observables(long long n, const T *rho, const T *vx, const T *
     template cudaError_t launch_moments<T>(const Model<T> &, bool, bool, const T *, const T *, T *, T *, T *,   \
                                            cudaStream_t);                                                        \
     template cudaError_t launch_observables<T>(long long, const T *, const T *, const T *, double *, lbm_obs *,  \
-                                               cudaStream_t);
+                                               cudaStream_t);                                                    \
+    template cudaError_t launch_gradient<T>(const Model<T> &, bool, const T *, T, T *, T *, cudaStream_t);
 LBM_INSTANTIATE(float)
 LBM_INSTANTIATE(double)
 

@@ -78,6 +78,7 @@ SIGNATURES = {
     "lbm_set_segment_rows": (ctypes.c_int, [_V, ctypes.c_int]),
     "lbm_get_segment_rows": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int)]),
     "lbm_tune_segment_rows": (ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_gradient": (ctypes.c_int, [_V, _D, ctypes.c_double, _D, _D]),
     "lbm_adjoint_backward": (ctypes.c_int, [_V, _V, _V, _D, _D, _D]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.c_int, ctypes.POINTER(_V)]),
     "lbm_batch_init_density": (ctypes.c_int, [_V, _D]),
@@ -239,6 +240,16 @@ class Lattice:
 
     def moments_device(self, rho_ptr: int, vx_ptr: int, vy_ptr: int):
         self._check(self._lib.lbm_moments_device(self._h, rho_ptr, vx_ptr, vy_ptr))
+
+    def gradient(self, q, h: float = 1.0):
+        """The context's gradient operator (HDM Eq. 20 or CDM Eq. 15) of a (ny, nx)
+        field on a grid of spacing h: returns (d/dx, d/dy) as FP64 arrays."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        if q.shape != self.shape:
+            raise ValueError(f"q must have shape {self.shape}")
+        gx, gy = np.empty(self.shape), np.empty(self.shape)
+        self._check(self._lib.lbm_gradient(self._h, _dp(q), float(h), _dp(gx), _dp(gy)))
+        return gx, gy
 
     def observables(self) -> dict:
         o = _Obs()
