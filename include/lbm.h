@@ -75,11 +75,22 @@ typedef enum { LBM_FORCE_SC = 0, LBM_FORCE_ZC = 1 } lbm_force;
 typedef enum { LBM_GRAD_HDM = 0, LBM_GRAD_CDM = 1 } lbm_grad;
 typedef enum { LBM_F32 = 0, LBM_F64 = 1 } lbm_prec;
 /* LBM_FLAG_TWO_PASS: never use the single-pass FP32 step kernel (keep the
- * potential pass + collide pass form even where the fused kernel applies). */
-enum { LBM_FLAG_TWO_PASS = 1 };
+ * potential pass + collide pass form even where the fused kernel applies).
+ * LBM_FLAG_WALLS_Y: no-slip walls half a lattice spacing below row 0 and above
+ * row ny-1 instead of periodicity in y (the splash case of Sec. 5.5; x stays
+ * periodic).  The paper gives no wall closures; the library takes half-way
+ * bounce-back (a population that would cross a wall returns to its node,
+ * reversed) and continues the interaction field across each wall by its mirror
+ * image (zero normal gradient), so Eq. 20 along a column is the periodic
+ * operator of the mirrored column of period 2 ny and Eq. 15 reads mirrored
+ * neighbours.  Walled lattices run the two-pass kernels (FP32 and FP64) and
+ * lbm_step_noalloc; the batch and the reverse mode reject them
+ * (LBM_E_INVALID). */
+enum { LBM_FLAG_TWO_PASS = 1, LBM_FLAG_WALLS_Y = 2 };
 
 typedef struct {
-    int nx, ny;      /* lattice size, >= 1 each, periodic in both axes (Sec. 5.2) */
+    int nx, ny;      /* lattice size, >= 1 each, periodic in both axes (Sec. 5.2)
+                        unless flags has LBM_FLAG_WALLS_Y */
     int prec;        /* lbm_prec: arithmetic and storage precision of f */
     int eos;         /* lbm_eos */
     int force;       /* lbm_force */

@@ -51,7 +51,7 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("eos", ctypes.c_int),
-                ("force", ctypes.c_int), ("grad", ctypes.c_int), ("pad", ctypes.c_int),
+                ("force", ctypes.c_int), ("grad", ctypes.c_int), ("walls", ctypes.c_int),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double),
                 ("omega", ctypes.c_double), ("T", ctypes.c_double), ("Tc", ctypes.c_double),
                 ("k", ctypes.c_double), ("tau", ctypes.c_double), ("G", ctypes.c_double),
@@ -74,6 +74,7 @@ def _load():
             lib.orc_hdm_grad.argtypes = [D, D, D, ctypes.c_int, ctypes.c_int]
             lib.orc_cdm_grad.argtypes = [D, D, D, ctypes.c_int, ctypes.c_int]
             lib.orc_force.argtypes = [P, D, D, D]
+            lib.orc_grad.argtypes = [P, D, D, D]
             lib.orc_init.argtypes = [P, D, D, D, D]
             lib.orc_step.argtypes = [P, D, D]
             lib.orc_run.argtypes = [P, D, ctypes.c_int]
@@ -120,9 +121,10 @@ class Params:
     grad: str = "hdm"
     G: float = 0.0       # eos "psi": interaction strength of Eq. 4
     rho0: float = 1.0    # eos "psi": reference density of the effective mass
+    walls: bool = False  # no-slip walls below row 0 and above row ny-1 (Sec. 5.5); else periodic in y
 
     def c(self) -> _Params:
-        return _Params(self.nx, self.ny, EOS[self.eos], FORCE[self.force], GRAD[self.grad], 0,
+        return _Params(self.nx, self.ny, EOS[self.eos], FORCE[self.force], GRAD[self.grad], int(self.walls),
                        self.a, self.b, self.R, self.omega, self.T, self.Tc, self.k, self.tau, self.G, self.rho0)
 
 
@@ -137,9 +139,9 @@ def critical_point(eos: str, a: float, b: float, R: float = 1.0):
 
 
 def params_at(nx, ny, eos, a, b, Tr, *, R=1.0, omega=0.0, k=1.0, tau=1.0,
-              force="sc", grad="hdm") -> Params:
+              force="sc", grad="hdm", walls=False) -> Params:
     Tc, _ = critical_point(eos, a, b, R)
-    return Params(nx, ny, eos, a, b, R, omega, Tr * Tc, Tc, k, tau, force, grad)
+    return Params(nx, ny, eos, a, b, R, omega, Tr * Tc, Tc, k, tau, force, grad, walls=walls)
 
 
 def params_psi(nx, ny, G, *, rho0=1.0, tau=1.0, force="sc", grad="hdm") -> Params:
@@ -209,6 +211,16 @@ def cdm_grad(q):
     q = np.ascontiguousarray(q, dtype=np.float64)
     gx, gy = np.empty_like(q), np.empty_like(q)
     _load().orc_cdm_grad(_ptr(q), _ptr(gx), _ptr(gy), q.shape[1], q.shape[0])
+    return gx, gy
+
+
+def grad(p: Params, q):
+    """(d/dx, d/dy) of a (ny, nx) field as the step of p takes it: HDM (Eq. 20)
+    or CDM (Eq. 15), periodic, or with p.walls the field mirrored across the
+    walls (Eq. 20 on the mirrored column of period 2 ny)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    gx, gy = np.empty_like(q), np.empty_like(q)
+    _load().orc_grad(ctypes.byref(p.c()), _ptr(q), _ptr(gx), _ptr(gy))
     return gx, gy
 
 

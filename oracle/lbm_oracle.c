@@ -43,7 +43,8 @@ typedef struct {
     int eos;      /* ORC_VDW .. ORC_RKS, or ORC_PSI: the effective mass of Eq. 4 */
     int force;    /* ORC_SC (Eq. 22) or ORC_ZC (Eq. 7) */
     int grad;     /* ORC_HDM (Eq. 20) or ORC_CDM (Eq. 15) */
-    int pad;
+    int walls;    /* 0: periodic in y; 1: no-slip walls half a spacing below row 0
+                     and above row ny-1 (Sec. 5.5) */
     double a, b, R, omega;
     double T;     /* absolute temperature */
     double Tc;    /* critical temperature (used by the alpha(T) of PR and RKS) */
@@ -552,6 +553,59 @@ void orc_cdm_grad(const double *q, double *gx, double *gy, int nx, int ny) {
         }
 }
 
+/* Walls (Sec. 5.5; the paper gives no closure of Eq. 20 or Eq. 15 there).    */
+/* Reading: the field is continued across each wall by its mirror image,     */
+/* q(-1-j) = q(j) and q(ny+j) = q(ny-1-j), i.e. zero normal gradient at the    */
+/* wall (neutral wetting).  Eq. 20 along a column is then solved on the        */
+/* mirrored column of period 2 ny, and Eq. 15 reads mirrored neighbours.       */
+static int mirror(int i, int n) {
+    int m = wrap(i, 2 * n);
+    return m < n ? m : 2 * n - 1 - m;
+}
+
+static void hdm_grad_walls(const double *q, double *gx, double *gy, int nx, int ny) {
+#pragma omp parallel
+    {
+        double *lin = (double *)malloc(sizeof(double) * (size_t)(nx > 2 * ny ? nx : 2 * ny) * 2);
+        double *lout = lin + (nx > 2 * ny ? nx : 2 * ny);
+#pragma omp for schedule(static)
+        for (int y = 0; y < ny; ++y) orc_hdm_line(q + (size_t)y * nx, gx + (size_t)y * nx, nx);
+#pragma omp for schedule(static)
+        for (int x = 0; x < nx; ++x) {
+            for (int y = 0; y < ny; ++y) lin[y] = lin[2 * ny - 1 - y] = q[(size_t)y * nx + x];
+            orc_hdm_line(lin, lout, 2 * ny);
+            for (int y = 0; y < ny; ++y) gy[(size_t)y * nx + x] = lout[y];
+        }
+        free(lin);
+    }
+}
+
+static void cdm_grad_walls(const double *q, double *gx, double *gy, int nx, int ny) {
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double sx = 0.0, sy = 0.0;
+            for (int i = 1; i < 9; ++i) {
+                double v = q[(size_t)mirror(y + EY[i], ny) * nx + wrap(x + EX[i], nx)];
+                sx += W9[i] * v * EX[i];
+                sy += W9[i] * v * EY[i];
+            }
+            gx[(size_t)y * nx + x] = sx / CS2;
+            gy[(size_t)y * nx + x] = sy / CS2;
+        }
+}
+
+/* The gradient of a field as the step takes it: HDM or CDM, periodic or walled. */
+void orc_grad(const orc_params *q, const double *fld, double *gx, double *gy) {
+    if (q->walls) {
+        if (q->grad == ORC_HDM) hdm_grad_walls(fld, gx, gy, q->nx, q->ny);
+        else cdm_grad_walls(fld, gx, gy, q->nx, q->ny);
+    } else {
+        if (q->grad == ORC_HDM) orc_hdm_grad(fld, gx, gy, q->nx, q->ny);
+        else orc_cdm_grad(fld, gx, gy, q->nx, q->ny);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Interaction force from the density field.                                  */
 /*   U = k p_EOS - rho c_s^2 (Eq. 8 with Hu's scaling, Sec. 5)                 */
@@ -580,8 +634,7 @@ void orc_force(const orc_params *q, const double *rho, double *Fx, double *Fy) {
             fld[c] = (q->force == ORC_SC) ? sqrt(fabs(U[c])) : U[c];
         }
     }
-    if (q->grad == ORC_HDM) orc_hdm_grad(fld, gx, gy, q->nx, q->ny);
-    else orc_cdm_grad(fld, gx, gy, q->nx, q->ny);
+    orc_grad(q, fld, gx, gy);
     for (size_t c = 0; c < n; ++c) {
         if (q->force == ORC_SC && psi_mode) {
             Fx[c] = -q->G * fld[c] * gx[c];
@@ -644,7 +697,11 @@ static int work_alloc(orc_work *w, size_t n) {
 
 /* One time step, Eq. 1 with Eq. 10 forcing:
  *   f_i*(x) = f_i - (f_i - f^eq(rho,u))/tau + [f^eq(rho,u+du) - f^eq(rho,u)],
- *   du = F/rho (dt = 1),  then  f_i(x + e_i, t+1) = f_i*(x). */
+ *   du = F/rho (dt = 1),  then  f_i(x + e_i, t+1) = f_i*(x).
+ * With walls a population whose target row lies beyond a wall comes back to
+ * the node it left, reversed: f_opp(i)(x, t+1) = f_i*(x) (half-way bounce-back,
+ * the no-slip condition of Sec. 5.5; the paper does not say which form). */
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 static void step_with(const orc_params *q, const double *f, double *fout, orc_work *w) {
     int nx = q->nx, ny = q->ny;
     size_t n = (size_t)nx * ny;
@@ -662,8 +719,13 @@ static void step_with(const orc_params *q, const double *f, double *fout, orc_wo
             for (int i = 0; i < 9; ++i) {
                 double fi = f[i * n + c];
                 double post = fi - (fi - fe[i]) / q->tau + (fs[i] - fe[i]);
-                size_t d = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
-                fout[i * n + d] = post;
+                int yd = y + EY[i];
+                if (q->walls && (yd < 0 || yd >= ny)) {
+                    fout[OPP[i] * n + c] = post;
+                } else {
+                    size_t d = (size_t)wrap(yd, ny) * nx + wrap(x + EX[i], nx);
+                    fout[i * n + d] = post;
+                }
             }
         }
 }

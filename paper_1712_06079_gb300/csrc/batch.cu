@@ -444,7 +444,8 @@ lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out) {
     for (int i = 0; i < n; ++i) {
         const lbm_params &q = p[i];
         const char *why = "";
-        if (q.prec != prec || check_params(q, &why) != LBM_OK || (long long)q.nx * q.ny > (1LL << 30))
+        if (q.prec != prec || check_params(q, &why) != LBM_OK || (long long)q.nx * q.ny > (1LL << 30) ||
+            (q.flags & LBM_FLAG_WALLS_Y))   // the batch steps periodic lattices only
             return LBM_E_INVALID;
     }
     lbm_batch *b = new (std::nothrow) lbm_batch();

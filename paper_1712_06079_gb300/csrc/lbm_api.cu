@@ -27,7 +27,7 @@ lbm_status check_params(const lbm_params &p, const char **why) {
     if (p.force != LBM_FORCE_SC && p.force != LBM_FORCE_ZC) return bad("unknown force form");
     if (p.grad != LBM_GRAD_HDM && p.grad != LBM_GRAD_CDM) return bad("unknown gradient");
     if (p.hdm_radius < 0 || p.hdm_radius > kMaxRadius) return bad("hdm_radius must be in [0, 48]");
-    if (p.flags & ~LBM_FLAG_TWO_PASS) return bad("unknown flags");
+    if (p.flags & ~(LBM_FLAG_TWO_PASS | LBM_FLAG_WALLS_Y)) return bad("unknown flags");
     if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return bad("tau must be > 0.5");
     if (p.eos == LBM_EOS_PSI_EXP) {
         if (!std::isfinite(p.G) || p.G == 0.0) return bad("G must be finite and non-zero");
@@ -160,6 +160,7 @@ Model<T> model_of(const lbm_ctx *c) {
     m.eos = c->p.eos;
     m.kx = c->kx;
     m.ky = c->ky;
+    m.walls = (c->p.flags & LBM_FLAG_WALLS_Y) ? 1 : 0;
     m.RT = (T)c->ms.RT;
     m.a = (T)c->ms.a;
     m.b = (T)c->ms.b;
@@ -496,6 +497,7 @@ lbm_status lbm_adjoint_forward(lbm_ctx *c, const void *rho0, int nsteps, int che
     if (!c) return LBM_E_INVALID;
     if (!rho0 || !rho_T) return fail(c, LBM_E_INVALID, "rho0 and rho_T must be device arrays");
     if (nsteps < 1 || checkpoint_interval < 1) return fail(c, LBM_E_INVALID, "need nsteps >= 1, checkpoint_interval >= 1");
+    if (c->p.flags & LBM_FLAG_WALLS_Y) return fail(c, LBM_E_INVALID, "the reverse mode covers periodic lattices only");
     return is_f64(c) ? tape_forward<double>(c, (const double *)rho0, nsteps, checkpoint_interval, (double *)rho_T)
                      : tape_forward<float>(c, (const float *)rho0, nsteps, checkpoint_interval, (float *)rho_T);
 }
@@ -536,7 +538,8 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     c->ms = ms;
     int radius = p->hdm_radius ? p->hdm_radius : (p->prec == LBM_F64 ? 40 : 26);
     lbm_hdm_weights(p->nx, radius, c->wx, &c->kx);
-    lbm_hdm_weights(p->ny, radius, c->wy, &c->ky);
+    // with walls the column operator is the periodic one of the mirrored column
+    lbm_hdm_weights((p->flags & LBM_FLAG_WALLS_Y) ? 2 * p->ny : p->ny, radius, c->wy, &c->ky);
 
     auto bail = [&](cudaError_t e, const char *what) {
         lbm_status st = (e == cudaErrorMemoryAllocation) ? LBM_E_NOMEM : LBM_E_CUDA;
@@ -553,7 +556,7 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if ((e = cudaMalloc(&c->f[0], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f0)");
     if ((e = cudaMalloc(&c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
     if ((e = cudaMalloc(&c->q, (size_t)c->n * c->esz)) != cudaSuccess) return bail(e, "cudaMalloc(q)");
-    c->fused = p->prec == LBM_F32 && !(p->flags & LBM_FLAG_TWO_PASS) &&
+    c->fused = p->prec == LBM_F32 && !(p->flags & (LBM_FLAG_TWO_PASS | LBM_FLAG_WALLS_Y)) &&
                fused_step_supported(model_of<float>(c), p->grad == LBM_GRAD_CDM, radius);
     if (c->fused) {
         size_t qb = sizeof(float) * (size_t)fused_q_pitch(p->nx) * p->ny;

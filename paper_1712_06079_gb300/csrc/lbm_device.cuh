@@ -38,6 +38,7 @@ struct Model {
     int nx, ny;
     int eos;       // lbm_eos
     int kx, ky;    // HDM stencil radius along x and y (already folded to the period)
+    int walls;     // 0: periodic in y; 1: no-slip walls below row 0 and above row ny-1
     T RT;          // R * T
     T a, b;        // EOS constants; for LBM_EOS_PSI_EXP a = G/2, b = 1/rho0 (Eq. 4-5)
     T aal;         // a * alpha(T) (PR, RK, RKS)
@@ -83,6 +84,18 @@ __device__ __forceinline__ T potential_field(const Model<T> &m, T rho, bool sc) 
     if (!sc) return U;
     return U >= T(0) ? sqrt(U) : -sqrt(-U);
 }
+
+// Row index across no-slip walls: the field's mirror image continues it
+// (q(-1-j) = q(j), q(n+j) = q(n-1-j)), period 2n.
+__device__ __forceinline__ int mirror_index(int i, int n) {
+    const int p = 2 * n;
+    int m = i % p;
+    if (m < 0) m += p;
+    return m < n ? m : p - 1 - m;
+}
+
+// Opposite direction of population i (e_opp = -e_i).
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i < 5 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5); }
 
 // Periodic wrap of an index that may lie several periods outside [0, n).
 __device__ __forceinline__ int wrap_index(int i, int n) {

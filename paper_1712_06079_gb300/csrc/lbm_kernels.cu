@@ -99,7 +99,8 @@ __device__ __forceinline__ void stage_tile(const Model<T> &m, const T *__restric
         int r = idx / W, c = idx - r * W;
         bool inx = c >= hx && c < hx + TX, iny = r >= hy && r < hy + TY;
         if (!CDM && !inx && !iny) continue;
-        int gx = wrap_index(x0 - hx + c, m.nx), gy = wrap_index(y0 - hy + r, m.ny);
+        int gx = wrap_index(x0 - hx + c, m.nx);
+        int gy = m.walls ? mirror_index(y0 - hy + r, m.ny) : wrap_index(y0 - hy + r, m.ny);
         S[idx] = q[(long long)gy * m.nx + gx];
     }
 }
@@ -170,7 +171,10 @@ __global__ void __launch_bounds__(TX *TYT) collide_kernel(Model<T> m, const T *_
             moved += post;
             const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
             const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
-            fout[i * n + (long long)dys * m.nx + dxs] = post;
+            if (m.walls && ((ey(i) == 1 && y == m.ny - 1) || (ey(i) == -1 && y == 0)))
+                fout[opp(i) * n + c] = post;   // half-way bounce-back off the wall
+            else
+                fout[i * n + (long long)dys * m.nx + dxs] = post;
         }
         fout[c] = r - moved;
     }

@@ -57,7 +57,9 @@ lbm_status run_step(const lbm_params &p, const lbm::ModelScalars &ms, const void
     m.omega = (T)(1.0 / p.tau);
     const int radius = p.hdm_radius ? p.hdm_radius : (p.prec == LBM_F64 ? 40 : 26);
     double wx[kMaxRadius + 1] = {}, wy[kMaxRadius + 1] = {};
-    if (lbm_hdm_weights(p.nx, radius, wx, &m.kx) != LBM_OK || lbm_hdm_weights(p.ny, radius, wy, &m.ky) != LBM_OK)
+    m.walls = (p.flags & LBM_FLAG_WALLS_Y) ? 1 : 0;
+    const int ny_line = m.walls ? 2 * p.ny : p.ny;   // walls: the mirrored column's period
+    if (lbm_hdm_weights(p.nx, radius, wx, &m.kx) != LBM_OK || lbm_hdm_weights(ny_line, radius, wy, &m.ky) != LBM_OK)
         return LBM_E_INVALID;
     for (int j = 0; j <= kMaxRadius; ++j) {
         m.wx[j] = (T)wx[j];

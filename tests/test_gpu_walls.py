@@ -1,0 +1,110 @@
+"""GPU: no-slip walls in y (Sec. 5.5) through the C ABI against the FP64
+oracle's walled step (half-way bounce-back, field mirrored across the walls).
+
+Bars as in the periodic parity tests: FP64 within 1e-12 relative per step over
+all nine populations and over 20 steps; FP32 within 1e-5 on rho after 300
+steps; mass conserved to FP64 rounding.  Walled lattices run the two-pass
+kernels; the batch and the reverse mode refuse them."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_06079_gb300 import inputs, lbm
+
+pytestmark = pytest.mark.gpu
+EOS = dict(inputs.EOS_TABLE)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1712_06079_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def make(nx, ny, eos="cs", Tr=0.8, force="sc", grad="hdm", tau=1.0, prec="f64"):
+    t = EOS[eos]
+    gp = lbm.Params(nx=nx, ny=ny, eos=eos, a=t["a"], b=t["b"], omega=t["omega"], Tr=Tr, k=t["k"], tau=tau,
+                    force=force, grad=grad, prec=prec, walls=True)
+    op = oracle.params_at(nx, ny, eos, t["a"], t["b"], Tr, omega=t["omega"], k=t["k"], tau=tau, force=force,
+                          grad=grad, walls=True)
+    return gp, op
+
+
+def wall_drop(op, nx, ny, seed):
+    # a droplet resting on the bottom wall, a film along the top wall, small seeded velocities
+    g, l, _ = oracle.maxwell(op)
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    r = min(nx, ny) / 4
+    drop = 0.5 * (1 - np.tanh((np.hypot(X - nx / 2, Y - r * 0.6) - r) / 2))
+    film = 0.5 * (1 + np.tanh((Y - (ny - 1 - max(2, ny // 8))) / 2))
+    rho = g + (l - g) * np.clip(drop + film, 0, 1)
+    xi = inputs.uniform01(seed, 2 * nx * ny).reshape(2, ny, nx)
+    return oracle.init(op, rho, 0.01 * (xi[0] - 0.5), 0.01 * (xi[1] - 0.5))
+
+
+CASES = [
+    # (nx, ny, eos, Tr, force, grad, tau)
+    (96, 64, "cs", 0.8, "sc", "hdm", 1.0),
+    (64, 40, "pr", 0.75, "zc", "hdm", 0.8),
+    (70, 36, "vdw", 0.85, "sc", "cdm", 1.2),
+    (40, 8, "cs", 0.8, "zc", "hdm", 1.0),     # mirrored column shorter than the stencil: folded
+    (33, 21, "rk", 0.8, "sc", "hdm", 0.9),    # ragged tiles
+]
+
+
+@pytest.mark.parametrize("nx,ny,eos,Tr,force,grad,tau", CASES)
+def test_f64_walls_parity(nx, ny, eos, Tr, force, grad, tau):
+    gp, op = make(nx, ny, eos, Tr, force, grad, tau)
+    f0 = wall_drop(op, nx, ny, seed=nx + 7 * ny)
+    with lbm.Lattice(gp) as lat:
+        assert lat.segment_rows() == 0          # the two-pass kernels
+        lat.set_f(f0)
+        lat.step(1)
+        f1 = lat.get_f()
+        lat.step(19)
+        f20 = lat.get_f()
+    o1 = oracle.step(op, f0)
+    assert (np.abs(f1 - o1) / np.abs(o1)).max() < 1e-12
+    o20 = oracle.run(op, o1, 19)
+    assert (np.abs(f20 - o20) / np.abs(o20)).max() < 1e-11
+    assert abs(f20.sum() - f0.sum()) < 1e-13 * f0.sum()
+
+
+def test_f32_walls_parity():
+    nx, ny = 128, 72
+    gp, op = make(nx, ny, "cs", 0.8, "sc", "hdm", 0.9, prec="f32")
+    f0 = wall_drop(op, nx, ny, seed=3)
+    with lbm.Lattice(gp) as lat:
+        lat.set_f(f0)
+        lat.step(300)
+        r, _, _ = lat.moments()
+    ro, _, _ = oracle.moments(op, oracle.run(op, f0, 300))
+    assert np.abs(r - ro).max() / ro.max() < 1e-5
+
+
+@pytest.mark.parametrize("grad", ["hdm", "cdm"])
+@pytest.mark.parametrize("ny", [5, 48])
+def test_gradient_with_walls(grad, ny):
+    nx = 24
+    gp, op = make(nx, ny, grad=grad)
+    xi = inputs.uniform01(ny + 11, nx * ny).reshape(ny, nx)
+    with lbm.Lattice(gp) as lat:
+        gx, gy = lat.gradient(xi, 0.5)
+    ox, oy = oracle.grad(op, xi)
+    scale = max(np.abs(ox).max(), np.abs(oy).max())
+    assert np.abs(gx - ox / 0.5).max() < 1e-12 * scale
+    assert np.abs(gy - oy / 0.5).max() < 1e-12 * scale
+
+
+def test_walls_refused_where_unsupported():
+    torch = pytest.importorskip("torch")
+    gp, _ = make(64, 32)
+    with lbm.Lattice(gp) as lat:
+        x = torch.full((32, 64), 0.3, dtype=torch.float64, device="cuda")
+        r = torch.empty_like(x)
+        with pytest.raises(lbm.LBMError) as ei:
+            lat.adjoint_forward(x.data_ptr(), 10, 3, r.data_ptr())
+        assert ei.value.status == lbm.E_INVALID
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch([gp, gp])

@@ -35,14 +35,16 @@ def state(nx, ny, eos, Tr):
     return oracle.init(op, rho, 0.01 * (xi[0] - 0.5), 0.01 * (xi[1] - 0.5)), t
 
 
-@pytest.mark.parametrize("prec,nx,ny,eos,tol", [("f64", 96, 80, "cs", 1e-12), ("f32", 200, 136, "pr", 1e-5)])
-def test_noalloc_matches_context_two_calls(torch_cuda, prec, nx, ny, eos, tol):
+@pytest.mark.parametrize("prec,nx,ny,eos,tol,walls", [("f64", 96, 80, "cs", 1e-12, False),
+                                                     ("f32", 200, 136, "pr", 1e-5, False),
+                                                     ("f64", 64, 40, "cs", 1e-12, True)])
+def test_noalloc_matches_context_two_calls(torch_cuda, prec, nx, ny, eos, tol, walls):
     torch = torch_cuda
     f0, t = state(nx, ny, eos, 0.8)
     dt = torch.float64 if prec == "f64" else torch.float32
     stream = torch.cuda.current_stream()
     params = lbm.Params(nx=nx, ny=ny, eos=eos, a=t["a"], b=t["b"], omega=t["omega"], Tr=0.8, k=t["k"],
-                        prec=prec, two_pass=True, stream=stream.cuda_stream)
+                        prec=prec, two_pass=True, walls=walls, stream=stream.cuda_stream)
     # reference: the context path (same two-pass kernels)
     with lbm.Lattice(params) as lat:
         lat.set_f(f0)
