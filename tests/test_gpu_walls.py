@@ -108,3 +108,32 @@ def test_walls_refused_where_unsupported():
         assert ei.value.status == lbm.E_INVALID
     with pytest.raises(lbm.LBMError):
         lbm.Batch([gp, gp])
+
+
+def test_splash_small_spreads_and_forces_agree():
+    # the Sec. 5.5 set-up at a fifth of the size (200 x 60, film 6, R 10,
+    # U 0.1), PR at T/Tc = 0.7, tau = 1 (Re = U D / nu = 12): stable, mass conserved, the
+    # liquid spreads along the film after impact, and the Shan-Chen (Eq. 22)
+    # and Zhang-Chen (Eq. 7) forms, the same force, give the same spread
+    t = EOS["pr"]
+    nx, ny, film, R, U = 200, 60, 6, 10, 0.1
+    g, l = lbm.maxwell(lbm.Params(nx=8, ny=8, eos="pr", a=t["a"], b=t["b"], omega=t["omega"], Tr=0.7, k=t["k"]))
+    rho, ux, uy = inputs.splash(nx, ny, film, R, U, g, l, 4.0)
+    tau = 1.0
+    widths = {}
+    for force in ("sc", "zc"):
+        p = lbm.Params(nx=nx, ny=ny, eos="pr", a=t["a"], b=t["b"], omega=t["omega"], Tr=0.7, k=t["k"], tau=tau,
+                       force=force, grad="hdm", prec="f32", walls=True)
+        with lbm.Lattice(p) as lat:
+            lat.init_density(rho, ux, uy)
+            w = []
+            for _ in range(8):
+                lat.step(40)
+                r, _, _ = lat.moments()
+                w.append(int(np.count_nonzero(r[film + 1] > 0.5 * (g + l))))
+            obs = lat.observables()
+        assert abs(obs["mass"] - rho.sum()) < 1e-5 * rho.sum()
+        widths[force] = w
+    assert widths["sc"][0] == 0 or widths["sc"][0] < widths["sc"][-1]
+    assert widths["sc"][-1] > widths["sc"][2] > 0        # spreads along the film after contact
+    assert max(abs(a - b) for a, b in zip(widths["sc"], widths["zc"])) <= 2
