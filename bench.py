@@ -57,6 +57,24 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(x: float) -> float:
+    """Largest x over the ranks of the process group (x itself without one):
+    every rank's timed interval enters, and all ranks report the slowest."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world: int, cells: int, steps: int, seconds: float) -> float:
+    """Whole-job MLUPS of `world` replicas, each `cells` x `steps`, in `seconds`."""
+    return world * cells * steps / seconds / 1e6
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples while the timed region runs."""
 
@@ -234,11 +252,8 @@ def run_ours(args):
     timing = lat.timing()
     lat.set_timing(False)
     lat.sync()
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * cells * args.steps / (ms * 1e-3) / 1e6
+    ms = reduce_max(ms)
+    value = weak_value(world, cells, args.steps, ms * 1e-3)
 
     # --- end to end through the C ABI with host buffers ---
     host_rho = np.ascontiguousarray(rho0)
@@ -249,11 +264,8 @@ def run_ours(args):
     lat.step(args.steps)
     r, vx, vy = lat.moments()
     e2e_s = time.perf_counter() - te
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = world * cells * args.steps / e2e_s / 1e6
+    e2e_s = reduce_max(e2e_s)
+    e2e = weak_value(world, cells, args.steps, e2e_s)
     assert np.isfinite(r).all()
     lat.close()
 
