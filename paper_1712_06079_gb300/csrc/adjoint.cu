@@ -333,13 +333,10 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
                 if (ly >= hy && ly < hy + TY) ptx::bulk_g2s(S + ly * W, src - XO, wide, &bars[0]);
                 else ptx::bulk_g2s(S + ly * W + XO, src, core, &bars[0]);
             }
-            if (TAU1)
-                for (int r = tid; r < 3 * LH; r += 32) {
-                    const int k = r / LH, ly = r - k * LH;
-                    const T *src = a.lam + k * a.lstride + (long long)wrap_index(y0 - 1 + ly, ny) * a.lpitch + a.loff + x0;
-                    ptx::bulk_g2s(L + r * LW, src - LO, lrow, &bars[1]);
-                }
         }
+        // The next kernel (B of this step) may begin launching; lambda, the
+        // previous B's output, is staged only after griddep_wait below.
+        ptx::griddep_launch_dependents();
     } else {
         // element-wise: a cross for the separable HDM, the full box for the CDM
         if (CDM) {
@@ -397,6 +394,22 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
             if (k == 0) {
                 tile_hdm<SC>(S + hy * W, W, S, W, XO, DT, m, a.r, a.r5, a.r25);
                 __syncthreads();
+                // Everything so far reads only the state and its field, written
+                // two or more launches back.  lambda (and every write of this
+                // kernel) waits for the preceding kernel: with programmatic
+                // launch the previous reverse step's B may still be running.
+                ptx::griddep_wait();
+                if (TAU1 && threadIdx.x + TX * threadIdx.y < 32) {
+                    const int tid = threadIdx.x + TX * threadIdx.y;
+                    const int ncore = min(TX, nx - x0);
+                    const uint32_t lrow = (ncore + 2 * LO) * sizeof(T);
+                    for (int r = tid; r < 3 * LH; r += 32) {
+                        const int kk = r / LH, ry = r - kk * LH;
+                        const T *src = a.lam + kk * a.lstride + (long long)wrap_index(y0 - 1 + ry, ny) * a.lpitch +
+                                       a.loff + x0;
+                        ptx::bulk_g2s(L + r * LW, src - LO, lrow, &bars[1]);
+                    }
+                }
             }
             Dx = DT[ly * TX + lx];
             Dy = DT[TX * TY + ly * TX + lx];
@@ -507,6 +520,10 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
             ptx::fence_mbar_init();
         }
         __syncthreads();
+        // the next reverse step's A may begin its state-only work; this kernel
+        // reads A's output, so it waits for A first
+        ptx::griddep_launch_dependents();
+        ptx::griddep_wait();
         if (tid < 32) {
             const int ncore = min(TX, nx - x0);
             const uint32_t wide = (ncore + 2 * XO) * sizeof(T), core = ncore * sizeof(T);
@@ -655,8 +672,26 @@ dim3 adj_grid(int nx, int ny) {
     return dim3((nx + AdjTile<T>::TX - 1) / AdjTile<T>::TX, (ny + AdjTile<T>::TY - 1) / AdjTile<T>::TY);
 }
 
+// Launch with programmatic stream serialization when `pdl`: the kernel may
+// start while the preceding one finishes (its griddep_wait guards every read
+// of that kernel's output and every write).
+template <typename K, typename A>
+cudaError_t launch_pdl(bool pdl, K kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const A &arg) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
 template <typename T, bool SC, bool CDM, bool TAU1, int KC, bool PAD>
-cudaError_t launch_adj_t(const AdjArgs<T> &a, cudaStream_t s) {
+cudaError_t launch_adj_t(const AdjArgs<T> &a, bool overlap_prev, cudaStream_t s) {
     constexpr int TX = AdjTile<T>::TX, TY = AdjTile<T>::TY, TYT = AdjTile<T>::TYT;
     const int hx = CDM ? 1 : (KC ? KC : a.m.kx), hy = CDM ? 1 : (KC ? KC : a.m.ky);
     const int XS = PAD ? XO : hx;
@@ -674,10 +709,15 @@ cudaError_t launch_adj_t(const AdjArgs<T> &a, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
     if (e != cudaSuccess) return e;
     const dim3 grid = adj_grid<T>(a.m.nx, a.m.ny), block(TX, TYT);
-    ka<<<grid, block, smem_a, s>>>(a);
+    // the padded FP32 kernels wait for their predecessor's output (griddep_wait),
+    // so they may overlap it: A with the previous step's B unless the state
+    // was just recomputed (A stages that state's field), B always with its A
+    e = launch_pdl(PAD && overlap_prev, ka, grid, block, smem_a, s, a);
+    if (e != cudaSuccess) return e;
     AdjArgs<T> b = a;
     b.Tpart = a.Tpart + grid.x * grid.y;
-    kb<<<grid, block, smem_b, s>>>(b);
+    e = launch_pdl(PAD, kb, grid, block, smem_b, s, b);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -686,15 +726,15 @@ template <typename T>
 constexpr int adj_kc() { return sizeof(T) == 4 ? 26 : 40; }
 
 template <typename T, bool SC, bool CDM, bool TAU1>
-cudaError_t launch_adj_k(const AdjArgs<T> &a, bool padded, cudaStream_t s) {
+cudaError_t launch_adj_k(const AdjArgs<T> &a, bool padded, bool overlap_prev, cudaStream_t s) {
     if constexpr (CDM) {
-        return launch_adj_t<T, SC, CDM, TAU1, 0, false>(a, s);
+        return launch_adj_t<T, SC, CDM, TAU1, 0, false>(a, overlap_prev, s);
     } else {
         if constexpr (sizeof(T) == 4)
-            if (padded) return launch_adj_t<T, SC, CDM, TAU1, adj_kc<T>(), true>(a, s);
+            if (padded) return launch_adj_t<T, SC, CDM, TAU1, adj_kc<T>(), true>(a, overlap_prev, s);
         if (a.m.kx <= adj_kc<T>() && a.m.ky <= adj_kc<T>())
-            return launch_adj_t<T, SC, CDM, TAU1, adj_kc<T>(), false>(a, s);
-        return launch_adj_t<T, SC, CDM, TAU1, 0, false>(a, s);
+            return launch_adj_t<T, SC, CDM, TAU1, adj_kc<T>(), false>(a, overlap_prev, s);
+        return launch_adj_t<T, SC, CDM, TAU1, 0, false>(a, overlap_prev, s);
     }
 }
 
@@ -723,7 +763,7 @@ AdjLayout adjoint_layout(int nx, int ny, bool padded, bool tau1) {
 template <typename T>
 cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cdm, bool tau1, bool padded,
                                 const AdjLayout &l, const T *f, const T *q, int qpitch, int qoff, const T *lam_next,
-                                T *aux, T *lam_out, double *Tpart, int *err, cudaStream_t s) {
+                                T *aux, T *lam_out, double *Tpart, int *err, bool overlap_prev, cudaStream_t s) {
     AdjArgs<T> a;
     a.m = m;
     a.R = R;
@@ -748,7 +788,8 @@ cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cd
     a.r5 = (T)std::pow(r, 5);
     a.r25 = (T)std::pow(r, 25);
 #define LBM_ADJ_PICK(SC, CDM)                                                                             \
-    return tau1 ? launch_adj_k<T, SC, CDM, true>(a, padded, s) : launch_adj_k<T, SC, CDM, false>(a, padded, s)
+    return tau1 ? launch_adj_k<T, SC, CDM, true>(a, padded, overlap_prev, s)                               \
+                : launch_adj_k<T, SC, CDM, false>(a, padded, overlap_prev, s)
     if (sc) {
         if (cdm) LBM_ADJ_PICK(true, true);
         LBM_ADJ_PICK(true, false);
@@ -791,7 +832,7 @@ cudaError_t launch_density(long long n, const T *f, T *rho, cudaStream_t s) {
     template int adjoint_slots<T>(int, int);                                                                \
     template cudaError_t launch_adjoint_step<T>(const Model<T> &, T, T, bool, bool, bool, bool, const AdjLayout &, \
                                                 const T *, const T *, int, int, const T *, T *, T *, double *, int *, \
-                                                cudaStream_t);                                              \
+                                                bool, cudaStream_t);                                        \
     template cudaError_t launch_adjoint_seed<T>(int, int, bool, const AdjLayout &, const T *, T *, cudaStream_t); \
     template cudaError_t launch_adjoint_initial<T>(int, int, const AdjLayout &, const T *, T *, cudaStream_t);   \
     template cudaError_t launch_density<T>(long long, const T *, T *, cudaStream_t);

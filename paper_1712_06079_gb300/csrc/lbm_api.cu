@@ -475,7 +475,7 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
             const T *ft = (const T *)(t == t0 ? c->ckpt[k] : seg[t - t0 - 1]);
             e = launch_adjoint_step<T>(m, R, aalp, is_sc(c), is_cdm(c), tau1, c->fused, lay, ft,
                                        (const T *)segq[t - t0], qpitch, qoff, (const T *)lam[li], (T *)aux,
-                                       (T *)lam[1 - li], slots, c->err, c->stream);
+                                       (T *)lam[1 - li], slots, c->err, /*overlap_prev=*/t != t1 - 1, c->stream);
             li = 1 - li;
         }
     }

@@ -77,7 +77,10 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
 // rows with 32 periodic ghost columns on each side for the FP32 single-pass
 // layout (padded = true: q in that layout, nx % 4 == 0, nx >= 64, HDM radius
 // 26), plain rows otherwise.  R is the gas constant, aalp = a dalpha/dT; err
-// receives kErrTimeout if a bounded wait on a copy gives up.
+// receives kErrTimeout if a bounded wait on a copy gives up.  overlap_prev:
+// the preceding launch on the stream is the previous reverse step's kernel B
+// (not a kernel that wrote f or q), so in the padded layout this step's first
+// kernel may start while it finishes.
 struct AdjLayout {
     int dpitch, doff, naux;
     long long dstride;
@@ -90,7 +93,7 @@ int adjoint_slots(int nx, int ny);
 template <typename T>
 cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cdm, bool tau1, bool padded,
                                 const AdjLayout &l, const T *f, const T *q, int qpitch, int qoff, const T *lam_next,
-                                T *aux, T *lam_out, double *Tpart, int *err, cudaStream_t s);
+                                T *aux, T *lam_out, double *Tpart, int *err, bool overlap_prev, cudaStream_t s);
 // lambda at the final step from dL/drho_T (rho_T = sum_i f_i).
 template <typename T>
 cudaError_t launch_adjoint_seed(int nx, int ny, bool padded, const AdjLayout &l, const T *grad_rho, T *lam,

@@ -99,5 +99,16 @@ __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Programmatic dependent launch (sm_90 and later).  launch_dependents lets the
+// next kernel of the stream begin launching; wait blocks until the preceding
+// kernel has completed and its memory operations are visible.  For a kernel
+// launched without the programmatic-serialization attribute the preceding
+// kernel has already completed and wait returns at once.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace ptx
 }  // namespace lbm
