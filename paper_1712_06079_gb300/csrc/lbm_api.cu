@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lbm.h"
@@ -491,6 +493,39 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
 
 }  // namespace
 
+namespace {
+
+// fn(lo, hi) over [0, n) split across the host's threads (the precision
+// conversions between the caller's FP64 arrays and the pinned FP32 staging run
+// at memory speed only when many cores share them); one thread below 1M items.
+template <typename F>
+void parallel_for(long long n, F fn) {
+    const long long kMinPerThread = 1 << 20;
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    nt = (unsigned)std::max<long long>(1, std::min<long long>(nt, n / kMinPerThread));
+    if (nt == 1) {
+        fn(0LL, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    const long long chunk = (n + nt - 1) / nt;
+    for (unsigned t = 1; t < nt; ++t) {
+        const long long lo = t * chunk, hi = std::min(n, lo + chunk);
+        if (lo < hi) pool.emplace_back([=] { fn(lo, hi); });
+    }
+    fn(0LL, std::min(n, chunk));
+    for (auto &th : pool) th.join();
+}
+
+template <typename D, typename S>
+void convert(D *dst, const S *src, long long n) {
+    parallel_for(n, [=](long long lo, long long hi) {
+        for (long long i = lo; i < hi; ++i) dst[i] = (D)src[i];
+    });
+}
+
+}  // namespace
+
 extern "C" {
 
 lbm_status lbm_adjoint_forward(lbm_ctx *c, const void *rho0, int nsteps, int checkpoint_interval, void *rho_T) {
@@ -655,8 +690,21 @@ lbm_status lbm_init_density_device(lbm_ctx *c, const void *rho, const void *ux, 
 lbm_status lbm_init_density(lbm_ctx *c, const double *rho, const double *ux, const double *uy) {
     if (!c) return LBM_E_INVALID;
     if (!rho) return fail(c, LBM_E_INVALID, "rho is NULL");
-    for (long long i = 0; i < c->n; ++i)
-        if (!(rho[i] > 0) || !std::isfinite(rho[i])) return fail(c, LBM_E_INVALID, "rho[%lld] is not a positive finite number", i);
+    std::vector<long long> bad(33, -1);   // first bad index per chunk, the lowest reported
+    {
+        const long long n = c->n;
+        const long long chunk = (n + 31) / 32;
+        parallel_for(32, [&](long long lo, long long hi) {
+            for (long long t = lo; t < hi; ++t)
+                for (long long i = t * chunk; i < std::min(n, (t + 1) * chunk); ++i)
+                    if (!(rho[i] > 0) || !std::isfinite(rho[i])) {
+                        bad[t] = i;
+                        break;
+                    }
+        });
+    }
+    for (long long i : bad)
+        if (i >= 0) return fail(c, LBM_E_INVALID, "rho[%lld] is not a positive finite number", i);
     lbm_status st = ensure_mom(c);
     if (st != LBM_OK) return st;
     char *dev = (char *)c->mom;
@@ -670,7 +718,7 @@ lbm_status lbm_init_density(lbm_ctx *c, const double *rho, const double *ux, con
             CK(c, cudaMemcpyAsync(dev + k * fb, src[k], fb, cudaMemcpyHostToDevice, c->stream), "copy init field");
         } else {
             float *h = (float *)c->stage + k * c->n;
-            for (long long i = 0; i < c->n; ++i) h[i] = (float)src[k][i];
+            convert(h, src[k], c->n);
             CK(c, cudaMemcpyAsync(dev + k * fb, h, fb, cudaMemcpyHostToDevice, c->stream), "copy init field");
         }
     }
@@ -690,7 +738,7 @@ lbm_status lbm_set_f(lbm_ctx *c, const double *f) {
         if (st != LBM_OK) return st;
         CK(c, cudaStreamSynchronize(c->stream), "sync before staging");
         float *h = (float *)c->stage;
-        for (size_t i = 0; i < cnt; ++i) h[i] = (float)f[i];
+        convert(h, f, (long long)cnt);
         CK(c, cudaMemcpyAsync(c->f[0], h, cnt * sizeof(float), cudaMemcpyHostToDevice, c->stream), "copy f");
         CK(c, cudaStreamSynchronize(c->stream), "sync f copy");
     }
@@ -711,7 +759,7 @@ lbm_status lbm_get_f(lbm_ctx *c, double *f) {
         float *h = (float *)c->stage;
         CK(c, cudaMemcpyAsync(h, c->f[c->cur], cnt * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy f");
         CK(c, cudaStreamSynchronize(c->stream), "sync f copy");
-        for (size_t i = 0; i < cnt; ++i) f[i] = h[i];
+        convert(f, h, (long long)cnt);
     }
     return read_error_word(c);
 }
@@ -768,8 +816,7 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy) {
             if (dst[k]) CK(c, cudaMemcpyAsync(h + k * c->n, dev + k * fb, fb, cudaMemcpyDeviceToHost, c->stream), "copy moments");
         CK(c, cudaStreamSynchronize(c->stream), "sync moments");
         for (int k = 0; k < 3; ++k)
-            if (dst[k])
-                for (long long i = 0; i < c->n; ++i) dst[k][i] = h[k * c->n + i];
+            if (dst[k]) convert(dst[k], h + k * c->n, c->n);
     }
     return read_error_word(c);
 }
@@ -793,16 +840,14 @@ lbm_status lbm_gradient(lbm_ctx *c, const double *q, double h, double *gx, doubl
         if ((st = ensure_stage(c, 3 * fb)) != LBM_OK) return st;
         CK(c, cudaStreamSynchronize(c->stream), "sync before staging");
         float *hs = (float *)c->stage;
-        for (long long i = 0; i < c->n; ++i) hs[i] = (float)q[i];
+        convert(hs, q, c->n);
         CK(c, cudaMemcpyAsync(dev, hs, fb, cudaMemcpyHostToDevice, c->stream), "copy field");
         CK(c, launch_gradient<float>(model_of<float>(c), is_cdm(c), (const float *)dev, (float)h, (float *)(dev + fb),
                                      (float *)(dev + 2 * fb), c->stream), "gradient kernel");
         CK(c, cudaMemcpyAsync(hs + c->n, dev + fb, 2 * fb, cudaMemcpyDeviceToHost, c->stream), "copy gradient");
         CK(c, cudaStreamSynchronize(c->stream), "sync gradient");
-        for (long long i = 0; i < c->n; ++i) {
-            gx[i] = hs[c->n + i];
-            gy[i] = hs[2 * c->n + i];
-        }
+        convert(gx, hs + c->n, c->n);
+        convert(gy, hs + 2 * c->n, c->n);
     }
     return LBM_OK;
 }
