@@ -208,6 +208,11 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         ptx::fence_mbar_init();
     }
     __syncthreads();
+    // Launched with programmatic serialization: the next step's grid may be
+    // scheduled as soon as every CTA of this one runs, and this grid waits for
+    // the previous step to complete before any read of f(t), q(t) or any write.
+    ptx::griddep_launch_dependents();
+    ptx::griddep_wait();
 
     // d/dy ring chunk c: relative rows 8c .. 8c+7 = global rows ys - QBASE + 8c + k,
     // lane columns x0 - 4 .. x0 + nint + 3 (padded x0 + QG - 4 ..), ring row (8c + k) % QRING
@@ -596,7 +601,18 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
 #undef LBM_PICK
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    kern<<<grid, NTHR, kSmemBytes, s>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(NTHR);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
