@@ -9,13 +9,15 @@
 // (Eq. 8) for the Zhang-Chen form.
 //
 // Decomposition.  A CTA of 8 warps owns a strip of TXI = 120 columns and a
-// segment of up to seg_h rows (a launch parameter; 126 on large lattices,
-// fewer on small ones so that the grid fills the GPU).  It sweeps the segment
-// in slabs of 8
-// rows, one warp per row and one lane per 4 consecutive cells.  Lanes 1..30
-// hold the strip's columns; lanes 0 and 31 hold the 4-column groups just
-// outside it, whose collision is recomputed so that the density at t+1 of
-// every strip cell can be formed on chip.
+// segment of up to seg_h rows (a launch parameter: by default the tallest of
+// 126, 62, 30, 14, 6 that gives every SM a CTA; the library's tuner times the
+// heights on the live state).  It sweeps the segment in slabs of 8 rows, one
+// warp per row and one lane per 4 consecutive cells.  Lanes 1..30 hold the
+// strip's columns; lanes 0 and 31 hold the 4-column groups just outside it,
+// whose collision is recomputed so that the density at t+1 of every strip
+// cell can be formed on chip.  Launches use programmatic serialization: a
+// grid waits for the previous step at its top (griddepcontrol.wait), before
+// any read or write, so the next step's CTAs are scheduled while it drains.
 //
 // f(t) of a lane's 4 cells is read with nine float4 loads into registers,
 // issued during the previous slab (for tau = 1 right after its moments, which
@@ -23,9 +25,8 @@
 // latency hides behind the barrier and the density pass.  A slab takes the
 // moments first, so f(t) is out of the registers before the derivatives
 // stage their rows (the kernel runs at the 128-register limit of two CTAs
-// per SM).  The
-// potential rows arrive by the bulk-copy engine (cp.async.bulk, completion on
-// mbarriers, bounded waits), issued a slab ahead by warp 0:
+// per SM).  The potential rows arrive by the bulk-copy engine (cp.async.bulk,
+// completion on mbarriers, bounded waits), issued a slab ahead by warp 0:
 //  - the slab's 8 potential rows at full width (the 26-column HDM halo on
 //    each side, for d/dx), double-buffered;
 //  - a 48-row ring of potential rows at the lanes' 128 columns (the slab's
@@ -44,9 +45,9 @@
 // Horner groups each) and steps them to its other cells.  Along y every ring
 // column carries a forward sum down the segment and a 25-row backward sum per
 // slab, and each row reads two values per cell; the sums of slab s+1 are
-// formed at the end of slab s.  Per slab each lane forms the force (Eq. 22
-// Shan-Chen or Eq. 7 Zhang-Chen), the moments (Eq. 3) and the
-// exact-difference forcing with BGK (Eq. 1, 2, 10).  It then streams (Eq. 1)
+// formed at the end of slab s.  Per slab each lane forms the moments (Eq. 3),
+// the force (Eq. 22 Shan-Chen or Eq. 7 Zhang-Chen) and the exact-difference
+// forcing with BGK (Eq. 1, 2, 10).  It then streams (Eq. 1)
 // by push: the x shift is a warp shuffle, the destination float4 of f(t+1) is
 // stored straight to HBM, and the three partial sums of what lands in rows
 // y-1, y, y+1 go to an 18-row shared ring.  After the slab's one barrier each
