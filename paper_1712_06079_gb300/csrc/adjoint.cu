@@ -35,7 +35,13 @@
 // the three fields (rho_bar, jx_bar, jy_bar) instead of nine, staged in
 // shared memory with a one-cell halo for the pull g_i = lambda_i(x + e_i).
 // The HDM stencils run at a compile-time radius (26 in FP32, 40 in FP64)
-// over weights that are zero past the folded radius of the lattice.  T_bar
+// over weights that are zero past the folded radius of the lattice; in the
+// padded FP32 layout each kernel forms the tile's derivatives once, in
+// recurrence form (hdm_window4), before its per-cell work.  The padded FP32
+// kernels are launched with programmatic serialization: A does its
+// state-only work (field staging, f, EOS terms, tile derivatives) while the
+// previous step's B finishes, and every read of a predecessor's output and
+// every write waits for it (griddepcontrol.wait).  T_bar
 // terms are summed over each warp in the working precision (32 terms), then
 // in FP64 over the warps of a CTA into one slot per CTA (no atomics, so the
 // sum is reproducible), over the steps in the same slots, and over the slots

@@ -8,11 +8,16 @@
 // Pass 2 (collide_kernel): a CTA owns a TX x TY tile.  It stages q over the
 // tile plus the cross-shaped halo the gradient needs (K cells left/right on
 // the tile's rows for d/dx, K rows above/below on its columns for d/dy, with
-// the periodic wrap) in shared memory, then each thread takes TY/TYT cells of
-// one column: the explicit HDM stencil (the exact periodic solve of Eq. 20,
-// truncated at radius K where the weights fall below the working precision)
-// or the CDM of Eq. 15, the force (Eq. 22 or Eq. 7), the exact-difference
-// forcing with BGK (Eq. 1, 2, 10), and a push store of f_i* to x + e_i.
+// the periodic wrap, or across no-slip walls in y the mirror image of the
+// field) in shared memory, then each thread takes TY/TYT cells of one column:
+// the explicit HDM stencil (the exact periodic solve of Eq. 20, truncated at
+// radius K where the weights fall below the working precision; with walls the
+// periodic operator of the mirrored column) or the CDM of Eq. 15, the force
+// (Eq. 22 or Eq. 7), the exact-difference forcing with BGK (Eq. 1, 2, 10),
+// and a push store of f_i* to x + e_i (with walls, a population that would
+// cross one returns to its cell reversed: half-way bounce-back).
+//
+// gradient_kernel applies the same staging and operator to a caller's field.
 // The bytes per cell are f read twice (pass 1 and 2), f written once and q
 // written once and read once (halo re-reads hit L2).
 #include <cuda_runtime.h>
