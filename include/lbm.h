@@ -13,7 +13,8 @@
  *     or F = -grad U      (Zhang-Chen form, Eq. 7)
  *   f_i* = f_i - (f_i - f_i^eq(rho,u))/tau
  *          + f_i^eq(rho, u + F/rho) - f_i^eq(rho, u)           (Eq. 1, 2, 10)
- *   f_i(x + e_i, t+1) = f_i*(x)  on a lattice periodic in x and y  (Eq. 1)
+ *   f_i(x + e_i, t+1) = f_i*(x)  on a lattice periodic in x and y  (Eq. 1),
+ *     or periodic in x with half-way bounce-back walls in y (LBM_FLAG_WALLS_Y)
  *
  * Conventions shared by every entry point:
  *  - Fields are row-major, x fastest: index = y * nx + x, nx * ny entries.
@@ -196,6 +197,8 @@ lbm_status lbm_observables(lbm_ctx *c, lbm_obs *out);
  * HDM, the periodic solution of Eq. 20 along every row (d/dx) and column
  * (d/dy) as the folded explicit stencil of the context's radius, or CDM, Eq. 15
  * times 1/c_s^2 = 3; both divided by the grid spacing h (the step uses h = 1).
+ * With LBM_FLAG_WALLS_Y the columns are closed by the mirror image, as in the
+ * step (d/dy of a line of ny points is the periodic operator on 2 ny points).
  * q, gx, gy: host FP64 arrays of nx*ny values, row-major (x fastest), q taken
  * as given (no magnitude, unlike the Shan-Chen field); computed in the
  * context precision (q rounded to FP32 for FP32 contexts).  The lattice state
