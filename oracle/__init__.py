@@ -81,6 +81,8 @@ def _load():
             lib.orc_moments.argtypes = [P, D, D, D, D]
             lib.orc_flat_profile.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, D, D]
+            lib.orc_cs_run.argtypes = [P, D, D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, D, D]
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -267,3 +269,21 @@ def moments(p: Params, f):
     if _load().orc_moments(ctypes.byref(p.c()), _ptr(f), _ptr(rho), _ptr(vx), _ptr(vy)):
         raise MemoryError
     return rho, vx, vy
+
+
+def tangent(p: Params, rho0, nsteps: int, *, drho0=None, dTr: float = 0.0, dG: float = 0.0, h: float = 1e-30):
+    """Complex-step derivative of the discrete map (Squire & Trapp 1998): the
+    step run in complex arithmetic from f = f^eq(rho0 + i h drho0, 0) with
+    T + i h dTr Tc and G + i h dG.  Returns (rho_T, d rho_T) where d rho_T is
+    the derivative of the density after nsteps steps along the direction
+    (drho0, dTr, dG), exact to rounding (no difference quotient).  dTr is a
+    direction in the reduced temperature (T = Tr Tc); dG applies in psi mode."""
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    d0 = None if drho0 is None else np.ascontiguousarray(drho0, dtype=np.float64)
+    if d0 is not None and d0.shape != rho0.shape:
+        raise ValueError("drho0 must have the shape of rho0")
+    rho, drho = np.empty_like(rho0), np.empty_like(rho0)
+    if _load().orc_cs_run(ctypes.byref(p.c()), _ptr(rho0), _ptr(d0), float(dTr) * p.Tc, float(dG), float(h),
+                          int(nsteps), _ptr(rho), _ptr(drho)):
+        raise MemoryError
+    return rho, drho

@@ -21,12 +21,15 @@
  *   Eq. 10  Kupershtokh exact-difference forcing;  Eq. 2 equilibrium
  *   Eq. 1   BGK collision and streaming on the periodic lattice
  *   Eq. 11  the observable half-step velocity
- * plus the Maxwell equal-area construction (Sec. 5.2) and the critical point.
+ * plus the Maxwell equal-area construction (Sec. 5.2), the critical point, the
+ * flat-interface profile (Eq. 25-26) and a complex-step derivative of the step
+ * (the same step in complex arithmetic) that checks reverse-mode gradients.
  *
  * No FMA contraction, no fast math: compile with -ffp-contract=off.
  * Threads (OpenMP) split the lattice by rows only; every cell's arithmetic and
  * every reduction order is independent of the thread count.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -771,5 +774,204 @@ int orc_moments(const orc_params *q, const double *f, double *rho, double *vx, d
         if (vy) vy[c] = w.uy[c] + 0.5 * w.Fy[c] / r;
     }
     free(w.rho);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Complex-step derivative of the discrete map (Squire & Trapp, SIAM Rev. 40, */
+/* 1998; Martins, Sturdza & Alonso, ACM TOMS 29, 2003).                       */
+/*                                                                            */
+/* The step above, evaluated in complex arithmetic.  Give the temperature,    */
+/* G and the initial density imaginary parts i h dT, i h dG, i h drho0 for a  */
+/* tiny real h: after n steps the imaginary part of rho is h times the        */
+/* directional derivative of rho_n along (drho0, dT, dG), free of the         */
+/* cancellation of a difference quotient, and the real part is the real run   */
+/* up to O(h^2).  Every operation of the step is analytic where U != 0; the   */
+/* magnitude |U| of Eq. 21 continues as s U with s = sign(Re U), the branch   */
+/* the real step takes.  The derivative operators (Eq. 15, Eq. 20) are real   */
+/* and linear, so they act on the real and imaginary parts separately with    */
+/* the real solvers above.  Serial except inside those solvers.              */
+/* ------------------------------------------------------------------------ */
+
+typedef double complex cplx;
+
+static cplx mk_c(double re, double im) {
+    cplx z;
+    __real__ z = re;
+    __imag__ z = im;
+    return z;
+}
+
+/* alpha(T) of Eq. 27, Eq. 28 and the RKS form, at a complex temperature. */
+static cplx alpha_c(int eos, double omega, cplx T, double Tc) {
+    double m;
+    cplx s;
+    switch (eos) {
+    case ORC_PR:
+        m = 0.37464 + 1.54226 * omega - 0.26992 * omega * omega;
+        s = 1.0 + m * (1.0 - csqrt(T / Tc));
+        return s * s;
+    case ORC_RKS:
+        m = 0.480 + 1.574 * omega - 0.176 * omega * omega;
+        s = 1.0 + m * (1.0 - csqrt(T / Tc));
+        return s * s;
+    case ORC_RK:
+        return 1.0 / csqrt(T);
+    default:
+        return 1.0;
+    }
+}
+
+/* p_EOS(rho) at temperature T (Eq. 24, 27, 28, 29; no Hu factor). */
+static cplx p_eos_c(const orc_params *q, cplx T, cplx rho) {
+    const double a = q->a, b = q->b, R = q->R;
+    if (q->eos == ORC_CS) {
+        cplx e = b * rho / 4.0;
+        cplx num = 1.0 + e + e * e - e * e * e;
+        cplx om = 1.0 - e;
+        cplx Z = num / (om * om * om);
+        return rho * R * T * Z - a * rho * rho;
+    }
+    cplx rep = rho * R * T / (1.0 - b * rho);
+    if (q->eos == ORC_VDW) return rep - a * rho * rho;
+    cplx al = alpha_c(q->eos, q->omega, T, q->Tc);
+    if (q->eos == ORC_PR) return rep - a * al * rho * rho / (1.0 + 2.0 * b * rho - b * b * rho * rho);
+    return rep - a * al * rho * rho / (1.0 + b * rho); /* RK, RKS */
+}
+
+/* Equilibrium of Eq. 2. */
+static void feq_c(cplx rho, cplx ux, cplx uy, cplx *feq) {
+    cplx uu = ux * ux + uy * uy;
+    for (int i = 0; i < 9; ++i) {
+        cplx eu = EX[i] * ux + EY[i] * uy;
+        feq[i] = rho * W9[i] * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+    }
+}
+
+typedef struct {
+    cplx *rho, *ux, *uy, *Fx, *Fy, *U, *fld, *gx, *gy;
+    double *re, *im, *gxr, *gyr, *gxi, *gyi;
+} cs_work;
+
+/* The gradient of the step (orc_grad) applied to the real and the imaginary
+ * part of a complex field. */
+static void grad_c(const orc_params *q, cs_work *w, size_t n) {
+    for (size_t c = 0; c < n; ++c) {
+        w->re[c] = creal(w->fld[c]);
+        w->im[c] = cimag(w->fld[c]);
+    }
+    orc_grad(q, w->re, w->gxr, w->gyr);
+    orc_grad(q, w->im, w->gxi, w->gyi);
+    for (size_t c = 0; c < n; ++c) {
+        w->gx[c] = mk_c(w->gxr[c], w->gxi[c]);
+        w->gy[c] = mk_c(w->gyr[c], w->gyi[c]);
+    }
+}
+
+/* Interaction force of orc_force (Eq. 7, 22; Eq. 4-5 in psi mode). */
+static void force_c(const orc_params *q, cplx T, cplx G, cs_work *w, size_t n) {
+    const int psi_mode = q->eos == ORC_PSI;
+    for (size_t c = 0; c < n; ++c) {
+        cplx r = w->rho[c];
+        if (psi_mode) {
+            cplx psi = 1.0 - cexp(-r / q->rho0);
+            w->U[c] = 0.5 * G * psi * psi;
+            w->fld[c] = (q->force == ORC_SC) ? psi : w->U[c];
+        } else {
+            w->U[c] = q->k * p_eos_c(q, T, r) - r * CS2;
+            double s = creal(w->U[c]) >= 0.0 ? 1.0 : -1.0;
+            w->fld[c] = (q->force == ORC_SC) ? csqrt(s * w->U[c]) : w->U[c];
+        }
+    }
+    grad_c(q, w, n);
+    for (size_t c = 0; c < n; ++c) {
+        if (q->force == ORC_SC && psi_mode) {
+            w->Fx[c] = -G * w->fld[c] * w->gx[c];
+            w->Fy[c] = -G * w->fld[c] * w->gy[c];
+        } else if (q->force == ORC_SC) {
+            double s = creal(w->U[c]) >= 0.0 ? 1.0 : -1.0;
+            w->Fx[c] = -2.0 * s * w->fld[c] * w->gx[c];
+            w->Fy[c] = -2.0 * s * w->fld[c] * w->gy[c];
+        } else {
+            w->Fx[c] = -w->gx[c];
+            w->Fy[c] = -w->gy[c];
+        }
+    }
+}
+
+/* One step of step_with (Eq. 3, force, Eq. 10 forcing, Eq. 1 BGK and
+ * streaming, walls by half-way bounce-back) in complex arithmetic. */
+static void step_c(const orc_params *q, cplx T, cplx G, const cplx *f, cplx *fout, cs_work *w) {
+    int nx = q->nx, ny = q->ny;
+    size_t n = (size_t)nx * ny;
+    for (size_t c = 0; c < n; ++c) {
+        cplx r = 0, jx = 0, jy = 0;
+        for (int i = 0; i < 9; ++i) {
+            cplx v = f[i * n + c];
+            r += v;
+            jx += EX[i] * v;
+            jy += EY[i] * v;
+        }
+        w->rho[c] = r;
+        w->ux[c] = jx / r;
+        w->uy[c] = jy / r;
+    }
+    force_c(q, T, G, w, n);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
+            cplx r = w->rho[c], ux = w->ux[c], uy = w->uy[c];
+            cplx dux = w->Fx[c] / r, duy = w->Fy[c] / r;
+            cplx fe[9], fs[9];
+            feq_c(r, ux, uy, fe);
+            feq_c(r, ux + dux, uy + duy, fs);
+            for (int i = 0; i < 9; ++i) {
+                cplx fi = f[i * n + c];
+                cplx post = fi - (fi - fe[i]) / q->tau + (fs[i] - fe[i]);
+                int yd = y + EY[i];
+                if (q->walls && (yd < 0 || yd >= ny)) {
+                    fout[OPP[i] * n + c] = post;
+                } else {
+                    size_t d = (size_t)wrap(yd, ny) * nx + wrap(x + EX[i], nx);
+                    fout[i * n + d] = post;
+                }
+            }
+        }
+}
+
+/* nsteps steps from f = f^eq(rho0 + i h drho0, 0) with the temperature
+ * q->T + i h dT and the interaction strength q->G + i h dG.  Writes the
+ * density after the steps (real part) to rho and its derivative along the
+ * direction (drho0, dT, dG), Im(rho) / h, to drho.  drho0 may be NULL (zero).
+ * Returns 0 on success, 1 on allocation failure or h <= 0. */
+int orc_cs_run(const orc_params *q, const double *rho0, const double *drho0, double dT, double dG,
+               double h, int nsteps, double *rho, double *drho) {
+    if (!(h > 0.0)) return 1;
+    size_t n = (size_t)q->nx * q->ny;
+    cplx *f = (cplx *)malloc(sizeof(cplx) * n * 27);
+    double *dw = (double *)malloc(sizeof(double) * n * 6);
+    if (!f || !dw) { free(f); free(dw); return 1; }
+    cplx *g = f + 9 * n, *cw = g + 9 * n;
+    cs_work w = {cw, cw + n, cw + 2 * n, cw + 3 * n, cw + 4 * n, cw + 5 * n, cw + 6 * n, cw + 7 * n, cw + 8 * n,
+                 dw, dw + n, dw + 2 * n, dw + 3 * n, dw + 4 * n, dw + 5 * n};
+    const cplx T = mk_c(q->T, h * dT), G = mk_c(q->G, h * dG);
+    for (size_t c = 0; c < n; ++c) {
+        cplx fe[9];
+        feq_c(mk_c(rho0[c], drho0 ? h * drho0[c] : 0.0), 0.0, 0.0, fe);
+        for (int i = 0; i < 9; ++i) f[i * n + c] = fe[i];
+    }
+    cplx *src = f, *dst = g;
+    for (int s = 0; s < nsteps; ++s) {
+        step_c(q, T, G, src, dst, &w);
+        cplx *t = src; src = dst; dst = t;
+    }
+    for (size_t c = 0; c < n; ++c) {
+        cplx r = 0;
+        for (int i = 0; i < 9; ++i) r += src[i * n + c];
+        rho[c] = creal(r);
+        drho[c] = cimag(r) / h;
+    }
+    free(f);
+    free(dw);
     return 0;
 }

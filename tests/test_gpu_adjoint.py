@@ -1,8 +1,10 @@
 """GPU tests of the reverse-mode (adjoint) step: gradients of
 L = sum (rho_T - rho_target)^2 with respect to the initial density field and
 the reduced temperature, against central finite differences of the FP64 GPU
-path and of the FP64 oracle, for both force forms, both gradients and tau != 1;
-checkpoint intervals must not change the result; dL/dG = 0."""
+path and of the FP64 oracle and against the oracle's complex-step derivative
+(exact to rounding, so the bar is 1e-11 instead of the differences' 1e-4), for
+both force forms, both gradients and tau != 1; checkpoint intervals must not
+change the result; dL/dG = 0."""
 import math
 
 import numpy as np
@@ -84,6 +86,30 @@ def test_adjoint_against_central_differences_fp64(eos, Tr, force, grad, tau, nx,
     eps = 1e-6 * np.abs(rho0).max()
     fd_dir = (loss_of(p, rho0 + eps * d, target, nsteps) - loss_of(p, rho0 - eps * d, target, nsteps)) / (2 * eps)
     assert float((g_rho0 * d).sum()) == pytest.approx(fd_dir, rel=1e-4)
+
+
+@pytest.mark.parametrize("eos,Tr,force,grad,tau,nx,ny", CASES)
+def test_adjoint_matches_complex_step_oracle(eos, Tr, force, grad, tau, nx, ny):
+    nsteps = 40
+    p, rho0, target = setup(nx, ny, eos, Tr, force, grad, tau)
+    L, g_rho0, g_tr, _ = adjoint(p, rho0, target, nsteps, 7)
+    t = T[eos]
+    op = oracle.params_at(nx, ny, eos, t["a"], t["b"], Tr, omega=t["omega"], k=t["k"], tau=tau, force=force,
+                          grad=grad)
+    # dL/dtheta = sum 2 (rho_T - target) d rho_T/dtheta, d rho_T from the complex step
+    r, dT = oracle.tangent(op, rho0, nsteps, dTr=1.0)
+    assert L == pytest.approx(float(((r - target) ** 2).sum()), rel=1e-10)
+    assert g_tr == pytest.approx(float((2 * (r - target) * dT).sum()), rel=1e-11)
+    d = inputs.uniform01(7, nx * ny).reshape(ny, nx) - 0.5
+    _, dd = oracle.tangent(op, rho0, nsteps, drho0=d)
+    assert float((g_rho0 * d).sum()) == pytest.approx(float((2 * (r - target) * dd).sum()), rel=1e-11)
+    # and cell by cell at a few cells (unit directions)
+    for (y, x) in [(ny // 2, nx // 2), (ny // 2, nx // 2 + 9), (3, 4)]:
+        e = np.zeros_like(rho0)
+        e[y, x] = 1.0
+        _, de = oracle.tangent(op, rho0, nsteps, drho0=e)
+        assert g_rho0[y, x] == pytest.approx(float((2 * (r - target) * de).sum()), rel=1e-10,
+                                             abs=1e-12 * np.abs(g_rho0).max())
 
 
 def test_adjoint_matches_oracle_finite_differences():

@@ -132,6 +132,23 @@ def test_adjoint_dG_against_central_differences(force, grad, tau, G):
     assert float((gr * d).sum()) == pytest.approx(fdd, rel=1e-4)
 
 
+@pytest.mark.parametrize("force,grad,tau,G", [("sc", "hdm", 1.0, -1.7), ("zc", "hdm", 0.9, -1.6), ("sc", "cdm", 1.0, -1.7)])
+def test_adjoint_dG_matches_complex_step_oracle(force, grad, tau, G):
+    # the oracle's complex-step derivative is exact to rounding: a 1e-11 bar
+    nx, ny, n = 48, 40, 40
+    gp, op = pair(nx, ny, G, 1.0, force, grad, tau)
+    g, l, _ = oracle.maxwell(op)
+    rho0 = inputs.droplet(nx, ny, 10, g, l)
+    target = inputs.droplet(nx, ny, 11.5, g, l)
+    L, gr, _, gG = adjoint(gp, rho0, target, n, 7)
+    r, dG = oracle.tangent(op, rho0, n, dG=1.0)
+    assert L == pytest.approx(float(((r - target) ** 2).sum()), rel=1e-10)
+    assert gG == pytest.approx(float((2 * (r - target) * dG).sum()), rel=1e-11)
+    d = inputs.uniform01(11, nx * ny).reshape(ny, nx) - 0.5
+    _, dd = oracle.tangent(op, rho0, n, drho0=d)
+    assert float((gr * d).sum()) == pytest.approx(float((2 * (r - target) * dd).sum()), rel=1e-11)
+
+
 def test_adjoint_dG_fp32_close_to_fp64():
     nx, ny, n = 128, 96, 100
     gp64, op = pair(nx, ny, -1.7)
