@@ -84,11 +84,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, u
         : "memory");
 }
 
-// Prefetch `bytes` of global memory into L2 (bulk, no completion tracking).
-__device__ __forceinline__ void bulk_prefetch_l2(const void *src_gmem, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src_gmem), "r"(bytes) : "memory");
-}
-
 // Asynchronous global -> shared copy of BYTES (4, 8 or 16) through L1
 // (cp.async); completion by cp_async_wait_all.
 template <int BYTES>
