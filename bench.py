@@ -363,6 +363,7 @@ def run_sweep(args):
     b = lbm.Batch(params)
     b.init_density(rho0)
     shape = b.tune(trial_steps=50)
+    cluster = b.cluster()   # CTAs per instance of the cluster form, 0 for the grid form
     b.init_density(rho0)
     b.step(seq_steps)           # warm-up and the equal-accuracy comparison point
     rho_b_short = b.density()
@@ -414,7 +415,7 @@ def run_sweep(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "64 flat-interface lattices, Nx U[256,2048], Ny 8, EOS from {VdW, CS, PR, RK}, "
                                "Tr linspace(0.5, 0.95), tau U[0.8, 1.2], SC + HDM", "cells": cells,
-                   "launch": {"block_threads": shape[0], "grid_blocks": shape[1]}},
+                   "launch": {"block_threads": shape[0], "grid_blocks": shape[1], "cluster": cluster}},
         "batched_ms_per_step": per_step_batch, "sequential_ms_per_step": per_step_seq,
         "speedup": per_step_seq / per_step_batch,
         "batched_mlups": cells * steps / (ms_batch * 1e-3) / 1e6,

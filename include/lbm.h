@@ -261,8 +261,9 @@ lbm_status lbm_get_timing(lbm_ctx *c, lbm_timing *out);
  * Batched sweep: n independent periodic lattices of uneven size, each with its
  * own EOS, constants, T/Tc, tau, k, force form and gradient (the temperature
  * and EOS sweeps behind the coexistence curves of Sec. 5.2, Fig. 5), advanced
- * together by one persistent cooperative launch per lbm_batch_step call,
- * replayed from a CUDA graph.  All instances share p[0].prec and p[0].stream.
+ * together by one persistent launch per lbm_batch_step call (a cooperative
+ * grid over all cells, or one thread-block cluster per instance, see
+ * lbm_batch_set_cluster), replayed from a CUDA graph.  All instances share p[0].prec and p[0].stream.
  * Host fields are concatenated instance after instance: a density field has
  * nx_i*ny_i entries per instance, a distribution array 9*nx_i*ny_i (SoA within
  * the instance).  Grid-wide waits inside the launch are bounded (2 s); a wait
@@ -296,14 +297,32 @@ lbm_status lbm_batch_density(lbm_batch *b, double *rho);
 lbm_status lbm_batch_set_launch(lbm_batch *b, int block_threads, int blocks_per_sm);
 lbm_status lbm_batch_get_launch(lbm_batch *b, int *block_threads, int *grid_blocks);
 
-/* Autotuner: time trial_steps steps for every candidate launch shape on a copy
- * of the current state, keep the fastest (written to the out pointers, which
- * may be NULL) and restore the state.  Synchronising. */
+/* Cluster form of the batch: one thread-block cluster of `cluster` CTAs
+ * (1, 2, 4, 8 or 16) per instance, block_threads (128, 256, 512 or 1024)
+ * threads each, the clusters taking the instances largest first, the instance's distributions and potential field held in shared
+ * memory for the whole launch and the stencil halos and boundary populations
+ * exchanged through distributed shared memory; hardware cluster barriers
+ * replace the grid barriers.  The per-cell arithmetic is the grid form's, so
+ * both forms give the same results.  Every instance must split: nx a multiple
+ * of `cluster`, a slice of nx / cluster columns at least as wide as its x halo
+ * (the HDM radius, 1 for CDM), and both distribution buffers plus the haloed
+ * field of the largest slice within a block's shared memory; otherwise
+ * LBM_E_INVALID and the batch keeps its form.  cluster = 0 returns to the grid
+ * form.  lbm_batch_get_launch then reports block_threads and cluster * n. */
+lbm_status lbm_batch_set_cluster(lbm_batch *b, int cluster, int block_threads);
+lbm_status lbm_batch_get_cluster(lbm_batch *b, int *cluster);
+
+/* Autotuner: time trial_steps steps for every candidate launch shape (grid
+ * form: block size x blocks per SM; cluster form: cluster size x block size,
+ * where the instances split) on a copy of the current state, keep the fastest
+ * (its block size and grid, as lbm_batch_get_launch reports them, written to
+ * the out pointers, which may be NULL) and restore the state.  Synchronising. */
 lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int *grid_blocks);
 
 /* Test hook for the bounded grid barrier: block `block` (or none when -1)
  * skips its first arrival, so the other blocks give up after limit_seconds
- * (at most 60) and the next synchronising call answers LBM_E_TIMEOUT. */
+ * (at most 60) and the next synchronising call answers LBM_E_TIMEOUT.  While
+ * armed, steps take the grid form. */
 lbm_status lbm_batch_debug_skip_barrier(lbm_batch *b, int block, double limit_seconds);
 
 const char *lbm_batch_last_error(const lbm_batch *b);

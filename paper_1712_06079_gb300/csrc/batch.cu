@@ -16,6 +16,7 @@
 // The grid barrier is a counter/generation pair in global memory; every wait
 // is bounded by %globaltimer and sets LBM_E_TIMEOUT and an abort flag that
 // all blocks check, so no block can spin forever.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -106,6 +107,35 @@ __device__ __forceinline__ T qabs(T v, bool sc) {
     return sc ? fabs(v) : v;
 }
 
+// Moments (Eq. 3), exact-difference forcing (Eq. 10) and BGK (Eq. 1) of one
+// cell with interaction force (Fx, Fy): the post-collision populations
+// post[i]; the rest population takes rho minus the other eight.
+template <typename T>
+__device__ __forceinline__ void collide_cell(const Model<T> &m, const T (&fi)[kQ], T Fx, T Fy, T (&post)[kQ]) {
+    T r = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        r += fi[i];
+        jx += T(ex(i)) * fi[i];
+        jy += T(ey(i)) * fi[i];
+    }
+    const T inv = T(1) / r;
+    const T ux = jx * inv, uy = jy * inv;
+    const T vx = ux + Fx * inv, vy = uy + Fy * inv;
+    const T uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
+    T moved = T(0);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        const T eu = T(ex(i)) * ux + T(ey(i)) * uy;
+        const T ev = T(ex(i)) * vx + T(ey(i)) * vy;
+        const T feq = r * wq<T>(i) * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
+        const T fsh = r * wq<T>(i) * (T(1) + T(3) * ev + T(4.5) * ev * ev - T(1.5) * vv);
+        post[i] = fi[i] - (fi[i] - feq) * m.omega + (fsh - feq);
+        moved += post[i];
+    }
+    post[0] = r - moved;
+}
+
 template <typename T>
 __global__ void batch_kernel(const BatchArgs<T> a) {
     const unsigned int nblocks = gridDim.x;
@@ -179,38 +209,159 @@ __global__ void batch_kernel(const BatchArgs<T> a) {
                 Fx = -dx;
                 Fy = -dy;
             }
-            T fi[kQ];
+            T fi[kQ], post[kQ];
 #pragma unroll
             for (int i = 0; i < kQ; ++i) fi[i] = f[i * a.ntot + cell];
-            T r = T(0), jx = T(0), jy = T(0);
-#pragma unroll
-            for (int i = 0; i < kQ; ++i) {
-                r += fi[i];
-                jx += T(ex(i)) * fi[i];
-                jy += T(ey(i)) * fi[i];
-            }
-            const T inv = T(1) / r;
-            const T ux = jx * inv, uy = jy * inv;
-            const T vx = ux + Fx * inv, vy = uy + Fy * inv;
-            const T uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
+            collide_cell(m, fi, Fx, Fy, post);
             const int xp = x + 1 == m.nx ? 0 : x + 1, xm = x == 0 ? m.nx - 1 : x - 1;
             const int yp = y + 1 == m.ny ? 0 : y + 1, ym = y == 0 ? m.ny - 1 : y - 1;
-            T moved = T(0);
 #pragma unroll
             for (int i = 1; i < kQ; ++i) {
-                const T eu = T(ex(i)) * ux + T(ey(i)) * uy;
-                const T ev = T(ex(i)) * vx + T(ey(i)) * vy;
-                const T feq = r * wq<T>(i) * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
-                const T fsh = r * wq<T>(i) * (T(1) + T(3) * ev + T(4.5) * ev * ev - T(1.5) * vv);
-                const T post = fi[i] - (fi[i] - feq) * m.omega + (fsh - feq);
-                moved += post;
                 const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
                 const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
-                fo[i * a.ntot + I.off + (long long)dys * m.nx + dxs] = post;
+                fo[i * a.ntot + I.off + (long long)dys * m.nx + dxs] = post[i];
             }
-            fo[cell] = r - moved;
+            fo[cell] = post[0];
         }
         if (!grid_sync(a.bar, nblocks, a.err, a.limit_ns)) return;
+    }
+}
+
+// Cluster form: one thread-block cluster of C CTAs per instance, with the
+// instance's state on chip for the whole launch.  CTA rank k owns the columns
+// [k w, (k + 1) w), w = nx / C, of every row; its two distribution buffers and
+// its potential field (with hx halo columns on each side) live in shared
+// memory.  One step: phase A (rho and the potential field of the owned cells),
+// a cluster barrier, the halo columns copied from the neighbouring ranks'
+// shared memory (ranks k - 1 and k + 1 modulo C: x is periodic), phase B
+// (gradient, force, forcing + BGK, push streaming: a population that leaves
+// the owned columns is stored into the neighbour's buffer), a cluster barrier.
+// Global f is read before the first step and written after the last.  The
+// only waits are the cluster barriers, reached the same number of times by
+// every thread, and no CTA exits before the last barrier, so no access reaches
+// the shared memory of a CTA that has left.  The per-cell arithmetic is the
+// grid form's, term for term.
+template <typename T>
+struct ClusterArgs {
+    const Inst<T> *inst;
+    const int *order;  // instance of each cluster: largest first, so no large one starts last
+    const T *fin;    // state at the first step (concatenated layout)
+    T *fout;         // receives the state after nsteps (may be fin)
+    long long ntot;
+    int nsteps;
+    int *err;
+};
+
+template <typename T>
+__global__ void cluster_batch_kernel(const ClusterArgs<T> a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const Inst<T> &I = a.inst[a.order[blockIdx.x / C]];   // clusters lie along x, one per instance
+    const Model<T> &m = I.m;
+    const bool sc = I.sc != 0, cdm = I.cdm != 0;
+    const int nx = m.nx, ny = m.ny;
+    const int w = nx / C, x0 = rank * w;
+    const int hx = cdm ? 1 : m.kx;
+    const int W = w + 2 * hx;
+    const int ncell = w * ny;
+    T *fa = reinterpret_cast<T *>(smem_raw);   // [kQ][ny][w]
+    T *fb = fa + (size_t)kQ * ncell;
+    T *ph = fb + (size_t)kQ * ncell;           // [ny][W], owned column xl at hx + xl
+    const int left = rank == 0 ? C - 1 : rank - 1, right = rank == C - 1 ? 0 : rank + 1;
+
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const int y = c / w, xl = c - y * w;
+        const long long g = I.off + (long long)y * nx + x0 + xl;
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) fa[i * ncell + c] = a.fin[i * a.ntot + g];
+    }
+    __syncthreads();
+    for (int step = 0; step < a.nsteps; ++step) {
+        // ---- phase A: density and potential field of the owned cells ----
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int y = c / w, xl = c - y * w;
+            T r = T(0);
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) r += fa[i * ncell + c];
+            if (!(r > T(0)) || !isfinite(r)) atomicOr(a.err, kErrUnstable);
+            ph[y * W + hx + xl] = potential_field(m, r, sc);
+        }
+        cluster.sync();
+        // ---- halo: the left neighbour's columns w - hx .. w - 1, the right one's 0 .. hx - 1 ----
+        {
+            const T *pl = cluster.map_shared_rank(ph, left);
+            const T *pr = cluster.map_shared_rank(ph, right);
+            const int nh = hx * ny;
+            for (int c = threadIdx.x; c < 2 * nh; c += blockDim.x) {
+                const int side = c < nh ? 0 : 1, k = c - side * nh;
+                const int y = k / hx, j = k - y * hx;
+                if (side == 0) ph[y * W + j] = pl[y * W + w + j];
+                else ph[y * W + hx + w + j] = pr[y * W + hx + j];
+            }
+        }
+        __syncthreads();
+        // ---- phase B: gradient, force, forcing + BGK, push streaming ----
+        T *fbl = cluster.map_shared_rank(fb, left);
+        T *fbr = cluster.map_shared_rank(fb, right);
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int y = c / w, xl = c - y * w;
+            const T *row = ph + y * W + hx + xl;   // row[j]: the field at column xl + j
+            T dx = T(0), dy = T(0);
+            if (cdm) {
+                // Eq. 15 times 1/c_s^2
+                const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+                auto at = [&](int yy, int dxo) { return qabs(ph[yy * W + hx + xl + dxo], sc); };
+                const T e = at(y, 1), wv = at(y, -1), nn = at(yp, 0), so = at(ym, 0);
+                const T ne = at(yp, 1), nw = at(yp, -1), se = at(ym, 1), sw = at(ym, -1);
+                dx = T(1.0 / 3.0) * (e - wv) + T(1.0 / 12.0) * ((ne + se) - (nw + sw));
+                dy = T(1.0 / 3.0) * (nn - so) + T(1.0 / 12.0) * ((ne + nw) - (se + sw));
+            } else {
+                // explicit periodic form of Eq. 20 (folded weights for short lines)
+                for (int j = 1; j <= m.kx; ++j) dx += m.wx[j] * (qabs(row[j], sc) - qabs(row[-j], sc));
+                for (int j = 1; j <= m.ky; ++j) {
+                    int yp = y + j, ym = y - j;
+                    if (yp >= ny) yp -= ny;
+                    if (ym < 0) ym += ny;
+                    dy += m.wy[j] * (qabs(ph[yp * W + hx + xl], sc) - qabs(ph[ym * W + hx + xl], sc));
+                }
+            }
+            const T qc = row[0];
+            T Fx, Fy;
+            if (sc) {  // Eq. 22: F = -2 s Phi grad Phi, q = s Phi
+                Fx = T(-2) * qc * dx;
+                Fy = T(-2) * qc * dy;
+            } else {   // Eq. 7
+                Fx = -dx;
+                Fy = -dy;
+            }
+            T fi[kQ], post[kQ];
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) fi[i] = fa[i * ncell + c];
+            collide_cell(m, fi, Fx, Fy, post);
+            const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+#pragma unroll
+            for (int i = 1; i < kQ; ++i) {
+                const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
+                const int xd = xl + ex(i);
+                T *dst = xd < 0 ? fbl : (xd >= w ? fbr : fb);
+                const int xc = xd < 0 ? w - 1 : (xd >= w ? 0 : xd);
+                dst[i * ncell + dys * w + xc] = post[i];
+            }
+            fb[c] = post[0];
+        }
+        cluster.sync();
+        T *t = fa;
+        fa = fb;
+        fb = t;
+    }
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const int y = c / w, xl = c - y * w;
+        const long long g = I.off + (long long)y * nx + x0 + xl;
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) a.fout[i * a.ntot + g] = fa[i * ncell + c];
     }
 }
 
@@ -251,6 +402,7 @@ struct lbm_batch {
     std::vector<long long> off;
     void *inst_dev = nullptr;
     int *table_dev = nullptr;
+    int *order_dev = nullptr;      // instances by decreasing cell count (cluster form)
     void *f[2] = {nullptr, nullptr};
     void *q = nullptr;
     void *stage_dev = nullptr;   // rho staging (ntot values of the precision)
@@ -261,6 +413,10 @@ struct lbm_batch {
     cudaStream_t stream = nullptr;
     int block_threads = 256;
     int grid_blocks = 0;
+    int cluster = 0;               // CTAs per instance in the cluster form (0: grid form)
+    int cluster_threads = 256;
+    size_t cluster_smem = 0;       // dynamic shared memory per CTA of the cluster form
+    std::vector<int> halo;         // x halo of each instance (kx for HDM, 1 for CDM)
     unsigned long long limit_ns = 2000000000ull;  // 2 s per barrier wait
     int skip_block = -1;
     bool initialized = false;
@@ -269,6 +425,7 @@ struct lbm_batch {
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     int graph_steps[2] = {-1, -1}, graph_block[2] = {-1, -1}, graph_grid[2] = {-1, -1};
+    int graph_cluster[2] = {-1, -1};
     bool use_graph = true;
     int graph_launches = 0;  // persistent launches issued through a graph
     std::string msg;
@@ -290,6 +447,7 @@ lbm_status bfail(lbm_batch *b, lbm_status st, const std::string &m) {
 template <typename T>
 lbm_status build_instances(lbm_batch *b, std::vector<Inst<T>> &out) {
     out.resize(b->n);
+    b->halo.assign(b->n, 0);
     for (int i = 0; i < b->n; ++i) {
         const lbm_params &p = b->params[i];
         Inst<T> &I = out[i];
@@ -317,6 +475,7 @@ lbm_status build_instances(lbm_batch *b, std::vector<Inst<T>> &out) {
         I.off = (int)b->off[i];
         I.sc = p.force == LBM_FORCE_SC;
         I.cdm = p.grad == LBM_GRAD_CDM;
+        b->halo[i] = I.cdm ? 1 : I.m.kx;
     }
     return LBM_OK;
 }
@@ -353,9 +512,81 @@ int sm_count() {
     return n;
 }
 
-// Queue one persistent cooperative launch running nsteps steps.
+// Shared memory per CTA of the cluster form with `cluster` CTAs per instance
+// (both distribution buffers and the haloed potential field of the largest
+// slice), or 0 when some instance does not split: nx not a multiple of the
+// cluster size, a slice narrower than the instance's x halo, or more than the
+// opt-in shared memory of a block.
+size_t cluster_smem_bytes(const lbm_batch *b, int cluster) {
+    size_t need = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const int nx = b->params[i].nx, ny = b->params[i].ny;
+        if (nx % cluster != 0) return 0;
+        const int w = nx / cluster;
+        if (b->halo[i] > w) return 0;
+        const size_t bytes = ((size_t)2 * kQ * w * ny + (size_t)ny * (w + 2 * b->halo[i])) * b->esz;
+        need = std::max(need, bytes);
+    }
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return need <= (size_t)optin ? need : 0;
+}
+
+template <typename T>
+cudaLaunchConfig_t cluster_config(const lbm_batch *b, int cluster, int threads, size_t smem,
+                                  cudaLaunchAttribute *attr) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(cluster * b->n));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = b->stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// Prepare the cluster kernel for this shape and check that at least one
+// cluster of it can be resident.  Returns 0 or an error message.
+template <typename T>
+const char *configure_cluster(const lbm_batch *b, int cluster, int threads, size_t smem) {
+    if (cudaFuncSetAttribute(cluster_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return "shared memory of the cluster form not available";
+    if (cudaFuncSetAttribute(cluster_batch_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             cluster > 8 ? 1 : 0) != cudaSuccess)
+        return "cluster size not available";
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config<T>(b, cluster, threads, smem, attr);
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, cluster_batch_kernel<T>, &cfg) != cudaSuccess || nc < 1) {
+        cudaGetLastError();
+        return "no cluster of this shape fits on the device";
+    }
+    return nullptr;
+}
+
+// Queue one launch running nsteps steps: the cluster form when one is set
+// (and no barrier test hook is armed), else the persistent cooperative grid form.
 template <typename T>
 cudaError_t enqueue(lbm_batch *b, int nsteps) {
+    if (b->cluster > 0 && b->skip_block < 0) {
+        ClusterArgs<T> ca{};
+        ca.inst = (const Inst<T> *)b->inst_dev;
+        ca.order = b->order_dev;
+        ca.fin = (const T *)b->f[b->cur];
+        ca.fout = (T *)b->f[(b->cur + nsteps) & 1];
+        ca.ntot = b->ntot;
+        ca.nsteps = nsteps;
+        ca.err = b->err;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = cluster_config<T>(b, b->cluster, b->cluster_threads, b->cluster_smem, attr);
+        return cudaLaunchKernelEx(&cfg, cluster_batch_kernel<T>, ca);
+    }
     cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(BarrierState), b->stream);
     if (e != cudaSuccess) return e;
     BatchArgs<T> a = make_args<T>(b, nsteps);
@@ -387,8 +618,9 @@ lbm_status run_steps(lbm_batch *b, int nsteps) {
     if (nsteps == 0) return LBM_OK;
     const int k = b->cur;
     if (b->use_graph && b->skip_block < 0) {
-        if (!b->graph_exec[k] || b->graph_steps[k] != nsteps || b->graph_block[k] != b->block_threads ||
-            b->graph_grid[k] != b->grid_blocks) {
+        const int shape_block = b->cluster > 0 ? b->cluster_threads : b->block_threads;
+        if (!b->graph_exec[k] || b->graph_steps[k] != nsteps || b->graph_block[k] != shape_block ||
+            b->graph_grid[k] != b->grid_blocks || b->graph_cluster[k] != b->cluster) {
             drop_graph(b, k);
             bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
@@ -403,8 +635,9 @@ lbm_status run_steps(lbm_batch *b, int nsteps) {
                 b->use_graph = false;
             } else {
                 b->graph_steps[k] = nsteps;
-                b->graph_block[k] = b->block_threads;
+                b->graph_block[k] = shape_block;
                 b->graph_grid[k] = b->grid_blocks;
+                b->graph_cluster[k] = b->cluster;
             }
         }
         if (b->graph_exec[k]) {
@@ -414,7 +647,7 @@ lbm_status run_steps(lbm_batch *b, int nsteps) {
             return LBM_OK;
         }
     }
-    BCK(b, enqueue<T>(b, nsteps), "cooperative launch");
+    BCK(b, enqueue<T>(b, nsteps), "batch launch");
     b->cur = (b->cur + nsteps) & 1;
     return LBM_OK;
 }
@@ -472,6 +705,11 @@ lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out) {
         for (long long g = b->off[i] / kTableGrain; g < (b->off[i] + cells + kTableGrain - 1) / kTableGrain; ++g)
             table[g] = i;
     }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
+        return (long long)p[u].nx * p[u].ny > (long long)p[v].nx * p[v].ny;
+    });
     size_t inst_bytes;
     std::vector<unsigned char> inst_host;
     if (prec == LBM_F64) {
@@ -490,10 +728,12 @@ lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out) {
         cudaMalloc(&b->f[0], fbytes) != cudaSuccess || cudaMalloc(&b->f[1], fbytes) != cudaSuccess ||
         cudaMalloc(&b->q, b->ntot * b->esz) != cudaSuccess || cudaMalloc(&b->stage_dev, b->ntot * b->esz) != cudaSuccess ||
         cudaMalloc((void **)&b->err, sizeof(int)) != cudaSuccess || cudaMalloc((void **)&b->bar, sizeof(BarrierState)) != cudaSuccess ||
+        cudaMalloc((void **)&b->order_dev, n * sizeof(int)) != cudaSuccess ||
         cudaHostAlloc(&b->stage_host, b->ntot * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
         return bail(LBM_E_NOMEM);
     if (cudaMemcpy(b->inst_dev, inst_host.data(), inst_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->table_dev, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->order_dev, order.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->f[0], 0, fbytes) != cudaSuccess || cudaMemset(b->f[1], 0, fbytes) != cudaSuccess ||
         cudaMemset(b->err, 0, sizeof(int)) != cudaSuccess)
         return bail(LBM_E_CUDA);
@@ -520,8 +760,35 @@ lbm_status lbm_batch_set_launch(lbm_batch *b, int block_threads, int blocks_per_
 
 lbm_status lbm_batch_get_launch(lbm_batch *b, int *block_threads, int *grid_blocks) {
     if (!b || !block_threads || !grid_blocks) return LBM_E_INVALID;
-    *block_threads = b->block_threads;
-    *grid_blocks = b->grid_blocks;
+    *block_threads = b->cluster > 0 ? b->cluster_threads : b->block_threads;
+    *grid_blocks = b->cluster > 0 ? b->cluster * b->n : b->grid_blocks;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_cluster(lbm_batch *b, int cluster, int block_threads) {
+    if (!b) return LBM_E_INVALID;
+    if (cluster == 0) {
+        b->cluster = 0;
+        return LBM_OK;
+    }
+    if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8 && cluster != 16)
+        return bfail(b, LBM_E_INVALID, "cluster must be 0, 1, 2, 4, 8 or 16");
+    if (block_threads != 128 && block_threads != 256 && block_threads != 512 && block_threads != 1024)
+        return bfail(b, LBM_E_INVALID, "block_threads must be 128, 256, 512 or 1024");
+    const size_t smem = cluster_smem_bytes(b, cluster);
+    if (smem == 0) return bfail(b, LBM_E_INVALID, "an instance does not split over a cluster of this size");
+    const char *why = b->prec == LBM_F64 ? configure_cluster<double>(b, cluster, block_threads, smem)
+                                         : configure_cluster<float>(b, cluster, block_threads, smem);
+    if (why) return bfail(b, LBM_E_INVALID, why);
+    b->cluster = cluster;
+    b->cluster_threads = block_threads;
+    b->cluster_smem = smem;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_cluster(lbm_batch *b, int *cluster) {
+    if (!b || !cluster) return LBM_E_INVALID;
+    *cluster = b->cluster;
     return LBM_OK;
 }
 
@@ -659,29 +926,55 @@ lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int
     cudaEventCreate(&e1);
     float best = 1e30f;
     int best_t = b->block_threads, best_g = b->grid_blocks;
+    int best_c = b->cluster, best_ct = b->cluster_threads;
     const int threads[3] = {128, 256, 512};
     lbm_status st = LBM_OK;
     if (cudaMemcpyAsync(save, b->f[cur0], fbytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess) st = LBM_E_CUDA;
+    // a warm-up launch, then a timed one (plain launches: no graph per trial)
+    auto trial = [&](float *ms) -> bool {
+        const bool g = b->use_graph;
+        b->use_graph = false;
+        lbm_status s1 = b->prec == LBM_F64 ? run_steps<double>(b, 2) : run_steps<float>(b, 2);
+        cudaEventRecord(e0, b->stream);
+        lbm_status s2 = b->prec == LBM_F64 ? run_steps<double>(b, trial_steps) : run_steps<float>(b, trial_steps);
+        cudaEventRecord(e1, b->stream);
+        b->use_graph = g;
+        if (s1 != LBM_OK || s2 != LBM_OK || cudaEventSynchronize(e1) != cudaSuccess) return false;
+        return cudaEventElapsedTime(ms, e0, e1) == cudaSuccess;
+    };
+    // grid form: block sizes x co-resident blocks per SM
+    b->cluster = 0;
     for (int ti = 0; ti < 3 && st == LBM_OK; ++ti) {
         const int maxb = b->prec == LBM_F64 ? max_blocks_per_sm<double>(threads[ti]) : max_blocks_per_sm<float>(threads[ti]);
         for (int per = 1; per <= maxb && st == LBM_OK; per = per < maxb && per * 2 > maxb ? maxb : per * 2) {
             b->block_threads = threads[ti];
             b->grid_blocks = per * sm_count();
-            // warm-up launch, then a timed one (plain launches: no graph per trial)
-            const bool g = b->use_graph;
-            b->use_graph = false;
-            lbm_status s1 = b->prec == LBM_F64 ? run_steps<double>(b, 2) : run_steps<float>(b, 2);
-            cudaEventRecord(e0, b->stream);
-            lbm_status s2 = b->prec == LBM_F64 ? run_steps<double>(b, trial_steps) : run_steps<float>(b, trial_steps);
-            cudaEventRecord(e1, b->stream);
-            b->use_graph = g;
-            if (s1 != LBM_OK || s2 != LBM_OK || cudaEventSynchronize(e1) != cudaSuccess) { st = LBM_E_CUDA; break; }
             float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_t = b->block_threads; best_g = b->grid_blocks; }
+            if (!trial(&ms)) { st = LBM_E_CUDA; break; }
+            if (ms < best) { best = ms; best_t = b->block_threads; best_g = b->grid_blocks; best_c = 0; }
             if (per == maxb) break;
         }
     }
+    // cluster form: CTAs per instance x threads per CTA, where the instances split
+    const int grid_t = best_t, grid_g = best_g;
+    const int cthreads[3] = {256, 512, 1024};
+    for (int c = 1; c <= 16 && st == LBM_OK; c *= 2) {
+        for (int ti = 0; ti < 3 && st == LBM_OK; ++ti) {
+            if (lbm_batch_set_cluster(b, c, cthreads[ti]) != LBM_OK) continue;
+            float ms = 0;
+            if (!trial(&ms)) { st = LBM_E_CUDA; break; }
+            if (ms < best) {
+                best = ms;
+                best_c = c;
+                best_ct = cthreads[ti];
+            }
+        }
+    }
+    b->block_threads = grid_t;
+    b->grid_blocks = grid_g;
+    b->cluster = 0;
+    if (best_c > 0 && st == LBM_OK && lbm_batch_set_cluster(b, best_c, best_ct) != LBM_OK)
+        st = LBM_E_CUDA;   // re-applies the kernel attributes of the winning shape
     // restore the state and the error word
     if (cudaMemcpyAsync(b->f[cur0], save, fbytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess) st = LBM_E_CUDA;
     b->cur = cur0;
@@ -690,10 +983,10 @@ lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int
     cudaFree(save);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->block_threads = best_t;
-    b->grid_blocks = best_g;
-    if (block_threads) *block_threads = best_t;
-    if (grid_blocks) *grid_blocks = best_g;
+    int t_out = 0, g_out = 0;
+    lbm_batch_get_launch(b, &t_out, &g_out);
+    if (block_threads) *block_threads = t_out;
+    if (grid_blocks) *grid_blocks = g_out;
     return st == LBM_OK ? LBM_OK : bfail(b, st, "autotuning failed");
 }
 
@@ -714,6 +1007,7 @@ void lbm_batch_destroy(lbm_batch *b) {
     drop_graph(b, 1);
     cudaFree(b->inst_dev);
     cudaFree(b->table_dev);
+    cudaFree(b->order_dev);
     cudaFree(b->f[0]);
     cudaFree(b->f[1]);
     cudaFree(b->q);

@@ -90,6 +90,8 @@ SIGNATURES = {
     "lbm_batch_density": (ctypes.c_int, [_V, _D]),
     "lbm_batch_set_launch": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
     "lbm_batch_get_launch": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_set_cluster": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_get_cluster": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_tune": (ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_debug_skip_barrier": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_V]),
@@ -370,6 +372,16 @@ class Batch:
         t, g = ctypes.c_int(), ctypes.c_int()
         self._check(self._lib.lbm_batch_get_launch(self._h, ctypes.byref(t), ctypes.byref(g)))
         return t.value, g.value
+
+    def set_cluster(self, cluster: int, block_threads: int = 256):
+        """One cluster of ``cluster`` CTAs per instance, state in shared memory
+        (``cluster = 0``: the grid form)."""
+        self._check(self._lib.lbm_batch_set_cluster(self._h, int(cluster), int(block_threads)))
+
+    def cluster(self) -> int:
+        c = ctypes.c_int()
+        self._check(self._lib.lbm_batch_get_cluster(self._h, ctypes.byref(c)))
+        return c.value
 
     def tune(self, trial_steps: int = 50):
         t, g = ctypes.c_int(), ctypes.c_int()

@@ -81,6 +81,86 @@ def test_batch_f32_matches_single_lattice_contexts():
         assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-5, (gp.eos, gp.nx)
 
 
+CLUSTER_MIX = MIX[:4]   # split over 2 (FP32), 4 and 8 (FP32) CTAs per instance
+
+
+@pytest.mark.parametrize("prec,cluster,threads", [("f64", 4, 256), ("f32", 2, 512), ("f32", 4, 256),
+                                                  ("f32", 8, 128), ("f32", 8, 1024)])
+def test_cluster_form_equals_grid_form(prec, cluster, threads):
+    # the cluster form runs the grid form's per-cell arithmetic on shared
+    # memory: the same state after every launch, bit for bit, including graph
+    # replays from either buffer
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec=prec) for m in CLUSTER_MIX]
+    f0 = [slab_state(op, k + 31) for k, (_, op) in enumerate(pairs)]
+    outs = []
+    for c in (0, cluster):
+        with lbm.Batch([gp for gp, _ in pairs]) as b:
+            if c:
+                b.set_cluster(c, threads)
+                assert b.cluster() == c and b.launch() == (threads, c * len(pairs))
+            b.set_f(f0)
+            states = []
+            for n in (1, 6, 6):
+                b.step(n)
+                states.append(b.get_f())
+            outs.append(states)
+    for sg, sc in zip(outs[0], outs[1]):
+        for u, v in zip(sg, sc):
+            assert np.array_equal(u, v)
+
+
+def test_cluster_form_f64_matches_oracle():
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f64") for m in CLUSTER_MIX]
+    f0 = [slab_state(op, k + 41) for k, (_, op) in enumerate(pairs)]
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        b.set_cluster(4, 256)
+        b.set_f(f0)
+        b.step(3)
+        f3 = b.get_f()
+    for (gp, op), a, got in zip(pairs, f0, f3):
+        ref = oracle.run(op, a, 3)
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-12, (gp.eos, gp.nx)
+
+
+def test_cluster_form_refusals_and_instability():
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f32") for m in MIX]
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        for c, t in [(8, 256), (3, 256), (4, 96)]:   # 40 / 8 columns < the HDM halo; bad sizes
+            with pytest.raises(lbm.LBMError) as ei:
+                b.set_cluster(c, t)
+            assert ei.value.status == lbm.E_INVALID
+        assert b.cluster() == 0
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f32") for m in CLUSTER_MIX]
+    f0 = [slab_state(op, k + 51) for k, (_, op) in enumerate(pairs)]
+    f0[1][:, 3, 100] = -0.01   # a negative density in the second instance
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        b.set_cluster(8, 256)
+        b.set_f(f0)
+        b.step(2)
+        with pytest.raises(lbm.LBMError) as ei:
+            b.sync()
+        assert ei.value.status == lbm.E_UNSTABLE
+        b.set_cluster(0, 256)
+        assert b.cluster() == 0
+
+
+def test_cluster_autotuner_keeps_state():
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f32") for m in CLUSTER_MIX]
+    rho0 = [inputs.slab(op.nx, op.ny, *oracle.maxwell(op)[:2]) for _, op in pairs]
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        b.init_density(rho0)
+        before = b.density()
+        threads, grid = b.tune(trial_steps=20)
+        assert (threads, grid) == b.launch()
+        c = b.cluster()
+        assert c in (0, 2, 4, 8)
+        assert grid == (c * len(pairs) if c else grid) and threads in (128, 256, 512, 1024)
+        for x, y in zip(before, b.density()):
+            assert np.array_equal(x, y)
+        b.step(10)
+        b.sync()
+
+
 def test_batch_graph_replay_and_launch_shapes_agree():
     pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f64") for m in MIX[:4]]
     f0 = [slab_state(op, k + 21) for k, (_, op) in enumerate(pairs)]
