@@ -199,17 +199,24 @@ def ncu_traffic(kernel: str):
     return e.get("bytes_per_launch_full_size")
 
 
-def oracle_sample(n: int, steps: int):
-    """Time the oracle on an n x n lattice of the same recipe; returns (MLUPS, threads, seconds)."""
+_ORACLE_ALL_THREADS = []   # the oracle's OpenMP thread count before any sample changed it
+
+
+def oracle_sample(n: int, steps: int, threads: int = 0):
+    """Time the oracle on an n x n lattice of the same recipe with `threads`
+    OpenMP threads (0: all host threads); returns (MLUPS, threads, seconds)."""
     import oracle
     from paper_1712_06079_gb300 import inputs
-    oracle.set_threads(oracle.max_threads())
+    if not _ORACLE_ALL_THREADS:
+        _ORACLE_ALL_THREADS.append(oracle.max_threads())
+    oracle.set_threads(threads or _ORACLE_ALL_THREADS[0])
+    used = oracle.max_threads()
     op = oracle.params_at(n, n, EOS, 1.0, 4.0, TR, k=K_HU, tau=TAU, force="sc", grad="hdm")
     f = oracle.init(op, inputs.spinodal(n, n, inputs.CS_TR07_MEAN))
     t0 = time.perf_counter()
     oracle.run(op, f, steps)
     dt = time.perf_counter() - t0
-    return n * n * steps / dt / 1e6, oracle.max_threads(), dt
+    return n * n * steps / dt / 1e6, used, dt
 
 
 def run_reference(args):
@@ -323,13 +330,17 @@ def run_ours(args):
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        # bounded oracle sample: the same recipe on 1024 x 1024, enough steps for ~10 s
+        # bounded oracle samples: the same recipe on 1024 x 1024, all host threads for ~10 s,
+        # then one thread for two steps
         m1, cores, dt = oracle_sample(1024, 2)
         steps = max(2, min(200, int(10.0 / max(dt / 2, 1e-3))))
         mlups, cores, dt = oracle_sample(1024, steps)
+        m_one, _, dt_one = oracle_sample(1024, 2, threads=1)
         line["cpu_baseline"] = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{steps} oracle steps of a 1024x1024 lattice of the same recipe "
-                                          f"({dt:.1f} s)"}
+                                          f"({dt:.1f} s)",
+                                "single_thread": {"value": m_one, "cores": 1,
+                                                  "sample": f"2 steps of the same lattice ({dt_one:.1f} s)"}}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
