@@ -298,7 +298,7 @@ lbm_status lbm_batch_set_launch(lbm_batch *b, int block_threads, int blocks_per_
 lbm_status lbm_batch_get_launch(lbm_batch *b, int *block_threads, int *grid_blocks);
 
 /* Cluster form of the batch: one thread-block cluster of `cluster` CTAs
- * (1, 2, 4, 8 or 16) per instance, block_threads (128, 256, 512 or 1024)
+ * (2, 4 or 8: portable cluster sizes) per instance, block_threads (128, 256, 512 or 1024)
  * threads each, the clusters taking the instances largest first, the instance's distributions and potential field held in shared
  * memory for the whole launch and the stencil halos and boundary populations
  * exchanged through distributed shared memory; hardware cluster barriers

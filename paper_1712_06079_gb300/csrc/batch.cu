@@ -557,9 +557,6 @@ const char *configure_cluster(const lbm_batch *b, int cluster, int threads, size
     if (cudaFuncSetAttribute(cluster_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return "shared memory of the cluster form not available";
-    if (cudaFuncSetAttribute(cluster_batch_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                             cluster > 8 ? 1 : 0) != cudaSuccess)
-        return "cluster size not available";
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_config<T>(b, cluster, threads, smem, attr);
     int nc = 0;
@@ -771,8 +768,8 @@ lbm_status lbm_batch_set_cluster(lbm_batch *b, int cluster, int block_threads) {
         b->cluster = 0;
         return LBM_OK;
     }
-    if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8 && cluster != 16)
-        return bfail(b, LBM_E_INVALID, "cluster must be 0, 1, 2, 4, 8 or 16");
+    if (cluster != 2 && cluster != 4 && cluster != 8)
+        return bfail(b, LBM_E_INVALID, "cluster must be 0, 2, 4 or 8");
     if (block_threads != 128 && block_threads != 256 && block_threads != 512 && block_threads != 1024)
         return bfail(b, LBM_E_INVALID, "block_threads must be 128, 256, 512 or 1024");
     const size_t smem = cluster_smem_bytes(b, cluster);
@@ -958,7 +955,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int
     // cluster form: CTAs per instance x threads per CTA, where the instances split
     const int grid_t = best_t, grid_g = best_g;
     const int cthreads[3] = {256, 512, 1024};
-    for (int c = 1; c <= 16 && st == LBM_OK; c *= 2) {
+    for (int c = 2; c <= 8 && st == LBM_OK; c *= 2) {
         for (int ti = 0; ti < 3 && st == LBM_OK; ++ti) {
             if (lbm_batch_set_cluster(b, c, cthreads[ti]) != LBM_OK) continue;
             float ms = 0;

@@ -125,7 +125,7 @@ def test_cluster_form_f64_matches_oracle():
 def test_cluster_form_refusals_and_instability():
     pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f32") for m in MIX]
     with lbm.Batch([gp for gp, _ in pairs]) as b:
-        for c, t in [(8, 256), (3, 256), (4, 96)]:   # 40 / 8 columns < the HDM halo; bad sizes
+        for c, t in [(8, 256), (3, 256), (16, 256), (1, 256), (4, 96)]:   # 40 / 8 < the HDM halo; bad sizes
             with pytest.raises(lbm.LBMError) as ei:
                 b.set_cluster(c, t)
             assert ei.value.status == lbm.E_INVALID
