@@ -109,6 +109,28 @@ def test_cluster_form_equals_grid_form(prec, cluster, threads):
             assert np.array_equal(u, v)
 
 
+def test_full_sweep_in_the_benchmark_launch_equals_grid_form():
+    # the 64-lattice sweep at full size in the launch the benchmark times
+    # (8 CTAs x 1024 threads per lattice): the same state as the grid form
+    params, rho0 = [], []
+    for d in inputs.sweep_instances(64):
+        gp = lbm.Params(nx=d["nx"], ny=d["ny"], eos=d["eos"], a=d["a"], b=d["b"], omega=d["omega"], Tr=d["Tr"],
+                        k=d["k"], tau=d["tau"], force="sc", grad="hdm", prec="f32")
+        g, l = lbm.maxwell(gp)
+        params.append(gp)
+        rho0.append(inputs.slab(d["nx"], d["ny"], g, l))
+    out = []
+    for c in (0, 8):
+        with lbm.Batch(params) as b:
+            if c:
+                b.set_cluster(c, 1024)
+            b.init_density(rho0)
+            b.step(50)
+            out.append(b.density())
+    for u, v in zip(*out):
+        assert np.array_equal(u, v)
+
+
 def test_cluster_form_f64_matches_oracle():
     pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f64") for m in CLUSTER_MIX]
     f0 = [slab_state(op, k + 41) for k, (_, op) in enumerate(pairs)]
