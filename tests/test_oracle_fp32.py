@@ -1,0 +1,108 @@
+"""What FP32 can reach on the FP32 parity workloads (1000 steps of the 128^2 CS
+droplet and of the 1024 x 8 PR slab), measured with the oracle's step restated
+in numpy (oracle/fp32_restatement.py) at a chosen arithmetic and storage
+precision, against the FP64 oracle on the same inputs.
+
+The contract metric is max_x |rho32 - rho64| / |rho64|, bar 1e-5.
+ - In FP64 arithmetic the restatement is the oracle (pinned per step at 1e-12).
+ - FP32 storage of the distributions alone (FP64 arithmetic) stays under the
+   bar: the state's rounding is not what limits FP32, so storing shifted
+   distributions cannot help.
+ - A plain FP32 evaluation of every operation misses the bar on both
+   workloads.  Its rounding is identical in neighbouring cells of the same
+   state (a bulk phase, an interface profile), so it acts like a small
+   systematic force and moves the interfaces instead of averaging out; the
+   slab's grows to ~3e-4 at the vapour side of the interfaces.
+This is why the library's two-pass kernels compute FP32 lattices in FP64
+arithmetic.  The numbers are what tests/golden/fp32_restatement_errors.txt
+records for the GPU tests (written by tests/golden/make_fp32_limits.py).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.fp32_restatement import Restatement, periodic_weights
+from paper_1712_06079_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def workload(case):
+    if case == "droplet":   # 128^2 CS Tr=0.8 droplet R=30, SC + HDM, tau = 1
+        t = inputs.EOS_TABLE["cs"]
+        op = oracle.params_at(128, 128, "cs", t["a"], t["b"], 0.8, k=t["k"], force="sc")
+        g, l, _ = oracle.maxwell(op)
+        return op, inputs.droplet(128, 128, 30, g, l)
+    t = inputs.EOS_TABLE["pr"]  # 1024 x 8 PR Tr=0.7 slab, ZC + HDM, tau = 1
+    op = oracle.params_at(1024, 8, "pr", t["a"], t["b"], 0.7, omega=t["omega"], k=t["k"], force="zc")
+    g, l, _ = oracle.maxwell(op)
+    return op, inputs.slab(1024, 8, g, l)
+
+
+@pytest.fixture(scope="module")
+def reference():
+    out = {}
+    for case in ("droplet", "slab"):
+        op, rho0 = workload(case)
+        f0 = oracle.init(op, rho0)
+        out[case] = (op, f0, oracle.run(op, f0, 1000).sum(0))
+    return out
+
+
+def pointwise(rho, ro):
+    return float(np.max(np.abs(rho - ro) / np.abs(ro)))
+
+
+def test_periodic_weights_are_the_oracle_operator():
+    # the explicit weights reproduce the cyclic solve on a rough line, and are
+    # normalised as a first derivative (sum 2 j w_j = 1)
+    for n in (8, 37, 128, 1024):
+        w = periodic_weights(n)
+        u = inputs.uniform01(n, n) - 0.5
+        d = sum(w[j - 1] * (np.roll(u, -j) - np.roll(u, j)) for j in range(1, len(w) + 1))
+        assert np.max(np.abs(d - oracle.hdm_line(u))) < 1e-14
+        if n > 80:
+            assert abs(2 * np.dot(np.arange(1, len(w) + 1), w) - 1) < 1e-14
+
+
+@pytest.mark.parametrize("nx,ny,eos,Tr,force,tau", [(128, 128, "cs", 0.8, "sc", 1.0), (1024, 8, "pr", 0.7, "zc", 1.0),
+                                                    (37, 23, "rk", 0.75, "zc", 1.3), (40, 30, "vdw", 0.8, "sc", 0.8)])
+def test_restatement_in_fp64_is_the_oracle(nx, ny, eos, Tr, force, tau):
+    t = inputs.EOS_TABLE[eos]
+    op = oracle.params_at(nx, ny, eos, t["a"], t["b"], Tr, omega=t["omega"], k=t["k"], tau=tau, force=force)
+    g, l, _ = oracle.maxwell(op)
+    rho = inputs.droplet(nx, ny, min(nx, ny) / 4, g, l) if min(nx, ny) > 8 else inputs.slab(nx, ny, g, l)
+    f0 = oracle.init(op, rho)
+    fo = oracle.run(op, f0, 3)
+    fr = Restatement(op, np.float64, np.float64).run(f0, 3)
+    assert np.max(np.abs(fr - fo) / np.abs(fo)) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["droplet", "slab"])
+def test_fp32_storage_meets_the_bar_fp32_arithmetic_does_not(reference, case):
+    op, f0, ro = reference[case]
+    storage_only = pointwise(Restatement(op, np.float64, np.float32).run(f0, 1000).sum(0), ro)
+    plain_fp32 = pointwise(Restatement(op, np.float32, np.float32).run(f0, 1000).sum(0), ro)
+    print(f"{case}: FP32 storage {storage_only:.2e}, FP32 arithmetic {plain_fp32:.2e}")
+    assert storage_only < 1e-5
+    assert plain_fp32 > 2e-5
+    if case == "slab":
+        assert plain_fp32 > 1e-4
+
+
+def test_golden_fp32_limits_are_the_restatement():
+    # the stored figures the GPU tests read are this restatement's (written by
+    # tests/golden/make_fp32_limits.py); recompute the cheaper slab ones
+    rows = {}
+    for line in open(os.path.join(HERE, "golden", "fp32_restatement_errors.txt")):
+        if line.strip() and not line.startswith("#"):
+            case, arith, store, err = line.split()
+            rows[(case, arith, store)] = float(err)
+    op, rho0 = workload("slab")
+    f0 = oracle.init(op, rho0)
+    ro = oracle.run(op, f0, 1000).sum(0)
+    got = pointwise(Restatement(op, np.float32, np.float32).run(f0, 1000).sum(0), ro)
+    assert got == pytest.approx(rows[("slab", "f32", "f32")], rel=1e-6)
+    assert set(rows) == {(c, a, "f32") for c in ("droplet", "slab") for a in ("f32", "f64")}
