@@ -92,7 +92,10 @@ enum { LBM_FLAG_TWO_PASS = 1, LBM_FLAG_WALLS_Y = 2 };
 typedef struct {
     int nx, ny;      /* lattice size, >= 1 each, periodic in both axes (Sec. 5.2)
                         unless flags has LBM_FLAG_WALLS_Y */
-    int prec;        /* lbm_prec: arithmetic and storage precision of f */
+    int prec;        /* lbm_prec: storage precision of f.  LBM_F64 computes
+                        in FP64; LBM_F32 computes in FP32 in the single-pass
+                        kernel and in FP64 in the two-pass kernels (every
+                        lattice the single-pass kernel does not take) */
     int eos;         /* lbm_eos */
     int force;       /* lbm_force */
     int grad;        /* lbm_grad */
@@ -271,7 +274,10 @@ lbm_status lbm_get_timing(lbm_ctx *c, lbm_timing *out);
  * answer LBM_E_TIMEOUT.
  * ------------------------------------------------------------------------- */
 
-/* Validate p[0..n-1] and allocate the batch on the current device. */
+/* Validate p[0..n-1] and allocate the batch on the current device.  Each
+ * instance holds at most 2^30 cells and the instances together, each padded to
+ * a multiple of 512 cells, fewer than 2^31; otherwise LBM_E_INVALID before any
+ * allocation. */
 lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out);
 
 /* f = f^eq(rho, 0) (Eq. 2) for every instance from concatenated host FP64 rho. */
@@ -292,8 +298,19 @@ lbm_status lbm_batch_sync(lbm_batch *b);
 /* Density (Eq. 3) of every instance into concatenated host FP64 rho.  Synchronising. */
 lbm_status lbm_batch_density(lbm_batch *b, double *rho);
 
+/* Density (Eq. 3) and half-step velocity v = (sum_i e_i f_i + F/2) / rho
+ * (Eq. 11, F the step's interaction force) of every instance, in the batch's
+ * precision, into concatenated host FP64 arrays (nx_i*ny_i entries per
+ * instance, instance after instance; vx, vy may be NULL).  The conventions of
+ * lbm_moments, per instance.  LBM_E_STATE before initialisation, LBM_E_NOMEM
+ * if its buffers (three fields of the batch, allocated on the first call)
+ * cannot be had.  Synchronising. */
+lbm_status lbm_batch_moments(lbm_batch *b, double *rho, double *vx, double *vy);
+
 /* Launch shape of the persistent kernel: threads per block (128, 256 or 512)
- * and co-resident blocks per SM (1 .. the occupancy limit). */
+ * and co-resident blocks per SM (1 .. the occupancy limit).  Selects the grid
+ * form (a cluster form set earlier, by lbm_batch_set_cluster or the tuner, is
+ * dropped). */
 lbm_status lbm_batch_set_launch(lbm_batch *b, int block_threads, int blocks_per_sm);
 lbm_status lbm_batch_get_launch(lbm_batch *b, int *block_threads, int *grid_blocks);
 
@@ -341,11 +358,12 @@ void lbm_batch_destroy(lbm_batch *b);
  *          above: the state at t (read only);
  *   f_out  device array of the same size, distinct from f_in: receives the
  *          state at t+1.  Both stay owned by the caller.
- * The potential field and the error word live in one file-scope device array
- * of LBM_STATIC_SCRATCH_BYTES (4 MiB) that every GPU loading the library holds
- * until the process exits, so nx*ny may be at most (4 MiB - 256 B) / 4 =
- * 1,048,512 cells in LBM_F32 and 524,256 in LBM_F64; larger lattices are
- * rejected with LBM_E_INVALID before any device work.  The first call on a
+ * The step is lbm_step's two-pass form (for LBM_F32: FP32 distributions,
+ * FP64 arithmetic).  Its potential field (FP64 in both precisions) and the
+ * error word live in one file-scope device array of LBM_STATIC_SCRATCH_BYTES
+ * (4 MiB) that every GPU loading the library holds until the process exits,
+ * so nx*ny may be at most (4 MiB - 256 B) / 8 = 524,256 cells; larger
+ * lattices are rejected with LBM_E_INVALID before any device work.  The first call on a
  * device looks the array's device address up (with that device current), so
  * make the first call before any stream capture.  Every call, on any stream,
  * shares the one array and leaves its contents behind; the error word is

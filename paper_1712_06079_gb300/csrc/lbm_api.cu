@@ -241,6 +241,20 @@ cudaError_t step_once(lbm_ctx *c, const Model<T> &m) {
     return cudaSuccess;
 }
 
+// One time step of an FP32 lattice in the two-pass form: FP32 distributions,
+// FP64 arithmetic and an FP64 potential field (see lbm_kernels.cu).
+cudaError_t step_once_mixed(lbm_ctx *c, const Model<double> &m) {
+    const float *f = (const float *)c->f[c->cur];
+    float *g = (float *)c->f[1 - c->cur];
+    cudaError_t e = timed_launch(c, 0, [&] { return launch_potential_mixed(m, is_sc(c), f, (double *)c->q, c->err, c->stream); });
+    if (e != cudaSuccess) return e;
+    e = timed_launch(c, 1, [&] { return launch_collide_mixed(m, is_sc(c), is_cdm(c), f, (const double *)c->q, g, c->stream); });
+    if (e != cudaSuccess) return e;
+    if (c->timing) c->tm.steps += 1;
+    c->cur = 1 - c->cur;
+    return cudaSuccess;
+}
+
 int seg_rows_of(const lbm_ctx *c) {
     return c->seg_rows > 0 ? c->seg_rows : fused_auto_seg_rows(c->p.nx, c->p.ny, c->num_sms);
 }
@@ -266,6 +280,8 @@ cudaError_t step_fused(lbm_ctx *c, const Model<float> &m) {
     return cudaSuccess;
 }
 
+// Density and Eq. 11 velocity of the current state; FP32 lattices take the
+// mixed two-pass kernels (FP64 arithmetic), whichever step they run.
 template <typename T>
 cudaError_t moments_into(lbm_ctx *c, T *r, T *vx, T *vy) {
     Model<T> m = model_of<T>(c);
@@ -273,6 +289,14 @@ cudaError_t moments_into(lbm_ctx *c, T *r, T *vx, T *vy) {
     cudaError_t e = launch_potential<T>(m, is_sc(c), f, (T *)c->q, c->err, c->stream);
     if (e != cudaSuccess) return e;
     return launch_moments<T>(m, is_sc(c), is_cdm(c), f, (const T *)c->q, r, vx, vy, c->stream);
+}
+template <>
+cudaError_t moments_into<float>(lbm_ctx *c, float *r, float *vx, float *vy) {
+    Model<double> m = model_of<double>(c);
+    const float *f = (const float *)c->f[c->cur];
+    cudaError_t e = launch_potential_mixed(m, is_sc(c), f, (double *)c->q, c->err, c->stream);
+    if (e != cudaSuccess) return e;
+    return launch_moments_mixed(m, is_sc(c), is_cdm(c), f, (const double *)c->q, r, vx, vy, c->stream);
 }
 
 lbm_status ensure_mom(lbm_ctx *c) {
@@ -590,7 +614,8 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     size_t fbytes = (size_t)kQ * c->n * c->esz;
     if ((e = cudaMalloc(&c->f[0], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f0)");
     if ((e = cudaMalloc(&c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
-    if ((e = cudaMalloc(&c->q, (size_t)c->n * c->esz)) != cudaSuccess) return bail(e, "cudaMalloc(q)");
+    // the potential field of the two-pass kernels is FP64 for both precisions
+    if ((e = cudaMalloc(&c->q, (size_t)c->n * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc(q)");
     c->fused = p->prec == LBM_F32 && !(p->flags & (LBM_FLAG_TWO_PASS | LBM_FLAG_WALLS_Y)) &&
                fused_step_supported(model_of<float>(c), p->grad == LBM_GRAD_CDM, radius);
     if (c->fused) {
@@ -775,8 +800,8 @@ lbm_status lbm_step(lbm_ctx *c, int nsteps) {
         Model<float> m = model_of<float>(c);
         for (int s = 0; s < nsteps; ++s) CK(c, step_fused(c, m), "fused step");
     } else {
-        Model<float> m = model_of<float>(c);
-        for (int s = 0; s < nsteps; ++s) CK(c, step_once<float>(c, m), "step");
+        Model<double> m = model_of<double>(c);
+        for (int s = 0; s < nsteps; ++s) CK(c, step_once_mixed(c, m), "step");
     }
     return LBM_OK;
 }

@@ -40,6 +40,16 @@ template <typename T>
 cudaError_t launch_moments(const Model<T> &m, bool sc, bool cdm, const T *f, const T *q, T *rho, T *vx, T *vy,
                            cudaStream_t s);
 
+// The same three launches for FP32-stored distributions with FP64 arithmetic
+// and an FP64 potential field q (the two-pass form of FP32 lattices); rho, vx,
+// vy are rounded to FP32 on output.
+cudaError_t launch_potential_mixed(const Model<double> &m, bool sc, const float *f, double *q, int *err,
+                                   cudaStream_t s);
+cudaError_t launch_collide_mixed(const Model<double> &m, bool sc, bool cdm, const float *f, const double *q,
+                                 float *fout, cudaStream_t s);
+cudaError_t launch_moments_mixed(const Model<double> &m, bool sc, bool cdm, const float *f, const double *q,
+                                 float *rho, float *vx, float *vy, cudaStream_t s);
+
 // HDM (Eq. 20) or CDM (Eq. 15 times 1/c_s^2) gradient of the periodic field
 // q (nx * ny, row-major) on a grid of spacing h into gx, gy.
 template <typename T>

@@ -17,6 +17,14 @@
 // and a push store of f_i* to x + e_i (with walls, a population that would
 // cross one returns to its cell reversed: half-way bounce-back).
 //
+// FP32 lattices run these kernels in the mixed form: the distributions stay
+// FP32 in memory, every operation is FP64, and the potential field between the
+// passes is FP64.  A plain FP32 evaluation of the step drifts the interfaces of
+// a flat PR slab by ~1e-4 of a cell in 1000 steps through rounding that is
+// identical in neighbouring cells (so it does not average out), while FP32
+// storage alone stays within 1e-5 of the FP64 result; the single-pass FP32
+// kernel keeps FP32 arithmetic.
+//
 // gradient_kernel applies the same staging and operator to a caller's field.
 // The bytes per cell are f read twice (pass 1 and 2), f written once and q
 // written once and read once (halo re-reads hit L2).
@@ -54,14 +62,15 @@ __global__ void init_kernel(Model<T> m, const T *__restrict__ rho, const T *__re
     }
 }
 
-template <typename T>
-__global__ void potential_kernel(Model<T> m, bool sc, const T *__restrict__ f, T *__restrict__ q,
+// TS: storage type of f; T: arithmetic type (and the type of q).
+template <typename TS, typename T>
+__global__ void potential_kernel(Model<T> m, bool sc, const TS *__restrict__ f, T *__restrict__ q,
                                  int *__restrict__ err) {
     const long long n = (long long)m.nx * m.ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         T r = T(0);
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) r += f[i * n + c];
+        for (int i = 0; i < kQ; ++i) r += T(f[i * n + c]);
         if (!(r > T(0)) || !isfinite(r)) atomicOr(err, kErrUnstable);
         q[c] = potential_field(m, r, sc);
     }
@@ -110,10 +119,12 @@ __device__ __forceinline__ void stage_tile(const Model<T> &m, const T *__restric
     }
 }
 
-template <typename T, int TX, int TY, int TYT, bool SC, bool CDM, bool MOMENTS>
-__global__ void __launch_bounds__(TX *TYT) collide_kernel(Model<T> m, const T *__restrict__ f, const T *__restrict__ q,
-                                                          T *__restrict__ fout, T *__restrict__ rho_out,
-                                                          T *__restrict__ vx_out, T *__restrict__ vy_out) {
+// TS: storage type of f and of the outputs; T: arithmetic type (and the type
+// of q and of the staged tile).
+template <typename TS, typename T, int TX, int TY, int TYT, bool SC, bool CDM, bool MOMENTS>
+__global__ void __launch_bounds__(TX *TYT) collide_kernel(Model<T> m, const TS *__restrict__ f, const T *__restrict__ q,
+                                                          TS *__restrict__ fout, TS *__restrict__ rho_out,
+                                                          TS *__restrict__ vx_out, TS *__restrict__ vy_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);
     const int hx = CDM ? 1 : m.kx, hy = CDM ? 1 : m.ky;
@@ -144,7 +155,7 @@ __global__ void __launch_bounds__(TX *TYT) collide_kernel(Model<T> m, const T *_
         const long long c = (long long)y * m.nx + x;
         T fi[kQ];
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) fi[i] = f[i * n + c];
+        for (int i = 0; i < kQ; ++i) fi[i] = T(f[i * n + c]);
         T r = T(0), jx = T(0), jy = T(0);
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
@@ -153,9 +164,9 @@ __global__ void __launch_bounds__(TX *TYT) collide_kernel(Model<T> m, const T *_
             jy += T(ey(i)) * fi[i];
         }
         if (MOMENTS) {  // Eq. 3 and Eq. 11
-            rho_out[c] = r;
-            vx_out[c] = (jx + T(0.5) * Fx) / r;
-            vy_out[c] = (jy + T(0.5) * Fy) / r;
+            rho_out[c] = TS(r);
+            vx_out[c] = TS((jx + T(0.5) * Fx) / r);
+            vy_out[c] = TS((jy + T(0.5) * Fy) / r);
             continue;
         }
         const T inv = T(1) / r;
@@ -177,11 +188,11 @@ __global__ void __launch_bounds__(TX *TYT) collide_kernel(Model<T> m, const T *_
             const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
             const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
             if (m.walls && ((ey(i) == 1 && y == m.ny - 1) || (ey(i) == -1 && y == 0)))
-                fout[opp(i) * n + c] = post;   // half-way bounce-back off the wall
+                fout[opp(i) * n + c] = TS(post);   // half-way bounce-back off the wall
             else
-                fout[i * n + (long long)dys * m.nx + dxs] = post;
+                fout[i * n + (long long)dys * m.nx + dxs] = TS(post);
         }
-        fout[c] = r - moved;
+        fout[c] = TS(r - moved);
     }
 }
 
@@ -223,10 +234,11 @@ size_t smem_for(const Model<T> &m, bool cdm) {
     return sizeof(T) * (size_t)(Tl::TX + 2 * hx) * (Tl::TY + 2 * hy);
 }
 
-template <typename T, bool SC, bool CDM, bool MOM>
-cudaError_t launch_collide_t(const Model<T> &m, const T *f, const T *q, T *fout, T *r, T *vx, T *vy, cudaStream_t s) {
+template <typename TS, typename T, bool SC, bool CDM, bool MOM>
+cudaError_t launch_collide_t(const Model<T> &m, const TS *f, const T *q, TS *fout, TS *r, TS *vx, TS *vy,
+                             cudaStream_t s) {
     using Tl = Tile<T>;
-    auto kern = collide_kernel<T, Tl::TX, Tl::TY, Tl::TYT, SC, CDM, MOM>;
+    auto kern = collide_kernel<TS, T, Tl::TX, Tl::TY, Tl::TYT, SC, CDM, MOM>;
     size_t smem = smem_for(m, CDM);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -236,13 +248,13 @@ cudaError_t launch_collide_t(const Model<T> &m, const T *f, const T *q, T *fout,
     return cudaGetLastError();
 }
 
-template <typename T, bool MOM>
-cudaError_t dispatch_collide(const Model<T> &m, bool sc, bool cdm, const T *f, const T *q, T *fout, T *r, T *vx,
-                             T *vy, cudaStream_t s) {
-    if (sc) return cdm ? launch_collide_t<T, true, true, MOM>(m, f, q, fout, r, vx, vy, s)
-                       : launch_collide_t<T, true, false, MOM>(m, f, q, fout, r, vx, vy, s);
-    return cdm ? launch_collide_t<T, false, true, MOM>(m, f, q, fout, r, vx, vy, s)
-               : launch_collide_t<T, false, false, MOM>(m, f, q, fout, r, vx, vy, s);
+template <typename TS, typename T, bool MOM>
+cudaError_t dispatch_collide(const Model<T> &m, bool sc, bool cdm, const TS *f, const T *q, TS *fout, TS *r, TS *vx,
+                             TS *vy, cudaStream_t s) {
+    if (sc) return cdm ? launch_collide_t<TS, T, true, true, MOM>(m, f, q, fout, r, vx, vy, s)
+                       : launch_collide_t<TS, T, true, false, MOM>(m, f, q, fout, r, vx, vy, s);
+    return cdm ? launch_collide_t<TS, T, false, true, MOM>(m, f, q, fout, r, vx, vy, s)
+               : launch_collide_t<TS, T, false, false, MOM>(m, f, q, fout, r, vx, vy, s);
 }
 
 int flat_blocks(long long n, int threads) {
@@ -309,19 +321,36 @@ cudaError_t launch_init(const Model<T> &m, const T *rho, const T *ux, const T *u
 template <typename T>
 cudaError_t launch_potential(const Model<T> &m, bool sc, const T *f, T *q, int *err, cudaStream_t s) {
     long long n = (long long)m.nx * m.ny;
-    potential_kernel<T><<<flat_blocks(n, 256), 256, 0, s>>>(m, sc, f, q, err);
+    potential_kernel<T, T><<<flat_blocks(n, 256), 256, 0, s>>>(m, sc, f, q, err);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_collide(const Model<T> &m, bool sc, bool cdm, const T *f, const T *q, T *fout, cudaStream_t s) {
-    return dispatch_collide<T, false>(m, sc, cdm, f, q, fout, nullptr, nullptr, nullptr, s);
+    return dispatch_collide<T, T, false>(m, sc, cdm, f, q, fout, nullptr, nullptr, nullptr, s);
 }
 
 template <typename T>
 cudaError_t launch_moments(const Model<T> &m, bool sc, bool cdm, const T *f, const T *q, T *rho, T *vx, T *vy,
                            cudaStream_t s) {
-    return dispatch_collide<T, true>(m, sc, cdm, f, q, nullptr, rho, vx, vy, s);
+    return dispatch_collide<T, T, true>(m, sc, cdm, f, q, nullptr, rho, vx, vy, s);
+}
+
+cudaError_t launch_potential_mixed(const Model<double> &m, bool sc, const float *f, double *q, int *err,
+                                   cudaStream_t s) {
+    long long n = (long long)m.nx * m.ny;
+    potential_kernel<float, double><<<flat_blocks(n, 256), 256, 0, s>>>(m, sc, f, q, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collide_mixed(const Model<double> &m, bool sc, bool cdm, const float *f, const double *q,
+                                 float *fout, cudaStream_t s) {
+    return dispatch_collide<float, double, false>(m, sc, cdm, f, q, fout, nullptr, nullptr, nullptr, s);
+}
+
+cudaError_t launch_moments_mixed(const Model<double> &m, bool sc, bool cdm, const float *f, const double *q,
+                                 float *rho, float *vx, float *vy, cudaStream_t s) {
+    return dispatch_collide<float, double, true>(m, sc, cdm, f, q, nullptr, rho, vx, vy, s);
 }
 
 template <typename T>

@@ -42,7 +42,10 @@ lbm_status scratch_on_current_device(void **out) {
     return LBM_OK;
 }
 
-template <typename T>
+// The step of lbm_step's two-pass form: T is the arithmetic type, TS the
+// storage type of f (FP32 lattices: FP32 distributions, FP64 arithmetic and an
+// FP64 potential field, as lbm_step computes them).
+template <typename TS, typename T>
 lbm_status run_step(const lbm_params &p, const lbm::ModelScalars &ms, const void *f_in, void *f_out, void *scratch) {
     using namespace lbm;
     Model<T> m{};
@@ -70,8 +73,15 @@ lbm_status run_step(const lbm_params &p, const lbm::ModelScalars &ms, const void
     T *q = (T *)((unsigned char *)scratch + kErrBytes);
     const bool sc = p.force == LBM_FORCE_SC, cdm = p.grad == LBM_GRAD_CDM;
     if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return LBM_E_CUDA;
-    if (launch_potential<T>(m, sc, (const T *)f_in, q, err, s) != cudaSuccess) return LBM_E_CUDA;
-    if (launch_collide<T>(m, sc, cdm, (const T *)f_in, q, (T *)f_out, s) != cudaSuccess) return LBM_E_CUDA;
+    cudaError_t e;
+    if constexpr (sizeof(TS) == sizeof(T)) {
+        e = launch_potential<T>(m, sc, (const T *)f_in, q, err, s);
+        if (e == cudaSuccess) e = launch_collide<T>(m, sc, cdm, (const T *)f_in, q, (T *)f_out, s);
+    } else {
+        e = launch_potential_mixed(m, sc, (const float *)f_in, q, err, s);
+        if (e == cudaSuccess) e = launch_collide_mixed(m, sc, cdm, (const float *)f_in, q, (float *)f_out, s);
+    }
+    if (e != cudaSuccess) return LBM_E_CUDA;
     int h = 0;
     if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LBM_E_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return LBM_E_CUDA;
@@ -81,22 +91,20 @@ lbm_status run_step(const lbm_params &p, const lbm::ModelScalars &ms, const void
 }  // namespace
 
 namespace {
-long long max_cells(int prec) {
-    const size_t esz = prec == LBM_F64 ? sizeof(double) : sizeof(float);
-    return (long long)((LBM_STATIC_SCRATCH_BYTES - kErrBytes) / esz);
-}
+// the potential field is FP64 for both precisions
+long long max_cells() { return (long long)((LBM_STATIC_SCRATCH_BYTES - kErrBytes) / sizeof(double)); }
 }  // namespace
 
 extern "C" lbm_status lbm_step_noalloc(const lbm_params *p, const void *f_in, void *f_out) {
     if (!p || !f_in || !f_out || f_in == f_out) return LBM_E_INVALID;
     const char *why = "";
     if (lbm::check_params(*p, &why) != LBM_OK) return LBM_E_INVALID;
-    if ((long long)p->nx * p->ny > max_cells(p->prec)) return LBM_E_INVALID;
+    if ((long long)p->nx * p->ny > max_cells()) return LBM_E_INVALID;
     lbm::ModelScalars ms;
     if (lbm::model_scalars(*p, &ms) != LBM_OK) return LBM_E_INVALID;
     void *scratch = nullptr;
     lbm_status st = scratch_on_current_device(&scratch);
     if (st != LBM_OK) return st;
-    return p->prec == LBM_F64 ? run_step<double>(*p, ms, f_in, f_out, scratch)
-                              : run_step<float>(*p, ms, f_in, f_out, scratch);
+    return p->prec == LBM_F64 ? run_step<double, double>(*p, ms, f_in, f_out, scratch)
+                              : run_step<float, double>(*p, ms, f_in, f_out, scratch);
 }

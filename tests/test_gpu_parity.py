@@ -2,8 +2,11 @@
 identical seeded inputs.
 
 Bars: FP64 path within 1e-12 relative per step (element by element over all
-nine populations); FP32 path within 1e-5 relative on rho after 1000 steps for
-the relaxing droplet and flat-interface workloads; observables in FP64."""
+nine populations); FP32 path within 1e-5 relative on rho, cell by cell, after
+1000 steps of the relaxing droplet and flat-interface workloads; observables in
+FP64."""
+import os
+
 import numpy as np
 import pytest
 
@@ -11,6 +14,7 @@ import oracle
 from paper_1712_06079_gb300 import inputs, lbm
 
 pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 EOS = dict(inputs.EOS_TABLE)
 EOS["rks"] = dict(a=9 / 49, b=2 / 21, omega=0.344, k=0.01)  # Soave-Redlich-Kwong, water
@@ -122,15 +126,26 @@ def bulk_means(rho, case):
     return liq, gas
 
 
-@pytest.mark.parametrize("case", ["droplet", "slab"])
-def test_f32_1000_steps_against_f64_oracle(case):
-    # FP32 production path vs the FP64 oracle after 1000 steps.
-    # Bars: bulk liquid and vapour densities (the coexistence observables)
-    # within 1e-5 relative, total mass within 1e-5; the whole field within
-    # 2e-4 normwise (max|rho32 - rho64| / max|rho64|).  The field error sits
-    # at the interfaces: the lattice pressure rho/3 and the interaction
-    # potential nearly cancel there, so FP32 rounding of rho (relative 6e-8)
-    # moves the interface by ~1e-5 cells.
+def golden_fp32_limits():
+    # pointwise error after 1000 steps of the oracle's step restated with FP32
+    # storage and FP32 or FP64 arithmetic (tests/golden/make_fp32_limits.py)
+    rows = {}
+    for line in open(os.path.join(HERE, "golden", "fp32_restatement_errors.txt")):
+        if line.strip() and not line.startswith("#"):
+            case, arith, store, err = line.split()
+            rows[(case, arith)] = float(err)
+    return rows
+
+
+@pytest.mark.parametrize("case,two_pass", [("droplet", False), ("droplet", True), ("slab", False)])
+def test_f32_1000_steps_against_f64_oracle(case, two_pass):
+    # FP32 production path vs the FP64 oracle after 1000 steps, bar
+    # max_x |rho32 - rho64| / |rho64| < 1e-5.  The droplet runs the single-pass
+    # FP32 kernel (FP32 arithmetic) by default and the two-pass kernels with
+    # LBM_FLAG_TWO_PASS; the slab (ny = 8) always runs the two-pass kernels,
+    # which compute FP32 lattices in FP64 arithmetic: a plain FP32 evaluation
+    # of the step misses the bar on the slab by 30x (tests/test_oracle_fp32.py).
+    # Every reported observable's FP32 error is printed.
     if case == "droplet":   # 128^2 CS Tr=0.8 droplet R=30, SC + HDM
         gp, op = make(128, 128, "cs", 0.8, "sc", "hdm", prec="f32")
         g, l, _ = oracle.maxwell(op)
@@ -139,19 +154,31 @@ def test_f32_1000_steps_against_f64_oracle(case):
         gp, op = make(1024, 8, "pr", 0.7, "zc", "hdm", prec="f32")
         g, l, _ = oracle.maxwell(op)
         rho0 = inputs.slab(1024, 8, g, l)
+    gp.two_pass = two_pass
     with lbm.Lattice(gp) as lat:
         lat.init_density(rho0)
+        lat.set_timing(True)
         lat.step(1000)
-        r, _, _ = lat.moments()
+        kinds = set(lat.timing()["kernels"])
+        r, vx, vy = lat.moments()
         obs = lat.observables()
-    ro, _, _ = oracle.moments(op, oracle.run(op, oracle.init(op, rho0), 1000))
-    normwise = np.max(np.abs(r - ro)) / np.max(np.abs(ro))
+    assert ("fused_step" in kinds) == (case == "droplet" and not two_pass)
+    ro, vxo, vyo = oracle.moments(op, oracle.run(op, oracle.init(op, rho0), 1000))
+    pointwise = float(np.max(np.abs(r - ro) / np.abs(ro)))
+    normwise = float(np.max(np.abs(r - ro)) / np.max(np.abs(ro)))
     liq32, gas32 = bulk_means(r, case)
     liq64, gas64 = bulk_means(ro, case)
-    assert abs(liq32 / liq64 - 1) < 1e-5, (liq32, liq64)
-    assert abs(gas32 / gas64 - 1) < 1e-5, (gas32, gas64)
-    assert abs(obs["mass"] - ro.sum()) / ro.sum() < 1e-5
-    assert normwise < 2e-4, normwise
+    speed32, speed64 = np.hypot(vx, vy).max(), np.hypot(vxo, vyo).max()
+    errs = {"rho pointwise": pointwise, "rho normwise": normwise, "rho_l": liq32 / liq64 - 1,
+            "rho_g": gas32 / gas64 - 1, "ratio": (liq32 / gas32) / (liq64 / gas64) - 1,
+            "mass": obs["mass"] / ro.sum() - 1, "max|v|": speed32 / speed64 - 1}
+    print(f"FP32 vs FP64 oracle, {case}, two_pass={two_pass}: " +
+          ", ".join(f"{k} {v:+.2e}" for k, v in errs.items()))
+    assert pointwise < 1e-5, pointwise
+    assert abs(errs["rho_l"]) < 1e-5 and abs(errs["rho_g"]) < 1e-5 and abs(errs["mass"]) < 1e-6
+    assert abs(errs["max|v|"]) < 1e-3
+    # and well inside what a plain FP32 evaluation of the oracle's step reaches
+    assert pointwise < golden_fp32_limits()[(case, "f32")] / 2
 
 
 def test_f32_one_step_full_size_spinodal():

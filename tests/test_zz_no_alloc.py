@@ -36,7 +36,7 @@ def state(nx, ny, eos, Tr):
 
 
 @pytest.mark.parametrize("prec,nx,ny,eos,tol,walls", [("f64", 96, 80, "cs", 1e-12, False),
-                                                     ("f32", 200, 136, "pr", 1e-5, False),
+                                                     ("f32", 200, 136, "pr", 1e-6, False),
                                                      ("f64", 64, 40, "cs", 1e-12, True)])
 def test_noalloc_matches_context_two_calls(torch_cuda, prec, nx, ny, eos, tol, walls):
     torch = torch_cuda
@@ -65,6 +65,37 @@ def test_noalloc_matches_context_two_calls(torch_cuda, prec, nx, ny, eos, tol, w
     assert np.max(np.abs(out2 - ref2) / np.abs(ref2)) < tol
     # and the first call left its input untouched
     assert np.array_equal(fa.double().cpu().numpy(), f0.astype(np.float32 if prec == "f32" else np.float64))
+
+
+# (4 MiB - 256 B) / 8 B: the FP64 potential field's cells in the 4 MiB array
+MAX_CELLS = 524_256
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_noalloc_size_limit_at_its_boundary(torch_cuda, prec):
+    # exactly MAX_CELLS cells (1016 x 516) run and match the context path; one
+    # cell more (a 524,257 x 1 line) is refused before any device work
+    torch = torch_cuda
+    nx, ny = 1016, 516
+    assert nx * ny == MAX_CELLS
+    f0, t = state(nx, ny, "cs", 0.8)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    params = lbm.Params(nx=nx, ny=ny, eos="cs", a=t["a"], b=t["b"], Tr=0.8, k=t["k"], prec=prec, two_pass=True,
+                        stream=torch.cuda.current_stream().cuda_stream)
+    with lbm.Lattice(params) as lat:
+        lat.set_f(f0)
+        lat.step(1)
+        ref = lat.get_f()
+    fa = torch.tensor(f0, dtype=dt, device="cuda").contiguous()
+    fb = torch.empty_like(fa)
+    torch.cuda.synchronize()
+    assert lbm.step_noalloc(params, fa.data_ptr(), fb.data_ptr()) == lbm.OK
+    assert np.max(np.abs(fb.double().cpu().numpy() - ref) / np.abs(ref)) < (1e-12 if prec == "f64" else 1e-6)
+    over = lbm.Params(nx=MAX_CELLS + 1, ny=1, eos="cs", a=t["a"], b=t["b"], Tr=0.8, k=t["k"], prec=prec)
+    before = fb.clone()
+    assert lbm.step_noalloc(over, fa.data_ptr(), fb.data_ptr()) == lbm.E_INVALID
+    torch.cuda.synchronize()
+    assert torch.equal(fb, before)
 
 
 def test_noalloc_rejects_oversize_and_bad_arguments(torch_cuda):
