@@ -10,7 +10,7 @@ noise.  The distributions (2 x 604 MB) are larger than L2, so every timed
 step streams from HBM without an explicit flush.
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
-(on the host cores, a bounded 1024 x 1024 sample of the same recipe per step).
+(on the host cores, one oracle step of the same 4096 x 4096 lattice per step).
 Under torchrun each rank runs its own replica of the lattice (no exchange:
 the lattices are independent problems), timing is max over ranks.
 """
@@ -40,7 +40,9 @@ FALLBACK_HBM_GBS = 6800.0
 #   collide pass:   read 9 f (36 B) + read q (4 B) + write 9 f (36 B)
 #   fused step:     read 9 f (36 B) + write 9 f (36 B) + read q (4 B) + write q (4 B)
 ALGO_BYTES = {"potential": 40, "collide": 76, "fused_step": 80}
-STEP_MIN_BYTES = 72  # 9 f in + 9 f out: the method's minimum per cell update
+# The method's minimum per cell update, 9 f in + 9 f out (FP32): the algorithmic
+# bytes the roofline fraction is reported against, for any kernel of the step.
+STEP_MIN_BYTES = 72
 
 
 def workload_config():
@@ -76,22 +78,68 @@ def weak_value(world: int, cells: int, steps: int, seconds: float) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+    """SM clock and throttle reasons sampled while a region runs: NVML read
+    directly (libnvidia-ml, read-only queries) every `interval` seconds from a
+    thread, so a region of a few milliseconds still gets samples; nvidia-smi
+    at its shortest loop period where NVML cannot be opened."""
 
+    # clocks-event reason bits of NVML (nvml.h): the ones a measurement is judged by
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.idx = gpu_index
+    def __init__(self, gpu_index: int, pci_bus_id: str = "", interval: float = 0.0005):
+        self.idx, self.bus, self.interval = gpu_index, pci_bus_id, interval
+        self.samples = []           # (sm_mhz, max_mhz, reason bits)
         self.proc = None
         self.lines = []
+        self.source = None
+        self._stop = threading.Event()
+        self._nvml = self._open_nvml()
+
+    def _open_nvml(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            ok = False
+            if self.bus:
+                ok = lib.nvmlDeviceGetHandleByPciBusId_v2(self.bus.encode(), ctypes.byref(h)) == 0
+            if not ok:
+                ok = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.idx), ctypes.byref(h)) == 0
+            if not ok:
+                return None
+            reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            return lib, h, reasons
+        except (OSError, AttributeError):
+            return None
+
+    def _sample_nvml(self):
+        import ctypes
+        lib, h, reasons = self._nvml
+        sm, mx, bits = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    reasons(h, ctypes.byref(bits)) == 0):
+                self.samples.append((float(sm.value), float(mx.value), int(bits.value)))
+            time.sleep(self.interval)
 
     def __enter__(self):
+        if self._nvml is not None:
+            self.source = "nvml"
+            self._t = threading.Thread(target=self._sample_nvml, daemon=True)
+            self._t.start()
+            return self
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi"
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
         except (OSError, FileNotFoundError):
@@ -103,15 +151,22 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *exc):
+        self._stop.set()
         if self.proc is not None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        elif self.source == "nvml":
+            self._t.join(timeout=5)
 
     def summary(self):
         sm, smax, reasons = [], [], set()
+        for clk, mx, bits in self.samples:
+            sm.append(clk)
+            smax.append(mx)
+            reasons.update(n for b, n in self.REASONS.items() if bits & b)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -126,9 +181,9 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "source": self.source}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "sm_mhz_min": min(sm), "source": self.source}
 
 
 def measured_peak():
@@ -202,17 +257,23 @@ def ncu_traffic(kernel: str):
 _ORACLE_ALL_THREADS = []   # the oracle's OpenMP thread count before any sample changed it
 
 
+_ORACLE_STATE = {}         # (n, op, f) of the last sampled lattice
+
+
 def oracle_sample(n: int, steps: int, threads: int = 0):
     """Time the oracle on an n x n lattice of the same recipe with `threads`
-    OpenMP threads (0: all host threads); returns (MLUPS, threads, seconds)."""
+    OpenMP threads (0: all host threads); returns (MLUPS, threads, seconds).
+    The initial state is built once per size and reused."""
     import oracle
     from paper_1712_06079_gb300 import inputs
     if not _ORACLE_ALL_THREADS:
         _ORACLE_ALL_THREADS.append(oracle.max_threads())
     oracle.set_threads(threads or _ORACLE_ALL_THREADS[0])
     used = oracle.max_threads()
-    op = oracle.params_at(n, n, EOS, 1.0, 4.0, TR, k=K_HU, tau=TAU, force="sc", grad="hdm")
-    f = oracle.init(op, inputs.spinodal(n, n, inputs.CS_TR07_MEAN))
+    if _ORACLE_STATE.get("n") != n:
+        op = oracle.params_at(n, n, EOS, 1.0, 4.0, TR, k=K_HU, tau=TAU, force="sc", grad="hdm")
+        _ORACLE_STATE.update(n=n, op=op, f=oracle.init(op, inputs.spinodal(n, n, inputs.CS_TR07_MEAN)))
+    op, f = _ORACLE_STATE["op"], _ORACLE_STATE["f"]
     t0 = time.perf_counter()
     oracle.run(op, f, steps)
     dt = time.perf_counter() - t0
@@ -223,7 +284,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    n = 1024
+    n = NX
     for _ in range(args.warmup):
         oracle_sample(n, 1)
     mlups, cores, dt = oracle_sample(n, args.steps)
@@ -233,7 +294,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(),
         "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"each step = one oracle step of a {n}x{n} lattice of the same recipe"},
+                         "sample": f"each step = one oracle step of the {n}x{n} workload"},
         "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -261,11 +322,18 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
+    props = torch.cuda.get_device_properties(local)
+    bus = ""
+    if hasattr(props, "pci_bus_id"):
+        bus = f"{getattr(props, 'pci_domain_id', 0):08x}:{props.pci_bus_id:02x}:{getattr(props, 'pci_device_id', 0):02x}.0"
     lat = lbm.Lattice(params)
     lat.init_density(rho0)
     if args.segment_rows:
         lat.set_segment_rows(args.segment_rows)
     tuned = not args.no_tune and not args.segment_rows
+    # clocks over the whole GPU window (tuner, warm-up, timed steps) and, finer,
+    # over the timed steps alone
+    window = ClockSampler(local, bus, interval=0.002).__enter__()
     seg_rows = lat.tune_segment_rows(3) if tuned else lat.segment_rows()
     lat.step(args.warmup)
     lat.sync()
@@ -274,12 +342,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     lat.set_timing(True)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clocks:
+    with ClockSampler(local, bus) as clocks:
         t0.record(stream)
         for _ in range(args.steps):
             lat.step(1)
         t1.record(stream)
         t1.synchronize()
+    window.__exit__(None, None, None)
     torch.cuda.synchronize()
     barrier()
     ms = t0.elapsed_time(t1)
@@ -308,39 +377,45 @@ def run_ours(args):
     kern = timing["kernels"]
     dominant = max(kern, key=lambda k: kern[k]["ms"])
     avg_ms = kern[dominant]["ms"] / kern[dominant]["count"]
-    achieved = ALGO_BYTES[dominant] * cells / (avg_ms * 1e-3) / 1e9
+    # algorithmic bytes: the method's 72 B per cell update (9 f in, 9 f out);
+    # the kernel's own 80 B (the stored potential field read and written once
+    # more) and ncu's DRAM bytes are reported beside it
+    achieved = STEP_MIN_BYTES * cells / (avg_ms * 1e-3) / 1e9
+    design = ALGO_BYTES[dominant] * cells / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
+    traffic = ncu_traffic(dominant)
     clk = clocks.summary()
+    clk["window"] = window.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(),
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "algo_bytes_per_cell": ALGO_BYTES[dominant],
-                     "traffic": ncu_traffic(dominant),
-                     "step_frac_of_min_bytes": STEP_MIN_BYTES * value * 1e6 / world / (peak * 1e9)},
+                     "algo_bytes_per_cell": STEP_MIN_BYTES, "traffic": traffic,
+                     "design_bytes_per_cell": ALGO_BYTES[dominant], "design_achieved": design,
+                     "design_frac": design / peak,
+                     "dram_frac": None if traffic is None else traffic / (avg_ms * 1e-3) / 1e9 / peak},
         "kernels_ms_per_launch": {k: v["ms"] / v["count"] for k, v in kern.items()},
         "gpu_launches": timing["launches"],
         "launch": {"segment_rows": seg_rows, "tuned": tuned},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": cells * 4 / args.steps,
-                "d2h_bytes_per_step": (3 * cells * 4 + 4) / args.steps,
-                "note": "init_density from host FP64 rho (converted to FP32 in pinned staging), "
-                        "K steps, moments (rho, vx, vy) back to host FP64"},
+                "d2h_bytes_per_step": (3 * cells * 4 + 4) / args.steps, "steps": args.steps,
+                "note": f"init_density from host FP64 rho (converted to FP32 in pinned staging), {args.steps} "
+                        "steps, moments (rho, vx, vy) back to host FP64"},
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        # bounded oracle samples: the same recipe on 1024 x 1024, all host threads for ~10 s,
-        # then one thread for two steps
-        m1, cores, dt = oracle_sample(1024, 2)
-        steps = max(2, min(200, int(10.0 / max(dt / 2, 1e-3))))
-        mlups, cores, dt = oracle_sample(1024, steps)
-        m_one, _, dt_one = oracle_sample(1024, 2, threads=1)
+        # bounded oracle samples of the same workload (NX x NY): all host threads
+        # for ~10-20 s (at most 20 steps), then one thread for one step
+        m1, cores, dt = oracle_sample(NX, 1)
+        steps = max(1, min(20, int(15.0 / max(dt, 1e-3))))
+        mlups, cores, dt = oracle_sample(NX, steps)
+        m_one, _, dt_one = oracle_sample(NX, 1, threads=1)
         line["cpu_baseline"] = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{steps} oracle steps of a 1024x1024 lattice of the same recipe "
-                                          f"({dt:.1f} s)",
+                                "sample": f"{steps} oracle steps of the {NX}x{NY} workload ({dt:.1f} s)",
                                 "single_thread": {"value": m_one, "cores": 1,
-                                                  "sample": f"2 steps of the same lattice ({dt_one:.1f} s)"}}
+                                                  "sample": f"1 step of the same lattice ({dt_one:.1f} s)"}}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

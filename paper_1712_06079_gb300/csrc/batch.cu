@@ -136,6 +136,53 @@ __device__ __forceinline__ void collide_cell(const Model<T> &m, const T (&fi)[kQ
     post[0] = r - moved;
 }
 
+// Interaction force at cell `cell` = (x, y) of instance I from the potential
+// field q (concatenated layout): the HDM gradient (explicit periodic form of
+// Eq. 20, folded weights for short lines) or the CDM of Eq. 15, then Eq. 22
+// (Shan-Chen, q = s Phi) or Eq. 7 (Zhang-Chen).
+template <typename T>
+__device__ __forceinline__ void inst_force(const Inst<T> &I, const T *__restrict__ q, long long cell, int x, int y,
+                                           T &Fx, T &Fy) {
+    const Model<T> &m = I.m;
+    const bool sc = I.sc != 0;
+    const T *qi = q + I.off;
+    const T *qrow = qi + (long long)y * m.nx;
+    T dx = T(0), dy = T(0);
+    if (I.cdm) {
+        // Eq. 15 times 1/c_s^2 on the instance's periodic lattice
+        const int xp = x + 1 == m.nx ? 0 : x + 1, xm = x == 0 ? m.nx - 1 : x - 1;
+        const int yp = y + 1 == m.ny ? 0 : y + 1, ym = y == 0 ? m.ny - 1 : y - 1;
+        auto at = [&](int yy, int xx) { return qabs(__ldg(qi + (long long)yy * m.nx + xx), sc); };
+        const T e = at(y, xp), w = at(y, xm), nn = at(yp, x), s = at(ym, x);
+        const T ne = at(yp, xp), nw = at(yp, xm), se = at(ym, xp), sw = at(ym, xm);
+        dx = T(1.0 / 3.0) * (e - w) + T(1.0 / 12.0) * ((ne + se) - (nw + sw));
+        dy = T(1.0 / 3.0) * (nn - s) + T(1.0 / 12.0) * ((ne + nw) - (se + sw));
+    } else {
+        // explicit periodic form of Eq. 20 (folded weights for short lines)
+        for (int j = 1; j <= m.kx; ++j) {
+            int xp = x + j, xm = x - j;
+            if (xp >= m.nx) xp -= m.nx;
+            if (xm < 0) xm += m.nx;
+            dx += m.wx[j] * (qabs(__ldg(qrow + xp), sc) - qabs(__ldg(qrow + xm), sc));
+        }
+        for (int j = 1; j <= m.ky; ++j) {
+            int yp = y + j, ym = y - j;
+            if (yp >= m.ny) yp -= m.ny;
+            if (ym < 0) ym += m.ny;
+            dy += m.wy[j] * (qabs(__ldg(qi + (long long)yp * m.nx + x), sc) -
+                             qabs(__ldg(qi + (long long)ym * m.nx + x), sc));
+        }
+    }
+    const T qc = q[cell];
+    if (sc) {  // Eq. 22: F = -2 s Phi grad Phi, q = s Phi
+        Fx = T(-2) * qc * dx;
+        Fy = T(-2) * qc * dy;
+    } else {   // Eq. 7
+        Fx = -dx;
+        Fy = -dy;
+    }
+}
+
 template <typename T>
 __global__ void batch_kernel(const BatchArgs<T> a) {
     const unsigned int nblocks = gridDim.x;
@@ -170,45 +217,9 @@ __global__ void batch_kernel(const BatchArgs<T> a) {
             const Model<T> &m = I.m;
             const int local = (int)(cell - I.off);
             if (local >= m.nx * m.ny) continue;
-            const bool sc = I.sc != 0;
             const int y = local / m.nx, x = local - y * m.nx;
-            const T *qi = a.q + I.off;
-            const T *qrow = qi + (long long)y * m.nx;
-            T dx = T(0), dy = T(0);
-            if (I.cdm) {
-                // Eq. 15 times 1/c_s^2 on the instance's periodic lattice
-                const int xp = x + 1 == m.nx ? 0 : x + 1, xm = x == 0 ? m.nx - 1 : x - 1;
-                const int yp = y + 1 == m.ny ? 0 : y + 1, ym = y == 0 ? m.ny - 1 : y - 1;
-                auto at = [&](int yy, int xx) { return qabs(__ldg(qi + (long long)yy * m.nx + xx), sc); };
-                const T e = at(y, xp), w = at(y, xm), nn = at(yp, x), s = at(ym, x);
-                const T ne = at(yp, xp), nw = at(yp, xm), se = at(ym, xp), sw = at(ym, xm);
-                dx = T(1.0 / 3.0) * (e - w) + T(1.0 / 12.0) * ((ne + se) - (nw + sw));
-                dy = T(1.0 / 3.0) * (nn - s) + T(1.0 / 12.0) * ((ne + nw) - (se + sw));
-            } else {
-                // explicit periodic form of Eq. 20 (folded weights for short lines)
-                for (int j = 1; j <= m.kx; ++j) {
-                    int xp = x + j, xm = x - j;
-                    if (xp >= m.nx) xp -= m.nx;
-                    if (xm < 0) xm += m.nx;
-                    dx += m.wx[j] * (qabs(__ldg(qrow + xp), sc) - qabs(__ldg(qrow + xm), sc));
-                }
-                for (int j = 1; j <= m.ky; ++j) {
-                    int yp = y + j, ym = y - j;
-                    if (yp >= m.ny) yp -= m.ny;
-                    if (ym < 0) ym += m.ny;
-                    dy += m.wy[j] * (qabs(__ldg(qi + (long long)yp * m.nx + x), sc) -
-                                     qabs(__ldg(qi + (long long)ym * m.nx + x), sc));
-                }
-            }
-            const T qc = a.q[cell];
             T Fx, Fy;
-            if (sc) {  // Eq. 22: F = -2 s Phi grad Phi, q = s Phi
-                Fx = T(-2) * qc * dx;
-                Fy = T(-2) * qc * dy;
-            } else {   // Eq. 7
-                Fx = -dx;
-                Fy = -dy;
-            }
+            inst_force(I, a.q, cell, x, y, Fx, Fy);
             T fi[kQ], post[kQ];
 #pragma unroll
             for (int i = 0; i < kQ; ++i) fi[i] = f[i * a.ntot + cell];
@@ -388,6 +399,54 @@ __global__ void batch_density_kernel(const Inst<T> *inst, const int *table, cons
     }
 }
 
+// Density (Eq. 3) and the potential field (Eq. 8 / 21) of every cell: phase A
+// of the step as a launch of its own (for lbm_batch_moments).
+template <typename T>
+__global__ void batch_potential_kernel(const Inst<T> *inst, const int *table, const T *f, T *q, long long ntot,
+                                       int *err) {
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < ntot;
+         cell += (long long)gridDim.x * blockDim.x) {
+        const int ii = table[cell / kTableGrain];
+        if (ii < 0) continue;
+        const Inst<T> &I = inst[ii];
+        if (cell - I.off >= (long long)I.m.nx * I.m.ny) continue;
+        T r = T(0);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) r += f[i * ntot + cell];
+        if (!(r > T(0)) || !isfinite(r)) atomicOr(err, kErrUnstable);
+        q[cell] = potential_field(I.m, r, I.sc != 0);
+    }
+}
+
+// rho (Eq. 3) and the half-step velocity v = (sum_i e_i f_i + F/2) / rho of
+// Eq. 11, with F the step's interaction force from the potential field q.
+template <typename T>
+__global__ void batch_moments_kernel(const Inst<T> *inst, const int *table, const T *f, const T *q, T *rho, T *vx,
+                                     T *vy, long long ntot) {
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < ntot;
+         cell += (long long)gridDim.x * blockDim.x) {
+        const int ii = table[cell / kTableGrain];
+        if (ii < 0) continue;
+        const Inst<T> &I = inst[ii];
+        const int local = (int)(cell - I.off);
+        if (local >= I.m.nx * I.m.ny) continue;
+        const int y = local / I.m.nx, x = local - y * I.m.nx;
+        T Fx, Fy;
+        inst_force(I, q, cell, x, y, Fx, Fy);
+        T r = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const T v = f[i * ntot + cell];
+            r += v;
+            jx += T(ex(i)) * v;
+            jy += T(ey(i)) * v;
+        }
+        rho[cell] = r;
+        vx[cell] = (jx + T(0.5) * Fx) / r;
+        vy[cell] = (jy + T(0.5) * Fy) / r;
+    }
+}
+
 }  // namespace
 }  // namespace lbm
 
@@ -407,6 +466,8 @@ struct lbm_batch {
     void *q = nullptr;
     void *stage_dev = nullptr;   // rho staging (ntot values of the precision)
     void *stage_host = nullptr;  // pinned host staging
+    void *mom_dev = nullptr;     // rho, vx, vy of lbm_batch_moments (3 ntot values, allocated on first use)
+    void *mom_host = nullptr;    // their pinned host copy
     int *err = nullptr;
     BarrierState *bar = nullptr;
     int cur = 0;
@@ -671,13 +732,18 @@ lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out) {
     if (!p || n < 1) return LBM_E_INVALID;
     const int prec = p[0].prec;
     if (prec != LBM_F32 && prec != LBM_F64) return LBM_E_INVALID;
+    long long padded = 0;
     for (int i = 0; i < n; ++i) {
         const lbm_params &q = p[i];
         const char *why = "";
         if (q.prec != prec || check_params(q, &why) != LBM_OK || (long long)q.nx * q.ny > (1LL << 30) ||
             (q.flags & LBM_FLAG_WALLS_Y))   // the batch steps periodic lattices only
             return LBM_E_INVALID;
+        padded += ((long long)q.nx * q.ny + kAlign - 1) / kAlign * kAlign;
     }
+    // instance offsets are int cell indices on the device: the padded total
+    // must stay below 2^31 cells
+    if (padded >= (1LL << 31)) return LBM_E_INVALID;
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_E_NOMEM;
     b->n = n;
@@ -696,6 +762,7 @@ lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out) {
         lbm_batch_destroy(b);
         return st;
     };
+
     std::vector<int> table(b->ntot / kTableGrain, -1);
     for (int i = 0; i < n; ++i) {
         long long cells = (long long)p[i].nx * p[i].ny;
@@ -752,6 +819,7 @@ lbm_status lbm_batch_set_launch(lbm_batch *b, int block_threads, int blocks_per_
         return bfail(b, LBM_E_INVALID, "blocks_per_sm must be in [1, " + std::to_string(maxb) + "]");
     b->block_threads = block_threads;
     b->grid_blocks = blocks_per_sm * sm_count();
+    b->cluster = 0;   // an explicit grid shape selects the grid form
     return LBM_OK;
 }
 
@@ -858,6 +926,53 @@ lbm_status lbm_batch_density(lbm_batch *b, double *rho) {
             rho[dst + c] = b->esz == sizeof(double) ? ((double *)b->stage_host)[b->off[i] + c]
                                                     : (double)((float *)b->stage_host)[b->off[i] + c];
         dst += cells;
+    }
+    return st;
+}
+
+lbm_status lbm_batch_moments(lbm_batch *b, double *rho, double *vx, double *vy) {
+    if (!b || !rho) return LBM_E_INVALID;
+    if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
+    const size_t fb = b->ntot * b->esz;
+    if (!b->mom_dev && cudaMalloc(&b->mom_dev, 3 * fb) != cudaSuccess)
+        return bfail(b, LBM_E_NOMEM, "moment buffers");
+    if (!b->mom_host && cudaHostAlloc(&b->mom_host, 3 * fb, cudaHostAllocDefault) != cudaSuccess)
+        return bfail(b, LBM_E_NOMEM, "pinned moment staging");
+    const int blocks = (int)std::min<long long>((b->ntot + 255) / 256, 152 * 16);
+    unsigned char *md = (unsigned char *)b->mom_dev;
+    if (b->prec == LBM_F64) {
+        const Inst<double> *inst = (const Inst<double> *)b->inst_dev;
+        const double *f = (const double *)b->f[b->cur];
+        batch_potential_kernel<double><<<blocks, 256, 0, b->stream>>>(inst, b->table_dev, f, (double *)b->q, b->ntot,
+                                                                     b->err);
+        batch_moments_kernel<double><<<blocks, 256, 0, b->stream>>>(inst, b->table_dev, f, (const double *)b->q,
+                                                                    (double *)md, (double *)(md + fb),
+                                                                    (double *)(md + 2 * fb), b->ntot);
+    } else {
+        const Inst<float> *inst = (const Inst<float> *)b->inst_dev;
+        const float *f = (const float *)b->f[b->cur];
+        batch_potential_kernel<float><<<blocks, 256, 0, b->stream>>>(inst, b->table_dev, f, (float *)b->q, b->ntot,
+                                                                    b->err);
+        batch_moments_kernel<float><<<blocks, 256, 0, b->stream>>>(inst, b->table_dev, f, (const float *)b->q,
+                                                                   (float *)md, (float *)(md + fb),
+                                                                   (float *)(md + 2 * fb), b->ntot);
+    }
+    BCK(b, cudaGetLastError(), "moments kernels");
+    BCK(b, cudaMemcpyAsync(b->mom_host, b->mom_dev, 3 * fb, cudaMemcpyDeviceToHost, b->stream), "copy moments");
+    lbm_status st = batch_sync(b);
+    if (st != LBM_OK && st != LBM_E_UNSTABLE) return st;
+    double *out[3] = {rho, vx, vy};
+    for (int k = 0; k < 3; ++k) {
+        if (!out[k]) continue;
+        const unsigned char *h = (const unsigned char *)b->mom_host + k * fb;
+        long long dst = 0;
+        for (int i = 0; i < b->n; ++i) {
+            const long long cells = (long long)b->params[i].nx * b->params[i].ny;
+            for (long long c = 0; c < cells; ++c)
+                out[k][dst + c] = b->esz == sizeof(double) ? ((const double *)h)[b->off[i] + c]
+                                                           : (double)((const float *)h)[b->off[i] + c];
+            dst += cells;
+        }
     }
     return st;
 }
@@ -1009,6 +1124,8 @@ void lbm_batch_destroy(lbm_batch *b) {
     cudaFree(b->f[1]);
     cudaFree(b->q);
     cudaFree(b->stage_dev);
+    cudaFree(b->mom_dev);
+    if (b->mom_host) cudaFreeHost(b->mom_host);
     cudaFree(b->err);
     cudaFree(b->bar);
     if (b->stage_host) cudaFreeHost(b->stage_host);

@@ -88,6 +88,7 @@ SIGNATURES = {
     "lbm_batch_step": (ctypes.c_int, [_V, ctypes.c_int]),
     "lbm_batch_sync": (ctypes.c_int, [_V]),
     "lbm_batch_density": (ctypes.c_int, [_V, _D]),
+    "lbm_batch_moments": (ctypes.c_int, [_V, _D, _D, _D]),
     "lbm_batch_set_launch": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
     "lbm_batch_get_launch": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_set_cluster": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
@@ -364,6 +365,12 @@ class Batch:
         flat = np.empty(sum(self.cells))
         self._check(self._lib.lbm_batch_density(self._h, _dp(flat)))
         return self._split(flat, 1)
+
+    def moments(self) -> tuple:
+        """(rho, vx, vy) per instance: density and the Eq. 11 velocity."""
+        out = [np.empty(sum(self.cells)) for _ in range(3)]
+        self._check(self._lib.lbm_batch_moments(self._h, *(_dp(a) for a in out)))
+        return tuple(self._split(a, 1) for a in out)
 
     def set_launch(self, block_threads: int, blocks_per_sm: int):
         self._check(self._lib.lbm_batch_set_launch(self._h, block_threads, blocks_per_sm))

@@ -92,6 +92,22 @@ def test_create_rejects_bad_params_before_device_work(lib, bad):
     assert lib.lbm_last_error(None)
 
 
+def test_batch_create_rejects_oversize_totals_before_device_work(lib):
+    # device offsets are int cell indices: instances of 2^30 cells each (the
+    # per-instance maximum) pass alone, but two of them pad to 2^31 cells and
+    # the batch is refused before any allocation
+    import ctypes
+    one = lbm.Params(nx=32768, ny=32768, eos="cs", Tr=0.8, k=0.04)
+    arr = (lbm._Params * 2)(one.c(), one.c())
+    h = ctypes.c_void_p()
+    assert lib.lbm_batch_create(arr, 2, ctypes.byref(h)) == lbm.E_INVALID
+    assert h.value is None
+    big = lbm.Params(nx=32769, ny=32768, eos="cs", Tr=0.8, k=0.04)   # one instance over 2^30
+    arr1 = (lbm._Params * 1)(big.c())
+    assert lib.lbm_batch_create(arr1, 1, ctypes.byref(h)) == lbm.E_INVALID
+    assert lib.lbm_batch_create(arr1, 0, ctypes.byref(h)) == lbm.E_INVALID
+
+
 def test_null_handles_are_safe(lib):
     import ctypes
     lib.lbm_destroy(None)

@@ -65,6 +65,36 @@ def test_batch_f64_matches_oracle_per_instance():
         assert np.max(np.abs(g3 - o3) / np.abs(o3)) < 1e-11, (gp.eos, gp.nx)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batch_moments_match_oracle_per_instance(prec):
+    # lbm_batch_moments: rho (Eq. 3) and the half-step velocity of Eq. 11 of
+    # every instance against the oracle's moments of the same state (its own
+    # FP64 run of the same steps); FP64 at 1e-12, FP32 at its rounding level
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec=prec) for m in MIX]
+    f0 = [slab_state(op, k + 21) for k, (_, op) in enumerate(pairs)]
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        b.set_f(f0)
+        b.step(3)
+        rho, vx, vy = b.moments()
+        dens = b.density()
+    # FP32: a few ulp per step, more for PR where U = k p - rho/3 nearly cancels at liquid density
+    tol_r, tol_v = (1e-12, 1e-11) if prec == "f64" else (1e-5, 1e-3)
+    for (gp, op), a, r, u, v, d in zip(pairs, f0, rho, vx, vy, dens):
+        ro, vxo, vyo = oracle.moments(op, oracle.run(op, a, 3))
+        assert r.shape == ro.shape == (gp.ny, gp.nx)
+        assert np.array_equal(r, d)            # the density entry point's rho
+        assert np.max(np.abs(r - ro) / ro) < tol_r, (gp.eos, gp.nx)
+        scale = max(np.abs(vxo).max(), np.abs(vyo).max())
+        assert np.max(np.abs(u - vxo)) < tol_v * scale and np.max(np.abs(v - vyo)) < tol_v * scale, (gp.eos, gp.nx)
+    # vx / vy may be left out
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        b.set_f(f0)
+        flat = np.empty(sum(gp.nx * gp.ny for gp, _ in pairs))
+        assert b._lib.lbm_batch_moments(b._h, lbm._dp(flat), None, None) == lbm.OK
+        assert np.array_equal(flat[: pairs[0][0].nx * pairs[0][0].ny].reshape(pairs[0][0].ny, pairs[0][0].nx),
+                              b.density()[0])
+
+
 def test_batch_f32_matches_single_lattice_contexts():
     pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f32") for m in MIX]
     f0 = [slab_state(op, k + 11) for k, (_, op) in enumerate(pairs)]
@@ -78,7 +108,10 @@ def test_batch_f32_matches_single_lattice_contexts():
             lat.set_f(a)
             lat.step(100)
             ref = lat.get_f()
-        assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-5, (gp.eos, gp.nx)
+        # the batch computes in FP32, the contexts' two-pass kernels in FP64 on
+        # FP32-stored distributions: 100 steps apart by FP32 rounding (largest
+        # for PR, where U = k p - rho/3 nearly cancels at liquid density)
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < 3e-5, (gp.eos, gp.nx)
 
 
 CLUSTER_MIX = MIX[:4]   # split over 2 (FP32), 4 and 8 (FP32) CTAs per instance
