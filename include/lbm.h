@@ -320,11 +320,12 @@ lbm_status lbm_batch_get_launch(lbm_batch *b, int *block_threads, int *grid_bloc
  * memory for the whole launch and the stencil halos and boundary populations
  * exchanged through distributed shared memory; hardware cluster barriers
  * replace the grid barriers.  The per-cell arithmetic is the grid form's, so
- * both forms give the same results.  Every instance must split: nx a multiple
- * of `cluster`, a slice of nx / cluster columns at least as wide as its x halo
- * (the HDM radius, 1 for CDM), and both distribution buffers plus the haloed
- * field of the largest slice within a block's shared memory; otherwise
- * LBM_E_INVALID and the batch keeps its form.  cluster = 0 returns to the grid
+ * both forms give the same results.  CTA k of an instance's cluster owns the
+ * columns [k nx / cluster, (k + 1) nx / cluster).  Every instance must split:
+ * its narrowest slice at least as wide as its x halo (the HDM radius, 1 for
+ * CDM), and both distribution buffers plus the haloed field of the widest
+ * slice within a block's shared memory; otherwise LBM_E_INVALID and the batch
+ * keeps its form.  cluster = 0 returns to the grid
  * form.  lbm_batch_get_launch then reports block_threads and cluster * n. */
 lbm_status lbm_batch_set_cluster(lbm_batch *b, int cluster, int block_threads);
 lbm_status lbm_batch_get_cluster(lbm_batch *b, int *cluster);
@@ -373,6 +374,16 @@ void lbm_batch_destroy(lbm_batch *b);
  * CUDA error, LBM_E_INVALID on bad arguments.  Calls no cudaMalloc, cudaFree
  * or other allocating routine. */
 lbm_status lbm_step_noalloc(const lbm_params *p, const void *f_in, void *f_out);
+
+/* Test hook (not a passage of the paper): the number of device and of pinned
+ * host allocations the library holds right now, over all contexts and
+ * batches.  With the environment variable LBM_DEBUG_FAIL_ALLOC=n set, once n
+ * allocations have succeeded since it took its current value, every further
+ * allocation of the library fails as if the memory were exhausted (n = 0: all
+ * of them); the failing call answers LBM_E_NOMEM and frees what it took, so a
+ * test can walk every allocation of an entry point and check for leaks.  The
+ * failure is made on the host; no GPU call fails. */
+lbm_status lbm_debug_alloc_stats(long long *live_device, long long *live_host);
 
 /* Free everything the context owns.  NULL is a no-op. */
 void lbm_destroy(lbm_ctx *c);

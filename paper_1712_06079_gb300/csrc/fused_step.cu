@@ -178,6 +178,22 @@ __device__ __forceinline__ float feq_moving(int i, float rho, float ux, float uy
     return w * (a + eu * (3.0f + 4.5f * eu));
 }
 
+// Packed FP32 pairs (two cells per instruction; Blackwell's paired FP32
+// add/multiply/fma, each component rounded as the scalar operation).
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, splat2(-1.0f), a); }   // a - b
+
+// The bracket of f^eq_i (Eq. 2) for e_i . u = e v with e = +1 or -1 and
+// a = 1 - 1.5 |u|^2:  a + (e v)(3 + 4.5 (e v)), formed as a + v (e 3 + 4.5 v),
+// the same two roundings as with e v itself.
+template <int E>
+__device__ __forceinline__ float2 feq_bracket2(float2 v, float2 a) {
+    return fma2(v, fma2(splat2(4.5f), v, splat2(3.0f * E)), a);
+}
+
 template <bool SC, bool TAU1, int EOS>
 __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_constant__ FusedArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -351,16 +367,19 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         // columns and store nothing.
         {
             float dx[4], dy[4], qc[4];
-            // moments of f(t) (Eq. 3)
-            float r[4] = {0.f, 0.f, 0.f, 0.f}, jx[4] = {0.f, 0.f, 0.f, 0.f}, jy[4] = {0.f, 0.f, 0.f, 0.f};
+            // moments of f(t) (Eq. 3), cells (0, 1) and (2, 3) as packed pairs
+            float2 r2[2] = {splat2(0.f), splat2(0.f)}, jx2[2] = {splat2(0.f), splat2(0.f)},
+                   jy2[2] = {splat2(0.f), splat2(0.f)};
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const float v[4] = {fv[i].x, fv[i].y, fv[i].z, fv[i].w};
+                const float2 v[2] = {make_float2(fv[i].x, fv[i].y), make_float2(fv[i].z, fv[i].w)};
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    r[c] += v[c];
-                    if (ex(i)) jx[c] = fmaf(float(ex(i)), v[c], jx[c]);
-                    if (ey(i)) jy[c] = fmaf(float(ey(i)), v[c], jy[c]);
+                for (int h = 0; h < 2; ++h) {
+                    r2[h] = add2(r2[h], v[h]);
+                    if (ex(i) == 1) jx2[h] = add2(jx2[h], v[h]);
+                    if (ex(i) == -1) jx2[h] = sub2(jx2[h], v[h]);
+                    if (ey(i) == 1) jy2[h] = add2(jy2[h], v[h]);
+                    if (ey(i) == -1) jy2[h] = sub2(jy2[h], v[h]);
                 }
             }
             // for tau = 1 nothing after the moments reads f(t), so f(t) of the next
@@ -395,27 +414,31 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 dy[3] = fmaf(A.w1y, mag(qa.w) - mag(qb.w), A.w2y * (Q.w - P.w));
             }
             // force and the two velocities of the forcing (Eq. 10, 22 / 7)
-            float ux[4], uy[4], vx[4], vy[4], au[4], av[4], moved[4];
+            float2 ux[2], uy[2], vx[2], vy[2], au[2], av[2], moved[2];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                unstable |= active && !(r[c] > 0.f && r[c] < INFINITY);   // NaN fails both
-                float Fx, Fy;
+            for (int h = 0; h < 2; ++h) {
+                unstable |= active && !(r2[h].x > 0.f && r2[h].x < INFINITY);   // NaN fails both
+                unstable |= active && !(r2[h].y > 0.f && r2[h].y < INFINITY);
+                const float2 gx = make_float2(dx[2 * h], dx[2 * h + 1]), gy = make_float2(dy[2 * h], dy[2 * h + 1]);
+                float2 Fx, Fy;
                 if (SC) {   // Eq. 22: F = -2 s Phi grad Phi, s Phi the stored field at the cell
-                    Fx = -2.0f * qc[c] * dx[c];
-                    Fy = -2.0f * qc[c] * dy[c];
+                    const float2 m2q = mul2(splat2(-2.0f), make_float2(qc[2 * h], qc[2 * h + 1]));
+                    Fx = mul2(m2q, gx);
+                    Fy = mul2(m2q, gy);
                 } else {    // Eq. 7: F = -grad U
-                    Fx = -dx[c];
-                    Fy = -dy[c];
+                    Fx = mul2(splat2(-1.0f), gx);
+                    Fy = mul2(splat2(-1.0f), gy);
                 }
-                const float inv = __fdividef(1.0f, r[c]);
-                ux[c] = jx[c] * inv;
-                uy[c] = jy[c] * inv;
-                vx[c] = fmaf(Fx, inv, ux[c]);
-                vy[c] = fmaf(Fy, inv, uy[c]);
-                au[c] = 1.0f - 1.5f * (ux[c] * ux[c] + uy[c] * uy[c]);
-                av[c] = 1.0f - 1.5f * (vx[c] * vx[c] + vy[c] * vy[c]);
-                moved[c] = 0.f;
+                const float2 inv = make_float2(__fdividef(1.0f, r2[h].x), __fdividef(1.0f, r2[h].y));
+                ux[h] = mul2(jx2[h], inv);
+                uy[h] = mul2(jy2[h], inv);
+                vx[h] = fma2(Fx, inv, ux[h]);
+                vy[h] = fma2(Fy, inv, uy[h]);
+                au[h] = fma2(splat2(-1.5f), fma2(uy[h], uy[h], mul2(ux[h], ux[h])), splat2(1.0f));
+                av[h] = fma2(splat2(-1.5f), fma2(vy[h], vy[h], mul2(vx[h], vx[h])), splat2(1.0f));
+                moved[h] = splat2(0.f);
             }
+
             // post-collision populations, pushed: x shift by shuffle, store to
             // row yc + e_y if it lies in the segment, accumulate partial densities
             const int rd0 = yc - ys + 3;            // relative destination row of e_y = 0
@@ -429,24 +452,43 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
 #pragma unroll
             for (int ii = 0; ii < 9; ++ii) {
                 const int i = ii == 8 ? 0 : ii + 1;     // rest population last
-                float post[4];
+                float2 p2[2];
                 if (i == 0) {
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) post[c] = r[c] - moved[c];
-                } else {
+                    for (int h = 0; h < 2; ++h) p2[h] = sub2(r2[h], moved[h]);
+                } else if (TAU1) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        // f^eq_i(rho, v) = w_i rho (a + (e_i.v)(3 + 4.5 e_i.v)), a = 1 - 1.5 |v|^2
+                        const float2 w = mul2(r2[h], splat2(i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f));
+                        // e_i . v: v_x, v_y, or for the diagonals v_x + v_y (i = 5, 7), v_x - v_y (8, 6)
+                        const float2 ev = i == 1 || i == 3 ? vx[h]
+                                                           : (i == 2 || i == 4 ? vy[h]
+                                                                               : (i == 5 || i == 7 ? add2(vx[h], vy[h])
+                                                                                                   : sub2(vx[h], vy[h])));
+                        const bool pos = i == 1 || i == 2 || i == 5 || i == 8;
+                        p2[h] = mul2(w, pos ? feq_bracket2<1>(ev, av[h]) : feq_bracket2<-1>(ev, av[h]));
+                        moved[h] = add2(moved[h], p2[h]);
+                    }
+                } else {   // BGK towards f^eq(u) plus the forcing difference, one cell at a time
                     const float fi[4] = {fv[i].x, fv[i].y, fv[i].z, fv[i].w};
+                    float pc[4];
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const float eqv = feq_moving(i, r[c], vx[c], vy[c], av[c]);
-                        if (TAU1) {
-                            post[c] = eqv;
-                        } else {
-                            const float equ = feq_moving(i, r[c], ux[c], uy[c], au[c]);
-                            post[c] = fmaf(1.0f - m.omega, fi[c] - equ, eqv);
-                        }
-                        moved[c] += post[c];
+                        const int h = c >> 1;
+                        const float rc = c & 1 ? r2[h].y : r2[h].x;
+                        const float eqv = feq_moving(i, rc, c & 1 ? vx[h].y : vx[h].x, c & 1 ? vy[h].y : vy[h].x,
+                                                     c & 1 ? av[h].y : av[h].x);
+                        const float equ = feq_moving(i, rc, c & 1 ? ux[h].y : ux[h].x, c & 1 ? uy[h].y : uy[h].x,
+                                                     c & 1 ? au[h].y : au[h].x);
+                        pc[c] = fmaf(1.0f - m.omega, fi[c] - equ, eqv);
                     }
+                    p2[0] = make_float2(pc[0], pc[1]);
+                    p2[1] = make_float2(pc[2], pc[3]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) moved[h] = add2(moved[h], p2[h]);
                 }
+                const float post[4] = {p2[0].x, p2[0].y, p2[1].x, p2[1].y};
                 float4 d;  // values landing on this lane's 4 columns
                 if (ex(i) == 1) {
                     float left = __shfl_up_sync(0xffffffffu, post[3], 1);
@@ -460,7 +502,9 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 if (i != 0) dst += A.n4;                // plane i, stepped from plane i - 1
                 if (rowok[ey(i) + 1]) __stcs((i == 0 ? dst0 : dst) + ey(i) * (nx >> 2), d);
                 float4 &pp = part[ey(i) + 1];
-                pp.x += d.x; pp.y += d.y; pp.z += d.z; pp.w += d.w;
+                const float2 lo = add2(make_float2(pp.x, pp.y), make_float2(d.x, d.y));
+                const float2 hi = add2(make_float2(pp.z, pp.w), make_float2(d.z, d.w));
+                pp = make_float4(lo.x, lo.y, hi.x, hi.y);
             }
             if (!TAU1 && s + 1 < nslab) load_f(s + 1);   // in flight across the barrier
 #pragma unroll

@@ -124,7 +124,12 @@ struct lbm_ctx {
     // reverse sweep buffers, allocated with the tape: the states recomputed
     // inside a segment, the stencil field of every state of a segment, the
     // adjoint ping-pong, kernel scratch and the FP64 dL/dT slots
+    // (two sets: the recompute of one segment runs on rstream while the
+    // adjoint steps of the next later segment run on the context's stream)
     std::vector<void *> seg, segq;
+    cudaStream_t rstream = nullptr;
+    cudaStream_t astream = nullptr;   // the adjoint steps
+    cudaEvent_t rec_done[2] = {nullptr, nullptr}, adj_done[2] = {nullptr, nullptr}, bw_start = nullptr;
     void *lam[2] = {nullptr, nullptr};
     void *aux = nullptr;
     double *slots = nullptr;
@@ -145,7 +150,7 @@ lbm_status fail(lbm_ctx *c, lbm_status st, const char *fmt, ...) {
 }
 
 lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what) {
-    return fail(c, LBM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_E_NOMEM : LBM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
 #define CK(c, expr, what)                                   \
@@ -209,7 +214,7 @@ cudaError_t resolve_timing(lbm_ctx *c) {
 // Launch one kernel of a step through `fn`, bracketed by an event pair when
 // timing is enabled.
 template <typename Fn>
-cudaError_t timed_launch(lbm_ctx *c, int slot, Fn fn) {
+cudaError_t timed_launch(lbm_ctx *c, int slot, Fn fn, int kernels = 1) {
     if (!c->timing) return fn();
     if (c->pending.size() >= 8192) {
         cudaError_t e = resolve_timing(c);
@@ -223,7 +228,7 @@ cudaError_t timed_launch(lbm_ctx *c, int slot, Fn fn) {
     if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
     if (e != cudaSuccess) return e;
     c->pending.push_back({a, b, slot});
-    c->tm.launches += 1;
+    c->tm.launches += kernels;
     return cudaSuccess;
 }
 
@@ -301,7 +306,7 @@ cudaError_t moments_into<float>(lbm_ctx *c, float *r, float *vx, float *vy) {
 
 lbm_status ensure_mom(lbm_ctx *c) {
     if (c->mom) return LBM_OK;
-    CK(c, cudaMalloc(&c->mom, 3 * c->n * c->esz), "cudaMalloc(moments)");
+    CK(c, dev_alloc(&c->mom, 3 * c->n * c->esz), "cudaMalloc(moments)");
     return LBM_OK;
 }
 
@@ -336,32 +341,40 @@ lbm_status mark_initialized(lbm_ctx *c) {
 lbm_status ensure_stage(lbm_ctx *c, size_t bytes) {
     if (c->stage_bytes >= bytes) return LBM_OK;
     CK(c, cudaStreamSynchronize(c->stream), "sync before staging realloc");
-    if (c->stage) cudaFreeHost(c->stage);
+    if (c->stage) host_free(c->stage);
     c->stage = nullptr;
     c->stage_bytes = 0;
-    CK(c, cudaHostAlloc(&c->stage, bytes, cudaHostAllocDefault), "cudaHostAlloc(stage)");
+    CK(c, host_alloc(&c->stage, bytes), "cudaHostAlloc(stage)");
     c->stage_bytes = bytes;
     return LBM_OK;
 }
 
 void free_tape(lbm_ctx *c) {
-    for (void *p : c->ckpt) cudaFree(p);
+    for (void *p : c->ckpt) dev_free(p);
     c->ckpt.clear();
-    for (void *p : c->seg) cudaFree(p);
-    for (void *p : c->segq) cudaFree(p);
+    for (void *p : c->seg) dev_free(p);
+    for (void *p : c->segq) dev_free(p);
     c->seg.clear();
     c->segq.clear();
     for (int k = 0; k < 2; ++k) {
-        cudaFree(c->lam[k]);
+        dev_free(c->lam[k]);
         c->lam[k] = nullptr;
+        if (c->rec_done[k]) cudaEventDestroy(c->rec_done[k]);
+        if (c->adj_done[k]) cudaEventDestroy(c->adj_done[k]);
+        c->rec_done[k] = c->adj_done[k] = nullptr;
     }
-    cudaFree(c->aux);
-    cudaFree(c->slots);
+    if (c->rstream) cudaStreamDestroy(c->rstream);
+    if (c->astream) cudaStreamDestroy(c->astream);
+    if (c->bw_start) cudaEventDestroy(c->bw_start);
+    c->rstream = c->astream = nullptr;
+    c->bw_start = nullptr;
+    dev_free(c->aux);
+    dev_free(c->slots);
     c->aux = nullptr;
     c->slots = nullptr;
     for (int k = 0; k < 2; ++k) {
-        cudaFree(c->tmp[k]);
-        cudaFree(c->qpad_tape[k]);
+        dev_free(c->tmp[k]);
+        dev_free(c->qpad_tape[k]);
         c->tmp[k] = c->qpad_tape[k] = nullptr;
     }
     c->tape_steps = -1;
@@ -392,19 +405,19 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
         free_tape(c);
         for (int k = 0; k < nck; ++k) {
             void *p = nullptr;
-            if (cudaMalloc(&p, fbytes) != cudaSuccess) {
+            if (dev_alloc(&p, fbytes) != cudaSuccess) {
                 free_tape(c);
                 return fail(c, LBM_E_NOMEM, "not enough device memory for %d checkpoints", nck);
             }
             c->ckpt.push_back(p);
         }
-        if (cudaMalloc(&c->tmp[0], fbytes) != cudaSuccess || cudaMalloc(&c->tmp[1], fbytes) != cudaSuccess) {
+        if (dev_alloc(&c->tmp[0], fbytes) != cudaSuccess || dev_alloc(&c->tmp[1], fbytes) != cudaSuccess) {
             free_tape(c);
             return fail(c, LBM_E_NOMEM, "tape scratch");
         }
         if (c->fused) {
             size_t qb = sizeof(float) * (size_t)fused_q_pitch(c->p.nx) * c->p.ny;
-            if (cudaMalloc(&c->qpad_tape[0], qb) != cudaSuccess || cudaMalloc(&c->qpad_tape[1], qb) != cudaSuccess) {
+            if (dev_alloc(&c->qpad_tape[0], qb) != cudaSuccess || dev_alloc(&c->qpad_tape[1], qb) != cudaSuccess) {
                 free_tape(c);
                 return fail(c, LBM_E_NOMEM, "tape potential fields");
             }
@@ -416,13 +429,21 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
             const AdjLayout lay = adjoint_layout(c->p.nx, c->p.ny, c->fused, tau1);
             const size_t lbytes = (size_t)lay.nlam * lay.lstride * sizeof(T);
             bool ok = true;
-            c->seg.assign(C > 1 ? C - 1 : 0, nullptr);
-            c->segq.assign(C, nullptr);
-            for (auto &p : c->seg) ok = ok && cudaMalloc(&p, fbytes) == cudaSuccess;
-            for (auto &p : c->segq) ok = ok && cudaMalloc(&p, qbytes) == cudaSuccess;
-            ok = ok && cudaMalloc(&c->lam[0], lbytes) == cudaSuccess && cudaMalloc(&c->lam[1], lbytes) == cudaSuccess &&
-                 cudaMalloc(&c->aux, (size_t)lay.naux * lay.dstride * sizeof(T)) == cudaSuccess &&
-                 cudaMalloc((void **)&c->slots, sizeof(double) * (adjoint_slots<T>(c->p.nx, c->p.ny) + 1)) == cudaSuccess;
+            c->seg.assign(2 * (C > 1 ? C - 1 : 0), nullptr);
+            c->segq.assign(2 * C, nullptr);
+            for (auto &p : c->seg) ok = ok && dev_alloc(&p, fbytes) == cudaSuccess;
+            for (auto &p : c->segq) ok = ok && dev_alloc(&p, qbytes) == cudaSuccess;
+            // equal priorities: either stream favoured over the other (tried both
+            // ways) lets it starve the other and loses the overlap
+            ok = ok && cudaStreamCreateWithFlags(&c->rstream, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaStreamCreateWithFlags(&c->astream, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->bw_start, cudaEventDisableTiming) == cudaSuccess;
+            for (int k = 0; k < 2; ++k)
+                ok = ok && cudaEventCreateWithFlags(&c->rec_done[k], cudaEventDisableTiming) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&c->adj_done[k], cudaEventDisableTiming) == cudaSuccess;
+            ok = ok && dev_alloc(&c->lam[0], lbytes) == cudaSuccess && dev_alloc(&c->lam[1], lbytes) == cudaSuccess &&
+                 dev_alloc(&c->aux, (size_t)lay.naux * lay.dstride * sizeof(T)) == cudaSuccess &&
+                 dev_alloc((void **)&c->slots, sizeof(double) * (adjoint_slots<T>(c->p.nx, c->p.ny) + 1)) == cudaSuccess;
             if (!ok) {
                 free_tape(c);
                 return fail(c, LBM_E_NOMEM, "not enough device memory for the reverse sweep buffers");
@@ -466,47 +487,80 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     const int qpitch = c->fused ? fused_q_pitch(nx) : nx;
     const int qoff = (qpitch - nx) / 2;
     const int nslots = adjoint_slots<T>(nx, ny);
-    std::vector<void *> &seg = c->seg, &segq = c->segq;
     void **lam = c->lam, *aux = c->aux;
     double *slots = c->slots;
     const int rows = c->fused ? seg_rows_of(c) : 0;
-    cudaError_t e = cudaMemsetAsync(slots, 0, sizeof(double) * (nslots + 1), c->stream);
-    if (e == cudaSuccess) e = launch_adjoint_seed<T>(nx, ny, c->fused, lay, grad_rhoT, (T *)lam[0], c->stream);
-    int li = 0;
-    for (int k = (N - 1) / C; k >= 0 && e == cudaSuccess; --k) {
-        const int t0 = k * C, t1 = std::min(N, t0 + C);  // states t0 .. t1-1 are needed
-        // recompute f^{t0+1} .. f^{t1-1} from the checkpoint with the forward
-        // kernels, keeping the stencil field of every state t0 .. t1-1
+    const int nseg = C > 1 ? C - 1 : 0;
+    // states and stencil fields of segment slot sl: seg[sl * nseg + j], segq[sl * C + j]
+    auto segf = [&](int sl, int j) { return c->seg[sl * nseg + j]; };
+    auto segqf = [&](int sl, int j) { return c->segq[sl * C + j]; };
+    // Recompute f^{t0+1} .. f^{t1-1} of segment k from its checkpoint with the
+    // forward kernels on stream s, keeping the stencil field of every state
+    // t0 .. t1-1, into slot sl.
+    auto recompute = [&](int k, int sl, cudaStream_t s) {
+        const int t0 = k * C, t1 = std::min(N, t0 + C);
+        cudaError_t r = cudaSuccess;
         if (c->fused) {
             const Model<float> &mf = *(const Model<float> *)&m;
-            e = launch_potential_padded(mf, is_sc(c), (const float *)c->ckpt[k], (float *)segq[0], c->err, c->stream);
+            r = launch_potential_padded(mf, is_sc(c), (const float *)c->ckpt[k], (float *)segqf(sl, 0), c->err, s);
             const void *cur = c->ckpt[k];
-            for (int t = t0; t < t1 - 1 && e == cudaSuccess; ++t) {
-                e = launch_fused_step(mf, is_sc(c), (const float *)cur, (const float *)segq[t - t0],
-                                      (float *)seg[t - t0], (float *)segq[t - t0 + 1], c->err, rows, c->stream);
-                cur = seg[t - t0];
+            for (int t = t0; t < t1 - 1 && r == cudaSuccess; ++t) {
+                r = launch_fused_step(mf, is_sc(c), (const float *)cur, (const float *)segqf(sl, t - t0),
+                                      (float *)segf(sl, t - t0), (float *)segqf(sl, t - t0 + 1), c->err, rows, s);
+                cur = segf(sl, t - t0);
             }
         } else {
             const void *cur = c->ckpt[k];
-            for (int t = t0; t < t1 && e == cudaSuccess; ++t) {
-                e = launch_potential<T>(m, is_sc(c), (const T *)cur, (T *)segq[t - t0], c->err, c->stream);
-                if (e == cudaSuccess && t < t1 - 1) {
-                    e = launch_collide<T>(m, is_sc(c), is_cdm(c), (const T *)cur, (const T *)segq[t - t0],
-                                          (T *)seg[t - t0], c->stream);
-                    cur = seg[t - t0];
+            for (int t = t0; t < t1 && r == cudaSuccess; ++t) {
+                r = launch_potential<T>(m, is_sc(c), (const T *)cur, (T *)segqf(sl, t - t0), c->err, s);
+                if (r == cudaSuccess && t < t1 - 1) {
+                    r = launch_collide<T>(m, is_sc(c), is_cdm(c), (const T *)cur, (const T *)segqf(sl, t - t0),
+                                          (T *)segf(sl, t - t0), s);
+                    cur = segf(sl, t - t0);
                 }
             }
         }
+        return r;
+    };
+    // the sweep runs on the tape's own streams, ordered after the context's
+    // stream at the start and before it at the end
+    cudaStream_t as = c->astream;
+    cudaError_t e = cudaEventRecord(c->bw_start, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(as, c->bw_start, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(slots, 0, sizeof(double) * (nslots + 1), as);
+    if (e == cudaSuccess) e = launch_adjoint_seed<T>(nx, ny, c->fused, lay, grad_rhoT, (T *)lam[0], as);
+    // The recompute of segment k - 1 runs on rstream while the adjoint steps of
+    // segment k run on the context's stream: slot (k - 1) & 1 is free once the
+    // adjoint of segment k + 1 (the slot's previous user) is done.
+    const int K = (N - 1) / C;
+    if (e == cudaSuccess) e = cudaEventRecord(c->adj_done[0], as);   // orders rstream after the seed
+    if (e == cudaSuccess) e = cudaEventRecord(c->adj_done[1], as);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->rstream, c->adj_done[K & 1], 0);
+    if (e == cudaSuccess) e = recompute(K, K & 1, c->rstream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->rec_done[K & 1], c->rstream);
+    int li = 0;
+    for (int k = K; k >= 0 && e == cudaSuccess; --k) {
+        const int sl = k & 1;
+        if (k >= 1) {
+            e = cudaStreamWaitEvent(c->rstream, c->adj_done[(k - 1) & 1], 0);
+            if (e == cudaSuccess) e = recompute(k - 1, (k - 1) & 1, c->rstream);
+            if (e == cudaSuccess) e = cudaEventRecord(c->rec_done[(k - 1) & 1], c->rstream);
+        }
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(as, c->rec_done[sl], 0);
+        const int t0 = k * C, t1 = std::min(N, t0 + C);
         for (int t = t1 - 1; t >= t0 && e == cudaSuccess; --t) {
-            const T *ft = (const T *)(t == t0 ? c->ckpt[k] : seg[t - t0 - 1]);
+            const T *ft = (const T *)(t == t0 ? c->ckpt[k] : segf(sl, t - t0 - 1));
             e = launch_adjoint_step<T>(m, R, aalp, is_sc(c), is_cdm(c), tau1, c->fused, lay, ft,
-                                       (const T *)segq[t - t0], qpitch, qoff, (const T *)lam[li], (T *)aux,
-                                       (T *)lam[1 - li], slots, c->err, /*overlap_prev=*/t != t1 - 1, c->stream);
+                                       (const T *)segqf(sl, t - t0), qpitch, qoff, (const T *)lam[li], (T *)aux,
+                                       (T *)lam[1 - li], slots, c->err, /*overlap_prev=*/t != t1 - 1, as);
             li = 1 - li;
         }
+        if (e == cudaSuccess) e = cudaEventRecord(c->adj_done[sl], as);
     }
-    if (e == cudaSuccess) e = launch_adjoint_initial<T>(nx, ny, lay, (const T *)lam[li], grad_rho0, c->stream);
-    if (e == cudaSuccess) e = launch_sum_slots(slots, nslots, slots + nslots, c->stream);
+    if (e == cudaSuccess) e = launch_adjoint_initial<T>(nx, ny, lay, (const T *)lam[li], grad_rho0, as);
+    if (e == cudaSuccess) e = launch_sum_slots(slots, nslots, slots + nslots, as);
+    if (e == cudaSuccess) e = cudaEventRecord(c->bw_start, as);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->bw_start, 0);
     double h = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, slots + nslots, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -612,21 +666,21 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return bail(e, "cudaDeviceGetAttribute");
     size_t fbytes = (size_t)kQ * c->n * c->esz;
-    if ((e = cudaMalloc(&c->f[0], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f0)");
-    if ((e = cudaMalloc(&c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
+    if ((e = dev_alloc(&c->f[0], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f0)");
+    if ((e = dev_alloc(&c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
     // the potential field of the two-pass kernels is FP64 for both precisions
-    if ((e = cudaMalloc(&c->q, (size_t)c->n * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc(q)");
+    if ((e = dev_alloc(&c->q, (size_t)c->n * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc(q)");
     c->fused = p->prec == LBM_F32 && !(p->flags & (LBM_FLAG_TWO_PASS | LBM_FLAG_WALLS_Y)) &&
                fused_step_supported(model_of<float>(c), p->grad == LBM_GRAD_CDM, radius);
     if (c->fused) {
         size_t qb = sizeof(float) * (size_t)fused_q_pitch(p->nx) * p->ny;
-        if ((e = cudaMalloc(&c->qpad[0], qb)) != cudaSuccess) return bail(e, "cudaMalloc(qpad0)");
-        if ((e = cudaMalloc(&c->qpad[1], qb)) != cudaSuccess) return bail(e, "cudaMalloc(qpad1)");
+        if ((e = dev_alloc(&c->qpad[0], qb)) != cudaSuccess) return bail(e, "cudaMalloc(qpad0)");
+        if ((e = dev_alloc(&c->qpad[1], qb)) != cudaSuccess) return bail(e, "cudaMalloc(qpad1)");
     }
-    if ((e = cudaMalloc(&c->partial, sizeof(double) * 6 * observables_partial_count())) != cudaSuccess)
+    if ((e = dev_alloc(&c->partial, sizeof(double) * 6 * observables_partial_count())) != cudaSuccess)
         return bail(e, "cudaMalloc(partial)");
-    if ((e = cudaMalloc(&c->obs_dev, sizeof(lbm_obs))) != cudaSuccess) return bail(e, "cudaMalloc(obs)");
-    if ((e = cudaMalloc(&c->err, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc(err)");
+    if ((e = dev_alloc(&c->obs_dev, sizeof(lbm_obs))) != cudaSuccess) return bail(e, "cudaMalloc(obs)");
+    if ((e = dev_alloc(&c->err, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc(err)");
     if ((e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)) != cudaSuccess) return bail(e, "cudaMemset(err)");
     *out = c;
     return LBM_OK;
@@ -916,17 +970,17 @@ void lbm_destroy(lbm_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    cudaFree(c->f[0]);
-    cudaFree(c->f[1]);
-    cudaFree(c->q);
-    cudaFree(c->qpad[0]);
-    cudaFree(c->qpad[1]);
-    cudaFree(c->mom);
-    cudaFree(c->partial);
-    cudaFree(c->obs_dev);
-    cudaFree(c->err);
+    dev_free(c->f[0]);
+    dev_free(c->f[1]);
+    dev_free(c->q);
+    dev_free(c->qpad[0]);
+    dev_free(c->qpad[1]);
+    dev_free(c->mom);
+    dev_free(c->partial);
+    dev_free(c->obs_dev);
+    dev_free(c->err);
     free_tape(c);
-    if (c->stage) cudaFreeHost(c->stage);
+    if (c->stage) host_free(c->stage);
     for (auto &p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto ev : c->event_pool) cudaEventDestroy(ev);
     delete c;

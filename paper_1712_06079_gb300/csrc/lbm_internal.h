@@ -20,6 +20,22 @@ struct ModelScalars {
 lbm_status check_params(const lbm_params &p, const char **why);
 lbm_status model_scalars(const lbm_params &p, ModelScalars *s);
 
+// Every device and pinned-host allocation of the library goes through these
+// (alloc.cpp): a registry of live allocations and the allocation-failure
+// injection of LBM_DEBUG_FAIL_ALLOC.
+cudaError_t dev_alloc_raw(void **p, size_t bytes);
+cudaError_t host_alloc_raw(void **p, size_t bytes);
+template <typename P>
+cudaError_t dev_alloc(P **p, size_t bytes) {
+    return dev_alloc_raw((void **)p, bytes);
+}
+template <typename P>
+cudaError_t host_alloc(P **p, size_t bytes) {
+    return host_alloc_raw((void **)p, bytes);
+}
+void dev_free(void *p);
+void host_free(void *p);
+
 // f = f^eq(rho, u) (Eq. 2); ux/uy may be null (zero velocity).
 template <typename T>
 cudaError_t launch_init(const Model<T> &m, const T *rho, const T *ux, const T *uy, T *f, cudaStream_t s);

@@ -97,6 +97,7 @@ SIGNATURES = {
     "lbm_batch_debug_skip_barrier": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_V]),
     "lbm_batch_destroy": (None, [_V]),
+    "lbm_debug_alloc_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_destroy": (None, [_V]),
     "lbm_last_error": (ctypes.c_char_p, [_V]),
 }
@@ -129,6 +130,15 @@ def _dp(a):
         return None
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(_D)
+
+
+def alloc_stats():
+    """(live device allocations, live pinned host allocations) of the library."""
+    d, h = ctypes.c_longlong(), ctypes.c_longlong()
+    st = load().lbm_debug_alloc_stats(ctypes.byref(d), ctypes.byref(h))
+    if st != OK:
+        raise LBMError(st, "lbm_debug_alloc_stats failed")
+    return d.value, h.value
 
 
 def critical_point(eos: str, a: float, b: float, R: float = 1.0):
