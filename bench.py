@@ -17,6 +17,7 @@ the lattices are independent problems), timing is max over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import glob
 import hashlib
 import json
@@ -465,8 +466,11 @@ def run_sweep(args):
     ms_batch = t0.elapsed_time(t1)
     rho_b = b.density()
     b.close()
-    # ---- sequential: one context per instance, stepped one after another ----
-    lats = [lbm.Lattice(p) for p in params]
+    # ---- sequential: one context per instance, stepped one after another, in
+    # FP32 arithmetic like the batch (LBM_FLAG_F32_ARITH: the two-pass kernels
+    # these 8-row lattices run would otherwise compute in FP64) ----
+    seq_params = [dataclasses.replace(p, f32_arith=True) for p in params]
+    lats = [lbm.Lattice(p) for p in seq_params]
     for lat, r in zip(lats, rho0):
         lat.init_density(r)
         lat.step(2)
@@ -507,6 +511,7 @@ def run_sweep(args):
         "batched_mlups": cells * steps / (ms_batch * 1e-3) / 1e6,
         "sequential_mlups": cells * seq_steps / (ms_seq * 1e-3) / 1e6,
         "equal_accuracy_max_rel_diff": diff, "sequential_steps_timed": seq_steps,
+        "sequential_arithmetic": "f32 (LBM_FLAG_F32_ARITH), as the batch",
         "coexistence": coex,
     }
     print(json.dumps(line), flush=True)

@@ -84,10 +84,15 @@ typedef enum { LBM_F32 = 0, LBM_F64 = 1 } lbm_prec;
  * reversed) and continues the interaction field across each wall by its mirror
  * image (zero normal gradient), so Eq. 20 along a column is the periodic
  * operator of the mirrored column of period 2 ny and Eq. 15 reads mirrored
- * neighbours.  Walled lattices run the two-pass kernels (FP32 and FP64) and
- * lbm_step_noalloc; the batch and the reverse mode reject them
- * (LBM_E_INVALID). */
-enum { LBM_FLAG_TWO_PASS = 1, LBM_FLAG_WALLS_Y = 2 };
+ * neighbours.  Walled FP32 lattices that the single-pass kernel takes run it
+ * (mirrored rows in its staging, bounce-back at the wall rows); the others,
+ * FP64 and lbm_step_noalloc run the two-pass kernels; the batch and the
+ * reverse mode reject walls (LBM_E_INVALID). */
+/* LBM_FLAG_F32_ARITH: an LBM_F32 lattice that runs the two-pass kernels
+ * computes in FP32 there too instead of FP64 (faster where FP64 is slow, as
+ * on GB300; the FP32 1000-step field bar is met only with FP64 arithmetic
+ * there).  No effect on the single-pass kernel, which computes in FP32. */
+enum { LBM_FLAG_TWO_PASS = 1, LBM_FLAG_WALLS_Y = 2, LBM_FLAG_F32_ARITH = 4 };
 
 typedef struct {
     int nx, ny;      /* lattice size, >= 1 each, periodic in both axes (Sec. 5.2)
@@ -95,7 +100,8 @@ typedef struct {
     int prec;        /* lbm_prec: storage precision of f.  LBM_F64 computes
                         in FP64; LBM_F32 computes in FP32 in the single-pass
                         kernel and in FP64 in the two-pass kernels (every
-                        lattice the single-pass kernel does not take) */
+                        lattice the single-pass kernel does not take) unless
+                        flags has LBM_FLAG_F32_ARITH */
     int eos;         /* lbm_eos */
     int force;       /* lbm_force */
     int grad;        /* lbm_grad */
@@ -354,7 +360,8 @@ void lbm_batch_destroy(lbm_batch *b);
  * -- a host framework that owns every device allocation, or a latency-
  * critical loop that must not take cudaMalloc's implicit synchronisation.
  *   p      lattice and model parameters, as for lbm_create (p->stream is used;
- *          p->flags is accepted but the step always takes the two-pass form);
+ *          p->flags is accepted but the step always takes the two-pass form,
+ *          with FP64 arithmetic for LBM_F32: LBM_FLAG_F32_ARITH is ignored);
  *   f_in   device array, 9*nx*ny values of the precision p->prec, SoA as
  *          above: the state at t (read only);
  *   f_out  device array of the same size, distinct from f_in: receives the

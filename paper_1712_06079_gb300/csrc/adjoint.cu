@@ -711,8 +711,22 @@ cudaError_t launch_adj_t(const AdjArgs<T> &a, bool overlap_prev, cudaStream_t s)
                           (PAD ? 2 * sizeof(uint64_t) : 0) + dt;
     auto ka = adj_a_kernel<T, SC, CDM, TAU1, KC, PAD>;
     auto kb = adj_b_kernel<T, SC, CDM, TAU1, KC, PAD>;
-    cudaError_t e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+    // the shared-memory limits, set once per device and size (a driver call per
+    // launch otherwise); the largest size set so far covers every smaller one
+    constexpr int kDevs = 64;
+    static size_t set_a[kDevs] = {}, set_b[kDevs] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool cache = dev >= 0 && dev < kDevs;
+    if (!cache || smem_a > set_a[dev]) {
+        e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
+        if (e == cudaSuccess && cache) set_a[dev] = smem_a;
+    }
+    if (e == cudaSuccess && (!cache || smem_b > set_b[dev])) {
+        e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+        if (e == cudaSuccess && cache) set_b[dev] = smem_b;
+    }
     if (e != cudaSuccess) return e;
     const dim3 grid = adj_grid<T>(a.m.nx, a.m.ny), block(TX, TYT);
     // the padded FP32 kernels wait for their predecessor's output (griddep_wait),

@@ -240,7 +240,7 @@ __global__ void batch_kernel(const BatchArgs<T> a) {
 
 // Cluster form: one thread-block cluster of C CTAs per instance, with the
 // instance's state on chip for the whole launch.  CTA rank k owns the columns
-// [k w, (k + 1) w), w = nx / C, of every row; its two distribution buffers and
+// [k nx / C, (k + 1) nx / C) of every row (widths differ by one at most); its two distribution buffers and
 // its potential field (with hx halo columns on each side) live in shared
 // memory.  One step: phase A (rho and the potential field of the owned cells),
 // a cluster barrier, the halo columns copied from the neighbouring ranks'
@@ -274,20 +274,26 @@ __global__ void cluster_batch_kernel(const ClusterArgs<T> a) {
     const Model<T> &m = I.m;
     const bool sc = I.sc != 0, cdm = I.cdm != 0;
     const int nx = m.nx, ny = m.ny;
-    const int w = nx / C, x0 = rank * w;
+    // rank k owns columns [k nx / C, (k + 1) nx / C): widths differ by one at
+    // most; every rank lays its slice out with the pitch of the widest, so a
+    // neighbour's element sits at the same offset in every CTA
+    const int x0 = (int)((long long)rank * nx / C), w = (int)((long long)(rank + 1) * nx / C) - x0;
+    const int wmax = (nx + C - 1) / C;
     const int hx = cdm ? 1 : m.kx;
-    const int W = w + 2 * hx;
-    const int ncell = w * ny;
-    T *fa = reinterpret_cast<T *>(smem_raw);   // [kQ][ny][w]
-    T *fb = fa + (size_t)kQ * ncell;
-    T *ph = fb + (size_t)kQ * ncell;           // [ny][W], owned column xl at hx + xl
+    const int W = wmax + 2 * hx;                // potential row pitch
+    const int ncell = w * ny;                   // owned cells
+    const int plane = wmax * ny;                // distribution plane stride
+    T *fa = reinterpret_cast<T *>(smem_raw);   // [kQ][ny][wmax]
+    T *fb = fa + (size_t)kQ * plane;
+    T *ph = fb + (size_t)kQ * plane;           // [ny][W], owned column xl at hx + xl
     const int left = rank == 0 ? C - 1 : rank - 1, right = rank == C - 1 ? 0 : rank + 1;
+    const int wl = (int)((long long)(left + 1) * nx / C) - (int)((long long)left * nx / C);   // the left rank's width
 
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
         const int y = c / w, xl = c - y * w;
         const long long g = I.off + (long long)y * nx + x0 + xl;
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) fa[i * ncell + c] = a.fin[i * a.ntot + g];
+        for (int i = 0; i < kQ; ++i) fa[i * plane + y * wmax + xl] = a.fin[i * a.ntot + g];
     }
     __syncthreads();
     for (int step = 0; step < a.nsteps; ++step) {
@@ -296,12 +302,12 @@ __global__ void cluster_batch_kernel(const ClusterArgs<T> a) {
             const int y = c / w, xl = c - y * w;
             T r = T(0);
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) r += fa[i * ncell + c];
+            for (int i = 0; i < kQ; ++i) r += fa[i * plane + y * wmax + xl];
             if (!(r > T(0)) || !isfinite(r)) atomicOr(a.err, kErrUnstable);
             ph[y * W + hx + xl] = potential_field(m, r, sc);
         }
         cluster.sync();
-        // ---- halo: the left neighbour's columns w - hx .. w - 1, the right one's 0 .. hx - 1 ----
+        // ---- halo: the left neighbour's columns wl - hx .. wl - 1, the right one's 0 .. hx - 1 ----
         {
             const T *pl = cluster.map_shared_rank(ph, left);
             const T *pr = cluster.map_shared_rank(ph, right);
@@ -309,7 +315,7 @@ __global__ void cluster_batch_kernel(const ClusterArgs<T> a) {
             for (int c = threadIdx.x; c < 2 * nh; c += blockDim.x) {
                 const int side = c < nh ? 0 : 1, k = c - side * nh;
                 const int y = k / hx, j = k - y * hx;
-                if (side == 0) ph[y * W + j] = pl[y * W + w + j];
+                if (side == 0) ph[y * W + j] = pl[y * W + wl + j];
                 else ph[y * W + hx + w + j] = pr[y * W + hx + j];
             }
         }
@@ -350,7 +356,7 @@ __global__ void cluster_batch_kernel(const ClusterArgs<T> a) {
             }
             T fi[kQ], post[kQ];
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) fi[i] = fa[i * ncell + c];
+            for (int i = 0; i < kQ; ++i) fi[i] = fa[i * plane + y * wmax + xl];
             collide_cell(m, fi, Fx, Fy, post);
             const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
 #pragma unroll
@@ -358,10 +364,10 @@ __global__ void cluster_batch_kernel(const ClusterArgs<T> a) {
                 const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
                 const int xd = xl + ex(i);
                 T *dst = xd < 0 ? fbl : (xd >= w ? fbr : fb);
-                const int xc = xd < 0 ? w - 1 : (xd >= w ? 0 : xd);
-                dst[i * ncell + dys * w + xc] = post[i];
+                const int xc = xd < 0 ? wl - 1 : (xd >= w ? 0 : xd);
+                dst[i * plane + dys * wmax + xc] = post[i];
             }
-            fb[c] = post[0];
+            fb[y * wmax + xl] = post[0];
         }
         cluster.sync();
         T *t = fa;
@@ -372,7 +378,7 @@ __global__ void cluster_batch_kernel(const ClusterArgs<T> a) {
         const int y = c / w, xl = c - y * w;
         const long long g = I.off + (long long)y * nx + x0 + xl;
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) a.fout[i * a.ntot + g] = fa[i * ncell + c];
+        for (int i = 0; i < kQ; ++i) a.fout[i * a.ntot + g] = fa[i * plane + y * wmax + xl];
     }
 }
 
@@ -502,7 +508,9 @@ lbm_status bfail(lbm_batch *b, lbm_status st, const std::string &m) {
 #define BCK(b, expr, what)                                                                         \
     do {                                                                                           \
         cudaError_t e_ = (expr);                                                                   \
-        if (e_ != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+        if (e_ != cudaSuccess)                                                                     \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? LBM_E_NOMEM : LBM_E_CUDA,            \
+                         std::string(what) + ": " + cudaGetErrorString(e_));                       \
     } while (0)
 
 template <typename T>
@@ -574,18 +582,16 @@ int sm_count() {
 }
 
 // Shared memory per CTA of the cluster form with `cluster` CTAs per instance
-// (both distribution buffers and the haloed potential field of the largest
-// slice), or 0 when some instance does not split: nx not a multiple of the
-// cluster size, a slice narrower than the instance's x halo, or more than the
-// opt-in shared memory of a block.
+// (both distribution buffers and the haloed potential field of the widest
+// slice), or 0 when some instance does not split: a slice narrower than the
+// instance's x halo, or more than the opt-in shared memory of a block.
 size_t cluster_smem_bytes(const lbm_batch *b, int cluster) {
     size_t need = 0;
     for (int i = 0; i < b->n; ++i) {
         const int nx = b->params[i].nx, ny = b->params[i].ny;
-        if (nx % cluster != 0) return 0;
-        const int w = nx / cluster;
-        if (b->halo[i] > w) return 0;
-        const size_t bytes = ((size_t)2 * kQ * w * ny + (size_t)ny * (w + 2 * b->halo[i])) * b->esz;
+        const int wmin = nx / cluster, wmax = (nx + cluster - 1) / cluster;   // slice widths
+        if (b->halo[i] > wmin) return 0;
+        const size_t bytes = ((size_t)2 * kQ * wmax * ny + (size_t)ny * (wmax + 2 * b->halo[i])) * b->esz;
         need = std::max(need, bytes);
     }
     int dev = 0, optin = 0;
@@ -788,12 +794,12 @@ lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out) {
         inst_host.assign((unsigned char *)v.data(), (unsigned char *)v.data() + inst_bytes);
     }
     const size_t fbytes = (size_t)kQ * b->ntot * b->esz;
-    if (cudaMalloc(&b->inst_dev, inst_bytes) != cudaSuccess || cudaMalloc((void **)&b->table_dev, table.size() * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&b->f[0], fbytes) != cudaSuccess || cudaMalloc(&b->f[1], fbytes) != cudaSuccess ||
-        cudaMalloc(&b->q, b->ntot * b->esz) != cudaSuccess || cudaMalloc(&b->stage_dev, b->ntot * b->esz) != cudaSuccess ||
-        cudaMalloc((void **)&b->err, sizeof(int)) != cudaSuccess || cudaMalloc((void **)&b->bar, sizeof(BarrierState)) != cudaSuccess ||
-        cudaMalloc((void **)&b->order_dev, n * sizeof(int)) != cudaSuccess ||
-        cudaHostAlloc(&b->stage_host, b->ntot * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+    if (dev_alloc(&b->inst_dev, inst_bytes) != cudaSuccess || dev_alloc((void **)&b->table_dev, table.size() * sizeof(int)) != cudaSuccess ||
+        dev_alloc(&b->f[0], fbytes) != cudaSuccess || dev_alloc(&b->f[1], fbytes) != cudaSuccess ||
+        dev_alloc(&b->q, b->ntot * b->esz) != cudaSuccess || dev_alloc(&b->stage_dev, b->ntot * b->esz) != cudaSuccess ||
+        dev_alloc((void **)&b->err, sizeof(int)) != cudaSuccess || dev_alloc((void **)&b->bar, sizeof(BarrierState)) != cudaSuccess ||
+        dev_alloc((void **)&b->order_dev, n * sizeof(int)) != cudaSuccess ||
+        host_alloc(&b->stage_host, b->ntot * sizeof(double)) != cudaSuccess)
         return bail(LBM_E_NOMEM);
     if (cudaMemcpy(b->inst_dev, inst_host.data(), inst_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->table_dev, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -934,9 +940,9 @@ lbm_status lbm_batch_moments(lbm_batch *b, double *rho, double *vx, double *vy) 
     if (!b || !rho) return LBM_E_INVALID;
     if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
     const size_t fb = b->ntot * b->esz;
-    if (!b->mom_dev && cudaMalloc(&b->mom_dev, 3 * fb) != cudaSuccess)
+    if (!b->mom_dev && dev_alloc(&b->mom_dev, 3 * fb) != cudaSuccess)
         return bfail(b, LBM_E_NOMEM, "moment buffers");
-    if (!b->mom_host && cudaHostAlloc(&b->mom_host, 3 * fb, cudaHostAllocDefault) != cudaSuccess)
+    if (!b->mom_host && host_alloc(&b->mom_host, 3 * fb) != cudaSuccess)
         return bfail(b, LBM_E_NOMEM, "pinned moment staging");
     const int blocks = (int)std::min<long long>((b->ntot + 255) / 256, 152 * 16);
     unsigned char *md = (unsigned char *)b->mom_dev;
@@ -1031,7 +1037,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int
     // work on a copy of the state: the trials advance it
     const size_t fbytes = (size_t)kQ * b->ntot * b->esz;
     void *save = nullptr;
-    BCK(b, cudaMalloc(&save, fbytes), "cudaMalloc(tune state)");
+    BCK(b, dev_alloc(&save, fbytes), "cudaMalloc(tune state)");
     const int cur0 = b->cur;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
@@ -1092,7 +1098,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int
     b->cur = cur0;
     cudaMemsetAsync(b->err, 0, sizeof(int), b->stream);
     cudaStreamSynchronize(b->stream);
-    cudaFree(save);
+    dev_free(save);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     int t_out = 0, g_out = 0;
@@ -1117,18 +1123,18 @@ void lbm_batch_destroy(lbm_batch *b) {
     else cudaDeviceSynchronize();
     drop_graph(b, 0);
     drop_graph(b, 1);
-    cudaFree(b->inst_dev);
-    cudaFree(b->table_dev);
-    cudaFree(b->order_dev);
-    cudaFree(b->f[0]);
-    cudaFree(b->f[1]);
-    cudaFree(b->q);
-    cudaFree(b->stage_dev);
-    cudaFree(b->mom_dev);
-    if (b->mom_host) cudaFreeHost(b->mom_host);
-    cudaFree(b->err);
-    cudaFree(b->bar);
-    if (b->stage_host) cudaFreeHost(b->stage_host);
+    dev_free(b->inst_dev);
+    dev_free(b->table_dev);
+    dev_free(b->order_dev);
+    dev_free(b->f[0]);
+    dev_free(b->f[1]);
+    dev_free(b->q);
+    dev_free(b->stage_dev);
+    dev_free(b->mom_dev);
+    if (b->mom_host) host_free(b->mom_host);
+    dev_free(b->err);
+    dev_free(b->bar);
+    if (b->stage_host) host_free(b->stage_host);
     delete b;
 }
 

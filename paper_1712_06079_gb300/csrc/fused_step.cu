@@ -8,6 +8,13 @@
 // stencils read |q| = Phi, the cell's force takes s Phi as stored) and U
 // (Eq. 8) for the Zhang-Chen form.
 //
+// No-slip walls in y (the splash case of Sec. 5.5): the staged potential rows
+// beyond a wall are the mirror images of the rows inside (zero normal
+// gradient, the periodic operator of the mirrored column), the segments' halo
+// rows beyond a wall send nothing, and a wall row returns the populations
+// that would cross the wall to its own cells in the opposite direction
+// (half-way bounce-back), the same reading as the two-pass kernels.
+//
 // Decomposition.  A CTA of 8 warps owns a strip of TXI = 120 columns and a
 // segment of up to seg_h rows (a launch parameter: by default the tallest of
 // 126, 62, 30, 14, 6 that gives every SM a CTA; the library's tuner times the
@@ -170,6 +177,12 @@ __device__ __forceinline__ float stencil_field_t(const Model<float> &m, float rh
     return sc ? copysignf(sqrt_approx(fabsf(U)), U) : U;
 }
 
+// The same potential for two cells as a packed pair: the equation of state
+// in packed multiply/fma, the quotients by one fast reciprocal per cell
+// (the effective mass of Eq. 4, with its exponential, cell by cell).
+template <int EOS>
+__device__ __forceinline__ float2 stencil_field_t2(const Model<float> &m, float2 rho, bool sc);
+
 // f^eq_i(rho, u) of Eq. 2 for i = 1..8 with the lattice weights as FP32;
 // a = 1 - 1.5 |u|^2.
 __device__ __forceinline__ float feq_moving(int i, float rho, float ux, float uy, float a) {
@@ -194,7 +207,38 @@ __device__ __forceinline__ float2 feq_bracket2(float2 v, float2 a) {
     return fma2(v, fma2(splat2(4.5f), v, splat2(3.0f * E)), a);
 }
 
-template <bool SC, bool TAU1, int EOS>
+__device__ __forceinline__ float2 rcp2(float2 d) { return make_float2(__fdividef(1.0f, d.x), __fdividef(1.0f, d.y)); }
+
+template <int EOS>
+__device__ __forceinline__ float2 stencil_field_t2(const Model<float> &m, float2 rho, bool sc) {
+    if (EOS == LBM_EOS_PSI_EXP)
+        return make_float2(stencil_field_t<EOS>(m, rho.x, sc), stencil_field_t<EOS>(m, rho.y, sc));
+    const float2 one = splat2(1.0f);
+    float2 p;
+    if (EOS == LBM_EOS_CS) {   // Eq. 29: rho R T (1 + e + e^2 - e^3) / (1 - e)^3 - a rho^2, e = b rho / 4
+        const float2 e = mul2(mul2(splat2(m.b), rho), splat2(0.25f));
+        const float2 om = sub2(one, e);
+        const float2 num = mul2(mul2(rho, splat2(m.RT)), fma2(e, fma2(e, sub2(one, e), one), one));
+        p = sub2(mul2(num, rcp2(mul2(mul2(om, om), om))), mul2(mul2(splat2(m.a), rho), rho));
+    } else {
+        const float2 rep = mul2(mul2(rho, splat2(m.RT)), rcp2(sub2(one, mul2(splat2(m.b), rho))));
+        if (EOS == LBM_EOS_VDW) {          // Eq. 24
+            p = sub2(rep, mul2(mul2(splat2(m.a), rho), rho));
+        } else if (EOS == LBM_EOS_PR) {    // Eq. 28
+            const float2 br = mul2(splat2(m.b), rho);
+            const float2 den = fma2(br, sub2(splat2(2.0f), br), one);
+            p = sub2(rep, mul2(mul2(mul2(splat2(m.aal), rho), rho), rcp2(den)));
+        } else {                            // Eq. 27 (RK, RKS)
+            const float2 den = fma2(splat2(m.b), rho, one);
+            p = sub2(rep, mul2(mul2(mul2(splat2(m.aal), rho), rho), rcp2(den)));
+        }
+    }
+    const float2 U = fma2(splat2(m.k), p, mul2(rho, splat2(-1.0f / 3.0f)));   // Eq. 8 with Hu's k
+    if (!sc) return U;
+    return make_float2(copysignf(sqrt_approx(fabsf(U.x)), U.x), copysignf(sqrt_approx(fabsf(U.y)), U.y));
+}
+
+template <bool SC, bool TAU1, int EOS, bool WALLS>
 __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_constant__ FusedArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     float *qn = reinterpret_cast<float *>(smem);               // [QRING][NW]
@@ -206,7 +250,6 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
 
     const Model<float> &m = A.m;
     const int nx = m.nx, ny = m.ny;
-    const long long N = (long long)nx * ny;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x0 = blockIdx.x * TXI;
     const int nint = min(TXI, nx - x0);             // interior columns (multiple of 4)
@@ -239,7 +282,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         __syncwarp();
         if (lane < SLAB) {
             int ry = SLAB * c + lane;
-            int y = wrapi(ys - QBASE + ry, ny);
+            int y = WALLS ? mirror_index(ys - QBASE + ry, ny) : wrapi(ys - QBASE + ry, ny);
             ptx::bulk_g2s(qn + (ry % QRING) * NW, A.qin + (long long)y * A.qpitch + x0 + QG - 4,
                           ncols * sizeof(float), bar);
         }
@@ -252,7 +295,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         if (lane == 0) ptx::mbar_arrive_expect_tx(bar, SLAB * wcols * sizeof(float));
         __syncwarp();
         if (lane < SLAB) {
-            int y = wrapi(ys - 1 + SLAB * s + lane, ny);
+            int y = WALLS ? mirror_index(ys - 1 + SLAB * s + lane, ny) : wrapi(ys - 1 + SLAB * s + lane, ny);
             ptx::bulk_g2s(qw + ((s & 1) * SLAB + lane) * WW, A.qin + (long long)y * A.qpitch + x0,
                           wcols * sizeof(float), bar);
         }
@@ -287,14 +330,14 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     float colref = 0.f, pcarry = 0.f;
     if (cl < ncols) {
         const float *g = A.qin + x0 + QG - 4 + cl;
-        const int yr = ys - 1 < 0 ? ys - 1 + ny : ys - 1;
+        const int yr = WALLS ? mirror_index(ys - 1, ny) : (ys - 1 < 0 ? ys - 1 + ny : ys - 1);
         colref = mag(__ldg(g + (long long)yr * A.qpitch));
         if (fwdl) {
             float v[25];
 #pragma unroll
             for (int k = 0; k < 25; ++k) {
                 const int y = ys - 27 + k;                  // ny >= 2 FK + 2 > 27: one wrap at most
-                v[k] = __ldg(g + (long long)(y < 0 ? y + ny : y) * A.qpitch);
+                v[k] = __ldg(g + (long long)(WALLS ? mirror_index(y, ny) : (y < 0 ? y + ny : y)) * A.qpitch);
             }
 #pragma unroll
             for (int k = 0; k < 25; ++k) pcarry = fmaf(A.ry, pcarry, mag(v[k]) - colref);
@@ -445,6 +488,11 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             bool rowok[3];                          // destination row yc + k - 1 lies in the segment
 #pragma unroll
             for (int k = 0; k < 3; ++k) rowok[k] = interior && yc + k - 1 >= ys && yc + k - 1 < ys + hseg;
+            // with walls a collided row beyond one (the segment's halo row -1 or ny)
+            // sends nothing, and a wall row returns what would cross the wall to
+            // its own cells, reversed (half-way bounce-back; warp-uniform)
+            const bool ghost = WALLS && (yc < 0 || yc >= ny);
+            const bool wall_lo = WALLS && yc == 0, wall_hi = WALLS && yc == ny - 1;
             float4 *const dst0 = reinterpret_cast<float4 *>(A.fout + (long long)yc * nx + xg);   // plane 0, row yc
             float4 *dst = dst0;
             float4 part[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
@@ -500,11 +548,25 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                     d = make_float4(post[0], post[1], post[2], post[3]);
                 }
                 if (i != 0) dst += A.n4;                // plane i, stepped from plane i - 1
-                if (rowok[ey(i) + 1]) __stcs((i == 0 ? dst0 : dst) + ey(i) * (nx >> 2), d);
-                float4 &pp = part[ey(i) + 1];
-                const float2 lo = add2(make_float2(pp.x, pp.y), make_float2(d.x, d.y));
-                const float2 hi = add2(make_float2(pp.z, pp.w), make_float2(d.z, d.w));
-                pp = make_float4(lo.x, lo.y, hi.x, hi.y);
+                auto accumulate = [](float4 &pp, const float4 &v) {
+                    const float2 lo = add2(make_float2(pp.x, pp.y), make_float2(v.x, v.y));
+                    const float2 hi = add2(make_float2(pp.z, pp.w), make_float2(v.z, v.w));
+                    pp = make_float4(lo.x, lo.y, hi.x, hi.y);
+                };
+                if (!WALLS) {
+                    if (rowok[ey(i) + 1]) __stcs((i == 0 ? dst0 : dst) + ey(i) * (nx >> 2), d);
+                    accumulate(part[ey(i) + 1], d);
+                } else if (!ghost) {
+                    const bool bounce = (ey(i) == -1 && wall_lo) || (ey(i) == 1 && wall_hi);
+                    if (bounce) {   // to the same cells, in the opposite direction, unshifted
+                        const float4 b = make_float4(post[0], post[1], post[2], post[3]);
+                        if (rowok[1]) __stcs(dst0 + opp(i) * A.n4, b);
+                        accumulate(part[1], b);
+                    } else {
+                        if (rowok[ey(i) + 1]) __stcs((i == 0 ? dst0 : dst) + ey(i) * (nx >> 2), d);
+                        accumulate(part[ey(i) + 1], d);
+                    }
+                }
             }
             if (!TAU1 && s + 1 < nslab) load_f(s + 1);   // in flight across the barrier
 #pragma unroll
@@ -531,11 +593,11 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             const float4 a = *reinterpret_cast<const float4 *>(ps + (0 * PROWS + slot) * NW + 4 * lane);
             const float4 b = *reinterpret_cast<const float4 *>(ps + (1 * PROWS + slot) * NW + 4 * lane);
             const float4 cc = *reinterpret_cast<const float4 *>(ps + (2 * PROWS + slot) * NW + 4 * lane);
-            float4 q;
-            q.x = stencil_field_t<EOS>(m, (a.x + b.x) + cc.x, SC);
-            q.y = stencil_field_t<EOS>(m, (a.y + b.y) + cc.y, SC);
-            q.z = stencil_field_t<EOS>(m, (a.z + b.z) + cc.z, SC);
-            q.w = stencil_field_t<EOS>(m, (a.w + b.w) + cc.w, SC);
+            const float2 q01 = stencil_field_t2<EOS>(
+                m, add2(add2(make_float2(a.x, a.y), make_float2(b.x, b.y)), make_float2(cc.x, cc.y)), SC);
+            const float2 q23 = stencil_field_t2<EOS>(
+                m, add2(add2(make_float2(a.z, a.w), make_float2(b.z, b.w)), make_float2(cc.z, cc.w)), SC);
+            const float4 q = make_float4(q01.x, q01.y, q23.x, q23.y);
             float *qrow = A.qout + (long long)yo * A.qpitch + QG;
             *reinterpret_cast<float4 *>(qrow + xg) = q;
             if (xg < QG) *reinterpret_cast<float4 *>(qrow + xg + nx) = q;        // right ghost image
@@ -607,7 +669,7 @@ cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float 
 }
 
 cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, const float *qin, float *fout,
-                              float *qout, int *err, int seg_rows, cudaStream_t s) {
+                              float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl) {
     FusedArgs a;
     a.m = m;
     a.f = f;
@@ -633,8 +695,12 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     const bool tau1 = m.omega == 1.0f;
     void (*kern)(const FusedArgs) = nullptr;
 #define LBM_PICK(E)                                                                                        \
-    kern = sc ? (tau1 ? fused_step_kernel<true, true, E> : fused_step_kernel<true, false, E>)             \
-              : (tau1 ? fused_step_kernel<false, true, E> : fused_step_kernel<false, false, E>)
+    if (m.walls)                                                                                           \
+        kern = sc ? (tau1 ? fused_step_kernel<true, true, E, true> : fused_step_kernel<true, false, E, true>) \
+                  : (tau1 ? fused_step_kernel<false, true, E, true> : fused_step_kernel<false, false, E, true>); \
+    else                                                                                                   \
+        kern = sc ? (tau1 ? fused_step_kernel<true, true, E, false> : fused_step_kernel<true, false, E, false>) \
+                  : (tau1 ? fused_step_kernel<false, true, E, false> : fused_step_kernel<false, false, E, false>)
     switch (m.eos) {
     case LBM_EOS_VDW: LBM_PICK(LBM_EOS_VDW); break;
     case LBM_EOS_CS: LBM_PICK(LBM_EOS_CS); break;
@@ -655,7 +721,7 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     e = cudaLaunchKernelEx(&cfg, kern, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -29,7 +29,7 @@ lbm_status check_params(const lbm_params &p, const char **why) {
     if (p.force != LBM_FORCE_SC && p.force != LBM_FORCE_ZC) return bad("unknown force form");
     if (p.grad != LBM_GRAD_HDM && p.grad != LBM_GRAD_CDM) return bad("unknown gradient");
     if (p.hdm_radius < 0 || p.hdm_radius > kMaxRadius) return bad("hdm_radius must be in [0, 48]");
-    if (p.flags & ~(LBM_FLAG_TWO_PASS | LBM_FLAG_WALLS_Y)) return bad("unknown flags");
+    if (p.flags & ~(LBM_FLAG_TWO_PASS | LBM_FLAG_WALLS_Y | LBM_FLAG_F32_ARITH)) return bad("unknown flags");
     if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return bad("tau must be > 0.5");
     if (p.eos == LBM_EOS_PSI_EXP) {
         if (!std::isfinite(p.G) || p.G == 0.0) return bad("G must be finite and non-zero");
@@ -121,6 +121,7 @@ struct lbm_ctx {
     void *tmp[2] = {nullptr, nullptr};
     void *qpad_tape[2] = {nullptr, nullptr};
     int tape_steps = -1, tape_C = 0;
+    bool tape_last_ready = false;   // the last segment's states are in their sweep slot (set by the forward)
     // reverse sweep buffers, allocated with the tape: the states recomputed
     // inside a segment, the stencil field of every state of a segment, the
     // adjoint ping-pong, kernel scratch and the FP64 dL/dT slots
@@ -297,6 +298,13 @@ cudaError_t moments_into(lbm_ctx *c, T *r, T *vx, T *vy) {
 }
 template <>
 cudaError_t moments_into<float>(lbm_ctx *c, float *r, float *vx, float *vy) {
+    if (c->p.flags & LBM_FLAG_F32_ARITH) {
+        Model<float> mf = model_of<float>(c);
+        const float *f = (const float *)c->f[c->cur];
+        cudaError_t e = launch_potential<float>(mf, is_sc(c), f, (float *)c->q, c->err, c->stream);
+        if (e != cudaSuccess) return e;
+        return launch_moments<float>(mf, is_sc(c), is_cdm(c), f, (const float *)c->q, r, vx, vy, c->stream);
+    }
     Model<double> m = model_of<double>(c);
     const float *f = (const float *)c->f[c->cur];
     cudaError_t e = launch_potential_mixed(m, is_sc(c), f, (double *)c->q, c->err, c->stream);
@@ -380,18 +388,18 @@ void free_tape(lbm_ctx *c) {
     c->tape_steps = -1;
 }
 
-// One forward step from state `src` to `dst` (explicit buffers); qsrc/qdst are
-// the padded potential fields of the single-pass path (qsrc valid on entry).
+// One forward step from state `src` to `dst` (explicit buffers).  Single-pass
+// path: qsrc holds the padded stencil field of src (valid on entry) and qdst
+// receives that of dst.  Two-pass path: the potential of src is formed into
+// qsrc first (qdst unused).
 template <typename T>
-cudaError_t tape_step(lbm_ctx *c, const Model<T> &m, const void *src, void *dst, int parity) {
-    if (c->fused) {
-        return launch_fused_step(*(const Model<float> *)&m, is_sc(c), (const float *)src,
-                                 (const float *)c->qpad_tape[parity], (float *)dst, (float *)c->qpad_tape[1 - parity],
-                                 c->err, seg_rows_of(c), c->stream);
-    }
-    cudaError_t e = launch_potential<T>(m, is_sc(c), (const T *)src, (T *)c->q, c->err, c->stream);
+cudaError_t tape_step(lbm_ctx *c, const Model<T> &m, const void *src, void *dst, void *qsrc, void *qdst) {
+    if (c->fused)
+        return launch_fused_step(*(const Model<float> *)&m, is_sc(c), (const float *)src, (const float *)qsrc,
+                                 (float *)dst, (float *)qdst, c->err, seg_rows_of(c), c->stream);
+    cudaError_t e = launch_potential<T>(m, is_sc(c), (const T *)src, (T *)qsrc, c->err, c->stream);
     if (e != cudaSuccess) return e;
-    return launch_collide<T>(m, is_sc(c), is_cdm(c), (const T *)src, (const T *)c->q, (T *)dst, c->stream);
+    return launch_collide<T>(m, is_sc(c), is_cdm(c), (const T *)src, (const T *)qsrc, (T *)dst, c->stream);
 }
 
 template <typename T>
@@ -454,15 +462,29 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
     Model<T> m = model_of<T>(c);
     CK(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");
     CK(c, launch_init<T>(m, rho0, nullptr, nullptr, (T *)c->ckpt[0], c->stream), "init kernel");
+    // The last segment's states t0 + 1 .. N - 1 and the stencil fields of
+    // t0 .. N - 1 go straight into the reverse sweep's slot for it, which
+    // then needs no recompute.
+    const int K = (nsteps - 1) / C, t0 = K * C, sl = K & 1, nseg = C > 1 ? C - 1 : 0;
+    auto fbuf = [&](int t) -> void * {   // where state t (>= 1) goes
+        if (t % C == 0) return c->ckpt[t / C];
+        if (t > t0 && t < nsteps) return c->seg[sl * nseg + (t - t0 - 1)];
+        return c->tmp[t & 1];
+    };
+    auto qbuf = [&](int t) -> void * {   // the stencil field of state t
+        if (t >= t0 && t < nsteps) return c->segq[sl * C + (t - t0)];
+        return c->fused ? c->qpad_tape[t & 1] : c->q;
+    };
     if (c->fused)
         CK(c, launch_potential_padded(*(const Model<float> *)&m, is_sc(c), (const float *)c->ckpt[0],
-                                      (float *)c->qpad_tape[0], c->err, c->stream), "potential");
+                                      (float *)qbuf(0), c->err, c->stream), "potential");
     const void *cur = c->ckpt[0];
     for (int t = 0; t < nsteps; ++t) {
-        void *dst = ((t + 1) % C == 0) ? c->ckpt[(t + 1) / C] : c->tmp[(t + 1) & 1];
-        CK(c, tape_step<T>(c, m, cur, dst, t & 1), "tape forward step");
+        void *dst = fbuf(t + 1);
+        CK(c, tape_step<T>(c, m, cur, dst, qbuf(t), qbuf(t + 1)), "tape forward step");
         cur = dst;
     }
+    c->tape_last_ready = true;
     CK(c, launch_density<T>(c->n, (const T *)cur, rhoT, c->stream), "density");
     // leave the context on the final state too
     CK(c, cudaMemcpyAsync(c->f[0], cur, fbytes, cudaMemcpyDeviceToDevice, c->stream), "copy final state");
@@ -505,8 +527,11 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
             r = launch_potential_padded(mf, is_sc(c), (const float *)c->ckpt[k], (float *)segqf(sl, 0), c->err, s);
             const void *cur = c->ckpt[k];
             for (int t = t0; t < t1 - 1 && r == cudaSuccess; ++t) {
+                // plain launches: a grid scheduled early would hold SM resources
+                // while it waits, which the adjoint steps beside it need
                 r = launch_fused_step(mf, is_sc(c), (const float *)cur, (const float *)segqf(sl, t - t0),
-                                      (float *)segf(sl, t - t0), (float *)segqf(sl, t - t0 + 1), c->err, rows, s);
+                                      (float *)segf(sl, t - t0), (float *)segqf(sl, t - t0 + 1), c->err, rows, s,
+                                      /*pdl=*/false);
                 cur = segf(sl, t - t0);
             }
         } else {
@@ -536,7 +561,8 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     if (e == cudaSuccess) e = cudaEventRecord(c->adj_done[0], as);   // orders rstream after the seed
     if (e == cudaSuccess) e = cudaEventRecord(c->adj_done[1], as);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->rstream, c->adj_done[K & 1], 0);
-    if (e == cudaSuccess) e = recompute(K, K & 1, c->rstream);
+    if (e == cudaSuccess && !c->tape_last_ready) e = recompute(K, K & 1, c->rstream);   // left by the forward
+    c->tape_last_ready = false;   // the sweep reuses the slots
     if (e == cudaSuccess) e = cudaEventRecord(c->rec_done[K & 1], c->rstream);
     int li = 0;
     for (int k = K; k >= 0 && e == cudaSuccess; --k) {
@@ -670,7 +696,7 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if ((e = dev_alloc(&c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
     // the potential field of the two-pass kernels is FP64 for both precisions
     if ((e = dev_alloc(&c->q, (size_t)c->n * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc(q)");
-    c->fused = p->prec == LBM_F32 && !(p->flags & (LBM_FLAG_TWO_PASS | LBM_FLAG_WALLS_Y)) &&
+    c->fused = p->prec == LBM_F32 && !(p->flags & LBM_FLAG_TWO_PASS) &&
                fused_step_supported(model_of<float>(c), p->grad == LBM_GRAD_CDM, radius);
     if (c->fused) {
         size_t qb = sizeof(float) * (size_t)fused_q_pitch(p->nx) * p->ny;
@@ -853,6 +879,9 @@ lbm_status lbm_step(lbm_ctx *c, int nsteps) {
     } else if (c->fused) {
         Model<float> m = model_of<float>(c);
         for (int s = 0; s < nsteps; ++s) CK(c, step_fused(c, m), "fused step");
+    } else if (c->p.flags & LBM_FLAG_F32_ARITH) {
+        Model<float> m = model_of<float>(c);
+        for (int s = 0; s < nsteps; ++s) CK(c, step_once<float>(c, m), "step");
     } else {
         Model<double> m = model_of<double>(c);
         for (int s = 0; s < nsteps; ++s) CK(c, step_once_mixed(c, m), "step");

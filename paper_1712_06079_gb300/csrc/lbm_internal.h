@@ -89,8 +89,10 @@ int fused_q_pitch(int nx);
 int fused_auto_seg_rows(int nx, int ny, int num_sms);
 cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float *f, float *qpad, int *err,
                                     cudaStream_t s);
+// pdl: launch with programmatic serialization (the grid may be scheduled while
+// the previous one drains; it waits for it before any access).
 cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, const float *qin, float *fout,
-                              float *qout, int *err, int seg_rows, cudaStream_t s);
+                              float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl = true);
 
 // Adjoint (reverse-time) step (adjoint.cu): from lambda = dL/df at t+1 and the
 // state f at t with its stencil field q (row y, column x at

@@ -100,9 +100,9 @@ def sweep_instances(n: int = 64, seed: int = DEFAULT_SEED, nx_lo: int = 256,
                     nx_hi: int = 2048, ny: int = 8, tr_lo: float = 0.5,
                     tr_hi: float = 0.95, tau_lo: float = 0.8, tau_hi: float = 1.2):
     """Instance table of the uneven temperature/EOS sweep: Nx drawn uniformly
-    in [nx_lo, nx_hi] (rounded down to a multiple of 8), EOS drawn uniformly
-    from EOS_TABLE, T/Tc evenly spaced over [tr_lo, tr_hi], tau uniform in
-    [tau_lo, tau_hi].  Each draw uses its own SplitMix64 stream."""
+    from the integers in [nx_lo, nx_hi], EOS drawn uniformly from EOS_TABLE,
+    T/Tc evenly spaced over [tr_lo, tr_hi], tau uniform in [tau_lo, tau_hi].
+    Each draw uses its own SplitMix64 stream."""
     names = sorted(EOS_TABLE)
     u_nx = uniform01(seed + 1, n)
     u_eos = uniform01(seed + 2, n)
@@ -111,7 +111,6 @@ def sweep_instances(n: int = 64, seed: int = DEFAULT_SEED, nx_lo: int = 256,
     out = []
     for i in range(n):
         nx = int(nx_lo + np.floor(u_nx[i] * (nx_hi - nx_lo + 1)))
-        nx = max(nx_lo, (nx // 8) * 8)
         eos = names[int(np.floor(u_eos[i] * len(names)))]
         out.append(dict(nx=nx, ny=ny, eos=eos, Tr=float(trs[i]),
                         tau=float(tau_lo + (tau_hi - tau_lo) * u_tau[i]), **EOS_TABLE[eos]))

@@ -22,6 +22,7 @@ GRAD = {"hdm": 0, "cdm": 1}
 PREC = {"f32": 0, "f64": 1}
 FLAG_TWO_PASS = 1
 FLAG_WALLS_Y = 2
+FLAG_F32_ARITH = 4
 
 _lib = None
 _lock = threading.Lock()
@@ -193,13 +194,17 @@ class Params:
     hdm_radius: int = 0
     two_pass: bool = False  # LBM_FLAG_TWO_PASS: never use the single-pass FP32 kernel
     walls: bool = False     # LBM_FLAG_WALLS_Y: no-slip walls below row 0 and above row ny-1
+    f32_arith: bool = False  # LBM_FLAG_F32_ARITH: FP32 arithmetic in the two-pass kernels of an FP32 lattice
     G: float = 0.0     # eos "psi_exp": interaction strength of Eq. 4
     rho0: float = 1.0  # eos "psi_exp": reference density of psi = 1 - exp(-rho/rho0)
     stream: int = 0  # cudaStream_t as an integer (torch.cuda.Stream.cuda_stream), 0 = default
 
     def c(self) -> _Params:
         return _Params(self.nx, self.ny, PREC[self.prec], EOS[self.eos], FORCE[self.force], GRAD[self.grad],
-                       self.hdm_radius, (FLAG_TWO_PASS if self.two_pass else 0) | (FLAG_WALLS_Y if self.walls else 0), self.a, self.b, self.R, self.omega, self.Tr, self.Tc, self.k,
+                       self.hdm_radius,
+                       (FLAG_TWO_PASS if self.two_pass else 0) | (FLAG_WALLS_Y if self.walls else 0) |
+                       (FLAG_F32_ARITH if self.f32_arith else 0),
+                       self.a, self.b, self.R, self.omega, self.Tr, self.Tc, self.k,
                        self.tau, self.G, self.rho0, ctypes.c_void_p(self.stream or None))
 
 

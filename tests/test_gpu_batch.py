@@ -164,6 +164,39 @@ def test_full_sweep_in_the_benchmark_launch_equals_grid_form():
         assert np.array_equal(u, v)
 
 
+ODD_MIX = [  # widths no cluster size divides: slices of uneven width
+    (257, 8, "pr", 0.7, 1.0, "zc", "hdm"),
+    (331, 8, "cs", 0.8, 0.9, "sc", "hdm"),
+    (1001, 8, "vdw", 0.85, 1.1, "sc", "cdm"),
+    (613, 8, "rk", 0.75, 1.2, "zc", "hdm"),
+]
+
+
+@pytest.mark.parametrize("prec,cluster,threads", [("f32", 8, 1024), ("f32", 4, 256), ("f64", 4, 256)])
+def test_cluster_form_with_uneven_slices_equals_grid_form(prec, cluster, threads):
+    # FP64: HDM radius 40 needs slices of 40 columns, and the 1001-wide lattice's
+    # slices of 251 FP64 columns do not fit a block's shared memory
+    mix = ODD_MIX if prec == "f32" else [m for m in ODD_MIX if m[0] != 1001]
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec=prec) for m in mix]
+    f0 = [slab_state(op, k + 61) for k, (_, op) in enumerate(pairs)]
+    outs = []
+    for c in (0, cluster):
+        with lbm.Batch([gp for gp, _ in pairs]) as b:
+            if c:
+                b.set_cluster(c, threads)
+                assert b.cluster() == c
+            b.set_f(f0)
+            b.step(7)
+            b.step(6)
+            outs.append(b.get_f())
+    for u, v in zip(*outs):
+        assert np.array_equal(u, v)
+    if prec == "f64":   # and the oracle's step
+        for (gp, op), a, got in zip(pairs, f0, outs[1]):
+            ref = oracle.run(op, a, 13)
+            assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-11, (gp.eos, gp.nx)
+
+
 def test_cluster_form_f64_matches_oracle():
     pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f64") for m in CLUSTER_MIX]
     f0 = [slab_state(op, k + 41) for k, (_, op) in enumerate(pairs)]
@@ -262,6 +295,57 @@ def test_batch_barrier_timeout_is_reported_without_hanging():
         b.init_density(rho0)
         b.step(3)
         b.sync()
+
+
+def test_full_sweep_coexistence_against_maxwell():
+    # the 64-lattice sweep as the benchmark runs it (Nx uniform in [256, 2048],
+    # EOS drawn from {VdW, CS, PR, RK}, T/Tc 0.5-0.95, tau in [0.8, 1.2], FP32,
+    # SC + HDM, the tuned launch) for 20000 steps: HDM coexistence densities
+    # against the Maxwell construction (Sec. 5.2), liquid within 2 %, vapour
+    # within 10 %.  The PR lattices below T/Tc 0.6 (density ratio above 800)
+    # relax their vapour phase more slowly than 20000 steps allow: for them
+    # the test asserts instead that the batch follows the FP64 oracle's run of
+    # the same lattice, so what remains is the model's, not the kernel's.
+    table = inputs.sweep_instances(64)
+    params, rho0, ref = [], [], []
+    for d in table:
+        gp = lbm.Params(nx=d["nx"], ny=d["ny"], eos=d["eos"], a=d["a"], b=d["b"], omega=d["omega"], Tr=d["Tr"],
+                        k=d["k"], tau=d["tau"], force="sc", grad="hdm", prec="f32")
+        g, l = lbm.maxwell(gp)
+        params.append(gp)
+        rho0.append(inputs.slab(d["nx"], d["ny"], g, l))
+        ref.append((g, l))
+    assert any(p.nx % 8 for p in params)   # widths the cluster form splits unevenly
+    with lbm.Batch(params) as b:
+        b.init_density(rho0)
+        b.tune(trial_steps=20)
+        b.init_density(rho0)
+        b.step(20000)
+        rho = b.density()
+    slow = []
+    for gp, r, (g, l), d in zip(params, rho, ref, table):
+        liq, gas = bulk_slab(r)
+        print(f"{gp.eos} T/Tc {gp.Tr:.3f} nx {gp.nx}: rho_l {liq / l - 1:+.2%} rho_g {gas / g - 1:+.2%}")
+        if gp.eos == "pr" and gp.Tr < 0.6:
+            slow.append((gp, r, d))
+            continue
+        assert abs(liq / l - 1) < 0.02, (gp.eos, gp.Tr, liq, l)
+        assert abs(gas / g - 1) < 0.10, (gp.eos, gp.Tr, gas, g)
+    oracle.set_threads(oracle.max_threads())
+    for gp, r, d in slow:
+        op = oracle.params_at(gp.nx, 8, "pr", d["a"], d["b"], gp.Tr, omega=d["omega"], k=d["k"], tau=gp.tau)
+        ro = oracle.run(op, oracle.init(op, inputs.slab(gp.nx, 8, *oracle.maxwell(op)[:2])), 20000).sum(0)
+        liq, gas = bulk_slab(r)
+        liq_o, gas_o = bulk_slab(ro)
+        assert abs(liq / liq_o - 1) < 1e-3 and abs(gas / gas_o - 1) < 1e-2, (gp.Tr, liq, liq_o, gas, gas_o)
+
+
+def bulk_slab(r):
+    prof = r.mean(0)
+    nx = prof.size
+    liq = prof[nx // 2 - nx // 16: nx // 2 + nx // 16 + 1].mean()
+    gas = np.r_[prof[: nx // 16 + 1], prof[-nx // 16:]].mean()
+    return liq, gas
 
 
 def test_batch_sweep_coexistence_close_to_maxwell():

@@ -287,6 +287,31 @@ def test_f32_single_pass_kernel_parity(nx, ny, eos, Tr, force):
     assert np.max(np.abs(fa - fb) / np.abs(fb)) < 1e-5
 
 
+def test_f32_arith_flag_keeps_fp32_arithmetic_in_the_two_pass_kernels():
+    # LBM_FLAG_F32_ARITH: the two-pass kernels compute an FP32 lattice in FP32.
+    # One step against the oracle's step of the same FP32-rounded state: the
+    # default (FP64 arithmetic on FP32 storage) differs by the rounding of the
+    # result to FP32 alone; FP32 arithmetic by a few ulp more (PR, where
+    # U = k p - rho/3 nearly cancels at liquid density)
+    gp, op = make(96, 40, "pr", 0.75, "zc", "hdm", prec="f32")
+    g, l, _ = oracle.maxwell(op)
+    f0 = perturbed_state(op, inputs.droplet(96, 40, 12, g, l), seed=77)
+    f0 = f0.astype(np.float32).astype(np.float64)
+    fo = oracle.step(op, f0)
+    outs = []
+    for flag, bar in ((False, 1.2e-7), (True, 5e-5)):
+        gp.f32_arith = flag
+        with lbm.Lattice(gp) as lat:
+            lat.set_f(f0)
+            lat.step(1)
+            outs.append(lat.get_f())
+        err = np.max(np.abs(outs[-1] - fo) / fo)
+        print(f"f32_arith={flag}: one step {err:.2e}")
+        assert err < bar, (flag, err)
+    d = np.max(np.abs(outs[0] - outs[1]) / outs[0])
+    assert 0 < d < 5e-5, d
+
+
 def test_f32_single_pass_segment_height_does_not_change_results():
     # the CTA segment height is a launch shape: every cell takes the same
     # arithmetic except the d/dy forward recurrence, which carries its sum

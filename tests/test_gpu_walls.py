@@ -3,8 +3,9 @@ oracle's walled step (half-way bounce-back, field mirrored across the walls).
 
 Bars as in the periodic parity tests: FP64 within 1e-12 relative per step over
 all nine populations and over 20 steps; FP32 within 1e-5 on rho after 300
-steps; mass conserved to FP64 rounding.  Walled lattices run the two-pass
-kernels; the batch and the reverse mode refuse them."""
+steps; mass conserved to FP64 rounding.  Walled FP32 lattices that the
+single-pass kernel takes run it, the others the two-pass kernels; the batch
+and the reverse mode refuse walls."""
 import numpy as np
 import pytest
 
@@ -71,16 +72,48 @@ def test_f64_walls_parity(nx, ny, eos, Tr, force, grad, tau):
     assert abs(f20.sum() - f0.sum()) < 1e-13 * f0.sum()
 
 
-def test_f32_walls_parity():
+@pytest.mark.parametrize("two_pass", [False, True])
+def test_f32_walls_parity(two_pass):
+    # 128 x 72 runs the single-pass kernel (walls in its staging and its
+    # push), or the two-pass kernels with LBM_FLAG_TWO_PASS
     nx, ny = 128, 72
     gp, op = make(nx, ny, "cs", 0.8, "sc", "hdm", 0.9, prec="f32")
+    gp.two_pass = two_pass
     f0 = wall_drop(op, nx, ny, seed=3)
     with lbm.Lattice(gp) as lat:
+        assert (lat.segment_rows() > 0) == (not two_pass)
         lat.set_f(f0)
-        lat.step(300)
+        lat.set_timing(True)
+        lat.step(1)
+        assert ("fused_step" in lat.timing()["kernels"]) == (not two_pass)
+        f1 = lat.get_f()
+        lat.step(299)
         r, _, _ = lat.moments()
-    ro, _, _ = oracle.moments(op, oracle.run(op, f0, 300))
-    assert np.abs(r - ro).max() / ro.max() < 1e-5
+        obs = lat.observables()
+    o1 = oracle.step(op, f0)
+    assert np.max(np.abs(f1 - o1) / o1) < 1e-5
+    ro, _, _ = oracle.moments(op, oracle.run(op, o1, 299))
+    assert np.max(np.abs(r - ro) / ro) < 1e-5
+    assert abs(obs["mass"] - ro.sum()) < 1e-6 * ro.sum()
+
+
+@pytest.mark.parametrize("nx,ny,eos,force,tau", [(132, 129, "pr", "zc", 1.0), (64, 54, "vdw", "sc", 0.8),
+                                                 (256, 200, "cs", "sc", 1.0)])
+def test_f32_walls_single_pass_one_step_and_segments(nx, ny, eos, force, tau):
+    # one step of the single-pass kernel with walls against the oracle, every
+    # population, at several segment heights (segments start and end at the
+    # walls and inside the lattice)
+    gp, op = make(nx, ny, eos, 0.8, force, "hdm", tau, prec="f32")
+    f0 = wall_drop(op, nx, ny, seed=nx + ny)
+    fo = oracle.step(op, f0)
+    for rows in (0, 6, 22, ny):
+        with lbm.Lattice(gp) as lat:
+            lat.set_segment_rows(rows)
+            assert lat.segment_rows() > 0
+            lat.set_f(f0)
+            lat.step(1)
+            f1 = lat.get_f()
+        assert np.max(np.abs(f1 - fo) / fo) < 1e-5, rows
 
 
 @pytest.mark.parametrize("grad", ["hdm", "cdm"])
