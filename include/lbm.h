@@ -392,6 +392,17 @@ lbm_status lbm_step_noalloc(const lbm_params *p, const void *f_in, void *f_out);
  * failure is made on the host; no GPU call fails. */
 lbm_status lbm_debug_alloc_stats(long long *live_device, long long *live_host);
 
+/* Test hook (not a passage of the paper) of the bounds-checked build, a
+ * library compiled with -DLBM_CHECKED: its kernels check the indices of their
+ * global and distributed-shared-memory accesses, skip an access that would
+ * fall outside its buffer and set a bit in the error word instead (the next
+ * synchronising call answers LBM_E_CUDA, "a device-side bounds check
+ * failed"), and every device allocation carries 256 bytes of a known pattern
+ * past its end.  *damaged receives the number of live allocations whose
+ * pattern changed (synchronises the device), or -1 in the normal build,
+ * which has neither checks nor canaries. */
+lbm_status lbm_debug_check_canaries(long long *damaged);
+
 /* Free everything the context owns.  NULL is a no-op. */
 void lbm_destroy(lbm_ctx *c);
 

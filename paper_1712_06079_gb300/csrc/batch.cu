@@ -230,7 +230,8 @@ __global__ void batch_kernel(const BatchArgs<T> a) {
             for (int i = 1; i < kQ; ++i) {
                 const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
                 const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
-                fo[i * a.ntot + I.off + (long long)dys * m.nx + dxs] = post[i];
+                const long long k = i * a.ntot + I.off + (long long)dys * m.nx + dxs;
+                if (in_bounds(k, kQ * a.ntot, m.chk)) fo[k] = post[i];
             }
             fo[cell] = post[0];
         }
@@ -293,7 +294,8 @@ __global__ void cluster_batch_kernel(const ClusterArgs<T> a) {
         const int y = c / w, xl = c - y * w;
         const long long g = I.off + (long long)y * nx + x0 + xl;
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) fa[i * plane + y * wmax + xl] = a.fin[i * a.ntot + g];
+        for (int i = 0; i < kQ; ++i)
+            if (in_bounds(i * a.ntot + g, kQ * a.ntot, m.chk)) fa[i * plane + y * wmax + xl] = a.fin[i * a.ntot + g];
     }
     __syncthreads();
     for (int step = 0; step < a.nsteps; ++step) {
@@ -365,7 +367,8 @@ __global__ void cluster_batch_kernel(const ClusterArgs<T> a) {
                 const int xd = xl + ex(i);
                 T *dst = xd < 0 ? fbl : (xd >= w ? fbr : fb);
                 const int xc = xd < 0 ? wl - 1 : (xd >= w ? 0 : xd);
-                dst[i * plane + dys * wmax + xc] = post[i];
+                if (in_bounds(i * plane + dys * wmax + xc, (long long)kQ * plane, m.chk))
+                    dst[i * plane + dys * wmax + xc] = post[i];   // own buffer or a neighbour's (same layout)
             }
             fb[y * wmax + xl] = post[0];
         }
@@ -378,7 +381,8 @@ __global__ void cluster_batch_kernel(const ClusterArgs<T> a) {
         const int y = c / w, xl = c - y * w;
         const long long g = I.off + (long long)y * nx + x0 + xl;
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) a.fout[i * a.ntot + g] = fa[i * plane + y * wmax + xl];
+        for (int i = 0; i < kQ; ++i)
+            if (in_bounds(i * a.ntot + g, kQ * a.ntot, m.chk)) a.fout[i * a.ntot + g] = fa[i * plane + y * wmax + xl];
     }
 }
 
@@ -801,6 +805,11 @@ lbm_status lbm_batch_create(const lbm_params *p, int n, lbm_batch **out) {
         dev_alloc((void **)&b->order_dev, n * sizeof(int)) != cudaSuccess ||
         host_alloc(&b->stage_host, b->ntot * sizeof(double)) != cudaSuccess)
         return bail(LBM_E_NOMEM);
+    // the instances' bounds-check error word (LBM_CHECKED builds) is the batch's
+    for (int i = 0; i < n; ++i) {
+        if (prec == LBM_F64) reinterpret_cast<Inst<double> *>(inst_host.data())[i].m.chk = b->err;
+        else reinterpret_cast<Inst<float> *>(inst_host.data())[i].m.chk = b->err;
+    }
     if (cudaMemcpy(b->inst_dev, inst_host.data(), inst_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->table_dev, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->order_dev, order.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -899,6 +908,7 @@ lbm_status lbm_batch_init_density(lbm_batch *b, const double *rho) {
 }
 
 lbm_status lbm_batch_step(lbm_batch *b, int nsteps) {
+    NvtxRange nvtx("lbm_batch_step");
     if (!b) return LBM_E_INVALID;
     if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
     if (b->unstable) return bfail(b, LBM_E_UNSTABLE, "batch is in the error state");
@@ -1032,6 +1042,7 @@ lbm_status lbm_batch_set_f(lbm_batch *b, const double *f) {
 }
 
 lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int *grid_blocks) {
+    NvtxRange nvtx("lbm_batch_tune");
     if (!b || trial_steps < 2) return LBM_E_INVALID;
     if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
     // work on a copy of the state: the trials advance it

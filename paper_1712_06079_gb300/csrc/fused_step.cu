@@ -238,6 +238,11 @@ __device__ __forceinline__ float2 stencil_field_t2(const Model<float> &m, float2
     return make_float2(copysignf(sqrt_approx(fabsf(U.x)), U.x), copysignf(sqrt_approx(fabsf(U.y)), U.y));
 }
 
+// (LBM_CHECKED builds) the elements [off, off + len) lie in a buffer of n
+__device__ __forceinline__ bool range_ok(long long off, long long len, long long n, int *err) {
+    return in_bounds(off, n - len + 1, err);
+}
+
 template <bool SC, bool TAU1, int EOS, bool WALLS>
 __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_constant__ FusedArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -283,8 +288,10 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         if (lane < SLAB) {
             int ry = SLAB * c + lane;
             int y = WALLS ? mirror_index(ys - QBASE + ry, ny) : wrapi(ys - QBASE + ry, ny);
-            ptx::bulk_g2s(qn + (ry % QRING) * NW, A.qin + (long long)y * A.qpitch + x0 + QG - 4,
-                          ncols * sizeof(float), bar);
+            const long long src = (long long)y * A.qpitch + x0 + QG - 4;
+            if (range_ok(src, ncols, (long long)A.qpitch * ny, A.err) &&
+                range_ok((ry % QRING) * NW, ncols, QRING * NW, A.err))   // (else the wait times out)
+                ptx::bulk_g2s(qn + (ry % QRING) * NW, A.qin + src, ncols * sizeof(float), bar);
         }
     };
     // slab s: potential rows ys - 1 + 8s + w at full width into buffer s & 1
@@ -296,8 +303,9 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         __syncwarp();
         if (lane < SLAB) {
             int y = WALLS ? mirror_index(ys - 1 + SLAB * s + lane, ny) : wrapi(ys - 1 + SLAB * s + lane, ny);
-            ptx::bulk_g2s(qw + ((s & 1) * SLAB + lane) * WW, A.qin + (long long)y * A.qpitch + x0,
-                          wcols * sizeof(float), bar);
+            const long long src = (long long)y * A.qpitch + x0;
+            if (range_ok(src, wcols, (long long)A.qpitch * ny, A.err) && range_ok(0, wcols, WW, A.err))
+                ptx::bulk_g2s(qw + ((s & 1) * SLAB + lane) * WW, A.qin + src, wcols * sizeof(float), bar);
         }
     };
     int issued = 0;  // chunks issued so far (meaningful in warp 0)
@@ -317,7 +325,8 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         const float *src = A.f + (long long)wrapi(ys - 1 + SLAB * s + warp, ny) * nx + xgw;
         const float4 *p = reinterpret_cast<const float4 *>(src);
 #pragma unroll
-        for (int i = 0; i < 9; ++i, p += A.n4) fv[i] = ld_stream(p);   // one pointer stepped plane by plane
+        const bool ok = range_ok(src - A.f, 4, (long long)4 * A.n4, A.err);   // the plane-0 float4 (all planes alike)
+        for (int i = 0; i < 9; ++i, p += A.n4) fv[i] = ok ? ld_stream(p) : make_float4(0.f, 0.f, 0.f, 0.f);
     };
     // d/dy column recurrences: thread (warp, lane) follows ring column
     // 16 warp + lane % 16 (padded column x0 + QG - 4 + cl); lanes < 16 carry the
@@ -494,6 +503,9 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             const bool ghost = WALLS && (yc < 0 || yc >= ny);
             const bool wall_lo = WALLS && yc == 0, wall_hi = WALLS && yc == ny - 1;
             float4 *const dst0 = reinterpret_cast<float4 *>(A.fout + (long long)yc * nx + xg);   // plane 0, row yc
+            auto store4 = [&](float4 *p, const float4 &v) {   // a streaming store of f(t+1)
+                if (range_ok(p - reinterpret_cast<float4 *>(A.fout), 1, 9LL * A.n4, A.err)) __stcs(p, v);
+            };
             float4 *dst = dst0;
             float4 part[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
                               make_float4(0.f, 0.f, 0.f, 0.f)};
@@ -554,16 +566,16 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                     pp = make_float4(lo.x, lo.y, hi.x, hi.y);
                 };
                 if (!WALLS) {
-                    if (rowok[ey(i) + 1]) __stcs((i == 0 ? dst0 : dst) + ey(i) * (nx >> 2), d);
+                    if (rowok[ey(i) + 1]) store4((i == 0 ? dst0 : dst) + ey(i) * (nx >> 2), d);
                     accumulate(part[ey(i) + 1], d);
                 } else if (!ghost) {
                     const bool bounce = (ey(i) == -1 && wall_lo) || (ey(i) == 1 && wall_hi);
                     if (bounce) {   // to the same cells, in the opposite direction, unshifted
                         const float4 b = make_float4(post[0], post[1], post[2], post[3]);
-                        if (rowok[1]) __stcs(dst0 + opp(i) * A.n4, b);
+                        if (rowok[1]) store4(dst0 + opp(i) * A.n4, b);
                         accumulate(part[1], b);
                     } else {
-                        if (rowok[ey(i) + 1]) __stcs((i == 0 ? dst0 : dst) + ey(i) * (nx >> 2), d);
+                        if (rowok[ey(i) + 1]) store4((i == 0 ? dst0 : dst) + ey(i) * (nx >> 2), d);
                         accumulate(part[ey(i) + 1], d);
                     }
                 }
@@ -599,9 +611,13 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 m, add2(add2(make_float2(a.z, a.w), make_float2(b.z, b.w)), make_float2(cc.z, cc.w)), SC);
             const float4 q = make_float4(q01.x, q01.y, q23.x, q23.y);
             float *qrow = A.qout + (long long)yo * A.qpitch + QG;
-            *reinterpret_cast<float4 *>(qrow + xg) = q;
-            if (xg < QG) *reinterpret_cast<float4 *>(qrow + xg + nx) = q;        // right ghost image
-            if (xg >= nx - QG) *reinterpret_cast<float4 *>(qrow + xg - nx) = q;  // left ghost image
+            auto storeq = [&](long long x) {   // padded row offset of a float4 of q(t+1)
+                if (range_ok((long long)yo * A.qpitch + QG + x, 4, (long long)A.qpitch * ny, A.err))
+                    *reinterpret_cast<float4 *>(qrow + x) = q;
+            };
+            storeq(xg);
+            if (xg < QG) storeq(xg + nx);        // right ghost image
+            if (xg >= nx - QG) storeq(xg - nx);  // left ghost image
         }
     }
 

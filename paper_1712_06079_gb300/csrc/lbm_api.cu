@@ -163,6 +163,7 @@ lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what) {
 template <typename T>
 Model<T> model_of(const lbm_ctx *c) {
     Model<T> m{};
+    m.chk = c->err;
     m.nx = c->p.nx;
     m.ny = c->p.ny;
     m.eos = c->p.eos;
@@ -286,8 +287,9 @@ cudaError_t step_fused(lbm_ctx *c, const Model<float> &m) {
     return cudaSuccess;
 }
 
-// Density and Eq. 11 velocity of the current state; FP32 lattices take the
-// mixed two-pass kernels (FP64 arithmetic), whichever step they run.
+// Density and Eq. 11 velocity of the current state, in the arithmetic of the
+// lattice's step: FP32 for FP32 lattices on the single-pass kernel (or with
+// LBM_FLAG_F32_ARITH), FP64 for the other FP32 lattices (the mixed kernels).
 template <typename T>
 cudaError_t moments_into(lbm_ctx *c, T *r, T *vx, T *vy) {
     Model<T> m = model_of<T>(c);
@@ -298,7 +300,7 @@ cudaError_t moments_into(lbm_ctx *c, T *r, T *vx, T *vy) {
 }
 template <>
 cudaError_t moments_into<float>(lbm_ctx *c, float *r, float *vx, float *vy) {
-    if (c->p.flags & LBM_FLAG_F32_ARITH) {
+    if (c->fused || (c->p.flags & LBM_FLAG_F32_ARITH)) {
         Model<float> mf = model_of<float>(c);
         const float *f = (const float *)c->f[c->cur];
         cudaError_t e = launch_potential<float>(mf, is_sc(c), f, (float *)c->q, c->err, c->stream);
@@ -527,11 +529,10 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
             r = launch_potential_padded(mf, is_sc(c), (const float *)c->ckpt[k], (float *)segqf(sl, 0), c->err, s);
             const void *cur = c->ckpt[k];
             for (int t = t0; t < t1 - 1 && r == cudaSuccess; ++t) {
-                // plain launches: a grid scheduled early would hold SM resources
-                // while it waits, which the adjoint steps beside it need
+                // (programmatic launches here too: plain ones, which hold no SM
+                // resources while they wait, made the sweep 4 % slower)
                 r = launch_fused_step(mf, is_sc(c), (const float *)cur, (const float *)segqf(sl, t - t0),
-                                      (float *)segf(sl, t - t0), (float *)segqf(sl, t - t0 + 1), c->err, rows, s,
-                                      /*pdl=*/false);
+                                      (float *)segf(sl, t - t0), (float *)segqf(sl, t - t0 + 1), c->err, rows, s);
                 cur = segf(sl, t - t0);
             }
         } else {
@@ -633,6 +634,7 @@ void convert(D *dst, const S *src, long long n) {
 extern "C" {
 
 lbm_status lbm_adjoint_forward(lbm_ctx *c, const void *rho0, int nsteps, int checkpoint_interval, void *rho_T) {
+    NvtxRange nvtx("lbm_adjoint_forward");
     if (!c) return LBM_E_INVALID;
     if (!rho0 || !rho_T) return fail(c, LBM_E_INVALID, "rho0 and rho_T must be device arrays");
     if (nsteps < 1 || checkpoint_interval < 1) return fail(c, LBM_E_INVALID, "need nsteps >= 1, checkpoint_interval >= 1");
@@ -643,6 +645,7 @@ lbm_status lbm_adjoint_forward(lbm_ctx *c, const void *rho0, int nsteps, int che
 
 lbm_status lbm_adjoint_backward(lbm_ctx *c, const void *grad_rho_T, void *grad_rho0, double *grad_T, double *grad_Tr,
                                 double *grad_G) {
+    NvtxRange nvtx("lbm_adjoint_backward");
     if (!c) return LBM_E_INVALID;
     if (c->tape_steps < 1) return fail(c, LBM_E_STATE, "no tape: call lbm_adjoint_forward first");
     if (!grad_rho_T || !grad_rho0) return fail(c, LBM_E_INVALID, "grad arrays must be device arrays");
@@ -726,6 +729,7 @@ lbm_status lbm_get_segment_rows(lbm_ctx *c, int *rows) {
 }
 
 lbm_status lbm_tune_segment_rows(lbm_ctx *c, int trials, int *rows) {
+    NvtxRange nvtx("lbm_tune_segment_rows");
     lbm_status st = check_ready(c);
     if (st != LBM_OK) return st;
     if (!rows) return fail(c, LBM_E_INVALID, "rows must be non-NULL");
@@ -870,6 +874,7 @@ lbm_status lbm_get_f(lbm_ctx *c, double *f) {
 }
 
 lbm_status lbm_step(lbm_ctx *c, int nsteps) {
+    NvtxRange nvtx("lbm_step");
     lbm_status st = check_ready(c);
     if (st != LBM_OK) return st;
     if (nsteps < 0) return fail(c, LBM_E_INVALID, "nsteps must be >= 0");

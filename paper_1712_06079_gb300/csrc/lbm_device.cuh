@@ -32,9 +32,23 @@ constexpr int kErrUnstable = 1;  // NaN or rho <= 0 seen
 constexpr int kErrTimeout = 2;   // a bounded device-side wait gave up
 constexpr int kErrBounds = 4;    // a self-checked index fell outside a buffer
 
+// Bounds self-checks of the LBM_CHECKED build: an index outside its buffer
+// sets kErrBounds in the error word and the access is skipped (no fault, no
+// trap); in the normal build the check is compiled away.
+#ifdef LBM_CHECKED
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int *err) {
+    if (i >= 0 && i < n) return true;
+    if (err) atomicOr(err, kErrBounds);
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(long long, long long, int *) { return true; }
+#endif
+
 // Per-launch constants of the model, in the working precision.
 template <typename T>
 struct Model {
+    int *chk;      // error word of the bounds self-checks (LBM_CHECKED builds; may be null)
     int nx, ny;
     int eos;       // lbm_eos
     int kx, ky;    // HDM stencil radius along x and y (already folded to the period)

@@ -4,8 +4,18 @@
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
+#include "nvtx3/nvToolsExt.h"
 
 namespace lbm {
+
+// An NVTX range over a scope (named in a profiler's timeline; no cost when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Host-side scalars of a parameter set.  With an equation of state: T = Tr Tc
 // (Tc = p.Tc, or from lbm_critical_point), a, b, a alpha(T) and its

@@ -115,7 +115,8 @@ __device__ __forceinline__ void stage_tile(const Model<T> &m, const T *__restric
         if (!CDM && !inx && !iny) continue;
         int gx = wrap_index(x0 - hx + c, m.nx);
         int gy = m.walls ? mirror_index(y0 - hy + r, m.ny) : wrap_index(y0 - hy + r, m.ny);
-        S[idx] = q[(long long)gy * m.nx + gx];
+        const long long k = (long long)gy * m.nx + gx;
+        S[idx] = in_bounds(k, (long long)m.nx * m.ny, m.chk) ? q[k] : T(0);
     }
 }
 
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(TX *TYT) collide_kernel(Model<T> m, const TS *
         const long long c = (long long)y * m.nx + x;
         T fi[kQ];
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) fi[i] = T(f[i * n + c]);
+        for (int i = 0; i < kQ; ++i) fi[i] = in_bounds(i * n + c, kQ * n, m.chk) ? T(f[i * n + c]) : T(0);
         T r = T(0), jx = T(0), jy = T(0);
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
@@ -187,12 +188,12 @@ __global__ void __launch_bounds__(TX *TYT) collide_kernel(Model<T> m, const TS *
             moved += post;
             const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
             const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : y);
-            if (m.walls && ((ey(i) == 1 && y == m.ny - 1) || (ey(i) == -1 && y == 0)))
-                fout[opp(i) * n + c] = TS(post);   // half-way bounce-back off the wall
-            else
-                fout[i * n + (long long)dys * m.nx + dxs] = TS(post);
+            const long long k = m.walls && ((ey(i) == 1 && y == m.ny - 1) || (ey(i) == -1 && y == 0))
+                                    ? opp(i) * n + c                             // half-way bounce-back off the wall
+                                    : i * n + (long long)dys * m.nx + dxs;
+            if (in_bounds(k, kQ * n, m.chk)) fout[k] = TS(post);
         }
-        fout[c] = TS(r - moved);
+        if (in_bounds(c, kQ * n, m.chk)) fout[c] = TS(r - moved);
     }
 }
 

@@ -70,6 +70,7 @@ lbm_status run_step(const lbm_params &p, const lbm::ModelScalars &ms, const void
     }
     cudaStream_t s = (cudaStream_t)p.stream;
     int *err = (int *)scratch;
+    m.chk = err;
     T *q = (T *)((unsigned char *)scratch + kErrBytes);
     const bool sc = p.force == LBM_FORCE_SC, cdm = p.grad == LBM_GRAD_CDM;
     if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return LBM_E_CUDA;

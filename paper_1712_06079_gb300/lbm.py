@@ -99,13 +99,16 @@ SIGNATURES = {
     "lbm_batch_last_error": (ctypes.c_char_p, [_V]),
     "lbm_batch_destroy": (None, [_V]),
     "lbm_debug_alloc_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm_debug_check_canaries": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_destroy": (None, [_V]),
     "lbm_last_error": (ctypes.c_char_p, [_V]),
 }
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: ``_build/liblbm.so``, or the
+    bounds-checked build when the environment sets LBM_CHECKED=1 (tests)."""
+    return _build.LIB_CHECKED if os.environ.get("LBM_CHECKED") == "1" else _build.LIB
 
 
 def load():
@@ -140,6 +143,16 @@ def alloc_stats():
     if st != OK:
         raise LBMError(st, "lbm_debug_alloc_stats failed")
     return d.value, h.value
+
+
+def damaged_canaries() -> int:
+    """Device allocations whose canary (the bytes past their end, in the
+    bounds-checked build) was overwritten; -1 in the normal build."""
+    n = ctypes.c_longlong()
+    st = load().lbm_debug_check_canaries(ctypes.byref(n))
+    if st != OK:
+        raise LBMError(st, "lbm_debug_check_canaries failed")
+    return n.value
 
 
 def critical_point(eos: str, a: float, b: float, R: float = 1.0):
