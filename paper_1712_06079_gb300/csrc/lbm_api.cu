@@ -121,7 +121,7 @@ struct lbm_ctx {
     void *tmp[2] = {nullptr, nullptr};
     void *qpad_tape[2] = {nullptr, nullptr};
     int tape_steps = -1, tape_C = 0;
-    bool tape_last_ready = false;   // the last segment's states are in their sweep slot (set by the forward)
+    bool tape_last_ready = false;   // the last two segments' states are in their sweep slots (set by the forward)
     // reverse sweep buffers, allocated with the tape: the states recomputed
     // inside a segment, the stencil field of every state of a segment, the
     // adjoint ping-pong, kernel scratch and the FP64 dL/dT slots
@@ -464,17 +464,20 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
     Model<T> m = model_of<T>(c);
     CK(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");
     CK(c, launch_init<T>(m, rho0, nullptr, nullptr, (T *)c->ckpt[0], c->stream), "init kernel");
-    // The last segment's states t0 + 1 .. N - 1 and the stencil fields of
-    // t0 .. N - 1 go straight into the reverse sweep's slot for it, which
-    // then needs no recompute.
+    // The states and stencil fields of the last two segments go straight
+    // into the reverse sweep's two slots (segment k's states k C + 1 .. and
+    // fields k C .. in slot k & 1), so the sweep starts with no recompute.
     const int K = (nsteps - 1) / C, t0 = K * C, sl = K & 1, nseg = C > 1 ? C - 1 : 0;
+    const int tp = K >= 1 ? t0 - C : t0;   // the first step of the taped segments
     auto fbuf = [&](int t) -> void * {   // where state t (>= 1) goes
         if (t % C == 0) return c->ckpt[t / C];
         if (t > t0 && t < nsteps) return c->seg[sl * nseg + (t - t0 - 1)];
+        if (t > tp && t < t0) return c->seg[(1 - sl) * nseg + (t - tp - 1)];
         return c->tmp[t & 1];
     };
     auto qbuf = [&](int t) -> void * {   // the stencil field of state t
         if (t >= t0 && t < nsteps) return c->segq[sl * C + (t - t0)];
+        if (t >= tp && t < t0) return c->segq[(1 - sl) * C + (t - tp)];
         return c->fused ? c->qpad_tape[t & 1] : c->q;
     };
     if (c->fused)
@@ -562,15 +565,17 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     if (e == cudaSuccess) e = cudaEventRecord(c->adj_done[0], as);   // orders rstream after the seed
     if (e == cudaSuccess) e = cudaEventRecord(c->adj_done[1], as);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->rstream, c->adj_done[K & 1], 0);
-    if (e == cudaSuccess && !c->tape_last_ready) e = recompute(K, K & 1, c->rstream);   // left by the forward
+    // segments K and K - 1 are left in their slots by the forward
+    const bool taped = c->tape_last_ready;
     c->tape_last_ready = false;   // the sweep reuses the slots
+    if (e == cudaSuccess && !taped) e = recompute(K, K & 1, c->rstream);
     if (e == cudaSuccess) e = cudaEventRecord(c->rec_done[K & 1], c->rstream);
     int li = 0;
     for (int k = K; k >= 0 && e == cudaSuccess; --k) {
         const int sl = k & 1;
         if (k >= 1) {
             e = cudaStreamWaitEvent(c->rstream, c->adj_done[(k - 1) & 1], 0);
-            if (e == cudaSuccess) e = recompute(k - 1, (k - 1) & 1, c->rstream);
+            if (e == cudaSuccess && !(taped && k == K)) e = recompute(k - 1, (k - 1) & 1, c->rstream);
             if (e == cudaSuccess) e = cudaEventRecord(c->rec_done[(k - 1) & 1], c->rstream);
         }
         if (e == cudaSuccess) e = cudaStreamWaitEvent(as, c->rec_done[sl], 0);
