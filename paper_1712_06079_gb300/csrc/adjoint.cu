@@ -26,22 +26,25 @@
 // the effective mass of Eq. 4 (dU/dG = psi^2 / 2).
 //   lambda_i(t) = (1 - omega) g_i + rho_bar + e_i . j_bar.
 //
-// Two tiled kernels per step.  Kernel A stages the stencil field of the
-// tile with its halo in shared memory (asynchronous copies) and does
-// everything up to D_bar, with the centre term already folded into rho_bar
-// and T_bar; it writes D_bar, the partial rho_bar and rho.  Kernel B stages
-// D_bar with its halo and finishes rho_bar, T_bar and lambda(t).  For tau = 1
-// (omega = 1) every lambda_i(t) is rho_bar + e_i . j_bar, so lambda is kept as
-// the three fields (rho_bar, jx_bar, jy_bar) instead of nine, staged in
-// shared memory with a one-cell halo for the pull g_i = lambda_i(x + e_i).
-// The HDM stencils run at a compile-time radius (26 in FP32, 40 in FP64)
-// over weights that are zero past the folded radius of the lattice; in the
-// padded FP32 layout each kernel forms the tile's derivatives once, in
-// recurrence form (hdm_window4), before its per-cell work.  The padded FP32
-// kernels are launched with programmatic serialization: A does its
-// state-only work (field staging, f, EOS terms, tile derivatives) while the
-// previous step's B finishes, and every read of a predecessor's output and
-// every write waits for it (griddepcontrol.wait).  T_bar
+// Two tiled kernels per step.  Kernel A does everything up to D_bar, with
+// the centre term already folded into rho_bar and T_bar; it writes D_bar, the
+// partial rho_bar and rho.  Kernel B stages D_bar with its halo and finishes
+// rho_bar, T_bar and lambda(t).  For tau = 1 (omega = 1) every lambda_i(t) is
+// rho_bar + e_i . j_bar, so lambda is kept as the three fields (rho_bar,
+// jx_bar, jy_bar) instead of nine, staged in shared memory with a one-cell
+// halo for the pull g_i = lambda_i(x + e_i).  On plain rows kernel A stages
+// the stencil field of its tile with the halo and differentiates it; in the
+// padded FP32 layout of the single-pass kernel it reads instead that kernel's
+// record of the state (rho, j and the derivatives D the forward step used,
+// written by the taped and the recomputed forward steps), so the reverse step
+// differentiates only D_bar.  The HDM stencils run at a compile-time radius
+// (26 in FP32, 40 in FP64) over weights that are zero past the folded radius
+// of the lattice; in the padded layout kernel B forms the tile's derivatives
+// once, in recurrence form (hdm_window4), before its per-cell work.  The
+// padded FP32 kernels are launched with programmatic serialization: A reads
+// the record and forms the forward quantities while the previous step's B
+// finishes, and every read of a predecessor's output and every write waits
+// for it (griddepcontrol.wait).  T_bar
 // terms are summed over each warp in the working precision (32 terms), then
 // in FP64 over the warps of a CTA into one slot per CTA (no atomics, so the
 // sum is reproducible), over the steps in the same slots, and over the slots
@@ -71,6 +74,22 @@ __device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x);
 __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rsqrt_fast(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_fast(double x) { return 1.0 / sqrt(x); }
+
+// e_i . (vx, vy) from the signs of e_i (no multiplications by 0 or 1)
+template <typename T>
+__device__ __forceinline__ T dot_e(int i, T vx, T vy) {
+    switch (i) {
+        case 1: return vx;
+        case 2: return vy;
+        case 3: return -vx;
+        case 4: return -vy;
+        case 5: return vx + vy;
+        case 6: return vy - vx;
+        case 7: return -(vx + vy);
+        case 8: return vx - vy;
+        default: return T(0);
+    }
+}
 
 // U (Eq. 8) with its derivatives in rho and in the model's scalar parameter
 // theta: with an equation of state U = k p_EOS - rho/3 and theta = T (Eq. 24,
@@ -146,7 +165,7 @@ struct AdjArgs {
     Model<T> m;
     T R;            // gas constant
     T aalp;         // a dalpha/dT
-    const T *f;     // state at t (nine unpadded fields)
+    const T *f;     // state at t (nine unpadded fields); padded layout: its record (five)
     // Every other field is addressed as base[k * stride + y * pitch + off + x].
     const T *q;     // stencil field of f; |q| = Phi (SC) or U (ZC)
     int qpitch, qoff;
@@ -296,7 +315,70 @@ __device__ __forceinline__ bool cta_wait_copies(uint64_t *bars, int nbar, int k,
     return true;
 }
 
-template <typename T, bool SC, bool CDM, bool TAU1, int KC, bool PAD>
+// The local adjoint of one cell's forcing and collision.  From g_i =
+// lambda_i(x + e_i) and the cell's forward quantities (rho, 1/rho, u, v, F,
+// D, Phi or U, s) it forms rho_bar without the transposed-derivative and EOS
+// terms, j_bar, D_bar and the centre part pc of Phi_bar (Shan-Chen).  With
+// feq_i(rho, v) = w_i rho (a + e_i.v (3 + 4.5 e_i.v)), a = 1 - 1.5 |v|^2,
+//   sum_i b_i dfeq_i/drho = sum_i b_i w_i (a + e_i.v (3 + 4.5 e_i.v)),
+//   sum_i b_i dfeq_i/dv = rho (sum_i b_i w_i e_i (3 + 9 e_i.v) - 3 v sum_i b_i w_i),
+// so one pass over the directions forms the weighted sums (e_i.v by its signs).
+template <typename T, bool SC, bool TAU1>
+__device__ __forceinline__ void adj_local(const T (&g)[kQ], T om1, T r, T inv, T ux, T uy, T vx, T vy, T Fx, T Fy,
+                                          T Dx, T Dy, T phi, T sgn, T &rb, T &jbx, T &jby, T &Dbx, T &Dby, T &pc) {
+    T G0 = T(0), Gx = T(0), Gy = T(0), Rv = T(0), Hx = T(0), Hy = T(0), Ru = T(0);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const T gw = g[i] * wq<T>(i);
+        G0 += gw;
+        if (i == 0) continue;
+        const T ev = dot_e(i, vx, vy);
+        const T gt = gw * (T(3) + T(9) * ev);
+        if (ex(i) == 1) Gx += gt;
+        if (ex(i) == -1) Gx -= gt;
+        if (ey(i) == 1) Gy += gt;
+        if (ey(i) == -1) Gy -= gt;
+        Rv += gw * ev * (T(3) + T(4.5) * ev);
+        if (!TAU1) {
+            const T eu = dot_e(i, ux, uy);
+            const T gu = gw * (T(3) + T(9) * eu);
+            if (ex(i) == 1) Hx += gu;
+            if (ex(i) == -1) Hx -= gu;
+            if (ey(i) == 1) Hy += gu;
+            if (ey(i) == -1) Hy -= gu;
+            Ru += gw * eu * (T(3) + T(4.5) * eu);
+        }
+    }
+    const T vv = vx * vx + vy * vy;
+    rb = (T(1) - T(1.5) * vv) * G0 + Rv;
+    const T vbx = r * (Gx - T(3) * vx * G0), vby = r * (Gy - T(3) * vy * G0);
+    T ubx = vbx, uby = vby;
+    if (!TAU1) {   // the f^eq(u) terms enter with the weights -(1 - omega) g_i
+        const T uu = ux * ux + uy * uy;
+        rb -= om1 * ((T(1) - T(1.5) * uu) * G0 + Ru);
+        ubx -= om1 * r * (Hx - T(3) * ux * G0);
+        uby -= om1 * r * (Hy - T(3) * uy * G0);
+    }
+    const T Fbx = vbx * inv, Fby = vby * inv;
+    rb -= (vbx * Fx + vby * Fy) * inv * inv;
+    jbx = ubx * inv;
+    jby = uby * inv;
+    rb -= (ubx * ux + uby * uy) * inv;
+    if (SC) {
+        Dbx = T(-2) * sgn * phi * Fbx;
+        Dby = T(-2) * sgn * phi * Fby;
+        pc = T(-2) * sgn * (Fbx * Dx + Fby * Dy);
+    } else {
+        Dbx = -Fbx;
+        Dby = -Fby;
+        pc = T(0);
+    }
+}
+
+// Kernel A on plain rows (FP64, and FP32 off the single-pass layout): the
+// stencil field is staged with its halo (element-wise asynchronous copies)
+// and differentiated here.
+template <typename T, bool SC, bool CDM, bool TAU1, int KC>
 __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(const AdjArgs<T> a) {
     constexpr int TX = AdjTile<T>::TX, TY = AdjTile<T>::TY, TYT = AdjTile<T>::TYT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -305,64 +387,29 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
     const long long n = (long long)nx * ny;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int hx = CDM ? 1 : (KC ? KC : m.kx), hy = CDM ? 1 : (KC ? KC : m.ky);
-    // staged field: S[ly * W + XS + lx] = q(x0 + lx, y0 - hy + ly); lambda tile
-    // L[(k * LH + ly) * LW + LS + lx] = lambda_k(x0 + lx, y0 - 1 + ly)
-    const int W = PAD ? TX + 2 * XO : TX + 2 * hx, H = TY + 2 * hy;
-    const int XS = PAD ? XO : hx;
-    constexpr int LW = PAD ? TX + 2 * LO : TX + 2, LH = TY + 2, LS = PAD ? LO : 1;
+    // staged field: S[ly * W + hx + lx] = q(x0 + lx, y0 - hy + ly); lambda tile
+    // L[(k * LH + ly) * LW + 1 + lx] = lambda_k(x0 + lx, y0 - 1 + ly)
+    const int W = TX + 2 * hx, H = TY + 2 * hy;
+    constexpr int LW = TX + 2, LH = TY + 2;
     T *S = reinterpret_cast<T *>(smem_raw);
     T *L = S + W * H;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(L + (TAU1 ? 3 * LW * LH : 0));  // PAD: field, lambda
-    // padded FP32 tiles: the field's derivatives over the tile, formed once
-    constexpr bool RECUR = PAD && KC == 26 && !CDM;
-    static_assert(!RECUR || TX * TYT >= 512, "the tile phase takes one work item per thread");
-    T *DT = reinterpret_cast<T *>(bars + 2);
-    if constexpr (PAD) {
-        const int tid = threadIdx.x + TX * threadIdx.y;
-        if (tid == 0) {
-            ptx::mbar_init(&bars[0], 1);
-            ptx::mbar_init(&bars[1], 1);
-            ptx::fence_mbar_init();
-        }
-        __syncthreads();
-        if (tid < 32) {  // warp 0 issues one bulk copy per staged row
-            const int ncore = min(TX, nx - x0);                 // a multiple of 4
-            const uint32_t wide = (ncore + 2 * XO) * sizeof(T), core = ncore * sizeof(T);
-            const uint32_t lrow = (ncore + 2 * LO) * sizeof(T);
-            if (tid == 0) {
-                ptx::mbar_arrive_expect_tx(&bars[0], TY * wide + 2 * hy * core);
-                ptx::mbar_arrive_expect_tx(&bars[1], TAU1 ? 3 * LH * lrow : 0);
-            }
-            __syncwarp();
-            for (int ly = tid; ly < H; ly += 32) {
-                const T *src = a.q + (long long)wrap_index(y0 - hy + ly, ny) * a.qpitch + a.qoff + x0;
-                if (ly >= hy && ly < hy + TY) ptx::bulk_g2s(S + ly * W, src - XO, wide, &bars[0]);
-                else ptx::bulk_g2s(S + ly * W + XO, src, core, &bars[0]);
-            }
-        }
-        // The next kernel (B of this step) may begin launching; lambda, the
-        // previous B's output, is staged only after griddep_wait below.
-        ptx::griddep_launch_dependents();
+    // element-wise: a cross for the separable HDM, the full box for the CDM
+    if (CDM) {
+        stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, 0, W, 0, H);
     } else {
-        // element-wise: a cross for the separable HDM, the full box for the CDM
-        if (CDM) {
-            stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, 0, W, 0, H);
-        } else {
-            stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, 0, W, hy, hy + TY);
-            stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, hx, hx + TX, 0, hy);
-            stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, hx, hx + TX, hy + TY, H);
-        }
-        if (TAU1)
-            for (int k = 0; k < 3; ++k)
-                stage_rect<T, TX, TYT>(L + k * LW * LH, LW, a.lam + k * a.lstride, a.lpitch, a.loff, nx, ny, x0 - 1,
-                                       y0 - 1, 0, LW, 0, LH);
-        ptx::cp_async_wait_all();
-        __syncthreads();
+        stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, 0, W, hy, hy + TY);
+        stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, hx, hx + TX, 0, hy);
+        stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, hx, hx + TX, hy + TY, H);
     }
+    if (TAU1)
+        for (int k = 0; k < 3; ++k)
+            stage_rect<T, TX, TYT>(L + k * LW * LH, LW, a.lam + k * a.lstride, a.lpitch, a.loff, nx, ny, x0 - 1,
+                                   y0 - 1, 0, LW, 0, LH);
+    ptx::cp_async_wait_all();
+    __syncthreads();
 
-    // Every thread runs the cell loop (the waits are CTA-wide); cells outside
-    // the lattice compute on a clamped index and store nothing.  With the bulk
-    // copies in flight, the cell's own loads and the EOS terms come first.
+    // Every thread runs the cell loop; cells outside the lattice compute on a
+    // clamped index and store nothing.
     T tacc = T(0);
     const int lx = threadIdx.x, x = x0 + lx;
     const int xc = min(x, nx - 1);
@@ -372,23 +419,24 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
         const int ly = threadIdx.y + k * TYT, y = y0 + ly;
         const bool valid = x < nx && y < ny;
         const int yc = min(y, ny - 1);
-        const long long c = (long long)yc * nx + xc;
         const int yp = yc + 1 == ny ? 0 : yc + 1, ym = yc == 0 ? ny - 1 : yc - 1;
+        const long long c = (long long)yc * nx + xc;
         T r = T(0), jx = T(0), jy = T(0);
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
             const T fi = a.f[i * n + c];
             r += fi;
-            jx += T(ex(i)) * fi;
-            jy += T(ey(i)) * fi;
+            if (ex(i) == 1) jx += fi;
+            if (ex(i) == -1) jx -= fi;
+            if (ey(i) == 1) jy += fi;
+            if (ey(i) == -1) jy -= fi;
         }
         T kappa, theta, sgn;
         eos_coeffs<T, SC>(m, a.R, a.aalp, r, kappa, theta, sgn);
-        const T inv = T(1) / r;
+        const T inv = rcp_fast(r);
         const T ux = jx * inv, uy = jy * inv;
-        if (PAD && k == 0 && !cta_wait_copies(bars, 2, 0, a.err)) return;
         // D of the field at the cell (Eq. 15 / 20) from the staged tile
-        const T *row = S + (ly + hy) * W + (XS + lx);
+        const T *row = S + (ly + hy) * W + (hx + lx);
         auto fld = [&](int o) { return SC ? fabs(row[o]) : row[o]; };
         T Dx, Dy;
         if (CDM) {
@@ -396,29 +444,6 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
             const T ne = fld(W + 1), nw = fld(W - 1), se = fld(-W + 1), sw = fld(-W - 1);
             Dx = T(1.0 / 3.0) * (e - w) + T(1.0 / 12.0) * ((ne + se) - (nw + sw));
             Dy = T(1.0 / 3.0) * (nn - s) + T(1.0 / 12.0) * ((ne + nw) - (se + sw));
-        } else if constexpr (RECUR) {
-            if (k == 0) {
-                tile_hdm<SC>(S + hy * W, W, S, W, XO, DT, m, a.r, a.r5, a.r25);
-                __syncthreads();
-                // Everything so far reads only the state and its field, written
-                // two or more launches back.  lambda (and every write of this
-                // kernel) waits for the preceding kernel: with programmatic
-                // launch the previous reverse step's B may still be running.
-                ptx::griddep_wait();
-                if (TAU1 && threadIdx.x + TX * threadIdx.y < 32) {
-                    const int tid = threadIdx.x + TX * threadIdx.y;
-                    const int ncore = min(TX, nx - x0);
-                    const uint32_t lrow = (ncore + 2 * LO) * sizeof(T);
-                    for (int r = tid; r < 3 * LH; r += 32) {
-                        const int kk = r / LH, ry = r - kk * LH;
-                        const T *src = a.lam + kk * a.lstride + (long long)wrap_index(y0 - 1 + ry, ny) * a.lpitch +
-                                       a.loff + x0;
-                        ptx::bulk_g2s(L + r * LW, src - LO, lrow, &bars[1]);
-                    }
-                }
-            }
-            Dx = DT[ly * TX + lx];
-            Dy = DT[TX * TY + ly * TX + lx];
         } else {
             Dx = stencil<T, KC, SC, false>(row, 1, m);
             Dy = stencil<T, KC, SC, true>(row, W, m);
@@ -428,67 +453,171 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
         if (SC) { Fx = T(-2) * sgn * phi * Dx; Fy = T(-2) * sgn * phi * Dy; }
         else { Fx = -Dx; Fy = -Dy; }
         const T vx = ux + Fx * inv, vy = uy + Fy * inv;
-        const T uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
-        if (PAD && TAU1 && k == 0 && !cta_wait_copies(bars, 2, 1, a.err)) return;
         T g[kQ];
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {  // g_i = lambda_i(x + e_i)
-            if (TAU1) {
-                const int o = (ly + 1 + ey(i)) * LW + (LS + lx + ex(i));
-                g[i] = L[o] + T(ex(i)) * L[LW * LH + o] + T(ey(i)) * L[2 * LW * LH + o];
+            if (TAU1) {   // lambda_i = rho_bar + e_i . j_bar, by the signs of e_i
+                const int o = (ly + 1 + ey(i)) * LW + (1 + lx + ex(i));
+                T gi = L[o];
+                if (ex(i) == 1) gi += L[LW * LH + o];
+                if (ex(i) == -1) gi -= L[LW * LH + o];
+                if (ey(i) == 1) gi += L[2 * LW * LH + o];
+                if (ey(i) == -1) gi -= L[2 * LW * LH + o];
+                g[i] = gi;
             } else {
                 const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : xc);
                 const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : yc);
                 g[i] = __ldg(a.lam + i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs);
             }
         }
-        const T om1 = T(1) - m.omega;
-        T rb = T(0), ubx = T(0), uby = T(0), vbx = T(0), vby = T(0);
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-            const T exi = T(ex(i)), eyi = T(ey(i)), w = wq<T>(i);
-            const T ev = exi * vx + eyi * vy;
-            const T feq_v = r * w * (T(1) + T(3) * ev + T(4.5) * ev * ev - T(1.5) * vv);
-            const T cv = g[i] * r * w;
-            rb += g[i] * feq_v * inv;
-            vbx += cv * (T(3) * exi + T(9) * ev * exi - T(3) * vx);
-            vby += cv * (T(3) * eyi + T(9) * ev * eyi - T(3) * vy);
-            if (!TAU1) {
-                const T eu = exi * ux + eyi * uy;
-                const T feq_u = r * w * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
-                const T ai = -om1 * g[i], cu = ai * r * w;
-                rb += ai * feq_u * inv;
-                ubx += cu * (T(3) * exi + T(9) * eu * exi - T(3) * ux);
-                uby += cu * (T(3) * eyi + T(9) * eu * eyi - T(3) * uy);
-            }
-        }
-        ubx += vbx;
-        uby += vby;
-        const T Fbx = vbx * inv, Fby = vby * inv;
-        rb -= (vbx * Fx + vby * Fy) * inv * inv;
-        const T jbx = ubx * inv, jby = uby * inv;
-        rb -= (ubx * ux + uby * uy) * inv;
-        T Dbx, Dby;
+        T rb, jbx, jby, Dbx, Dby, pc;
+        adj_local<T, SC, TAU1>(g, T(1) - m.omega, r, inv, ux, uy, vx, vy, Fx, Fy, Dx, Dy, phi, sgn, rb, jbx, jby,
+                               Dbx, Dby, pc);
         if (SC) {
-            Dbx = T(-2) * sgn * phi * Fbx;
-            Dby = T(-2) * sgn * phi * Fby;
-            const T pc = T(-2) * sgn * (Fbx * Dx + Fby * Dy);  // centre part of Phi_bar
             rb += pc * kappa;
             if (valid) tacc += pc * theta;
-        } else {
-            Dbx = -Fbx;
-            Dby = -Fby;
         }
         if (valid) {
             T *drow = a.aux + (long long)y * a.dpitch + a.doff;
-            store_field<T, PAD>(drow, x, nx, Dbx);
-            store_field<T, PAD>(drow + a.dstride, x, nx, Dby);
+            drow[x] = Dbx;
+            drow[a.dstride + x] = Dby;
             drow[2 * a.dstride + x] = rb;
             drow[3 * a.dstride + x] = r;
             if (TAU1) {
                 T *lrow = a.lam_out + (long long)y * a.lpitch + a.loff;
-                store_field<T, PAD>(lrow + a.lstride, x, nx, jbx);
-                store_field<T, PAD>(lrow + 2 * a.lstride, x, nx, jby);
+                lrow[a.lstride + x] = jbx;
+                lrow[2 * a.lstride + x] = jby;
+            } else {
+                drow[4 * a.dstride + x] = jbx;
+                drow[5 * a.dstride + x] = jby;
+            }
+        }
+    }
+    if (SC) block_sum_into(tacc, a.Tpart + blockIdx.x + gridDim.x * blockIdx.y);
+}
+
+// Kernel A in the padded FP32 layout of the single-pass kernel.  The forward
+// quantities come from that kernel's record of the state (rho, j and the HDM
+// derivatives D it used), so nothing is differentiated here: the kernel reads
+// the record and the field at each of its cells, and for tau = 1 stages the
+// lambda tile (three fields, one-cell halo) by per-row bulk copies.  Launched
+// with programmatic serialization: everything before griddep_wait reads only
+// the record and the field, written at least one launch back on another
+// stream (ordered by an event); lambda and every write wait for the previous
+// reverse step's kernel B.
+template <bool SC, bool TAU1>
+__global__ void __launch_bounds__(AdjTile<float>::TX *AdjTile<float>::TYT) adj_a_rec_kernel(const AdjArgs<float> a) {
+    constexpr int TX = AdjTile<float>::TX, TY = AdjTile<float>::TY, TYT = AdjTile<float>::TYT, NC = TY / TYT;
+    constexpr int LW = TX + 2 * LO, LH = TY + 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // lambda tile L[(k * LH + ly) * LW + LO + lx] = lambda_k(x0 + lx, y0 - 1 + ly)
+    float *L = reinterpret_cast<float *>(smem_raw);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(L + (TAU1 ? 3 * LW * LH : 0));
+    const Model<float> &m = a.m;
+    const int nx = m.nx, ny = m.ny;
+    const long long n = (long long)nx * ny;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int ncore = min(TX, nx - x0);   // a multiple of 4
+    const uint32_t lrow = (ncore + 2 * LO) * sizeof(float);
+    if (TAU1) {
+        if (tid == 0) {
+            ptx::mbar_init(bar, 1);
+            ptx::fence_mbar_init();
+            ptx::mbar_arrive_expect_tx(bar, 3 * LH * lrow);
+        }
+        __syncthreads();
+    }
+    // the next kernel (B of this step) may begin launching
+    ptx::griddep_launch_dependents();
+
+    const int lx = threadIdx.x, x = x0 + lx;
+    const int xc = min(x, nx - 1);
+    float r_k[NC], jx_k[NC], jy_k[NC], Dx_k[NC], Dy_k[NC], q_k[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int yc = min(y0 + (int)threadIdx.y + k * TYT, ny - 1);
+        const long long c = (long long)yc * nx + xc;
+        r_k[k] = a.f[c];
+        jx_k[k] = a.f[n + c];
+        jy_k[k] = a.f[2 * n + c];
+        Dx_k[k] = a.f[3 * n + c];
+        Dy_k[k] = a.f[4 * n + c];
+        q_k[k] = a.q[(long long)yc * a.qpitch + a.qoff + xc];
+    }
+    float inv_k[NC], ux_k[NC], uy_k[NC], vx_k[NC], vy_k[NC], Fx_k[NC], Fy_k[NC], phi_k[NC], sgn_k[NC];
+    float kap_k[NC], th_k[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        eos_coeffs<float, SC>(m, a.R, a.aalp, r_k[k], kap_k[k], th_k[k], sgn_k[k]);
+        const float inv = rcp_fast(r_k[k]);
+        const float phi = SC ? fabsf(q_k[k]) : q_k[k];   // Phi (SC) or U (ZC)
+        float Fx, Fy;
+        if (SC) { Fx = -2.0f * sgn_k[k] * phi * Dx_k[k]; Fy = -2.0f * sgn_k[k] * phi * Dy_k[k]; }
+        else { Fx = -Dx_k[k]; Fy = -Dy_k[k]; }
+        inv_k[k] = inv;
+        ux_k[k] = jx_k[k] * inv;
+        uy_k[k] = jy_k[k] * inv;
+        vx_k[k] = ux_k[k] + Fx * inv;
+        vy_k[k] = uy_k[k] + Fy * inv;
+        Fx_k[k] = Fx;
+        Fy_k[k] = Fy;
+        phi_k[k] = phi;
+    }
+    ptx::griddep_wait();
+    if (TAU1) {
+        if (tid < 32) {  // warp 0 issues one bulk copy per lambda row
+            for (int rr = tid; rr < 3 * LH; rr += 32) {
+                const int kk = rr / LH, ry = rr - kk * LH;
+                const float *src = a.lam + kk * a.lstride + (long long)wrap_index(y0 - 1 + ry, ny) * a.lpitch +
+                                   a.loff + x0;
+                ptx::bulk_g2s(L + rr * LW, src - LO, lrow, bar);
+            }
+        }
+        if (!cta_wait_copies(bar, 1, 0, a.err)) return;
+    }
+    float tacc = 0.0f;
+    const int xp = xc + 1 == nx ? 0 : xc + 1, xm = xc == 0 ? nx - 1 : xc - 1;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int ly = threadIdx.y + k * TYT, y = y0 + ly;
+        const bool valid = x < nx && y < ny;
+        const int yc = min(y, ny - 1);
+        const int yp = yc + 1 == ny ? 0 : yc + 1, ym = yc == 0 ? ny - 1 : yc - 1;
+        float g[kQ];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {  // g_i = lambda_i(x + e_i)
+            if (TAU1) {   // lambda_i = rho_bar + e_i . j_bar, by the signs of e_i
+                const int o = (ly + 1 + ey(i)) * LW + (LO + lx + ex(i));
+                float gi = L[o];
+                if (ex(i) == 1) gi += L[LW * LH + o];
+                if (ex(i) == -1) gi -= L[LW * LH + o];
+                if (ey(i) == 1) gi += L[2 * LW * LH + o];
+                if (ey(i) == -1) gi -= L[2 * LW * LH + o];
+                g[i] = gi;
+            } else {
+                const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : xc);
+                const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : yc);
+                g[i] = __ldg(a.lam + i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs);
+            }
+        }
+        float rb, jbx, jby, Dbx, Dby, pc;
+        adj_local<float, SC, TAU1>(g, 1.0f - m.omega, r_k[k], inv_k[k], ux_k[k], uy_k[k], vx_k[k], vy_k[k], Fx_k[k],
+                                   Fy_k[k], Dx_k[k], Dy_k[k], phi_k[k], sgn_k[k], rb, jbx, jby, Dbx, Dby, pc);
+        if (SC) {
+            rb += pc * kap_k[k];
+            if (valid) tacc += pc * th_k[k];
+        }
+        if (valid) {
+            float *drow = a.aux + (long long)y * a.dpitch + a.doff;
+            store_field<float, true>(drow, x, nx, Dbx);
+            store_field<float, true>(drow + a.dstride, x, nx, Dby);
+            drow[2 * a.dstride + x] = rb;
+            drow[3 * a.dstride + x] = r_k[k];
+            if (TAU1) {
+                float *lrow = a.lam_out + (long long)y * a.lpitch + a.loff;
+                store_field<float, true>(lrow + a.lstride, x, nx, jbx);
+                store_field<float, true>(lrow + 2 * a.lstride, x, nx, jby);
             } else {
                 drow[4 * a.dstride + x] = jbx;
                 drow[5 * a.dstride + x] = jby;
@@ -551,21 +680,33 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
         __syncthreads();
     }
 
+    // the density and partial rho_bar of all of the thread's cells first (their
+    // loads in flight together), with the EOS terms, while the copies land
+    constexpr int NC = TY / TYT;
     T tacc = T(0);
     const int lx = threadIdx.x, x = x0 + lx;
     const int xc = min(x, nx - 1);
     const int xp = xc + 1 == nx ? 0 : xc + 1, xm = xc == 0 ? nx - 1 : xc - 1;
+    T rk[NC], rb0k[NC], kap_k[NC], th_k[NC];
 #pragma unroll
-    for (int k = 0; k < TY / TYT; ++k) {
+    for (int k = 0; k < NC; ++k) {
+        const T *drow = a.aux + (long long)min(y0 + (int)threadIdx.y + k * TYT, ny - 1) * a.dpitch + a.doff;
+        rk[k] = drow[3 * a.dstride + xc];
+        rb0k[k] = drow[2 * a.dstride + xc];
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        T sgn;
+        eos_coeffs<T, SC>(m, a.R, a.aalp, rk[k], kap_k[k], th_k[k], sgn);
+    }
+    if (PAD && !cta_wait_copies(bars, 1, 0, a.err)) return;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
         const int ly = threadIdx.y + k * TYT, y = y0 + ly;
         const bool valid = x < nx && y < ny;
         const int yc = min(y, ny - 1);
         const T *drow = a.aux + (long long)yc * a.dpitch + a.doff;
-        const T r = drow[3 * a.dstride + xc];
-        const T rb0 = drow[2 * a.dstride + xc];
-        T kappa, theta, sgn;
-        eos_coeffs<T, SC>(m, a.R, a.aalp, r, kappa, theta, sgn);
-        if (PAD && k == 0 && !cta_wait_copies(bars, 1, 0, a.err)) return;
+        const T rb0 = rb0k[k], kappa = kap_k[k], theta = th_k[k];
         // the transposed derivative: Dx^T = -Dx, Dy^T = -Dy
         const T *rx = SX + (ly + oy) * WX + (lx + XS);
         const T *ry = SY + (ly + hy) * WY + (lx + ox);
@@ -601,7 +742,12 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
                 const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
                 const int dys = ey(i) == 1 ? yp_of(y, ny) : (ey(i) == -1 ? ym_of(y, ny) : y);
                 const T gi = a.lam[i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs];
-                lrow[i * a.lstride + x] = om1 * gi + rb + T(ex(i)) * jbx + T(ey(i)) * jby;
+                T li = om1 * gi + rb;
+                if (ex(i) == 1) li += jbx;
+                if (ex(i) == -1) li -= jbx;
+                if (ey(i) == 1) li += jby;
+                if (ey(i) == -1) li -= jby;
+                lrow[i * a.lstride + x] = li;
             }
         }
     }
@@ -701,15 +847,18 @@ cudaError_t launch_adj_t(const AdjArgs<T> &a, bool overlap_prev, cudaStream_t s)
     constexpr int TX = AdjTile<T>::TX, TY = AdjTile<T>::TY, TYT = AdjTile<T>::TYT;
     const int hx = CDM ? 1 : (KC ? KC : a.m.kx), hy = CDM ? 1 : (KC ? KC : a.m.ky);
     const int XS = PAD ? XO : hx;
-    const int LW = PAD ? TX + 2 * LO : TX + 2;
-    constexpr bool RECUR = PAD && KC == 26 && !CDM;   // tile derivatives after the barriers
+    constexpr bool RECUR = PAD && KC == 26 && !CDM;   // B: tile derivatives after the barrier
     const size_t dt = RECUR ? 2 * sizeof(T) * TX * TY : 0;
-    const size_t smem_a = sizeof(T) * ((size_t)(TX + 2 * XS) * (TY + 2 * hy) + (TAU1 ? 3 * LW * (TY + 2) : 0)) +
-                          (PAD ? 2 * sizeof(uint64_t) : 0) + dt;
+    // A: in the padded layout the lambda tile (tau = 1) and its barrier; else
+    // the field with its halo and the lambda tile
+    const size_t smem_a = PAD ? (TAU1 ? sizeof(T) * 3 * (TX + 2 * LO) * (TY + 2) + sizeof(uint64_t) : 0)
+                              : sizeof(T) * ((size_t)(TX + 2 * hx) * (TY + 2 * hy) + (TAU1 ? 3 * (TX + 2) * (TY + 2) : 0));
     const size_t smem_b = (CDM ? sizeof(T) * 2 * (size_t)(TX + 2) * (TY + 2)
                                : sizeof(T) * ((size_t)(TX + 2 * XS) * TY + (size_t)TX * (TY + 2 * hy))) +
                           (PAD ? 2 * sizeof(uint64_t) : 0) + dt;
-    auto ka = adj_a_kernel<T, SC, CDM, TAU1, KC, PAD>;
+    void (*ka)(const AdjArgs<T>) = nullptr;
+    if constexpr (PAD) ka = adj_a_rec_kernel<SC, TAU1>;   // T = float
+    else ka = adj_a_kernel<T, SC, CDM, TAU1, KC>;
     auto kb = adj_b_kernel<T, SC, CDM, TAU1, KC, PAD>;
     // the shared-memory limits, set once per device and size (a driver call per
     // launch otherwise); the largest size set so far covers every smaller one
@@ -730,8 +879,9 @@ cudaError_t launch_adj_t(const AdjArgs<T> &a, bool overlap_prev, cudaStream_t s)
     if (e != cudaSuccess) return e;
     const dim3 grid = adj_grid<T>(a.m.nx, a.m.ny), block(TX, TYT);
     // the padded FP32 kernels wait for their predecessor's output (griddep_wait),
-    // so they may overlap it: A with the previous step's B unless the state
-    // was just recomputed (A stages that state's field), B always with its A
+    // so they may overlap it: A with the previous step's B unless an event wait
+    // on the recompute's stream precedes it (the first step of a segment), B
+    // always with its A
     e = launch_pdl(PAD && overlap_prev, ka, grid, block, smem_a, s, a);
     if (e != cudaSuccess) return e;
     AdjArgs<T> b = a;

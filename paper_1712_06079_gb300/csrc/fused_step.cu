@@ -63,6 +63,11 @@
 // rho minus the other eight, so the FP32 collision conserves mass up to
 // unbiased rounding.  For tau = 1 the BGK term vanishes exactly and the
 // equilibrium at u is skipped.
+//
+// The TAPE variant (used by the reverse mode's taped and recomputed forward
+// steps, never for walls) also writes, for every cell of its own rows, the
+// record of f(t) the adjoint step reads in place of f(t) and the stencil
+// field: rho and j (Eq. 3) and the two HDM derivatives, five planes of nx ny.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -105,6 +110,7 @@ struct FusedArgs {
     float *fout;
     const float *qin;   // padded field of f(t): row pitch qpitch, column x at x + QG
     float *qout;        // padded field of f(t+1)
+    float *rec;         // TAPE: record of f(t), planes rho, jx, jy, Dx, Dy (nx ny each)
     int *err;
     int qpitch;         // nx + 2 * QG
     int seg_h;          // rows per CTA segment
@@ -243,8 +249,9 @@ __device__ __forceinline__ bool range_ok(long long off, long long len, long long
     return in_bounds(off, n - len + 1, err);
 }
 
-template <bool SC, bool TAU1, int EOS, bool WALLS>
+template <bool SC, bool TAU1, int EOS, bool WALLS, bool TAPE = false>
 __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_constant__ FusedArgs A) {
+    static_assert(!(TAPE && WALLS), "the reverse mode takes periodic lattices");
     extern __shared__ __align__(128) unsigned char smem[];
     float *qn = reinterpret_cast<float *>(smem);               // [QRING][NW]
     float *qw = reinterpret_cast<float *>(smem + kOffQw);      // [2][SLAB][WW]
@@ -464,6 +471,18 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 dy[1] = fmaf(A.w1y, mag(qa.y) - mag(qb.y), A.w2y * (Q.y - P.y));
                 dy[2] = fmaf(A.w1y, mag(qa.z) - mag(qb.z), A.w2y * (Q.z - P.z));
                 dy[3] = fmaf(A.w1y, mag(qa.w) - mag(qb.w), A.w2y * (Q.w - P.w));
+            }
+            if constexpr (TAPE) {   // the record of f(t) at the lane's 4 cells of an own row
+                if (interior && yc >= ys && yc < ys + hseg) {
+                    float4 *rp = reinterpret_cast<float4 *>(A.rec + (long long)yc * nx + xg);
+                    if (range_ok(rp - reinterpret_cast<float4 *>(A.rec), 4LL * A.n4 + 1, 5LL * A.n4, A.err)) {
+                        rp[0] = make_float4(r2[0].x, r2[0].y, r2[1].x, r2[1].y);
+                        rp[A.n4] = make_float4(jx2[0].x, jx2[0].y, jx2[1].x, jx2[1].y);
+                        rp[2 * A.n4] = make_float4(jy2[0].x, jy2[0].y, jy2[1].x, jy2[1].y);
+                        rp[3 * A.n4] = make_float4(dx[0], dx[1], dx[2], dx[3]);
+                        rp[4 * A.n4] = make_float4(dy[0], dy[1], dy[2], dy[3]);
+                    }
+                }
             }
             // force and the two velocities of the forcing (Eq. 10, 22 / 7)
             float2 ux[2], uy[2], vx[2], vy[2], au[2], av[2], moved[2];
@@ -685,13 +704,15 @@ cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float 
 }
 
 cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, const float *qin, float *fout,
-                              float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl) {
+                              float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl, float *rec) {
+    if (rec && m.walls) return cudaErrorInvalidValue;
     FusedArgs a;
     a.m = m;
     a.f = f;
     a.fout = fout;
     a.qin = qin;
     a.qout = qout;
+    a.rec = rec;
     a.err = err;
     a.qpitch = fused_q_pitch(m.nx);
     a.seg_h = seg_rows;
@@ -711,7 +732,12 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     const bool tau1 = m.omega == 1.0f;
     void (*kern)(const FusedArgs) = nullptr;
 #define LBM_PICK(E)                                                                                        \
-    if (m.walls)                                                                                           \
+    if (rec)                                                                                               \
+        kern = sc ? (tau1 ? fused_step_kernel<true, true, E, false, true>                                  \
+                          : fused_step_kernel<true, false, E, false, true>)                                \
+                  : (tau1 ? fused_step_kernel<false, true, E, false, true>                                 \
+                          : fused_step_kernel<false, false, E, false, true>);                              \
+    else if (m.walls)                                                                                      \
         kern = sc ? (tau1 ? fused_step_kernel<true, true, E, true> : fused_step_kernel<true, false, E, true>) \
                   : (tau1 ? fused_step_kernel<false, true, E, true> : fused_step_kernel<false, false, E, true>); \
     else                                                                                                   \

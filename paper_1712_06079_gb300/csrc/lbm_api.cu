@@ -123,10 +123,11 @@ struct lbm_ctx {
     int tape_steps = -1, tape_C = 0;
     bool tape_last_ready = false;   // the last two segments' states are in their sweep slots (set by the forward)
     // reverse sweep buffers, allocated with the tape: the states recomputed
-    // inside a segment, the stencil field of every state of a segment, the
-    // adjoint ping-pong, kernel scratch and the FP64 dL/dT slots
+    // inside a segment (single-pass contexts: the forward kernel's record of
+    // every state of a segment), the stencil field of every state of a
+    // segment, the adjoint ping-pong, kernel scratch and the FP64 dL/dT slots
     // (two sets: the recompute of one segment runs on rstream while the
-    // adjoint steps of the next later segment run on the context's stream)
+    // adjoint steps of the next later segment run on astream)
     std::vector<void *> seg, segq;
     cudaStream_t rstream = nullptr;
     cudaStream_t astream = nullptr;   // the adjoint steps
@@ -393,12 +394,14 @@ void free_tape(lbm_ctx *c) {
 // One forward step from state `src` to `dst` (explicit buffers).  Single-pass
 // path: qsrc holds the padded stencil field of src (valid on entry) and qdst
 // receives that of dst.  Two-pass path: the potential of src is formed into
-// qsrc first (qdst unused).
+// qsrc first (qdst unused).  rec (single-pass): where the record of src goes,
+// or nullptr.
 template <typename T>
-cudaError_t tape_step(lbm_ctx *c, const Model<T> &m, const void *src, void *dst, void *qsrc, void *qdst) {
+cudaError_t tape_step(lbm_ctx *c, const Model<T> &m, const void *src, void *dst, void *qsrc, void *qdst,
+                      float *rec) {
     if (c->fused)
         return launch_fused_step(*(const Model<float> *)&m, is_sc(c), (const float *)src, (const float *)qsrc,
-                                 (float *)dst, (float *)qdst, c->err, seg_rows_of(c), c->stream);
+                                 (float *)dst, (float *)qdst, c->err, seg_rows_of(c), c->stream, true, rec);
     cudaError_t e = launch_potential<T>(m, is_sc(c), (const T *)src, (T *)qsrc, c->err, c->stream);
     if (e != cudaSuccess) return e;
     return launch_collide<T>(m, is_sc(c), is_cdm(c), (const T *)src, (const T *)qsrc, (T *)dst, c->stream);
@@ -439,9 +442,12 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
             const AdjLayout lay = adjoint_layout(c->p.nx, c->p.ny, c->fused, tau1);
             const size_t lbytes = (size_t)lay.nlam * lay.lstride * sizeof(T);
             bool ok = true;
-            c->seg.assign(2 * (C > 1 ? C - 1 : 0), nullptr);
+            // single-pass contexts keep the forward kernel's record of every state
+            // of a segment (five planes); the others keep the states after the first
+            const size_t sbytes = c->fused ? (size_t)5 * c->n * sizeof(float) : fbytes;
+            c->seg.assign(c->fused ? 2 * C : 2 * (C > 1 ? C - 1 : 0), nullptr);
             c->segq.assign(2 * C, nullptr);
-            for (auto &p : c->seg) ok = ok && dev_alloc(&p, fbytes) == cudaSuccess;
+            for (auto &p : c->seg) ok = ok && dev_alloc(&p, sbytes) == cudaSuccess;
             for (auto &p : c->segq) ok = ok && dev_alloc(&p, qbytes) == cudaSuccess;
             // equal priorities: either stream favoured over the other (tried both
             // ways) lets it starve the other and loses the overlap
@@ -464,16 +470,22 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
     Model<T> m = model_of<T>(c);
     CK(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");
     CK(c, launch_init<T>(m, rho0, nullptr, nullptr, (T *)c->ckpt[0], c->stream), "init kernel");
-    // The states and stencil fields of the last two segments go straight
-    // into the reverse sweep's two slots (segment k's states k C + 1 .. and
-    // fields k C .. in slot k & 1), so the sweep starts with no recompute.
+    // What the reverse sweep needs of the last two segments goes straight
+    // into its two slots, so the sweep starts with no recompute: segment k's
+    // stencil fields of states k C .. in slot k & 1, and its states k C + 1 ..
+    // (single-pass contexts: the records of states k C .., the states
+    // themselves staying in the scratch pair).
     const int K = (nsteps - 1) / C, t0 = K * C, sl = K & 1, nseg = C > 1 ? C - 1 : 0;
     const int tp = K >= 1 ? t0 - C : t0;   // the first step of the taped segments
     auto fbuf = [&](int t) -> void * {   // where state t (>= 1) goes
         if (t % C == 0) return c->ckpt[t / C];
-        if (t > t0 && t < nsteps) return c->seg[sl * nseg + (t - t0 - 1)];
-        if (t > tp && t < t0) return c->seg[(1 - sl) * nseg + (t - tp - 1)];
+        if (!c->fused && t > t0 && t < nsteps) return c->seg[sl * nseg + (t - t0 - 1)];
+        if (!c->fused && t > tp && t < t0) return c->seg[(1 - sl) * nseg + (t - tp - 1)];
         return c->tmp[t & 1];
+    };
+    auto rbuf = [&](int t) -> float * {   // where the record of state t goes (single-pass)
+        if (!c->fused || t < tp) return nullptr;
+        return (float *)c->seg[((t / C) & 1) * C + t % C];
     };
     auto qbuf = [&](int t) -> void * {   // the stencil field of state t
         if (t >= t0 && t < nsteps) return c->segq[sl * C + (t - t0)];
@@ -486,7 +498,7 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
     const void *cur = c->ckpt[0];
     for (int t = 0; t < nsteps; ++t) {
         void *dst = fbuf(t + 1);
-        CK(c, tape_step<T>(c, m, cur, dst, qbuf(t), qbuf(t + 1)), "tape forward step");
+        CK(c, tape_step<T>(c, m, cur, dst, qbuf(t), qbuf(t + 1), rbuf(t)), "tape forward step");
         cur = dst;
     }
     c->tape_last_ready = true;
@@ -518,12 +530,16 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     double *slots = c->slots;
     const int rows = c->fused ? seg_rows_of(c) : 0;
     const int nseg = C > 1 ? C - 1 : 0;
-    // states and stencil fields of segment slot sl: seg[sl * nseg + j], segq[sl * C + j]
+    // slot sl: states (single-pass: records) seg[sl * nseg + j] (seg[sl * C + j]),
+    // stencil fields segq[sl * C + j]
     auto segf = [&](int sl, int j) { return c->seg[sl * nseg + j]; };
+    auto segrec = [&](int sl, int j) { return c->seg[sl * C + j]; };
     auto segqf = [&](int sl, int j) { return c->segq[sl * C + j]; };
-    // Recompute f^{t0+1} .. f^{t1-1} of segment k from its checkpoint with the
-    // forward kernels on stream s, keeping the stencil field of every state
-    // t0 .. t1-1, into slot sl.
+    // Recompute segment k from its checkpoint with the forward kernels on
+    // stream s into slot sl: the stencil field of every state t0 .. t1-1, and
+    // the states t0+1 .. t1-1 (single-pass: the records of states t0 .. t1-1,
+    // which takes the segment's last step too; the states pass through the
+    // scratch pair).
     auto recompute = [&](int k, int sl, cudaStream_t s) {
         const int t0 = k * C, t1 = std::min(N, t0 + C);
         cudaError_t r = cudaSuccess;
@@ -531,12 +547,14 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
             const Model<float> &mf = *(const Model<float> *)&m;
             r = launch_potential_padded(mf, is_sc(c), (const float *)c->ckpt[k], (float *)segqf(sl, 0), c->err, s);
             const void *cur = c->ckpt[k];
-            for (int t = t0; t < t1 - 1 && r == cudaSuccess; ++t) {
+            for (int t = t0; t < t1 && r == cudaSuccess; ++t) {
                 // (programmatic launches here too: plain ones, which hold no SM
                 // resources while they wait, made the sweep 4 % slower)
+                void *dst = c->tmp[(t + 1) & 1];
+                void *qn = t + 1 < t1 ? segqf(sl, t + 1 - t0) : c->qpad_tape[0];
                 r = launch_fused_step(mf, is_sc(c), (const float *)cur, (const float *)segqf(sl, t - t0),
-                                      (float *)segf(sl, t - t0), (float *)segqf(sl, t - t0 + 1), c->err, rows, s);
-                cur = segf(sl, t - t0);
+                                      (float *)dst, (float *)qn, c->err, rows, s, true, (float *)segrec(sl, t - t0));
+                cur = dst;
             }
         } else {
             const void *cur = c->ckpt[k];
@@ -581,7 +599,7 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
         if (e == cudaSuccess) e = cudaStreamWaitEvent(as, c->rec_done[sl], 0);
         const int t0 = k * C, t1 = std::min(N, t0 + C);
         for (int t = t1 - 1; t >= t0 && e == cudaSuccess; --t) {
-            const T *ft = (const T *)(t == t0 ? c->ckpt[k] : segf(sl, t - t0 - 1));
+            const T *ft = (const T *)(c->fused ? segrec(sl, t - t0) : (t == t0 ? c->ckpt[k] : segf(sl, t - t0 - 1)));
             e = launch_adjoint_step<T>(m, R, aalp, is_sc(c), is_cdm(c), tau1, c->fused, lay, ft,
                                        (const T *)segqf(sl, t - t0), qpitch, qoff, (const T *)lam[li], (T *)aux,
                                        (T *)lam[1 - li], slots, c->err, /*overlap_prev=*/t != t1 - 1, as);

@@ -100,15 +100,20 @@ int fused_auto_seg_rows(int nx, int ny, int num_sms);
 cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float *f, float *qpad, int *err,
                                     cudaStream_t s);
 // pdl: launch with programmatic serialization (the grid may be scheduled while
-// the previous one drains; it waits for it before any access).
+// the previous one drains; it waits for it before any access).  rec (periodic
+// lattices only): also write the reverse mode's record of f(t), five planes of
+// nx ny floats: rho, jx, jy and the HDM derivatives Dx, Dy of the stencil field.
 cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, const float *qin, float *fout,
-                              float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl = true);
+                              float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl = true,
+                              float *rec = nullptr);
 
 // Adjoint (reverse-time) step (adjoint.cu): from lambda = dL/df at t+1 and the
 // state f at t with its stencil field q (row y, column x at
 // q[y * qpitch + qoff + x]; |q| = Phi for the Shan-Chen form, U for
 // Zhang-Chen), writes lambda at t into lam_out and adds the step's dL/dT to
-// the FP64 slots Tpart[0 .. adjoint_slots).  lambda has nine fields, or three
+// the FP64 slots Tpart[0 .. adjoint_slots).  In the padded layout f is not
+// the state but the single-pass kernel's record of it (rho, jx, jy, Dx, Dy:
+// five planes of nx ny).  lambda has nine fields, or three
 // (rho_bar, jx_bar, jy_bar with lambda_i = rho_bar + e_i . j_bar) when tau1;
 // aux holds naux scratch fields.  Field k, row y, column x of lambda / aux
 // sits at [k * stride + y * pitch + off + x] as adjoint_layout gives: padded
