@@ -450,7 +450,8 @@ def run_sweep(args):
     b = lbm.Batch(params)
     b.init_density(rho0)
     shape = b.tune(trial_steps=50)
-    cluster = b.cluster()   # CTAs per instance of the cluster form, 0 for the grid form
+    cluster = b.cluster()   # CTAs per instance of the cluster form, 0 for the grid form, -1 grouped
+    groups = b.groups(smem=True)   # (cluster size, lattices, shared memory per CTA) of each grouped launch
     b.init_density(rho0)
     b.step(seq_steps)           # warm-up and the equal-accuracy comparison point
     rho_b_short = b.density()
@@ -505,7 +506,8 @@ def run_sweep(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "64 flat-interface lattices, Nx U[256,2048], Ny 8, EOS from {VdW, CS, PR, RK}, "
                                "Tr linspace(0.5, 0.95), tau U[0.8, 1.2], SC + HDM", "cells": cells,
-                   "launch": {"block_threads": shape[0], "grid_blocks": shape[1], "cluster": cluster}},
+                   "launch": {"block_threads": shape[0], "grid_blocks": shape[1], "cluster": cluster,
+                              "groups": [{"cluster": c, "lattices": n, "smem_bytes": sm} for c, n, sm in groups]}},
         "batched_ms_per_step": per_step_batch, "sequential_ms_per_step": per_step_seq,
         "speedup": per_step_seq / per_step_batch,
         "batched_mlups": cells * steps / (ms_batch * 1e-3) / 1e6,
@@ -537,7 +539,7 @@ def run_adjoint(args):
     stream = torch.cuda.Stream()
     nx = ny = 512
     N = args.adj_steps
-    C = max(1, math.ceil(math.sqrt(N)))
+    C = args.adj_checkpoint if args.adj_checkpoint > 0 else max(1, math.ceil(math.sqrt(N)))
     Tr = 0.75
 
     def params(prec, tr=Tr):
@@ -999,6 +1001,9 @@ def main():
     ap.add_argument("--droplet-steps", type=int, default=2000, help="steps of the droplet workload")
     ap.add_argument("--coex-steps", type=int, default=20000, help="steps of the coexistence workload")
     ap.add_argument("--adj-steps", type=int, default=5000, help="forward steps of the adjoint workload")
+    ap.add_argument("--adj-checkpoint", type=int, default=0,
+                    help="adjoint workload: checkpoint interval (0: ceil(sqrt(steps)); the steps themselves: "
+                         "every state taped, no recompute)")
     ap.add_argument("--splash-re", type=float, nargs="+", default=[40.0, 100.0, 173.0],
                     help="Reynolds numbers of the splash workload")
     ap.add_argument("--splash-tstar", type=float, default=2.5, help="splash: run to this U t / D")

@@ -484,9 +484,21 @@ struct lbm_batch {
     cudaStream_t stream = nullptr;
     int block_threads = 256;
     int grid_blocks = 0;
-    int cluster = 0;               // CTAs per instance in the cluster form (0: grid form)
+    int cluster = 0;               // CTAs per instance in the cluster form (0: grid form, -1: grouped)
     int cluster_threads = 256;
     size_t cluster_smem = 0;       // dynamic shared memory per CTA of the cluster form
+    // grouped cluster form: one cluster launch per cluster size, each on its own
+    // stream (forked from and joined to the batch's stream), instances of group
+    // g at gorder_dev[first .. first + count) by decreasing cell count
+    struct Group {
+        int cluster, first, count;
+        size_t smem;
+    };
+    std::vector<Group> groups;
+    int *gorder_dev = nullptr;
+    cudaStream_t gstream[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t gfork = nullptr, gjoin[3] = {nullptr, nullptr, nullptr};
+    int groups_gen = 0;            // changes with every grouping (graph cache key)
     std::vector<int> halo;         // x halo of each instance (kx for HDM, 1 for CDM)
     unsigned long long limit_ns = 2000000000ull;  // 2 s per barrier wait
     int skip_block = -1;
@@ -496,7 +508,7 @@ struct lbm_batch {
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     int graph_steps[2] = {-1, -1}, graph_block[2] = {-1, -1}, graph_grid[2] = {-1, -1};
-    int graph_cluster[2] = {-1, -1};
+    int graph_cluster[2] = {-1, -1}, graph_gen[2] = {-1, -1};
     bool use_graph = true;
     int graph_launches = 0;  // persistent launches issued through a graph
     std::string msg;
@@ -642,6 +654,29 @@ const char *configure_cluster(const lbm_batch *b, int cluster, int threads, size
 // (and no barrier test hook is armed), else the persistent cooperative grid form.
 template <typename T>
 cudaError_t enqueue(lbm_batch *b, int nsteps) {
+    if (b->cluster < 0 && b->skip_block < 0) {   // grouped: fork, one launch per group, join
+        cudaError_t e = cudaEventRecord(b->gfork, b->stream);
+        for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
+            const lbm_batch::Group &G = b->groups[g];
+            ClusterArgs<T> ca{};
+            ca.inst = (const Inst<T> *)b->inst_dev;
+            ca.order = b->gorder_dev + G.first;
+            ca.fin = (const T *)b->f[b->cur];
+            ca.fout = (T *)b->f[(b->cur + nsteps) & 1];
+            ca.ntot = b->ntot;
+            ca.nsteps = nsteps;
+            ca.err = b->err;
+            cudaLaunchAttribute attr[1];
+            cudaLaunchConfig_t cfg = cluster_config<T>(b, G.cluster, b->cluster_threads, G.smem, attr);
+            cfg.gridDim = dim3((unsigned)(G.cluster * G.count));
+            cfg.stream = b->gstream[g];
+            e = cudaStreamWaitEvent(b->gstream[g], b->gfork, 0);
+            if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, cluster_batch_kernel<T>, ca);
+            if (e == cudaSuccess) e = cudaEventRecord(b->gjoin[g], b->gstream[g]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->gjoin[g], 0);
+        }
+        return e;
+    }
     if (b->cluster > 0 && b->skip_block < 0) {
         ClusterArgs<T> ca{};
         ca.inst = (const Inst<T> *)b->inst_dev;
@@ -686,9 +721,10 @@ lbm_status run_steps(lbm_batch *b, int nsteps) {
     if (nsteps == 0) return LBM_OK;
     const int k = b->cur;
     if (b->use_graph && b->skip_block < 0) {
-        const int shape_block = b->cluster > 0 ? b->cluster_threads : b->block_threads;
+        const int shape_block = b->cluster != 0 ? b->cluster_threads : b->block_threads;
         if (!b->graph_exec[k] || b->graph_steps[k] != nsteps || b->graph_block[k] != shape_block ||
-            b->graph_grid[k] != b->grid_blocks || b->graph_cluster[k] != b->cluster) {
+            b->graph_grid[k] != b->grid_blocks || b->graph_cluster[k] != b->cluster ||
+            b->graph_gen[k] != b->groups_gen) {
             drop_graph(b, k);
             bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
@@ -706,6 +742,7 @@ lbm_status run_steps(lbm_batch *b, int nsteps) {
                 b->graph_block[k] = shape_block;
                 b->graph_grid[k] = b->grid_blocks;
                 b->graph_cluster[k] = b->cluster;
+                b->graph_gen[k] = b->groups_gen;
             }
         }
         if (b->graph_exec[k]) {
@@ -840,8 +877,14 @@ lbm_status lbm_batch_set_launch(lbm_batch *b, int block_threads, int blocks_per_
 
 lbm_status lbm_batch_get_launch(lbm_batch *b, int *block_threads, int *grid_blocks) {
     if (!b || !block_threads || !grid_blocks) return LBM_E_INVALID;
-    *block_threads = b->cluster > 0 ? b->cluster_threads : b->block_threads;
-    *grid_blocks = b->cluster > 0 ? b->cluster * b->n : b->grid_blocks;
+    *block_threads = b->cluster != 0 ? b->cluster_threads : b->block_threads;
+    int blocks = b->grid_blocks;
+    if (b->cluster > 0) blocks = b->cluster * b->n;
+    if (b->cluster < 0) {
+        blocks = 0;
+        for (const auto &G : b->groups) blocks += G.cluster * G.count;
+    }
+    *grid_blocks = blocks;
     return LBM_OK;
 }
 
@@ -863,6 +906,93 @@ lbm_status lbm_batch_set_cluster(lbm_batch *b, int cluster, int block_threads) {
     b->cluster = cluster;
     b->cluster_threads = block_threads;
     b->cluster_smem = smem;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_groups(lbm_batch *b, int max_smem_bytes, int block_threads) {
+    if (!b) return LBM_E_INVALID;
+    if (block_threads != 256 && block_threads != 512 && block_threads != 1024)
+        return bfail(b, LBM_E_INVALID, "block_threads must be 256, 512 or 1024");
+    if (max_smem_bytes < 0) return bfail(b, LBM_E_INVALID, "max_smem_bytes must be >= 0");
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return bfail(b, LBM_E_CUDA, "device attributes");
+    const size_t cap = max_smem_bytes > 0 ? std::min<size_t>(max_smem_bytes, optin) : (size_t)optin;
+    // each instance: the smallest cluster whose slices split it (no slice
+    // narrower than the x halo) within `cap`, else within the opt-in maximum
+    const int sizes[3] = {2, 4, 8};
+    std::vector<int> pick(b->n, -1);
+    std::vector<size_t> need(b->n, 0);
+    for (int i = 0; i < b->n; ++i) {
+        const int nx = b->params[i].nx, ny = b->params[i].ny;
+        for (size_t limit : {cap, (size_t)optin}) {
+            for (int g = 0; g < 3 && pick[i] < 0; ++g) {
+                const int C = sizes[g], wmin = nx / C, wmax = (nx + C - 1) / C;
+                const size_t bytes = ((size_t)2 * kQ * wmax * ny + (size_t)ny * (wmax + 2 * b->halo[i])) * b->esz;
+                if (b->halo[i] <= wmin && bytes <= limit) {
+                    pick[i] = g;
+                    need[i] = bytes;
+                }
+            }
+            if (pick[i] >= 0) break;
+        }
+        if (pick[i] < 0)
+            return bfail(b, LBM_E_INVALID, "instance " + std::to_string(i) + " does not split over a cluster of 8");
+    }
+    std::vector<int> order(b->n);
+    for (int i = 0; i < b->n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) {   // by group, then largest first
+        if (pick[u] != pick[v]) return pick[u] > pick[v];
+        return (long long)b->params[u].nx * b->params[u].ny > (long long)b->params[v].nx * b->params[v].ny;
+    });
+    std::vector<lbm_batch::Group> groups;
+    size_t smax = 0;
+    for (int k = 0; k < b->n; ++k) {
+        const int i = order[k];
+        if (groups.empty() || groups.back().cluster != sizes[pick[i]])
+            groups.push_back({sizes[pick[i]], k, 0, 0});
+        groups.back().count += 1;
+        groups.back().smem = std::max(groups.back().smem, need[i]);
+        smax = std::max(smax, need[i]);
+    }
+    // every group must place at least one cluster (the kernel attribute then
+    // covers the largest group's shared memory)
+    const bool f64 = b->prec == LBM_F64;
+    for (const auto &G : groups) {
+        const char *why = f64 ? configure_cluster<double>(b, G.cluster, block_threads, G.smem)
+                              : configure_cluster<float>(b, G.cluster, block_threads, G.smem);
+        if (why) return bfail(b, LBM_E_INVALID, why);
+    }
+    cudaError_t e = f64 ? cudaFuncSetAttribute(cluster_batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smax)
+                        : cudaFuncSetAttribute(cluster_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smax);
+    BCK(b, e, "cudaFuncSetAttribute(grouped cluster form)");
+    if (!b->gorder_dev) BCK(b, dev_alloc((void **)&b->gorder_dev, b->n * sizeof(int)), "cudaMalloc(group order)");
+    for (int g = 0; g < 3; ++g) {
+        if (!b->gstream[g]) BCK(b, cudaStreamCreateWithFlags(&b->gstream[g], cudaStreamNonBlocking), "stream");
+        if (!b->gjoin[g]) BCK(b, cudaEventCreateWithFlags(&b->gjoin[g], cudaEventDisableTiming), "event");
+    }
+    if (!b->gfork) BCK(b, cudaEventCreateWithFlags(&b->gfork, cudaEventDisableTiming), "event");
+    BCK(b, cudaMemcpyAsync(b->gorder_dev, order.data(), b->n * sizeof(int), cudaMemcpyHostToDevice, b->stream),
+        "group order upload");
+    BCK(b, cudaStreamSynchronize(b->stream), "group order upload");
+    b->groups = groups;
+    b->cluster = -1;
+    b->cluster_threads = block_threads;
+    b->groups_gen += 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_groups(lbm_batch *b, int *ngroups, int *cluster, int *count, int *smem_bytes) {
+    if (!b || !ngroups) return LBM_E_INVALID;
+    *ngroups = b->cluster < 0 ? (int)b->groups.size() : 0;
+    for (int g = 0; g < *ngroups; ++g) {
+        if (cluster) cluster[g] = b->groups[g].cluster;
+        if (count) count[g] = b->groups[g].count;
+        if (smem_bytes) smem_bytes[g] = (int)b->groups[g].smem;
+    }
     return LBM_OK;
 }
 
@@ -1099,11 +1229,30 @@ lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int
             }
         }
     }
+    // grouped cluster form: each instance on the smallest cluster whose slices
+    // fit a shared-memory cap (the whole opt-in size, or small enough for two
+    // or three CTAs per SM), one launch per cluster size
+    const int caps[3] = {0, 112 * 1024, 72 * 1024};
+    int best_cap = -1;
+    for (int ci = 0; ci < 3 && st == LBM_OK; ++ci) {
+        for (int ti = 0; ti < 3 && st == LBM_OK; ++ti) {
+            if (lbm_batch_set_groups(b, caps[ci], cthreads[ti]) != LBM_OK) continue;
+            float ms = 0;
+            if (!trial(&ms)) { st = LBM_E_CUDA; break; }
+            if (ms < best) {
+                best = ms;
+                best_c = -1;
+                best_ct = cthreads[ti];
+                best_cap = caps[ci];
+            }
+        }
+    }
     b->block_threads = grid_t;
     b->grid_blocks = grid_g;
     b->cluster = 0;
     if (best_c > 0 && st == LBM_OK && lbm_batch_set_cluster(b, best_c, best_ct) != LBM_OK)
         st = LBM_E_CUDA;   // re-applies the kernel attributes of the winning shape
+    if (best_c < 0 && st == LBM_OK && lbm_batch_set_groups(b, best_cap, best_ct) != LBM_OK) st = LBM_E_CUDA;
     // restore the state and the error word
     if (cudaMemcpyAsync(b->f[cur0], save, fbytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess) st = LBM_E_CUDA;
     b->cur = cur0;
@@ -1137,6 +1286,12 @@ void lbm_batch_destroy(lbm_batch *b) {
     dev_free(b->inst_dev);
     dev_free(b->table_dev);
     dev_free(b->order_dev);
+    dev_free(b->gorder_dev);
+    for (int g = 0; g < 3; ++g) {
+        if (b->gstream[g]) cudaStreamDestroy(b->gstream[g]);
+        if (b->gjoin[g]) cudaEventDestroy(b->gjoin[g]);
+    }
+    if (b->gfork) cudaEventDestroy(b->gfork);
     dev_free(b->f[0]);
     dev_free(b->f[1]);
     dev_free(b->q);

@@ -94,6 +94,9 @@ SIGNATURES = {
     "lbm_batch_get_launch": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_set_cluster": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
     "lbm_batch_get_cluster": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_set_groups": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_get_groups": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_tune": (ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_debug_skip_barrier": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_V]),
@@ -414,9 +417,26 @@ class Batch:
         self._check(self._lib.lbm_batch_set_cluster(self._h, int(cluster), int(block_threads)))
 
     def cluster(self) -> int:
+        """0: grid form; 2, 4, 8: the cluster form's cluster size; -1: grouped."""
         c = ctypes.c_int()
         self._check(self._lib.lbm_batch_get_cluster(self._h, ctypes.byref(c)))
         return c.value
+
+    def set_groups(self, max_smem_bytes: int = 0, block_threads: int = 1024):
+        """Grouped cluster form: each instance on the smallest cluster (2, 4, 8)
+        whose slices fit ``max_smem_bytes`` of shared memory (0: the opt-in
+        maximum), one launch per cluster size on its own stream."""
+        self._check(self._lib.lbm_batch_set_groups(self._h, int(max_smem_bytes), int(block_threads)))
+
+    def groups(self, smem: bool = False):
+        """[(cluster size, instance count)] of the grouped form ([] otherwise),
+        with the shared memory per CTA as a third entry when ``smem``."""
+        n = ctypes.c_int()
+        cl = (ctypes.c_int * 3)()
+        ct = (ctypes.c_int * 3)()
+        sm = (ctypes.c_int * 3)()
+        self._check(self._lib.lbm_batch_get_groups(self._h, ctypes.byref(n), cl, ct, sm))
+        return [(cl[g], ct[g], sm[g]) if smem else (cl[g], ct[g]) for g in range(n.value)]
 
     def tune(self, trial_steps: int = 50):
         t, g = ctypes.c_int(), ctypes.c_int()

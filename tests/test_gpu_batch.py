@@ -153,15 +153,19 @@ def test_full_sweep_in_the_benchmark_launch_equals_grid_form():
         params.append(gp)
         rho0.append(inputs.slab(d["nx"], d["ny"], g, l))
     out = []
-    for c in (0, 8):
+    for c in (0, 8, -1):
         with lbm.Batch(params) as b:
-            if c:
+            if c > 0:
                 b.set_cluster(c, 1024)
+            if c < 0:
+                b.set_groups(0, 1024)
+                assert len(b.groups()) >= 2
             b.init_density(rho0)
             b.step(50)
             out.append(b.density())
-    for u, v in zip(*out):
-        assert np.array_equal(u, v)
+    for k in (1, 2):
+        for u, v in zip(out[0], out[k]):
+            assert np.array_equal(u, v)
 
 
 ODD_MIX = [  # widths no cluster size divides: slices of uneven width
@@ -195,6 +199,51 @@ def test_cluster_form_with_uneven_slices_equals_grid_form(prec, cluster, threads
         for (gp, op), a, got in zip(pairs, f0, outs[1]):
             ref = oracle.run(op, a, 13)
             assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-11, (gp.eos, gp.nx)
+
+
+@pytest.mark.parametrize("prec,cap,threads", [("f32", 0, 1024), ("f32", 72 * 1024, 512), ("f64", 0, 256)])
+def test_grouped_form_equals_grid_form(prec, cap, threads):
+    # each lattice on the smallest cluster its slices fit: with the whole opt-in
+    # shared memory the FP32 mix runs as a group of 2-CTA clusters and one of
+    # 4-CTA clusters, each its own launch on its own stream
+    mix = ODD_MIX if prec == "f32" else [m for m in ODD_MIX if m[0] != 1001]
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec=prec) for m in mix]
+    f0 = [slab_state(op, k + 71) for k, (_, op) in enumerate(pairs)]
+    outs = []
+    for grouped in (False, True):
+        with lbm.Batch([gp for gp, _ in pairs]) as b:
+            if grouped:
+                b.set_groups(cap, threads)
+                assert b.cluster() == -1
+                groups = b.groups()
+                assert sum(n for _, n in groups) == len(pairs)
+                assert [c for c, _ in groups] == sorted({c for c, _ in groups}, reverse=True)
+                if prec == "f32" and cap == 0:
+                    assert groups == [(4, 1), (2, 3)]
+                assert b.launch() == (threads, sum(c * n for c, n in groups))
+            b.set_f(f0)
+            b.step(7)
+            b.step(6)
+            outs.append(b.get_f())
+    for u, v in zip(*outs):
+        assert np.array_equal(u, v)
+
+
+def test_grouped_form_refusal_keeps_the_form():
+    pairs = [instance(*m[:5], force=m[5], grad=m[6], prec="f32") for m in ODD_MIX]
+    big = instance(20000, 8, "cs", 0.8, 1.0, prec="f32")   # slices of 2500 columns exceed shared memory
+    with lbm.Batch([gp for gp, _ in pairs] + [big[0]]) as b:
+        with pytest.raises(lbm.LBMError) as ei:
+            b.set_groups(0, 1024)
+        assert ei.value.status == lbm.E_INVALID
+        assert b.cluster() == 0 and b.groups() == []
+    with lbm.Batch([gp for gp, _ in pairs]) as b:
+        for bad in (128, 96):
+            with pytest.raises(lbm.LBMError):
+                b.set_groups(0, bad)
+        b.set_groups(0, 512)
+        b.set_cluster(0, 256)   # back to the grid form
+        assert b.cluster() == 0 and b.groups() == []
 
 
 def test_cluster_form_f64_matches_oracle():
@@ -241,8 +290,12 @@ def test_cluster_autotuner_keeps_state():
         threads, grid = b.tune(trial_steps=20)
         assert (threads, grid) == b.launch()
         c = b.cluster()
-        assert c in (0, 2, 4, 8)
-        assert grid == (c * len(pairs) if c else grid) and threads in (128, 256, 512, 1024)
+        assert c in (-1, 0, 2, 4, 8)
+        if c > 0:
+            assert grid == c * len(pairs)
+        if c < 0:
+            assert grid == sum(cl * n for cl, n in b.groups())
+        assert threads in (128, 256, 512, 1024)
         for x, y in zip(before, b.density()):
             assert np.array_equal(x, y)
         b.step(10)
@@ -272,7 +325,10 @@ def test_batch_autotuner_keeps_state_and_picks_a_valid_shape():
         b.init_density(rho0)
         before = b.density()
         threads, grid = b.tune(trial_steps=20)
-        assert threads in (128, 256, 512) and grid > 0
+        # no single cluster size splits this mix (40 / 8 is below the HDM halo),
+        # so the tuner picks the grid form or the grouped cluster form
+        assert b.cluster() in (0, -1)
+        assert threads in (128, 256, 512, 1024) and grid > 0
         assert (threads, grid) == b.launch()
         after = b.density()
         for x, y in zip(before, after):
