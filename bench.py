@@ -361,6 +361,7 @@ def run_ours(args):
 
     # --- end to end through the C ABI with host buffers ---
     host_rho = np.ascontiguousarray(rho0)
+    lat.moments()   # the pinned staging buffer of the results exists from here on (allocated once)
     barrier()
     torch.cuda.synchronize()
     te = time.perf_counter()
@@ -371,6 +372,7 @@ def run_ours(args):
     e2e_s = reduce_max(e2e_s)
     e2e = weak_value(world, cells, args.steps, e2e_s)
     assert np.isfinite(r).all()
+    in_place = lat.host_in_place()
     lat.close()
 
     if rank != 0:
@@ -400,10 +402,16 @@ def run_ours(args):
         "kernels_ms_per_launch": {k: v["ms"] / v["count"] for k, v in kern.items()},
         "gpu_launches": timing["launches"],
         "launch": {"segment_rows": seg_rows, "tuned": tuned},
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": cells * 4 / args.steps,
-                "d2h_bytes_per_step": (3 * cells * 4 + 4) / args.steps, "steps": args.steps,
-                "note": f"init_density from host FP64 rho (converted to FP32 in pinned staging), {args.steps} "
-                        "steps, moments (rho, vx, vy) back to host FP64"},
+        "e2e": {"value": e2e, "unit": UNIT, "steps": args.steps,
+                # in place: the GPU reads the FP64 rho over NVLink-C2C; staged: FP32
+                # through pinned memory.  The moments come back staged (FP32).
+                "h2d_bytes_per_step": cells * (8 if in_place else 4) / args.steps,
+                "d2h_bytes_per_step": (3 * cells * 4 + (12 if in_place else 4)) / args.steps,
+                "host_arrays": ("rho read in place by the GPU (NVLink-C2C, host page tables); " if in_place
+                                else "rho FP64 -> FP32 in pinned staging by host threads; ")
+                + "moments FP32 -> FP64 through pinned staging",
+                "note": f"init_density from host FP64 rho, {args.steps} steps, moments (rho, vx, vy) back to "
+                        "host FP64"},
         "clocks": clk,
     }
     if not args.no_cpu_baseline:

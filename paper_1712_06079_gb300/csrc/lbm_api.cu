@@ -29,7 +29,8 @@ lbm_status check_params(const lbm_params &p, const char **why) {
     if (p.force != LBM_FORCE_SC && p.force != LBM_FORCE_ZC) return bad("unknown force form");
     if (p.grad != LBM_GRAD_HDM && p.grad != LBM_GRAD_CDM) return bad("unknown gradient");
     if (p.hdm_radius < 0 || p.hdm_radius > kMaxRadius) return bad("hdm_radius must be in [0, 48]");
-    if (p.flags & ~(LBM_FLAG_TWO_PASS | LBM_FLAG_WALLS_Y | LBM_FLAG_F32_ARITH)) return bad("unknown flags");
+    if (p.flags & ~(LBM_FLAG_TWO_PASS | LBM_FLAG_WALLS_Y | LBM_FLAG_F32_ARITH | LBM_FLAG_STAGED_HOST))
+        return bad("unknown flags");
     if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return bad("tau must be > 0.5");
     if (p.eos == LBM_EOS_PSI_EXP) {
         if (!std::isfinite(p.G) || p.G == 0.0) return bad("G must be finite and non-zero");
@@ -99,6 +100,7 @@ struct lbm_ctx {
     bool qpad_valid = false;      // qpad[cur] holds the potential of f[cur]
     int seg_rows = 0;             // rows per CTA segment of the fused path (0: automatic)
     int num_sms = 0;              // SMs of the context's device
+    bool direct_host = false;     // the device reads the caller's pageable host arrays in place
     void *mom = nullptr;          // rho, vx, vy scratch (3 n values), lazily allocated
     double *partial = nullptr;    // reduction partials
     lbm_obs *obs_dev = nullptr;
@@ -315,10 +317,18 @@ cudaError_t moments_into<float>(lbm_ctx *c, float *r, float *vx, float *vy) {
     return launch_moments_mixed(m, is_sc(c), is_cdm(c), f, (const double *)c->q, r, vx, vy, c->stream);
 }
 
+// Three fields of scratch and, past them, the 8-byte word of the host-array
+// check (mom_bad).
+size_t mom_fields_bytes(const lbm_ctx *c) { return (3 * c->n * c->esz + 255) / 256 * 256; }
+
 lbm_status ensure_mom(lbm_ctx *c) {
     if (c->mom) return LBM_OK;
-    CK(c, dev_alloc(&c->mom, 3 * c->n * c->esz), "cudaMalloc(moments)");
+    CK(c, dev_alloc(&c->mom, mom_fields_bytes(c) + 256), "cudaMalloc(moments)");
     return LBM_OK;
+}
+
+unsigned long long *mom_bad(lbm_ctx *c) {
+    return (unsigned long long *)((char *)c->mom + mom_fields_bytes(c));
 }
 
 lbm_status read_error_word(lbm_ctx *c) {
@@ -717,6 +727,15 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bail(e, "cudaGetDevice");
     if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return bail(e, "cudaDeviceGetAttribute");
+    {   // coherent access to pageable host memory through the host's page tables
+        int pageable = 0, host_tables = 0;
+        if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) != cudaSuccess) {
+            cudaGetLastError();
+            pageable = host_tables = 0;
+        }
+        c->direct_host = pageable == 1 && host_tables == 1 && !(p->flags & LBM_FLAG_STAGED_HOST);
+    }
     size_t fbytes = (size_t)kQ * c->n * c->esz;
     if ((e = dev_alloc(&c->f[0], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f0)");
     if ((e = dev_alloc(&c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
@@ -822,6 +841,27 @@ lbm_status lbm_init_density_device(lbm_ctx *c, const void *rho, const void *ux, 
 lbm_status lbm_init_density(lbm_ctx *c, const double *rho, const double *ux, const double *uy) {
     if (!c) return LBM_E_INVALID;
     if (!rho) return fail(c, LBM_E_INVALID, "rho is NULL");
+    if (c->direct_host) {   // the device reads the caller's arrays in place, checking rho
+        lbm_status st = ensure_mom(c);
+        if (st != LBM_OK) return st;
+        char *dev = (char *)c->mom;
+        const size_t fb = c->n * c->esz;
+        unsigned long long *badw = mom_bad(c), bad = 0;
+        const double *src[3] = {rho, ux, uy};
+        CK(c, cudaMemsetAsync(badw, 0xff, sizeof(*badw), c->stream), "clear check word");
+        for (int k = 0; k < 3; ++k) {
+            if (!src[k]) continue;
+            cudaError_t e = is_f64(c) ? launch_from_host<double>(src[k], (double *)(dev + k * fb), c->n,
+                                                                  k == 0 ? badw : nullptr, c->stream)
+                                      : launch_from_host<float>(src[k], (float *)(dev + k * fb), c->n,
+                                                                 k == 0 ? badw : nullptr, c->stream);
+            CK(c, e, "read host field");
+        }
+        CK(c, cudaMemcpyAsync(&bad, badw, sizeof(bad), cudaMemcpyDeviceToHost, c->stream), "read check word");
+        CK(c, cudaStreamSynchronize(c->stream), "sync host fields");
+        if (bad != ~0ull) return fail(c, LBM_E_INVALID, "rho[%lld] is not a positive finite number", (long long)bad);
+        return lbm_init_density_device(c, dev, ux ? dev + fb : nullptr, uy ? dev + 2 * fb : nullptr);
+    }
     std::vector<long long> bad(33, -1);   // first bad index per chunk, the lowest reported
     {
         const long long n = c->n;
@@ -939,8 +979,8 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy) {
     if ((st = ensure_mom(c)) != LBM_OK) return st;
     char *dev = (char *)c->mom;
     size_t fb = c->n * c->esz;
-    if ((st = lbm_moments_device(c, dev, dev + fb, dev + 2 * fb)) != LBM_OK) return st;
     double *dst[3] = {rho, vx, vy};
+    if ((st = lbm_moments_device(c, dev, dev + fb, dev + 2 * fb)) != LBM_OK) return st;
     if (is_f64(c)) {
         for (int k = 0; k < 3; ++k)
             if (dst[k]) CK(c, cudaMemcpyAsync(dst[k], dev + k * fb, fb, cudaMemcpyDeviceToHost, c->stream), "copy moments");
@@ -1046,5 +1086,7 @@ void lbm_destroy(lbm_ctx *c) {
 const char *lbm_last_error(const lbm_ctx *c) {
     return c ? c->msg.c_str() : g_create_error.c_str();
 }
+
+int lbm_host_in_place(const lbm_ctx *c) { return c ? (c->direct_host ? 1 : 0) : -1; }
 
 }  // extern "C"

@@ -49,6 +49,12 @@ void host_free(void *p);
 // f = f^eq(rho, u) (Eq. 2); ux/uy may be null (zero velocity).
 template <typename T>
 cudaError_t launch_init(const Model<T> &m, const T *rho, const T *ux, const T *uy, T *f, cudaStream_t s);
+// n FP64 values of a pageable host array read by the device in place and
+// converted to T; only on devices that access pageable memory through the
+// host's page tables.  bad (optional): receives the lowest index of a value
+// that is not a positive finite number (atomicMin, preset all ones).
+template <typename T>
+cudaError_t launch_from_host(const double *src, T *dst, long long n, unsigned long long *bad, cudaStream_t s);
 
 // Pass 1 of a step: rho = sum_i f_i (Eq. 3) and the potential field
 // (Eq. 8 / Eq. 21) into q; flags NaN or rho <= 0 in *err.

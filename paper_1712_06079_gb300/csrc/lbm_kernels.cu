@@ -312,6 +312,27 @@ __global__ void obs_final_kernel(int nb, const double *__restrict__ partial, lbm
 
 }  // namespace
 
+// Host arrays read by the GPU in place: on a device that reads pageable host
+// memory through the host's page tables (coherent NVLink-C2C), n FP64 values
+// of a caller's array are converted to T on the device.  With `bad`, the
+// lowest index of a value that is not a positive finite number is kept there
+// (atomicMin; all ones if none).
+template <typename T>
+__global__ void from_host_kernel(const double *__restrict__ src, T *__restrict__ dst, long long n,
+                                 unsigned long long *bad) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = src[i];
+        if (bad && !(v > 0.0 && v <= 1.7976931348623157e308)) atomicMin(bad, (unsigned long long)i);
+        dst[i] = (T)v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_from_host(const double *src, T *dst, long long n, unsigned long long *bad, cudaStream_t s) {
+    from_host_kernel<T><<<flat_blocks(n, 256), 256, 0, s>>>(src, dst, n, bad);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_init(const Model<T> &m, const T *rho, const T *ux, const T *uy, T *f, cudaStream_t s) {
     long long n = (long long)m.nx * m.ny;
@@ -379,6 +400,7 @@ cudaError_t launch_observables(long long n, const T *rho, const T *vx, const T *
 
 #define LBM_INSTANTIATE(T)                                                                                      \
     template cudaError_t launch_init<T>(const Model<T> &, const T *, const T *, const T *, T *, cudaStream_t);  \
+    template cudaError_t launch_from_host<T>(const double *, T *, long long, unsigned long long *, cudaStream_t); \
     template cudaError_t launch_potential<T>(const Model<T> &, bool, const T *, T *, int *, cudaStream_t);      \
     template cudaError_t launch_collide<T>(const Model<T> &, bool, bool, const T *, const T *, T *, cudaStream_t); \
     template cudaError_t launch_moments<T>(const Model<T> &, bool, bool, const T *, const T *, T *, T *, T *,   \

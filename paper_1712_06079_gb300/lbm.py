@@ -23,6 +23,7 @@ PREC = {"f32": 0, "f64": 1}
 FLAG_TWO_PASS = 1
 FLAG_WALLS_Y = 2
 FLAG_F32_ARITH = 4
+FLAG_STAGED_HOST = 8
 
 _lib = None
 _lock = threading.Lock()
@@ -105,6 +106,7 @@ SIGNATURES = {
     "lbm_debug_check_canaries": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_destroy": (None, [_V]),
     "lbm_last_error": (ctypes.c_char_p, [_V]),
+    "lbm_host_in_place": (ctypes.c_int, [_V]),
 }
 
 
@@ -211,6 +213,7 @@ class Params:
     two_pass: bool = False  # LBM_FLAG_TWO_PASS: never use the single-pass FP32 kernel
     walls: bool = False     # LBM_FLAG_WALLS_Y: no-slip walls below row 0 and above row ny-1
     f32_arith: bool = False  # LBM_FLAG_F32_ARITH: FP32 arithmetic in the two-pass kernels of an FP32 lattice
+    staged_host: bool = False  # LBM_FLAG_STAGED_HOST: host arrays through the pinned staging buffer
     G: float = 0.0     # eos "psi_exp": interaction strength of Eq. 4
     rho0: float = 1.0  # eos "psi_exp": reference density of psi = 1 - exp(-rho/rho0)
     stream: int = 0  # cudaStream_t as an integer (torch.cuda.Stream.cuda_stream), 0 = default
@@ -219,7 +222,7 @@ class Params:
         return _Params(self.nx, self.ny, PREC[self.prec], EOS[self.eos], FORCE[self.force], GRAD[self.grad],
                        self.hdm_radius,
                        (FLAG_TWO_PASS if self.two_pass else 0) | (FLAG_WALLS_Y if self.walls else 0) |
-                       (FLAG_F32_ARITH if self.f32_arith else 0),
+                       (FLAG_F32_ARITH if self.f32_arith else 0) | (FLAG_STAGED_HOST if self.staged_host else 0),
                        self.a, self.b, self.R, self.omega, self.Tr, self.Tc, self.k,
                        self.tau, self.G, self.rho0, ctypes.c_void_p(self.stream or None))
 
@@ -273,6 +276,10 @@ class Lattice:
         r, vx, vy = (np.empty(self.shape) for _ in range(3))
         self._check(self._lib.lbm_moments(self._h, _dp(r), _dp(vx), _dp(vy)))
         return r, vx, vy
+
+    def host_in_place(self) -> bool:
+        """True if the device reads and writes this context's host arrays in place."""
+        return self._lib.lbm_host_in_place(self._h) == 1
 
     def moments_device(self, rho_ptr: int, vx_ptr: int, vy_ptr: int):
         self._check(self._lib.lbm_moments_device(self._h, rho_ptr, vx_ptr, vy_ptr))

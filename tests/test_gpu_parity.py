@@ -397,3 +397,39 @@ def test_f32_single_pass_is_deterministic():
             lat.step(300)
             outs.append(lat.get_f())
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_host_arrays_in_place_equal_staged(prec):
+    # Where the device reads pageable host memory in place (Grace with
+    # NVLink-C2C), lbm_init_density reads the caller's FP64 arrays directly;
+    # LBM_FLAG_STAGED_HOST keeps the pinned staging path.  Both give the same
+    # values, report an invalid rho at its lowest index and leave the state as
+    # it was.
+    nx, ny = 200, 136
+    gp, op = make(nx, ny, "pr", 0.75, "zc", "hdm", prec=prec)
+    g, l, _ = oracle.maxwell(op)
+    rho = inputs.droplet(nx, ny, 30, g, l)
+    xi = inputs.uniform01(77, 2 * nx * ny).reshape(2, ny, nx)
+    ux, uy = 0.01 * (xi[0] - 0.5), 0.01 * (xi[1] - 0.5)
+    bad = rho.copy()
+    bad[9, 3] = np.nan
+    bad[3, 7] = -1.0   # the lowest bad index: 3 * nx + 7
+    outs = []
+    for staged in (False, True):
+        gp.staged_host = staged
+        with lbm.Lattice(gp) as lat:
+            if staged:
+                assert not lat.host_in_place()
+            lat.init_density(rho, ux, uy)
+            lat.step(5)
+            m1 = lat.moments()
+            with pytest.raises(lbm.LBMError) as ei:
+                lat.init_density(bad)
+            assert ei.value.status == lbm.E_INVALID and f"rho[{3 * nx + 7}]" in str(ei.value)
+            m2 = lat.moments()
+            for a, b in zip(m1, m2):
+                assert np.array_equal(a, b)
+            outs.append(m1)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
