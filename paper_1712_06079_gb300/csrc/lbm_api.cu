@@ -988,11 +988,23 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy) {
     } else {
         if ((st = ensure_stage(c, 3 * fb)) != LBM_OK) return st;
         float *h = (float *)c->stage;
-        for (int k = 0; k < 3; ++k)
-            if (dst[k]) CK(c, cudaMemcpyAsync(h + k * c->n, dev + k * fb, fb, cudaMemcpyDeviceToHost, c->stream), "copy moments");
-        CK(c, cudaStreamSynchronize(c->stream), "sync moments");
-        for (int k = 0; k < 3; ++k)
-            if (dst[k]) convert(dst[k], h + k * c->n, c->n);
+        // field k is converted on the host while field k + 1 is still copied
+        cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            if (!dst[k]) continue;
+            e = cudaMemcpyAsync(h + k * c->n, dev + k * fb, fb, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = take_event(c, &ev[k]);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[k], c->stream);
+        }
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            if (!dst[k]) continue;
+            e = cudaEventSynchronize(ev[k]);
+            if (e == cudaSuccess) convert(dst[k], h + k * c->n, c->n);
+        }
+        for (cudaEvent_t x : ev)
+            if (x) c->event_pool.push_back(x);
+        CK(c, e, "copy moments");
     }
     return read_error_word(c);
 }

@@ -272,8 +272,16 @@ class Lattice:
     def sync(self):
         self._check(self._lib.lbm_sync(self._h))
 
-    def moments(self):
-        r, vx, vy = (np.empty(self.shape) for _ in range(3))
+    def moments(self, out=None):
+        """(rho, vx, vy) as FP64 host arrays; ``out``: three C-contiguous FP64
+        arrays of the lattice's shape to write into (reused buffers spare the
+        page population of fresh ones)."""
+        if out is None:
+            out = tuple(np.empty(self.shape) for _ in range(3))
+        elif len(out) != 3 or any(not isinstance(o, np.ndarray) or o.dtype != np.float64 or o.shape != self.shape
+                                  or not o.flags.c_contiguous or not o.flags.writeable for o in out):
+            raise ValueError(f"out must be three writeable C-contiguous float64 arrays of shape {self.shape}")
+        r, vx, vy = out
         self._check(self._lib.lbm_moments(self._h, _dp(r), _dp(vx), _dp(vy)))
         return r, vx, vy
 
