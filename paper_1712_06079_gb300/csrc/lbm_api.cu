@@ -120,6 +120,11 @@ struct lbm_ctx {
     std::vector<cudaEvent_t> event_pool;
     // reverse-mode tape (lbm_adjoint_forward / lbm_adjoint_backward)
     std::vector<void *> ckpt;       // states at t = 0, C, 2C, ... (9 n values each)
+    // single-pass contexts: the padded stencil field of each checkpointed state
+    // as the forward formed it (the single-pass kernel finishes the field of
+    // t+1 from its partial densities, a different rounding from the potential
+    // kernel), so that a recompute from a checkpoint repeats the forward bit for bit
+    std::vector<void *> ckptq;
     void *tmp[2] = {nullptr, nullptr};
     void *qpad_tape[2] = {nullptr, nullptr};
     int tape_steps = -1, tape_C = 0;
@@ -373,6 +378,8 @@ lbm_status ensure_stage(lbm_ctx *c, size_t bytes) {
 void free_tape(lbm_ctx *c) {
     for (void *p : c->ckpt) dev_free(p);
     c->ckpt.clear();
+    for (void *p : c->ckptq) dev_free(p);
+    c->ckptq.clear();
     for (void *p : c->seg) dev_free(p);
     for (void *p : c->segq) dev_free(p);
     c->seg.clear();
@@ -444,6 +451,14 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
                 free_tape(c);
                 return fail(c, LBM_E_NOMEM, "tape potential fields");
             }
+            for (int k = 0; k < nck; ++k) {
+                void *p = nullptr;
+                if (dev_alloc(&p, qb) != cudaSuccess) {
+                    free_tape(c);
+                    return fail(c, LBM_E_NOMEM, "checkpoint potential fields");
+                }
+                c->ckptq.push_back(p);
+            }
         }
         {   // buffers of the reverse sweep
             const bool tau1 = model_of<T>(c).omega == T(1);
@@ -500,6 +515,7 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
     auto qbuf = [&](int t) -> void * {   // the stencil field of state t
         if (t >= t0 && t < nsteps) return c->segq[sl * C + (t - t0)];
         if (t >= tp && t < t0) return c->segq[(1 - sl) * C + (t - tp)];
+        if (c->fused && t % C == 0) return c->ckptq[t / C];
         return c->fused ? c->qpad_tape[t & 1] : c->q;
     };
     if (c->fused)
@@ -510,6 +526,12 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
         void *dst = fbuf(t + 1);
         CK(c, tape_step<T>(c, m, cur, dst, qbuf(t), qbuf(t + 1), rbuf(t)), "tape forward step");
         cur = dst;
+    }
+    if (c->fused) {   // the checkpointed fields of the taped segments, for a later recompute
+        const size_t qb = sizeof(float) * (size_t)fused_q_pitch(c->p.nx) * c->p.ny;
+        for (int t = tp; t <= t0; t += C)
+            CK(c, cudaMemcpyAsync(c->ckptq[t / C], qbuf(t), qb, cudaMemcpyDeviceToDevice, c->stream),
+               "checkpoint field");
     }
     c->tape_last_ready = true;
     CK(c, launch_density<T>(c->n, (const T *)cur, rhoT, c->stream), "density");
@@ -555,7 +577,8 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
         cudaError_t r = cudaSuccess;
         if (c->fused) {
             const Model<float> &mf = *(const Model<float> *)&m;
-            r = launch_potential_padded(mf, is_sc(c), (const float *)c->ckpt[k], (float *)segqf(sl, 0), c->err, s);
+            r = cudaMemcpyAsync(segqf(sl, 0), c->ckptq[k], sizeof(float) * (size_t)fused_q_pitch(nx) * ny,
+                                cudaMemcpyDeviceToDevice, s);
             const void *cur = c->ckpt[k];
             for (int t = t0; t < t1 && r == cudaSuccess; ++t) {
                 // (programmatic launches here too: plain ones, which hold no SM

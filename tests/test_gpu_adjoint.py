@@ -146,6 +146,38 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         assert np.array_equal(g, ref[1]) and gtr == ref[2]
 
 
+def test_single_pass_records_give_the_same_gradient_for_every_checkpoint_interval():
+    # FP32 single-pass layout: the reverse sweep reads the forward kernel's
+    # records (the last two segments' from the taped forward, the others
+    # recomputed), so the gradient must not depend on the interval, down to the
+    # bit, including C = 1, an interval that does not divide N and C > N
+    p, rho0, target = setup(64, 64, "cs", 0.75, prec="f32", R0=16, R1=18)
+    ref = adjoint(p, rho0, target, 25, 25)
+    for C in (1, 2, 4, 7, 13, 40):
+        L, g, gtr, _ = adjoint(p, rho0, target, 25, C)
+        assert L == ref[0]
+        assert np.array_equal(g, ref[1]) and gtr == ref[2], C
+
+
+def test_second_backward_after_one_forward_recomputes_the_same_gradient():
+    # the first sweep starts from the taped segments, the second recomputes them
+    for prec, C in (("f32", 6), ("f64", 6), ("f32", 50)):
+        p, rho0, target = setup(64, 64, "cs", 0.75, prec=prec, R0=16, R1=18)
+        dt = torch.float64 if prec == "f64" else torch.float32
+        with lbm.Lattice(p) as lat:
+            r0 = torch.tensor(rho0, dtype=dt, device="cuda")
+            rT = torch.empty_like(r0)
+            lat.adjoint_forward(r0.data_ptr(), 40, C, rT.data_ptr())
+            lat.sync()
+            gr = (2 * (rT.double() - torch.tensor(target, device="cuda"))).to(dt).contiguous()
+            outs = []
+            for _ in range(2):
+                g0 = torch.empty_like(r0)
+                _, gtr, _ = lat.adjoint_backward(gr.data_ptr(), g0.data_ptr())
+                outs.append((g0.cpu().numpy(), gtr))
+        assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1], (prec, C)
+
+
 def test_adjoint_fp32_close_to_fp64():
     p64, rho0, target = setup(64, 64, "cs", 0.75, R0=16, R1=18)
     p32 = lbm.Params(**{**p64.__dict__, "prec": "f32"})
