@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 NX = NY = 4096
 TR, EOS, K_HU, TAU = 0.7, "cs", 0.04, 1.0
+GRAD = "hdm"
 METRIC = "D2Q9 HDM-pseudopotential MLUPS (spinodal 4096^2, FP32)"
 UNIT = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
@@ -47,9 +48,9 @@ STEP_MIN_BYTES = 72
 
 
 def workload_config():
-    return {"workload": f"spinodal {NX}x{NY} periodic, CS a=1 b=4 T/Tc={TR}, SC force, HDM gradient, "
+    return {"workload": f"spinodal {NX}x{NY} periodic, CS a=1 b=4 T/Tc={TR}, SC force, {GRAD.upper()} gradient, "
                         f"k={K_HU}, tau={TAU}, FP32 SoA",
-            "nx": NX, "ny": NY, "eos": EOS, "Tr": TR, "force": "sc", "grad": "hdm", "k": K_HU, "tau": TAU,
+            "nx": NX, "ny": NY, "eos": EOS, "Tr": TR, "force": "sc", "grad": GRAD, "k": K_HU, "tau": TAU,
             "l2": "inputs larger than L2 (f = 2 x 604 MB), no flush"}
 
 
@@ -272,7 +273,7 @@ def oracle_sample(n: int, steps: int, threads: int = 0):
     oracle.set_threads(threads or _ORACLE_ALL_THREADS[0])
     used = oracle.max_threads()
     if _ORACLE_STATE.get("n") != n:
-        op = oracle.params_at(n, n, EOS, 1.0, 4.0, TR, k=K_HU, tau=TAU, force="sc", grad="hdm")
+        op = oracle.params_at(n, n, EOS, 1.0, 4.0, TR, k=K_HU, tau=TAU, force="sc", grad=GRAD)
         _ORACLE_STATE.update(n=n, op=op, f=oracle.init(op, inputs.spinodal(n, n, inputs.CS_TR07_MEAN)))
     op, f = _ORACLE_STATE["op"], _ORACLE_STATE["f"]
     t0 = time.perf_counter()
@@ -314,7 +315,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.Stream()
-    params = lbm.Params(nx=NX, ny=NY, eos=EOS, a=1.0, b=4.0, Tr=TR, k=K_HU, tau=TAU, force="sc", grad="hdm",
+    params = lbm.Params(nx=NX, ny=NY, eos=EOS, a=1.0, b=4.0, Tr=TR, k=K_HU, tau=TAU, force="sc", grad=GRAD,
                         prec="f32", stream=stream.cuda_stream)
     rho0 = inputs.spinodal(NX, NY, inputs.CS_TR07_MEAN, seed=inputs.DEFAULT_SEED + rank)
     cells = NX * NY
@@ -388,7 +389,7 @@ def run_ours(args):
     achieved = STEP_MIN_BYTES * cells / (avg_ms * 1e-3) / 1e9
     design = ALGO_BYTES[dominant] * cells / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
-    traffic = ncu_traffic(dominant)
+    traffic = ncu_traffic(dominant) if GRAD == "hdm" else None   # the committed capture is the HDM variant's
     clk = clocks.summary()
     clk["window"] = window.summary()
     line = {
@@ -986,7 +987,7 @@ def run_laplace(args):
 
 
 def main():
-    global NX, NY
+    global NX, NY, GRAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -999,6 +1000,8 @@ def main():
                     help="fix the segment height of the single-pass step (no tuning); 0: tune")
     ap.add_argument("--nx", type=int, default=NX, help="lattice size (default: the 4096 x 4096 workload)")
     ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--grad", choices=["hdm", "cdm"], default="hdm",
+                    help="spinodal workload: gradient operator (cdm: the weighted central difference of Eq. 15)")
     ap.add_argument("--workload", choices=["spinodal", "sweep", "adjoint", "coexistence", "droplet", "laplace",
                                            "profile", "splash"],
                     default="spinodal",
@@ -1026,7 +1029,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    NX, NY = args.nx, args.ny
+    NX, NY, GRAD = args.nx, args.ny, args.grad
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "sweep":

@@ -13,7 +13,9 @@ operation and in the same order, on whole fields:
   f_i* = f_i - (f_i - f^eq_i(rho, u))/tau
          + [f^eq_i(rho, u + F/rho) - f^eq_i(rho, u)]             (Eq. 1, 2, 10)
   f_i(x + e_i, t + 1) = f_i*(x), periodic.
-D is the periodic HDM operator of Eq. 20 along rows and columns.  Its explicit
+D is the periodic HDM operator of Eq. 20 along rows and columns, or with
+``grad == "cdm"`` the weighted central difference of Eq. 15 normalised by
+1/c_s^2 = 3 (D_x = 3 sum_i w_i q(x + e_i) e_ix, the eight neighbours).  The HDM's explicit
 form, d_i = sum_j w_j (q_(i+j) - q_(i-j)), takes its weights from the oracle's
 own cyclic solve (the response of ``oracle.hdm_line`` to a unit impulse), over
 the whole period, so with FP64 arithmetic this restatement is the oracle's
@@ -65,8 +67,8 @@ class Restatement:
     arithmetic and storage precision."""
 
     def __init__(self, p: Params, arith=np.float32, store=np.float32):
-        if p.walls or p.grad != "hdm" or p.eos == "psi":
-            raise ValueError("the restatement covers the periodic HDM step with an equation of state")
+        if p.walls or p.grad not in ("hdm", "cdm") or p.eos == "psi":
+            raise ValueError("the restatement covers the periodic step with an equation of state")
         self.p, self.t, self.store = p, arith, store
         t = arith
         self.wx = [t(w) for w in periodic_weights(p.nx)]
@@ -75,6 +77,11 @@ class Restatement:
                       third=t(1) / t(3), tau=t(p.tau), w=[t(w) for w in W9])
 
     def _D(self, q, w, axis):
+        if self.p.grad == "cdm":   # Eq. 15: 3 (w_axis (q_+ - q_-) + w_diag ((q_++ + q_+-) - (q_-+ + q_--)))
+            t, other = self.t, 1 - axis
+            up, dn = np.roll(q, -1, axis), np.roll(q, 1, axis)
+            diag = (np.roll(up, -1, other) + np.roll(up, 1, other)) - (np.roll(dn, -1, other) + np.roll(dn, 1, other))
+            return t(3) * (t(1 / 9) * (up - dn) + t(1 / 36) * diag)
         out = np.zeros_like(q)
         for j in range(len(w), 0, -1):
             out = out + w[j - 1] * (np.roll(q, -j, axis) - np.roll(q, j, axis))

@@ -64,8 +64,12 @@
 // unbiased rounding.  For tau = 1 the BGK term vanishes exactly and the
 // equilibrium at u is skipped.
 //
+// The CDMG variant takes the weighted central difference of Eq. 15 instead of
+// the HDM operator: three ring rows and one shuffle each way give it, so it
+// stages no full-width rows and runs no column recurrences.
+//
 // The TAPE variant (used by the reverse mode's taped and recomputed forward
-// steps, never for walls) also writes, for every cell of its own rows, the
+// steps, never for walls or the CDM) also writes, for every cell of its own rows, the
 // record of f(t) the adjoint step reads in place of f(t) and the stencil
 // field: rho and j (Eq. 3) and the two HDM derivatives, five planes of nx ny.
 #include <cuda_runtime.h>
@@ -249,9 +253,10 @@ __device__ __forceinline__ bool range_ok(long long off, long long len, long long
     return in_bounds(off, n - len + 1, err);
 }
 
-template <bool SC, bool TAU1, int EOS, bool WALLS, bool TAPE = false>
+template <bool SC, bool TAU1, int EOS, bool WALLS, bool TAPE = false, bool CDMG = false>
 __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_constant__ FusedArgs A) {
     static_assert(!(TAPE && WALLS), "the reverse mode takes periodic lattices");
+    static_assert(!(TAPE && CDMG), "the reverse mode of CDM lattices takes the two-pass kernels");
     extern __shared__ __align__(128) unsigned char smem[];
     float *qn = reinterpret_cast<float *>(smem);               // [QRING][NW]
     float *qw = reinterpret_cast<float *>(smem + kOffQw);      // [2][SLAB][WW]
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     int issued = 0;  // chunks issued so far (meaningful in warp 0)
     if (warp == 0) {
         for (; issued < min(QCH, nchunks); ++issued) issue_chunk(issued);
-        issue_rows(0);
+        if (!CDMG) issue_rows(0);
     }
 
     const int xg = x0 - 4 + 4 * lane;               // first of this lane's 4 columns
@@ -344,7 +349,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     const bool fwdl = lane < 16;
     auto mag = [](float v) { return SC ? fabsf(v) : v; };   // the stencil's field value
     float colref = 0.f, pcarry = 0.f;
-    if (cl < ncols) {
+    if (!CDMG && cl < ncols) {
         const float *g = A.qin + x0 + QG - 4 + cl;
         const int yr = WALLS ? mirror_index(ys - 1, ny) : (ys - 1 < 0 ? ys - 1 + ny : ys - 1);
         colref = mag(__ldg(g + (long long)yr * A.qpitch));
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     // slab 0's recurrences before the sweep (ring chunks 0 .. QAHEAD)
     for (int c = 0; c <= min(QAHEAD, nchunks - 1); ++c)
         if (!ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs)) timed_out = true;
-    column_phase(0);
+    if (!CDMG) column_phase(0);
     bool stop = __syncthreads_or(timed_out);   // CTA-uniform
 
     for (int s = 0; s < nslab && !stop; ++s) {
@@ -411,13 +416,13 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 issue_chunk(s + QCH - 1);
                 issued = s + QCH;
             }
-            if (s + 1 < nslab) issue_rows(s + 1);
-        } else if (warp == 0 && s + 1 < nslab) {
+            if (!CDMG && s + 1 < nslab) issue_rows(s + 1);
+        } else if (!CDMG && warp == 0 && s + 1 < nslab) {
             issue_rows(1);
         }
         const int yc = ys - 1 + SLAB * s + warp;    // collided row of this warp
         const int ryc = SLAB * s + warp + QBASE - 1;
-        if (!ptx::mbar_wait_bounded(&row_bar[s & 1], (s >> 1) & 1, kWaitLimitNs)) timed_out = true;
+        if (!CDMG && !ptx::mbar_wait_bounded(&row_bar[s & 1], (s >> 1) & 1, kWaitLimitNs)) timed_out = true;
         // A timed-out wait leaves stale shared rows: the slab then computes and
         // stores values of no use (in bounds), the barrier below ends the sweep
         // and the error word reports the timeout.
@@ -444,33 +449,60 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             // for tau = 1 nothing after the moments reads f(t), so f(t) of the next
             // slab goes in flight here, across the derivatives and the collision
             if (TAU1 && s + 1 < nslab) load_f(s + 1);
-            {   // d/dx: wide row columns 4 lane .. 4 lane + 59; cells at window positions 28..31.
-                // The radius-26 operator in recurrence form (hdm_window4); each staged
-                // value enters as its deviation t from the lane's second cell.
-                const float *qrow = qw + ((s & 1) * SLAB + warp) * WW + 4 * lane;
-                float t[60];
+            if constexpr (CDMG) {   // Eq. 15 from ring rows yc - 1, yc, yc + 1; columns +-1 by shuffles
+                const float4 vm = *reinterpret_cast<const float4 *>(qn + ((ryc - 1) % QRING) * NW + 4 * lane);
+                const float4 v0 = *reinterpret_cast<const float4 *>(qn + (ryc % QRING) * NW + 4 * lane);
+                const float4 vp = *reinterpret_cast<const float4 *>(qn + ((ryc + 1) % QRING) * NW + 4 * lane);
+                float rm[6], r0[6], rp[6];   // the field at lane columns 4 lane - 1 .. 4 lane + 4
+                auto fill = [&](float (&r)[6], const float4 &v) {
+                    r[0] = mag(__shfl_up_sync(0xffffffffu, v.w, 1));
+                    r[1] = mag(v.x);
+                    r[2] = mag(v.y);
+                    r[3] = mag(v.z);
+                    r[4] = mag(v.w);
+                    r[5] = mag(__shfl_down_sync(0xffffffffu, v.x, 1));
+                };
+                fill(rm, vm);
+                fill(r0, v0);
+                fill(rp, vp);
+                qc[0] = v0.x;
+                qc[1] = v0.y;
+                qc[2] = v0.z;
+                qc[3] = v0.w;
 #pragma unroll
-                for (int k = 0; k < 15; ++k) {
-                    const float4 v4 = *reinterpret_cast<const float4 *>(qrow + 4 * k);
-                    t[4 * k] = v4.x; t[4 * k + 1] = v4.y; t[4 * k + 2] = v4.z; t[4 * k + 3] = v4.w;
+                for (int c = 0; c < 4; ++c) {   // (1/cs^2) sum_i w_i q(x + e_i) e_i
+                    dx[c] = fmaf(1.0f / 3.0f, r0[c + 2] - r0[c], (1.0f / 12.0f) * ((rp[c + 2] + rm[c + 2]) - (rp[c] + rm[c])));
+                    dy[c] = fmaf(1.0f / 3.0f, rp[c + 1] - rm[c + 1], (1.0f / 12.0f) * ((rp[c + 2] + rp[c]) - (rm[c + 2] + rm[c])));
                 }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) qc[c] = t[28 + c];
-                const float qref = mag(t[29]);
-#pragma unroll
-                for (int p = 2; p <= 57; ++p) t[p] = mag(t[p]) - qref;
-                hdm_window4(t, A.w1x, A.w2x, A.ry, A.ry5, A.ry25, dx);
-            }
-            {   // d/dy from the column recurrences of this row
-                const float4 qa = *reinterpret_cast<const float4 *>(qn + ((ryc + 1) % QRING) * NW + 4 * lane);
-                const float4 qb = *reinterpret_cast<const float4 *>(qn + ((ryc - 1) % QRING) * NW + 4 * lane);
-                const float *abs_ = ab + (s & 1) * 2 * SLAB * NW;
-                const float4 P = *reinterpret_cast<const float4 *>(abs_ + warp * NW + 4 * lane);
-                const float4 Q = *reinterpret_cast<const float4 *>(abs_ + (SLAB + warp) * NW + 4 * lane);
-                dy[0] = fmaf(A.w1y, mag(qa.x) - mag(qb.x), A.w2y * (Q.x - P.x));
-                dy[1] = fmaf(A.w1y, mag(qa.y) - mag(qb.y), A.w2y * (Q.y - P.y));
-                dy[2] = fmaf(A.w1y, mag(qa.z) - mag(qb.z), A.w2y * (Q.z - P.z));
-                dy[3] = fmaf(A.w1y, mag(qa.w) - mag(qb.w), A.w2y * (Q.w - P.w));
+            } else {
+                {   // d/dx: wide row columns 4 lane .. 4 lane + 59; cells at window positions 28..31.
+                    // The radius-26 operator in recurrence form (hdm_window4); each staged
+                    // value enters as its deviation t from the lane's second cell.
+                    const float *qrow = qw + ((s & 1) * SLAB + warp) * WW + 4 * lane;
+                    float t[60];
+    #pragma unroll
+                    for (int k = 0; k < 15; ++k) {
+                        const float4 v4 = *reinterpret_cast<const float4 *>(qrow + 4 * k);
+                        t[4 * k] = v4.x; t[4 * k + 1] = v4.y; t[4 * k + 2] = v4.z; t[4 * k + 3] = v4.w;
+                    }
+    #pragma unroll
+                    for (int c = 0; c < 4; ++c) qc[c] = t[28 + c];
+                    const float qref = mag(t[29]);
+    #pragma unroll
+                    for (int p = 2; p <= 57; ++p) t[p] = mag(t[p]) - qref;
+                    hdm_window4(t, A.w1x, A.w2x, A.ry, A.ry5, A.ry25, dx);
+                }
+                {   // d/dy from the column recurrences of this row
+                    const float4 qa = *reinterpret_cast<const float4 *>(qn + ((ryc + 1) % QRING) * NW + 4 * lane);
+                    const float4 qb = *reinterpret_cast<const float4 *>(qn + ((ryc - 1) % QRING) * NW + 4 * lane);
+                    const float *abs_ = ab + (s & 1) * 2 * SLAB * NW;
+                    const float4 P = *reinterpret_cast<const float4 *>(abs_ + warp * NW + 4 * lane);
+                    const float4 Q = *reinterpret_cast<const float4 *>(abs_ + (SLAB + warp) * NW + 4 * lane);
+                    dy[0] = fmaf(A.w1y, mag(qa.x) - mag(qb.x), A.w2y * (Q.x - P.x));
+                    dy[1] = fmaf(A.w1y, mag(qa.y) - mag(qb.y), A.w2y * (Q.y - P.y));
+                    dy[2] = fmaf(A.w1y, mag(qa.z) - mag(qb.z), A.w2y * (Q.z - P.z));
+                    dy[3] = fmaf(A.w1y, mag(qa.w) - mag(qb.w), A.w2y * (Q.w - P.w));
+                }
             }
             if constexpr (TAPE) {   // the record of f(t) at the lane's 4 cells of an own row
                 if (interior && yc >= ys && yc < ys + hseg) {
@@ -609,7 +641,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         if (s + 1 < nslab) {   // slab s + 1's recurrences: its last ring chunk, then the column phase
             const int c = s + 1 + QAHEAD;
             if (c < nchunks && !ptx::mbar_wait_bounded(&bars[c % QCH], (c / QCH) & 1, kWaitLimitNs)) timed_out = true;
-            column_phase(s + 1);
+            if (!CDMG) column_phase(s + 1);
         }
         if (__syncthreads_or(timed_out)) {
             stop = true;
@@ -675,7 +707,7 @@ __global__ void potential_pad_kernel(Model<float> m, bool sc, const float *__res
 }  // namespace
 
 bool fused_step_supported(const Model<float> &m, bool cdm, int radius) {
-    return !cdm && radius == FK && m.kx == FK && m.ky == FK && m.nx % 4 == 0 && m.nx >= 2 * QG &&
+    return (cdm || (radius == FK && m.kx == FK && m.ky == FK)) && m.nx % 4 == 0 && m.nx >= 2 * QG &&
            m.ny >= 2 * FK + 2;
 }
 
@@ -703,9 +735,9 @@ cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float 
     return cudaGetLastError();
 }
 
-cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, const float *qin, float *fout,
-                              float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl, float *rec) {
-    if (rec && m.walls) return cudaErrorInvalidValue;
+cudaError_t launch_fused_step(const Model<float> &m, bool sc, bool cdm, const float *f, const float *qin,
+                              float *fout, float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl, float *rec) {
+    if (rec && (m.walls || cdm)) return cudaErrorInvalidValue;
     FusedArgs a;
     a.m = m;
     a.f = f;
@@ -732,7 +764,17 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, co
     const bool tau1 = m.omega == 1.0f;
     void (*kern)(const FusedArgs) = nullptr;
 #define LBM_PICK(E)                                                                                        \
-    if (rec)                                                                                               \
+    if (cdm && m.walls)                                                                                    \
+        kern = sc ? (tau1 ? fused_step_kernel<true, true, E, true, false, true>                            \
+                          : fused_step_kernel<true, false, E, true, false, true>)                          \
+                  : (tau1 ? fused_step_kernel<false, true, E, true, false, true>                           \
+                          : fused_step_kernel<false, false, E, true, false, true>);                        \
+    else if (cdm)                                                                                          \
+        kern = sc ? (tau1 ? fused_step_kernel<true, true, E, false, false, true>                           \
+                          : fused_step_kernel<true, false, E, false, false, true>)                         \
+                  : (tau1 ? fused_step_kernel<false, true, E, false, false, true>                          \
+                          : fused_step_kernel<false, false, E, false, false, true>);                       \
+    else if (rec)                                                                                          \
         kern = sc ? (tau1 ? fused_step_kernel<true, true, E, false, true>                                  \
                           : fused_step_kernel<true, false, E, false, true>)                                \
                   : (tau1 ? fused_step_kernel<false, true, E, false, true>                                 \

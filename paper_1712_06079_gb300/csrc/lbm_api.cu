@@ -194,6 +194,10 @@ Model<T> model_of(const lbm_ctx *c) {
 bool is_f64(const lbm_ctx *c) { return c->p.prec == LBM_F64; }
 bool is_sc(const lbm_ctx *c) { return c->p.force == LBM_FORCE_SC; }
 bool is_cdm(const lbm_ctx *c) { return c->p.grad == LBM_GRAD_CDM; }
+// The reverse mode takes the single-pass kernel (its recording variant and
+// the padded layout) for HDM lattices only; CDM lattices tape with the
+// two-pass kernels.
+bool tape_fused(const lbm_ctx *c) { return c->fused && !is_cdm(c); }
 
 cudaError_t take_event(lbm_ctx *c, cudaEvent_t *ev) {
     if (!c->event_pool.empty()) {
@@ -286,7 +290,7 @@ cudaError_t step_fused(lbm_ctx *c, const Model<float> &m) {
         c->qpad_valid = true;
     }
     e = timed_launch(c, 2, [&] {
-        return launch_fused_step(m, is_sc(c), f, (const float *)c->qpad[c->cur], (float *)c->f[1 - c->cur],
+        return launch_fused_step(m, is_sc(c), is_cdm(c), f, (const float *)c->qpad[c->cur], (float *)c->f[1 - c->cur],
                                  (float *)c->qpad[1 - c->cur], c->err, seg_rows_of(c), c->stream);
     });
     if (e != cudaSuccess) return e;
@@ -416,8 +420,8 @@ void free_tape(lbm_ctx *c) {
 template <typename T>
 cudaError_t tape_step(lbm_ctx *c, const Model<T> &m, const void *src, void *dst, void *qsrc, void *qdst,
                       float *rec) {
-    if (c->fused)
-        return launch_fused_step(*(const Model<float> *)&m, is_sc(c), (const float *)src, (const float *)qsrc,
+    if (tape_fused(c))
+        return launch_fused_step(*(const Model<float> *)&m, is_sc(c), is_cdm(c), (const float *)src, (const float *)qsrc,
                                  (float *)dst, (float *)qdst, c->err, seg_rows_of(c), c->stream, true, rec);
     cudaError_t e = launch_potential<T>(m, is_sc(c), (const T *)src, (T *)qsrc, c->err, c->stream);
     if (e != cudaSuccess) return e;
@@ -445,7 +449,7 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
             free_tape(c);
             return fail(c, LBM_E_NOMEM, "tape scratch");
         }
-        if (c->fused) {
+        if (tape_fused(c)) {
             size_t qb = sizeof(float) * (size_t)fused_q_pitch(c->p.nx) * c->p.ny;
             if (dev_alloc(&c->qpad_tape[0], qb) != cudaSuccess || dev_alloc(&c->qpad_tape[1], qb) != cudaSuccess) {
                 free_tape(c);
@@ -462,15 +466,15 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
         }
         {   // buffers of the reverse sweep
             const bool tau1 = model_of<T>(c).omega == T(1);
-            const int qpitch = c->fused ? fused_q_pitch(c->p.nx) : c->p.nx;
+            const int qpitch = tape_fused(c) ? fused_q_pitch(c->p.nx) : c->p.nx;
             const size_t qbytes = sizeof(T) * (size_t)qpitch * c->p.ny;
-            const AdjLayout lay = adjoint_layout(c->p.nx, c->p.ny, c->fused, tau1);
+            const AdjLayout lay = adjoint_layout(c->p.nx, c->p.ny, tape_fused(c), tau1);
             const size_t lbytes = (size_t)lay.nlam * lay.lstride * sizeof(T);
             bool ok = true;
             // single-pass contexts keep the forward kernel's record of every state
             // of a segment (five planes); the others keep the states after the first
-            const size_t sbytes = c->fused ? (size_t)5 * c->n * sizeof(float) : fbytes;
-            c->seg.assign(c->fused ? 2 * C : 2 * (C > 1 ? C - 1 : 0), nullptr);
+            const size_t sbytes = tape_fused(c) ? (size_t)5 * c->n * sizeof(float) : fbytes;
+            c->seg.assign(tape_fused(c) ? 2 * C : 2 * (C > 1 ? C - 1 : 0), nullptr);
             c->segq.assign(2 * C, nullptr);
             for (auto &p : c->seg) ok = ok && dev_alloc(&p, sbytes) == cudaSuccess;
             for (auto &p : c->segq) ok = ok && dev_alloc(&p, qbytes) == cudaSuccess;
@@ -504,21 +508,21 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
     const int tp = K >= 1 ? t0 - C : t0;   // the first step of the taped segments
     auto fbuf = [&](int t) -> void * {   // where state t (>= 1) goes
         if (t % C == 0) return c->ckpt[t / C];
-        if (!c->fused && t > t0 && t < nsteps) return c->seg[sl * nseg + (t - t0 - 1)];
-        if (!c->fused && t > tp && t < t0) return c->seg[(1 - sl) * nseg + (t - tp - 1)];
+        if (!tape_fused(c) && t > t0 && t < nsteps) return c->seg[sl * nseg + (t - t0 - 1)];
+        if (!tape_fused(c) && t > tp && t < t0) return c->seg[(1 - sl) * nseg + (t - tp - 1)];
         return c->tmp[t & 1];
     };
     auto rbuf = [&](int t) -> float * {   // where the record of state t goes (single-pass)
-        if (!c->fused || t < tp) return nullptr;
+        if (!tape_fused(c) || t < tp) return nullptr;
         return (float *)c->seg[((t / C) & 1) * C + t % C];
     };
     auto qbuf = [&](int t) -> void * {   // the stencil field of state t
         if (t >= t0 && t < nsteps) return c->segq[sl * C + (t - t0)];
         if (t >= tp && t < t0) return c->segq[(1 - sl) * C + (t - tp)];
-        if (c->fused && t % C == 0) return c->ckptq[t / C];
-        return c->fused ? c->qpad_tape[t & 1] : c->q;
+        if (tape_fused(c) && t % C == 0) return c->ckptq[t / C];
+        return tape_fused(c) ? c->qpad_tape[t & 1] : c->q;
     };
-    if (c->fused)
+    if (tape_fused(c))
         CK(c, launch_potential_padded(*(const Model<float> *)&m, is_sc(c), (const float *)c->ckpt[0],
                                       (float *)qbuf(0), c->err, c->stream), "potential");
     const void *cur = c->ckpt[0];
@@ -527,7 +531,7 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
         CK(c, tape_step<T>(c, m, cur, dst, qbuf(t), qbuf(t + 1), rbuf(t)), "tape forward step");
         cur = dst;
     }
-    if (c->fused) {   // the checkpointed fields of the taped segments, for a later recompute
+    if (tape_fused(c)) {   // the checkpointed fields of the taped segments, for a later recompute
         const size_t qb = sizeof(float) * (size_t)fused_q_pitch(c->p.nx) * c->p.ny;
         for (int t = tp; t <= t0; t += C)
             CK(c, cudaMemcpyAsync(c->ckptq[t / C], qbuf(t), qb, cudaMemcpyDeviceToDevice, c->stream),
@@ -553,14 +557,14 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     Model<T> m = model_of<T>(c);
     const T R = (T)c->p.R, aalp = (T)c->ms.aalp;
     const bool tau1 = m.omega == T(1);
-    const AdjLayout lay = adjoint_layout(nx, ny, c->fused, tau1);
+    const AdjLayout lay = adjoint_layout(nx, ny, tape_fused(c), tau1);
     // stencil fields: the single-pass layout (padded rows) or the plain one
-    const int qpitch = c->fused ? fused_q_pitch(nx) : nx;
+    const int qpitch = tape_fused(c) ? fused_q_pitch(nx) : nx;
     const int qoff = (qpitch - nx) / 2;
     const int nslots = adjoint_slots<T>(nx, ny);
     void **lam = c->lam, *aux = c->aux;
     double *slots = c->slots;
-    const int rows = c->fused ? seg_rows_of(c) : 0;
+    const int rows = tape_fused(c) ? seg_rows_of(c) : 0;
     const int nseg = C > 1 ? C - 1 : 0;
     // slot sl: states (single-pass: records) seg[sl * nseg + j] (seg[sl * C + j]),
     // stencil fields segq[sl * C + j]
@@ -575,7 +579,7 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     auto recompute = [&](int k, int sl, cudaStream_t s) {
         const int t0 = k * C, t1 = std::min(N, t0 + C);
         cudaError_t r = cudaSuccess;
-        if (c->fused) {
+        if (tape_fused(c)) {
             const Model<float> &mf = *(const Model<float> *)&m;
             r = cudaMemcpyAsync(segqf(sl, 0), c->ckptq[k], sizeof(float) * (size_t)fused_q_pitch(nx) * ny,
                                 cudaMemcpyDeviceToDevice, s);
@@ -585,7 +589,7 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
                 // resources while they wait, made the sweep 4 % slower)
                 void *dst = c->tmp[(t + 1) & 1];
                 void *qn = t + 1 < t1 ? segqf(sl, t + 1 - t0) : c->qpad_tape[0];
-                r = launch_fused_step(mf, is_sc(c), (const float *)cur, (const float *)segqf(sl, t - t0),
+                r = launch_fused_step(mf, is_sc(c), is_cdm(c), (const float *)cur, (const float *)segqf(sl, t - t0),
                                       (float *)dst, (float *)qn, c->err, rows, s, true, (float *)segrec(sl, t - t0));
                 cur = dst;
             }
@@ -608,7 +612,7 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     cudaError_t e = cudaEventRecord(c->bw_start, c->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(as, c->bw_start, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(slots, 0, sizeof(double) * (nslots + 1), as);
-    if (e == cudaSuccess) e = launch_adjoint_seed<T>(nx, ny, c->fused, lay, grad_rhoT, (T *)lam[0], as);
+    if (e == cudaSuccess) e = launch_adjoint_seed<T>(nx, ny, tape_fused(c), lay, grad_rhoT, (T *)lam[0], as);
     // The recompute of segment k - 1 runs on rstream while the adjoint steps of
     // segment k run on the context's stream: slot (k - 1) & 1 is free once the
     // adjoint of segment k + 1 (the slot's previous user) is done.
@@ -632,8 +636,8 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
         if (e == cudaSuccess) e = cudaStreamWaitEvent(as, c->rec_done[sl], 0);
         const int t0 = k * C, t1 = std::min(N, t0 + C);
         for (int t = t1 - 1; t >= t0 && e == cudaSuccess; --t) {
-            const T *ft = (const T *)(c->fused ? segrec(sl, t - t0) : (t == t0 ? c->ckpt[k] : segf(sl, t - t0 - 1)));
-            e = launch_adjoint_step<T>(m, R, aalp, is_sc(c), is_cdm(c), tau1, c->fused, lay, ft,
+            const T *ft = (const T *)(tape_fused(c) ? segrec(sl, t - t0) : (t == t0 ? c->ckpt[k] : segf(sl, t - t0 - 1)));
+            e = launch_adjoint_step<T>(m, R, aalp, is_sc(c), is_cdm(c), tau1, tape_fused(c), lay, ft,
                                        (const T *)segqf(sl, t - t0), qpitch, qoff, (const T *)lam[li], (T *)aux,
                                        (T *)lam[1 - li], slots, c->err, /*overlap_prev=*/t != t1 - 1, as);
             li = 1 - li;
@@ -812,7 +816,7 @@ lbm_status lbm_tune_segment_rows(lbm_ctx *c, int trials, int *rows) {
         c->qpad_valid = true;
     }
     auto launch = [&](int h) {
-        return launch_fused_step(m, is_sc(c), f, (const float *)c->qpad[c->cur], (float *)c->f[1 - c->cur],
+        return launch_fused_step(m, is_sc(c), is_cdm(c), f, (const float *)c->qpad[c->cur], (float *)c->f[1 - c->cur],
                                  (float *)c->qpad[1 - c->cur], c->err, h, c->stream);
     };
     cudaEvent_t ev[2] = {nullptr, nullptr};

@@ -107,10 +107,10 @@ cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float 
                                     cudaStream_t s);
 // pdl: launch with programmatic serialization (the grid may be scheduled while
 // the previous one drains; it waits for it before any access).  rec (periodic
-// lattices only): also write the reverse mode's record of f(t), five planes of
+// HDM lattices only): also write the reverse mode's record of f(t), five planes of
 // nx ny floats: rho, jx, jy and the HDM derivatives Dx, Dy of the stencil field.
-cudaError_t launch_fused_step(const Model<float> &m, bool sc, const float *f, const float *qin, float *fout,
-                              float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl = true,
+cudaError_t launch_fused_step(const Model<float> &m, bool sc, bool cdm, const float *f, const float *qin,
+                              float *fout, float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl = true,
                               float *rec = nullptr);
 
 // Adjoint (reverse-time) step (adjoint.cu): from lambda = dL/df at t+1 and the

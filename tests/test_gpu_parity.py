@@ -249,11 +249,13 @@ def test_step_before_init_is_rejected():
 
 
 FUSED_CASES = [
-    # (nx, ny, eos, Tr, force): strips of 120 columns, segments of 128 rows, ragged edges
-    (132, 129, "cs", 0.8, "sc"),
-    (64, 54, "vdw", 0.85, "zc"),   # smallest lattice the single-pass kernel takes
-    (256, 200, "pr", 0.75, "sc"),
-    (4096, 64, "rk", 0.8, "zc"),
+    # (nx, ny, eos, Tr, force, grad): strips of 120 columns, segments of 128 rows, ragged edges
+    (132, 129, "cs", 0.8, "sc", "hdm"),
+    (64, 54, "vdw", 0.85, "zc", "hdm"),   # smallest lattice the single-pass kernel takes
+    (256, 200, "pr", 0.75, "sc", "hdm"),
+    (4096, 64, "rk", 0.8, "zc", "hdm"),
+    (132, 129, "vdw", 0.85, "sc", "cdm"),   # the kernel's CDM variant (Eq. 15)
+    (256, 64, "pr", 0.9, "zc", "cdm"),   # (ZC + CDM at T/Tc 0.8 blows up within 20 steps, in the oracle too)
 ]
 
 
@@ -268,11 +270,11 @@ def run_f32(gp, f0, steps, two_pass):
     return fg, kinds
 
 
-@pytest.mark.parametrize("nx,ny,eos,Tr,force", FUSED_CASES)
-def test_f32_single_pass_kernel_parity(nx, ny, eos, Tr, force):
+@pytest.mark.parametrize("nx,ny,eos,Tr,force,grad", FUSED_CASES)
+def test_f32_single_pass_kernel_parity(nx, ny, eos, Tr, force, grad):
     # the single-pass FP32 kernel against the FP64 oracle (one step, all
     # populations) and against the two-pass FP32 kernels (20 steps)
-    gp, op = make(nx, ny, eos, Tr, force, "hdm", prec="f32")
+    gp, op = make(nx, ny, eos, Tr, force, grad, prec="f32")
     g, l, _ = oracle.maxwell(op)
     f0 = perturbed_state(op, inputs.droplet(nx, ny, min(nx, ny) / 4, g, l), seed=nx + 7 * ny)
     f1, kinds = run_f32(gp, f0, 1, two_pass=False)

@@ -97,13 +97,14 @@ def test_f32_walls_parity(two_pass):
     assert abs(obs["mass"] - ro.sum()) < 1e-6 * ro.sum()
 
 
-@pytest.mark.parametrize("nx,ny,eos,force,tau", [(132, 129, "pr", "zc", 1.0), (64, 54, "vdw", "sc", 0.8),
-                                                 (256, 200, "cs", "sc", 1.0)])
-def test_f32_walls_single_pass_one_step_and_segments(nx, ny, eos, force, tau):
+@pytest.mark.parametrize("nx,ny,eos,force,tau,grad", [(132, 129, "pr", "zc", 1.0, "hdm"), (64, 54, "vdw", "sc", 0.8, "hdm"),
+                                                      (256, 200, "cs", "sc", 1.0, "hdm"), (132, 70, "vdw", "sc", 1.0, "cdm"),
+                                                      (64, 54, "vdw", "zc", 0.8, "cdm")])
+def test_f32_walls_single_pass_one_step_and_segments(nx, ny, eos, force, tau, grad):
     # one step of the single-pass kernel with walls against the oracle, every
     # population, at several segment heights (segments start and end at the
-    # walls and inside the lattice)
-    gp, op = make(nx, ny, eos, 0.8, force, "hdm", tau, prec="f32")
+    # walls and inside the lattice); HDM and the CDM variant
+    gp, op = make(nx, ny, eos, 0.8, force, grad, tau, prec="f32")
     f0 = wall_drop(op, nx, ny, seed=nx + ny)
     fo = oracle.step(op, f0)
     for rows in (0, 6, 22, ny):

@@ -67,11 +67,16 @@ def test_periodic_weights_are_the_oracle_operator():
             assert abs(2 * np.dot(np.arange(1, len(w) + 1), w) - 1) < 1e-14
 
 
-@pytest.mark.parametrize("nx,ny,eos,Tr,force,tau", [(128, 128, "cs", 0.8, "sc", 1.0), (1024, 8, "pr", 0.7, "zc", 1.0),
-                                                    (37, 23, "rk", 0.75, "zc", 1.3), (40, 30, "vdw", 0.8, "sc", 0.8)])
-def test_restatement_in_fp64_is_the_oracle(nx, ny, eos, Tr, force, tau):
+@pytest.mark.parametrize("nx,ny,eos,Tr,force,tau,grad", [(128, 128, "cs", 0.8, "sc", 1.0, "hdm"),
+                                                         (1024, 8, "pr", 0.7, "zc", 1.0, "hdm"),
+                                                         (37, 23, "rk", 0.75, "zc", 1.3, "hdm"),
+                                                         (40, 30, "vdw", 0.8, "sc", 0.8, "hdm"),
+                                                         (64, 48, "pr", 0.8, "zc", 1.0, "cdm"),
+                                                         (37, 23, "vdw", 0.85, "sc", 1.2, "cdm")])
+def test_restatement_in_fp64_is_the_oracle(nx, ny, eos, Tr, force, tau, grad):
     t = inputs.EOS_TABLE[eos]
-    op = oracle.params_at(nx, ny, eos, t["a"], t["b"], Tr, omega=t["omega"], k=t["k"], tau=tau, force=force)
+    op = oracle.params_at(nx, ny, eos, t["a"], t["b"], Tr, omega=t["omega"], k=t["k"], tau=tau, force=force,
+                          grad=grad)
     g, l, _ = oracle.maxwell(op)
     rho = inputs.droplet(nx, ny, min(nx, ny) / 4, g, l) if min(nx, ny) > 8 else inputs.slab(nx, ny, g, l)
     f0 = oracle.init(op, rho)
