@@ -92,14 +92,15 @@ typedef enum { LBM_F32 = 0, LBM_F64 = 1 } lbm_prec;
  * computes in FP32 there too instead of FP64 (faster where FP64 is slow, as
  * on GB300; the FP32 1000-step field bar is met only with FP64 arithmetic
  * there).  No effect on the single-pass kernel, which computes in FP32. */
-/* LBM_FLAG_STAGED_HOST: the host arrays of lbm_init_density pass through the
- * library's pinned staging buffer (checked and converted by host threads,
- * then one DMA copy) even on a device that reads pageable host memory through
- * the host's page tables (Grace with NVLink-C2C), where by default the device
- * reads the caller's FP64 arrays in place, checking and converting them
- * itself.  Both give the same values and errors.  (Results always come back
- * through the staging buffer: device writes into fresh pageable pages measured
- * no faster.) */
+/* LBM_FLAG_STAGED_HOST: the host arrays of lbm_init_density and lbm_moments
+ * pass through the library's pinned staging buffer (checked and converted by
+ * host threads, one DMA copy each way) even on a device that accesses pageable
+ * host memory through the host's page tables (Grace with NVLink-C2C).  There,
+ * by default, the device reads lbm_init_density's FP64 arrays in place,
+ * checking and converting them itself, and writes lbm_moments' FP64 arrays in
+ * place when every page of them is resident (an array written before, as a
+ * reused buffer is; fresh pages are populated faster by the host threads of
+ * the staging path).  All give the same values and errors. */
 enum { LBM_FLAG_TWO_PASS = 1, LBM_FLAG_WALLS_Y = 2, LBM_FLAG_F32_ARITH = 4, LBM_FLAG_STAGED_HOST = 8 };
 
 typedef struct {
@@ -440,9 +441,9 @@ void lbm_destroy(lbm_ctx *c);
  * when c is NULL).  Never NULL. */
 const char *lbm_last_error(const lbm_ctx *c);
 
-/* 1 if the device reads lbm_init_density's host arrays in place (see
- * LBM_FLAG_STAGED_HOST), 0 if they pass through the pinned staging buffer,
- * -1 for NULL. */
+/* 1 if the device accesses this context's host arrays in place where it can
+ * (see LBM_FLAG_STAGED_HOST), 0 if they always pass through the pinned
+ * staging buffer, -1 for NULL. */
 int lbm_host_in_place(const lbm_ctx *c);
 
 #ifdef __cplusplus

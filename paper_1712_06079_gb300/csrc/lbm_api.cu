@@ -1,7 +1,11 @@
 // C ABI of the library (include/lbm.h): context life cycle, parameter
 // validation, host<->device marshalling and the launch sequence of a step.
+#include <sys/mman.h>
+#include <unistd.h>
+
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -338,6 +342,21 @@ lbm_status ensure_mom(lbm_ctx *c) {
 
 unsigned long long *mom_bad(lbm_ctx *c) {
     return (unsigned long long *)((char *)c->mom + mom_fields_bytes(c));
+}
+
+// True if every page of [p, p + bytes) is resident in host memory (mincore):
+// device writes then meet no page that has to be populated first.
+bool pages_resident(const void *p, size_t bytes) {
+    static const long ps = sysconf(_SC_PAGESIZE);
+    if (ps <= 0 || bytes == 0) return false;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p) / ps * ps;
+    const uintptr_t end = reinterpret_cast<uintptr_t>(p) + bytes;
+    const size_t pages = (end - a + ps - 1) / ps;
+    std::vector<unsigned char> vec(pages);
+    if (mincore(reinterpret_cast<void *>(a), end - a, vec.data()) != 0) return false;
+    for (unsigned char v : vec)
+        if (!(v & 1)) return false;
+    return true;
 }
 
 lbm_status read_error_word(lbm_ctx *c) {
@@ -1007,7 +1026,20 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy) {
     char *dev = (char *)c->mom;
     size_t fb = c->n * c->esz;
     double *dst[3] = {rho, vx, vy};
+    bool in_place = c->direct_host;   // every page of the caller's arrays resident: the device writes them
+    for (int k = 0; k < 3 && in_place; ++k)
+        if (dst[k]) in_place = pages_resident(dst[k], c->n * sizeof(double));
     if ((st = lbm_moments_device(c, dev, dev + fb, dev + 2 * fb)) != LBM_OK) return st;
+    if (in_place) {
+        for (int k = 0; k < 3; ++k) {
+            if (!dst[k]) continue;
+            cudaError_t e = is_f64(c) ? launch_to_host<double>((const double *)(dev + k * fb), dst[k], c->n, c->stream)
+                                      : launch_to_host<float>((const float *)(dev + k * fb), dst[k], c->n, c->stream);
+            CK(c, e, "write host field");
+        }
+        CK(c, cudaStreamSynchronize(c->stream), "sync moments");
+        return read_error_word(c);
+    }
     if (is_f64(c)) {
         for (int k = 0; k < 3; ++k)
             if (dst[k]) CK(c, cudaMemcpyAsync(dst[k], dev + k * fb, fb, cudaMemcpyDeviceToHost, c->stream), "copy moments");

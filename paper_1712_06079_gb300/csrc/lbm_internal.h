@@ -55,6 +55,10 @@ cudaError_t launch_init(const Model<T> &m, const T *rho, const T *ux, const T *u
 // that is not a positive finite number (atomicMin, preset all ones).
 template <typename T>
 cudaError_t launch_from_host(const double *src, T *dst, long long n, unsigned long long *bad, cudaStream_t s);
+// n values of T written as FP64 into a resident pageable host array in place
+// (same devices).
+template <typename T>
+cudaError_t launch_to_host(const T *src, double *dst, long long n, cudaStream_t s);
 
 // Pass 1 of a step: rho = sum_i f_i (Eq. 3) and the potential field
 // (Eq. 8 / Eq. 21) into q; flags NaN or rho <= 0 in *err.

@@ -333,6 +333,29 @@ cudaError_t launch_from_host(const double *src, T *dst, long long n, unsigned lo
     return cudaGetLastError();
 }
 
+// ... and written back: n values of T converted to FP64 into a caller's
+// resident pageable array, two per thread and step (16-byte stores where the
+// array is 16-byte aligned).
+template <typename T>
+__global__ void to_host_kernel(const T *__restrict__ src, double *__restrict__ dst, long long n) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        const long long n2 = n / 2;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += stride)
+            reinterpret_cast<double2 *>(dst)[i] = make_double2((double)src[2 * i], (double)src[2 * i + 1]);
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) dst[n - 1] = (double)src[n - 1];
+    } else {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
+            dst[i] = (double)src[i];
+    }
+}
+
+template <typename T>
+cudaError_t launch_to_host(const T *src, double *dst, long long n, cudaStream_t s) {
+    to_host_kernel<T><<<flat_blocks(n / 2 + 1, 256), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_init(const Model<T> &m, const T *rho, const T *ux, const T *uy, T *f, cudaStream_t s) {
     long long n = (long long)m.nx * m.ny;
@@ -401,6 +424,7 @@ cudaError_t launch_observables(long long n, const T *rho, const T *vx, const T *
 #define LBM_INSTANTIATE(T)                                                                                      \
     template cudaError_t launch_init<T>(const Model<T> &, const T *, const T *, const T *, T *, cudaStream_t);  \
     template cudaError_t launch_from_host<T>(const double *, T *, long long, unsigned long long *, cudaStream_t); \
+    template cudaError_t launch_to_host<T>(const T *, double *, long long, cudaStream_t);                       \
     template cudaError_t launch_potential<T>(const Model<T> &, bool, const T *, T *, int *, cudaStream_t);      \
     template cudaError_t launch_collide<T>(const Model<T> &, bool, bool, const T *, const T *, T *, cudaStream_t); \
     template cudaError_t launch_moments<T>(const Model<T> &, bool, bool, const T *, const T *, T *, T *, T *,   \

@@ -286,7 +286,8 @@ class Lattice:
         return r, vx, vy
 
     def host_in_place(self) -> bool:
-        """True if the device reads and writes this context's host arrays in place."""
+        """True if the device reads and writes this context's host arrays in place
+        where it can (results: into arrays whose pages are all resident)."""
         return self._lib.lbm_host_in_place(self._h) == 1
 
     def moments_device(self, rho_ptr: int, vx_ptr: int, vy_ptr: int):

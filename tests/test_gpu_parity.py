@@ -403,11 +403,12 @@ def test_f32_single_pass_is_deterministic():
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_host_arrays_in_place_equal_staged(prec):
-    # Where the device reads pageable host memory in place (Grace with
-    # NVLink-C2C), lbm_init_density reads the caller's FP64 arrays directly;
-    # LBM_FLAG_STAGED_HOST keeps the pinned staging path.  Both give the same
-    # values, report an invalid rho at its lowest index and leave the state as
-    # it was.
+    # Where the device accesses pageable host memory in place (Grace with
+    # NVLink-C2C), lbm_init_density reads the caller's FP64 arrays directly and
+    # lbm_moments writes arrays whose pages are all resident directly;
+    # LBM_FLAG_STAGED_HOST keeps the pinned staging path.  All give the same
+    # values; an invalid rho is reported at its lowest index and leaves the
+    # state as it was.
     nx, ny = 200, 136
     gp, op = make(nx, ny, "pr", 0.75, "zc", "hdm", prec=prec)
     g, l, _ = oracle.maxwell(op)
@@ -425,7 +426,11 @@ def test_host_arrays_in_place_equal_staged(prec):
                 assert not lat.host_in_place()
             lat.init_density(rho, ux, uy)
             lat.step(5)
-            m1 = lat.moments()
+            m1 = lat.moments()                         # fresh arrays: through the staging buffer
+            resident = tuple(np.full((ny, nx), -1.0) for _ in range(3))
+            m1b = lat.moments(out=resident)            # resident arrays: written in place where possible
+            for a, b in zip(m1, m1b):
+                assert np.array_equal(a, b)
             with pytest.raises(lbm.LBMError) as ei:
                 lat.init_density(bad)
             assert ei.value.status == lbm.E_INVALID and f"rho[{3 * nx + 7}]" in str(ei.value)
