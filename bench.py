@@ -469,7 +469,14 @@ def run_sweep(args):
     # ---- batched ----
     b = lbm.Batch(params)
     b.init_density(rho0)
-    shape = b.tune(trial_steps=50)
+    if args.sweep_form == "tune":
+        shape = b.tune(trial_steps=50)
+    elif args.sweep_form == "grouped":   # the form the tuner picks on this sweep
+        b.set_groups(72 * 1024, 1024)
+        shape = b.launch()
+    else:
+        b.set_cluster(8, 1024)
+        shape = b.launch()
     cluster = b.cluster()   # CTAs per instance of the cluster form, 0 for the grid form, -1 grouped
     groups = b.groups(smem=True)   # (cluster size, lattices, shared memory per CTA) of each grouped launch
     b.init_density(rho0)
@@ -1035,6 +1042,9 @@ def main():
     ap.add_argument("--adj-cost-only", action="store_true",
                     help="adjoint workload: time the FP32 forward and reverse sweeps only (no gradient checks)")
     ap.add_argument("--seq-steps", type=int, default=200, help="steps timed per lattice in the sequential arm")
+    ap.add_argument("--sweep-form", choices=["tune", "grouped", "cluster8"], default="tune",
+                    help="sweep: the tuner's pick, or a fixed form (grouped: 72 KB cap, 1024 threads; "
+                         "cluster8: 8 CTAs x 1024 threads per lattice)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

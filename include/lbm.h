@@ -79,7 +79,7 @@ typedef enum { LBM_F32 = 0, LBM_F64 = 1 } lbm_prec;
  * potential pass + collide pass form even where the fused kernel applies).
  * The single-pass kernel takes LBM_F32 lattices with nx a multiple of 4,
  * nx >= 64 and ny >= 54, with the HDM at radius 26 or with the CDM, periodic
- * or walled. */
+ * or walled.
  * LBM_FLAG_WALLS_Y: no-slip walls half a lattice spacing below row 0 and above
  * row ny-1 instead of periodicity in y (the splash case of Sec. 5.5; x stays
  * periodic).  The paper gives no wall closures; the library takes half-way
