@@ -470,9 +470,9 @@ def run_sweep(args):
     b = lbm.Batch(params)
     b.init_density(rho0)
     if args.sweep_form == "tune":
-        shape = b.tune(trial_steps=50)
-    elif args.sweep_form == "grouped":   # the form the tuner picks on this sweep
-        b.set_groups(72 * 1024, 1024)
+        shape = b.tune(trial_steps=400)
+    elif args.sweep_form == "grouped":   # the grouped cluster form (balanced by default)
+        b.set_groups(args.sweep_cap * 1024 if args.sweep_cap > 0 else lbm.GROUPS_BALANCED, 1024)
         shape = b.launch()
     else:
         b.set_cluster(8, 1024)
@@ -1043,8 +1043,10 @@ def main():
                     help="adjoint workload: time the FP32 forward and reverse sweeps only (no gradient checks)")
     ap.add_argument("--seq-steps", type=int, default=200, help="steps timed per lattice in the sequential arm")
     ap.add_argument("--sweep-form", choices=["tune", "grouped", "cluster8"], default="tune",
-                    help="sweep: the tuner's pick, or a fixed form (grouped: 72 KB cap, 1024 threads; "
-                         "cluster8: 8 CTAs x 1024 threads per lattice)")
+                    help="sweep: the tuner's pick, or a fixed form (grouped: --sweep-cap KB of shared memory per "
+                         "CTA, 1024 threads; cluster8: 8 CTAs x 1024 threads per lattice)")
+    ap.add_argument("--sweep-cap", type=int, default=0,
+                    help="sweep, grouped form: shared-memory cap in KB (0: balanced against the largest 8-CTA slice)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

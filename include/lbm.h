@@ -351,8 +351,10 @@ lbm_status lbm_batch_get_cluster(lbm_batch *b, int *cluster);
 
 /* Grouped cluster form: each instance takes the smallest cluster size of 2, 4
  * and 8 whose slices split it (as for lbm_batch_set_cluster) within
- * max_smem_bytes of shared memory per CTA (0: the device's opt-in maximum),
- * else the smallest within the opt-in maximum; the instances of one cluster
+ * max_smem_bytes of shared memory per CTA (0: the device's opt-in maximum;
+ * LBM_GROUPS_BALANCED: the shared memory of the widest slice any instance has
+ * on 8 CTAs, so that no CTA holds more than the largest lattice's 8-CTA
+ * slice), else the smallest within the opt-in maximum; the instances of one cluster
  * size form a group, run as one cluster launch with that group's own shared
  * memory size and block_threads (256, 512 or 1024) threads per CTA, each group
  * on its own stream forked from the batch's stream and joined back before the
@@ -363,6 +365,7 @@ lbm_status lbm_batch_get_cluster(lbm_batch *b, int *cluster);
  * 8 CTAs or a group's cluster cannot be placed; LBM_E_NOMEM if its order table
  * cannot be had.  lbm_batch_get_launch then reports block_threads and the
  * total CTA count; lbm_batch_set_launch or lbm_batch_set_cluster leave it. */
+enum { LBM_GROUPS_BALANCED = -1 };
 lbm_status lbm_batch_set_groups(lbm_batch *b, int max_smem_bytes, int block_threads);
 /* Groups of the grouped form (ngroups = 0 otherwise): cluster size, instance
  * count and shared memory per CTA of each, largest cluster first; cluster,
@@ -371,8 +374,8 @@ lbm_status lbm_batch_get_groups(lbm_batch *b, int *ngroups, int *cluster, int *c
 
 /* Autotuner: time trial_steps steps for every candidate launch shape (grid
  * form: block size x blocks per SM; cluster form: cluster size x block size,
- * where the instances split; grouped form: shared-memory cap (the opt-in
- * maximum, 112 KB, 72 KB) x block size) on a copy of the current state, keep the fastest
+ * where the instances split; grouped form: shared-memory cap (balanced, the
+ * opt-in maximum, 72 KB) x block size) on a copy of the current state, keep the fastest
  * (its block size and grid, as lbm_batch_get_launch reports them, written to
  * the out pointers, which may be NULL) and restore the state.  Synchronising. */
 lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int *grid_blocks);

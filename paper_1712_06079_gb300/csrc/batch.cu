@@ -913,23 +913,32 @@ lbm_status lbm_batch_set_groups(lbm_batch *b, int max_smem_bytes, int block_thre
     if (!b) return LBM_E_INVALID;
     if (block_threads != 256 && block_threads != 512 && block_threads != 1024)
         return bfail(b, LBM_E_INVALID, "block_threads must be 256, 512 or 1024");
-    if (max_smem_bytes < 0) return bfail(b, LBM_E_INVALID, "max_smem_bytes must be >= 0");
+    if (max_smem_bytes < LBM_GROUPS_BALANCED) return bfail(b, LBM_E_INVALID, "max_smem_bytes must be >= -1");
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return bfail(b, LBM_E_CUDA, "device attributes");
-    const size_t cap = max_smem_bytes > 0 ? std::min<size_t>(max_smem_bytes, optin) : (size_t)optin;
+    auto slice_bytes = [&](int i, int C) {   // both buffers and the haloed field of instance i's widest slice
+        const int nx = b->params[i].nx, ny = b->params[i].ny, wmax = (nx + C - 1) / C;
+        return ((size_t)2 * kQ * wmax * ny + (size_t)ny * (wmax + 2 * b->halo[i])) * b->esz;
+    };
+    size_t cap = max_smem_bytes > 0 ? std::min<size_t>(max_smem_bytes, optin) : (size_t)optin;
+    if (max_smem_bytes == LBM_GROUPS_BALANCED) {   // no CTA holds more than the largest 8-CTA slice
+        cap = 0;
+        for (int i = 0; i < b->n; ++i) cap = std::max(cap, slice_bytes(i, 8));
+        cap = std::min(cap, (size_t)optin);
+    }
     // each instance: the smallest cluster whose slices split it (no slice
     // narrower than the x halo) within `cap`, else within the opt-in maximum
     const int sizes[3] = {2, 4, 8};
     std::vector<int> pick(b->n, -1);
     std::vector<size_t> need(b->n, 0);
     for (int i = 0; i < b->n; ++i) {
-        const int nx = b->params[i].nx, ny = b->params[i].ny;
+        const int nx = b->params[i].nx;
         for (size_t limit : {cap, (size_t)optin}) {
             for (int g = 0; g < 3 && pick[i] < 0; ++g) {
-                const int C = sizes[g], wmin = nx / C, wmax = (nx + C - 1) / C;
-                const size_t bytes = ((size_t)2 * kQ * wmax * ny + (size_t)ny * (wmax + 2 * b->halo[i])) * b->esz;
+                const int C = sizes[g], wmin = nx / C;
+                const size_t bytes = slice_bytes(i, C);
                 if (b->halo[i] <= wmin && bytes <= limit) {
                     pick[i] = g;
                     need[i] = bytes;
@@ -1230,9 +1239,9 @@ lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_threads, int
         }
     }
     // grouped cluster form: each instance on the smallest cluster whose slices
-    // fit a shared-memory cap (the whole opt-in size, or small enough for two
-    // or three CTAs per SM), one launch per cluster size
-    const int caps[3] = {0, 112 * 1024, 72 * 1024};
+    // fit a shared-memory cap (balanced against the largest 8-CTA slice, the
+    // whole opt-in size, or 72 KB), one launch per cluster size
+    const int caps[3] = {LBM_GROUPS_BALANCED, 0, 72 * 1024};
     int best_cap = -1;
     for (int ci = 0; ci < 3 && st == LBM_OK; ++ci) {
         for (int ti = 0; ti < 3 && st == LBM_OK; ++ti) {

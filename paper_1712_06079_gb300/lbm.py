@@ -24,6 +24,7 @@ FLAG_TWO_PASS = 1
 FLAG_WALLS_Y = 2
 FLAG_F32_ARITH = 4
 FLAG_STAGED_HOST = 8
+GROUPS_BALANCED = -1   # lbm_batch_set_groups: cap at the largest 8-CTA slice
 
 _lib = None
 _lock = threading.Lock()
@@ -438,10 +439,11 @@ class Batch:
         self._check(self._lib.lbm_batch_get_cluster(self._h, ctypes.byref(c)))
         return c.value
 
-    def set_groups(self, max_smem_bytes: int = 0, block_threads: int = 1024):
+    def set_groups(self, max_smem_bytes: int = GROUPS_BALANCED, block_threads: int = 1024):
         """Grouped cluster form: each instance on the smallest cluster (2, 4, 8)
         whose slices fit ``max_smem_bytes`` of shared memory (0: the opt-in
-        maximum), one launch per cluster size on its own stream."""
+        maximum; GROUPS_BALANCED: the largest 8-CTA slice's), one launch per
+        cluster size on its own stream."""
         self._check(self._lib.lbm_batch_set_groups(self._h, int(max_smem_bytes), int(block_threads)))
 
     def groups(self, smem: bool = False):

@@ -201,7 +201,8 @@ def test_cluster_form_with_uneven_slices_equals_grid_form(prec, cluster, threads
             assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-11, (gp.eos, gp.nx)
 
 
-@pytest.mark.parametrize("prec,cap,threads", [("f32", 0, 1024), ("f32", 72 * 1024, 512), ("f64", 0, 256)])
+@pytest.mark.parametrize("prec,cap,threads", [("f32", 0, 1024), ("f32", 72 * 1024, 512), ("f64", 0, 256),
+                                              ("f32", lbm.GROUPS_BALANCED, 1024)])
 def test_grouped_form_equals_grid_form(prec, cap, threads):
     # each lattice on the smallest cluster its slices fit: with the whole opt-in
     # shared memory the FP32 mix runs as a group of 2-CTA clusters and one of
