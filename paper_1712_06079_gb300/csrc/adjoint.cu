@@ -178,6 +178,7 @@ struct AdjArgs {
     int dpitch, doff;
     double *Tpart;  // one FP64 slot per CTA of A, then per CTA of B
     int *err;       // error word (a bounded wait that gave up)
+    long long nf, nq, nl, nd;   // elements of f (or the record), q, each lambda buffer, aux (checked build)
     T r, r5, r25;   // r = (sqrt 5 - 3)/2 of Eq. 20's operator and its powers (padded FP32 tiles)
 };
 
@@ -204,15 +205,34 @@ __device__ __forceinline__ void block_sum_into(T v, double *slot) {
 // element (gx0 + lx, gy0 + ly) lands at dst[ly * P + lx].  Asynchronous,
 // element by element (cp.async).
 template <typename T, int TX, int TYT>
-__device__ __forceinline__ void stage_rect(T *dst, int P, const T *src, int spitch, int soff, int nx, int ny, int gx0,
-                                           int gy0, int lx0, int lx1, int ly0, int ly1) {
+__device__ __forceinline__ void stage_rect(T *dst, int P, const T *src, long long nsrc, int spitch, int soff, int nx,
+                                           int ny, int gx0, int gy0, int lx0, int lx1, int ly0, int ly1, int *err) {
     for (int lx = lx0 + (int)threadIdx.x; lx < lx1; lx += TX) {
         const int gx = wrap_index(gx0 + lx, nx) + soff;
         for (int ly = ly0 + (int)threadIdx.y; ly < ly1; ly += TYT) {
-            const int gy = wrap_index(gy0 + ly, ny);
-            ptx::cp_async<sizeof(T)>(dst + ly * P + lx, src + (long long)gy * spitch + gx);
+            const long long g = (long long)wrap_index(gy0 + ly, ny) * spitch + gx;
+            if (in_bounds(g, nsrc, err)) ptx::cp_async<sizeof(T)>(dst + ly * P + lx, src + g);
         }
     }
+}
+
+// Checked global accesses (the LBM_CHECKED build skips one outside its buffer
+// of n elements and flags it; otherwise plain accesses).
+template <typename T>
+__device__ __forceinline__ T ld_chk(const T *base, long long i, long long n, int *err) {
+    return in_bounds(i, n, err) ? base[i] : T(0);
+}
+template <typename T>
+__device__ __forceinline__ void st_chk(T *base, long long i, long long n, T v, int *err) {
+    if (in_bounds(i, n, err)) base[i] = v;
+}
+// Bulk copy of `bytes` from src element off into shared memory, if that range
+// lies in the buffer of n elements (else skipped: the barrier's wait then
+// gives up and reports it).
+template <typename T>
+__device__ __forceinline__ void bulk_chk(T *dst, const T *src, long long off, uint32_t bytes, long long n, uint64_t *bar,
+                                         int *err) {
+    if (in_bounds(off, n, err) && in_bounds(off + bytes / sizeof(T) - 1, n, err)) ptx::bulk_g2s(dst, src + off, bytes, bar);
 }
 
 // Antisymmetric stencil sum_j w_j (v[j s] - v[-j s]) with the x (YAX false)
@@ -238,11 +258,11 @@ constexpr int kGhost = 32;
 __device__ __forceinline__ int yp_of(int y, int ny) { return y + 1 == ny ? 0 : y + 1; }
 __device__ __forceinline__ int ym_of(int y, int ny) { return y == 0 ? ny - 1 : y - 1; }
 template <typename T, bool PAD>
-__device__ __forceinline__ void store_field(T *row, int x, int nx, T v) {
-    row[x] = v;
+__device__ __forceinline__ void store_field(T *base, long long n, long long row, int x, int nx, T v, int *err) {
+    st_chk(base, row + x, n, v, err);
     if (PAD) {
-        if (x < kGhost) row[x + nx] = v;
-        if (x >= nx - kGhost) row[x - nx] = v;
+        if (x < kGhost) st_chk(base, row + x + nx, n, v, err);
+        if (x >= nx - kGhost) st_chk(base, row + x - nx, n, v, err);
     }
 }
 
@@ -395,16 +415,17 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
     T *L = S + W * H;
     // element-wise: a cross for the separable HDM, the full box for the CDM
     if (CDM) {
-        stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, 0, W, 0, H);
+        stage_rect<T, TX, TYT>(S, W, a.q, a.nq, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, 0, W, 0, H, a.m.chk);
     } else {
-        stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, 0, W, hy, hy + TY);
-        stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, hx, hx + TX, 0, hy);
-        stage_rect<T, TX, TYT>(S, W, a.q, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, hx, hx + TX, hy + TY, H);
+        stage_rect<T, TX, TYT>(S, W, a.q, a.nq, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, 0, W, hy, hy + TY, a.m.chk);
+        stage_rect<T, TX, TYT>(S, W, a.q, a.nq, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, hx, hx + TX, 0, hy, a.m.chk);
+        stage_rect<T, TX, TYT>(S, W, a.q, a.nq, a.qpitch, a.qoff, nx, ny, x0 - hx, y0 - hy, hx, hx + TX, hy + TY, H,
+                               a.m.chk);
     }
     if (TAU1)
         for (int k = 0; k < 3; ++k)
-            stage_rect<T, TX, TYT>(L + k * LW * LH, LW, a.lam + k * a.lstride, a.lpitch, a.loff, nx, ny, x0 - 1,
-                                   y0 - 1, 0, LW, 0, LH);
+            stage_rect<T, TX, TYT>(L + k * LW * LH, LW, a.lam + k * a.lstride, a.nl - k * a.lstride, a.lpitch, a.loff,
+                                   nx, ny, x0 - 1, y0 - 1, 0, LW, 0, LH, a.m.chk);
     ptx::cp_async_wait_all();
     __syncthreads();
 
@@ -424,7 +445,7 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
         T r = T(0), jx = T(0), jy = T(0);
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
-            const T fi = a.f[i * n + c];
+            const T fi = ld_chk(a.f, i * n + c, a.nf, a.m.chk);
             r += fi;
             if (ex(i) == 1) jx += fi;
             if (ex(i) == -1) jx -= fi;
@@ -467,7 +488,7 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
             } else {
                 const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : xc);
                 const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : yc);
-                g[i] = __ldg(a.lam + i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs);
+                g[i] = ld_chk(a.lam, i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs, a.nl, a.m.chk);
             }
         }
         T rb, jbx, jby, Dbx, Dby, pc;
@@ -478,18 +499,18 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
             if (valid) tacc += pc * theta;
         }
         if (valid) {
-            T *drow = a.aux + (long long)y * a.dpitch + a.doff;
-            drow[x] = Dbx;
-            drow[a.dstride + x] = Dby;
-            drow[2 * a.dstride + x] = rb;
-            drow[3 * a.dstride + x] = r;
+            const long long d0 = (long long)y * a.dpitch + a.doff + x;
+            st_chk(a.aux, d0, a.nd, Dbx, a.m.chk);
+            st_chk(a.aux, a.dstride + d0, a.nd, Dby, a.m.chk);
+            st_chk(a.aux, 2 * a.dstride + d0, a.nd, rb, a.m.chk);
+            st_chk(a.aux, 3 * a.dstride + d0, a.nd, r, a.m.chk);
             if (TAU1) {
-                T *lrow = a.lam_out + (long long)y * a.lpitch + a.loff;
-                lrow[a.lstride + x] = jbx;
-                lrow[2 * a.lstride + x] = jby;
+                const long long l0 = (long long)y * a.lpitch + a.loff + x;
+                st_chk(a.lam_out, a.lstride + l0, a.nl, jbx, a.m.chk);
+                st_chk(a.lam_out, 2 * a.lstride + l0, a.nl, jby, a.m.chk);
             } else {
-                drow[4 * a.dstride + x] = jbx;
-                drow[5 * a.dstride + x] = jby;
+                st_chk(a.aux, 4 * a.dstride + d0, a.nd, jbx, a.m.chk);
+                st_chk(a.aux, 5 * a.dstride + d0, a.nd, jby, a.m.chk);
             }
         }
     }
@@ -538,12 +559,12 @@ __global__ void __launch_bounds__(AdjTile<float>::TX *AdjTile<float>::TYT) adj_a
     for (int k = 0; k < NC; ++k) {
         const int yc = min(y0 + (int)threadIdx.y + k * TYT, ny - 1);
         const long long c = (long long)yc * nx + xc;
-        r_k[k] = a.f[c];
-        jx_k[k] = a.f[n + c];
-        jy_k[k] = a.f[2 * n + c];
-        Dx_k[k] = a.f[3 * n + c];
-        Dy_k[k] = a.f[4 * n + c];
-        q_k[k] = a.q[(long long)yc * a.qpitch + a.qoff + xc];
+        r_k[k] = ld_chk(a.f, c, a.nf, a.m.chk);
+        jx_k[k] = ld_chk(a.f, n + c, a.nf, a.m.chk);
+        jy_k[k] = ld_chk(a.f, 2 * n + c, a.nf, a.m.chk);
+        Dx_k[k] = ld_chk(a.f, 3 * n + c, a.nf, a.m.chk);
+        Dy_k[k] = ld_chk(a.f, 4 * n + c, a.nf, a.m.chk);
+        q_k[k] = ld_chk(a.q, (long long)yc * a.qpitch + a.qoff + xc, a.nq, a.m.chk);
     }
     float inv_k[NC], ux_k[NC], uy_k[NC], vx_k[NC], vy_k[NC], Fx_k[NC], Fy_k[NC], phi_k[NC], sgn_k[NC];
     float kap_k[NC], th_k[NC];
@@ -569,9 +590,8 @@ __global__ void __launch_bounds__(AdjTile<float>::TX *AdjTile<float>::TYT) adj_a
         if (tid < 32) {  // warp 0 issues one bulk copy per lambda row
             for (int rr = tid; rr < 3 * LH; rr += 32) {
                 const int kk = rr / LH, ry = rr - kk * LH;
-                const float *src = a.lam + kk * a.lstride + (long long)wrap_index(y0 - 1 + ry, ny) * a.lpitch +
-                                   a.loff + x0;
-                ptx::bulk_g2s(L + rr * LW, src - LO, lrow, bar);
+                const long long off = kk * a.lstride + (long long)wrap_index(y0 - 1 + ry, ny) * a.lpitch + a.loff + x0;
+                bulk_chk(L + rr * LW, a.lam, off - LO, lrow, a.nl, bar, a.m.chk);
             }
         }
         if (!cta_wait_copies(bar, 1, 0, a.err)) return;
@@ -598,7 +618,7 @@ __global__ void __launch_bounds__(AdjTile<float>::TX *AdjTile<float>::TYT) adj_a
             } else {
                 const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : xc);
                 const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : yc);
-                g[i] = __ldg(a.lam + i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs);
+                g[i] = ld_chk(a.lam, i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs, a.nl, a.m.chk);
             }
         }
         float rb, jbx, jby, Dbx, Dby, pc;
@@ -609,18 +629,18 @@ __global__ void __launch_bounds__(AdjTile<float>::TX *AdjTile<float>::TYT) adj_a
             if (valid) tacc += pc * th_k[k];
         }
         if (valid) {
-            float *drow = a.aux + (long long)y * a.dpitch + a.doff;
-            store_field<float, true>(drow, x, nx, Dbx);
-            store_field<float, true>(drow + a.dstride, x, nx, Dby);
-            drow[2 * a.dstride + x] = rb;
-            drow[3 * a.dstride + x] = r_k[k];
+            const long long d0 = (long long)y * a.dpitch + a.doff;
+            store_field<float, true>(a.aux, a.nd, d0, x, nx, Dbx, a.m.chk);
+            store_field<float, true>(a.aux, a.nd, a.dstride + d0, x, nx, Dby, a.m.chk);
+            st_chk(a.aux, 2 * a.dstride + d0 + x, a.nd, rb, a.m.chk);
+            st_chk(a.aux, 3 * a.dstride + d0 + x, a.nd, r_k[k], a.m.chk);
             if (TAU1) {
-                float *lrow = a.lam_out + (long long)y * a.lpitch + a.loff;
-                store_field<float, true>(lrow + a.lstride, x, nx, jbx);
-                store_field<float, true>(lrow + 2 * a.lstride, x, nx, jby);
+                const long long l0 = (long long)y * a.lpitch + a.loff;
+                store_field<float, true>(a.lam_out, a.nl, a.lstride + l0, x, nx, jbx, a.m.chk);
+                store_field<float, true>(a.lam_out, a.nl, 2 * a.lstride + l0, x, nx, jby, a.m.chk);
             } else {
-                drow[4 * a.dstride + x] = jbx;
-                drow[5 * a.dstride + x] = jby;
+                st_chk(a.aux, 4 * a.dstride + d0 + x, a.nd, jbx, a.m.chk);
+                st_chk(a.aux, 5 * a.dstride + d0 + x, a.nd, jby, a.m.chk);
             }
         }
     }
@@ -665,17 +685,18 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
             if (tid == 0) ptx::mbar_arrive_expect_tx(&bars[0], HX * wide + HY * core);
             __syncwarp();
             for (int ly = tid; ly < HX; ly += 32) {
-                const T *src = a.aux + (long long)wrap_index(y0 + ly, ny) * a.dpitch + a.doff + x0;
-                ptx::bulk_g2s(SX + ly * WX, src - XO, wide, &bars[0]);
+                const long long off = (long long)wrap_index(y0 + ly, ny) * a.dpitch + a.doff + x0;
+                bulk_chk(SX + ly * WX, a.aux, off - XO, wide, a.nd, &bars[0], a.m.chk);
             }
             for (int ly = tid; ly < HY; ly += 32) {
-                const T *src = a.aux + a.dstride + (long long)wrap_index(y0 - hy + ly, ny) * a.dpitch + a.doff + x0;
-                ptx::bulk_g2s(SY + ly * WY, src, core, &bars[0]);
+                const long long off = a.dstride + (long long)wrap_index(y0 - hy + ly, ny) * a.dpitch + a.doff + x0;
+                bulk_chk(SY + ly * WY, a.aux, off, core, a.nd, &bars[0], a.m.chk);
             }
         }
     } else {
-        stage_rect<T, TX, TYT>(SX, WX, a.aux, a.dpitch, a.doff, nx, ny, x0 - hx, y0 - oy, 0, WX, 0, HX);
-        stage_rect<T, TX, TYT>(SY, WY, a.aux + a.dstride, a.dpitch, a.doff, nx, ny, x0 - ox, y0 - hy, 0, WY, 0, HY);
+        stage_rect<T, TX, TYT>(SX, WX, a.aux, a.nd, a.dpitch, a.doff, nx, ny, x0 - hx, y0 - oy, 0, WX, 0, HX, a.m.chk);
+        stage_rect<T, TX, TYT>(SY, WY, a.aux + a.dstride, a.nd - a.dstride, a.dpitch, a.doff, nx, ny, x0 - ox, y0 - hy,
+                               0, WY, 0, HY, a.m.chk);
         ptx::cp_async_wait_all();
         __syncthreads();
     }
@@ -690,9 +711,9 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
     T rk[NC], rb0k[NC], kap_k[NC], th_k[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-        const T *drow = a.aux + (long long)min(y0 + (int)threadIdx.y + k * TYT, ny - 1) * a.dpitch + a.doff;
-        rk[k] = drow[3 * a.dstride + xc];
-        rb0k[k] = drow[2 * a.dstride + xc];
+        const long long d0 = (long long)min(y0 + (int)threadIdx.y + k * TYT, ny - 1) * a.dpitch + a.doff + xc;
+        rk[k] = ld_chk(a.aux, 3 * a.dstride + d0, a.nd, a.m.chk);
+        rb0k[k] = ld_chk(a.aux, 2 * a.dstride + d0, a.nd, a.m.chk);
     }
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
@@ -704,8 +725,6 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
     for (int k = 0; k < NC; ++k) {
         const int ly = threadIdx.y + k * TYT, y = y0 + ly;
         const bool valid = x < nx && y < ny;
-        const int yc = min(y, ny - 1);
-        const T *drow = a.aux + (long long)yc * a.dpitch + a.doff;
         const T rb0 = rb0k[k], kappa = kap_k[k], theta = th_k[k];
         // the transposed derivative: Dx^T = -Dx, Dy^T = -Dy
         const T *rx = SX + (ly + oy) * WX + (lx + XS);
@@ -731,23 +750,25 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
         const T rb = rb0 + kappa * pbar;
         if (!valid) continue;
         tacc += theta * pbar;
-        T *lrow = a.lam_out + (long long)y * a.lpitch + a.loff;
+        const long long l0 = (long long)y * a.lpitch + a.loff;
         if (TAU1) {
-            store_field<T, PAD>(lrow, x, nx, rb);
+            store_field<T, PAD>(a.lam_out, a.nl, l0, x, nx, rb, a.m.chk);
         } else {
-            const T jbx = drow[4 * a.dstride + x], jby = drow[5 * a.dstride + x];
+            const long long d0 = (long long)y * a.dpitch + a.doff + x;
+            const T jbx = ld_chk(a.aux, 4 * a.dstride + d0, a.nd, a.m.chk);
+            const T jby = ld_chk(a.aux, 5 * a.dstride + d0, a.nd, a.m.chk);
             const T om1 = T(1) - m.omega;
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
                 const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : x);
                 const int dys = ey(i) == 1 ? yp_of(y, ny) : (ey(i) == -1 ? ym_of(y, ny) : y);
-                const T gi = a.lam[i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs];
+                const T gi = ld_chk(a.lam, i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs, a.nl, a.m.chk);
                 T li = om1 * gi + rb;
                 if (ex(i) == 1) li += jbx;
                 if (ex(i) == -1) li -= jbx;
                 if (ey(i) == 1) li += jby;
                 if (ey(i) == -1) li -= jby;
-                lrow[i * a.lstride + x] = li;
+                st_chk(a.lam_out, i * a.lstride + l0 + x, a.nl, li, a.m.chk);
             }
         }
     }
@@ -758,18 +779,18 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
 // for all i, i.e. (g, 0, 0) in the three-field form.
 template <typename T, bool PAD>
 __global__ void adj_seed_kernel(int nx, int ny, int nlam, const T *grad_rho, T *lam, long long lstride, int lpitch,
-                                int loff) {
-    const long long n = (long long)nx * ny;
+                                int loff, int *err) {
+    const long long n = (long long)nx * ny, nl = nlam * lstride;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(c / nx), x = (int)(c - (long long)y * nx);
         const T g = grad_rho[c];
-        T *row = lam + (long long)y * lpitch + loff;
+        const long long row = (long long)y * lpitch + loff;
         if (nlam == 3) {
-            store_field<T, PAD>(row, x, nx, g);
-            store_field<T, PAD>(row + lstride, x, nx, T(0));
-            store_field<T, PAD>(row + 2 * lstride, x, nx, T(0));
+            store_field<T, PAD>(lam, nl, row, x, nx, g, err);
+            store_field<T, PAD>(lam, nl, lstride + row, x, nx, T(0), err);
+            store_field<T, PAD>(lam, nl, 2 * lstride + row, x, nx, T(0), err);
         } else {
-            for (int i = 0; i < kQ; ++i) row[i * lstride + x] = g;
+            for (int i = 0; i < kQ; ++i) st_chk(lam, i * lstride + row + x, nl, g, err);
         }
     }
 }
@@ -778,17 +799,17 @@ __global__ void adj_seed_kernel(int nx, int ny, int nlam, const T *grad_rho, T *
 // lambda_i = rho_bar + e_i . j_bar is rho_bar (sum w_i = 1, sum w_i e_i = 0).
 template <typename T>
 __global__ void adj_initial_kernel(int nx, int ny, int nlam, const T *lam, long long lstride, int lpitch, int loff,
-                                   T *grad_rho0) {
-    const long long n = (long long)nx * ny;
+                                   T *grad_rho0, int *err) {
+    const long long n = (long long)nx * ny, nl = nlam * lstride;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(c / nx), x = (int)(c - (long long)y * nx);
-        const T *row = lam + (long long)y * lpitch + loff + x;
+        const long long row = (long long)y * lpitch + loff + x;
         if (nlam == 3) {
-            grad_rho0[c] = row[0];
+            grad_rho0[c] = ld_chk(lam, row, nl, err);
         } else {
             T s = T(0);
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) s += wq<T>(i) * row[i * lstride];
+            for (int i = 0; i < kQ; ++i) s += wq<T>(i) * ld_chk(lam, i * lstride + row, nl, err);
             grad_rho0[c] = s;
         }
     }
@@ -953,6 +974,11 @@ cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cd
     a.doff = l.doff;
     a.Tpart = Tpart;
     a.err = err;
+    const long long n = (long long)m.nx * m.ny;
+    a.nf = (padded && !cdm ? 5 : kQ) * n;   // the single-pass record or the state
+    a.nq = (long long)qpitch * m.ny;
+    a.nl = l.nlam * l.lstride;
+    a.nd = l.naux * l.dstride;
     const double r = 0.5 * (std::sqrt(5.0) - 3.0);   // root of r^2/3 + r + 1/3 = 0 (Eq. 20's operator)
     a.r = (T)r;
     a.r5 = (T)std::pow(r, 5);
@@ -971,19 +997,23 @@ cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cd
 
 template <typename T>
 cudaError_t launch_adjoint_seed(int nx, int ny, bool padded, const AdjLayout &l, const T *grad_rho, T *lam,
-                                cudaStream_t s) {
+                                int *err, cudaStream_t s) {
     const long long n = (long long)nx * ny;
     if (padded)
-        adj_seed_kernel<T, true><<<blocks_for(n), 256, 0, s>>>(nx, ny, l.nlam, grad_rho, lam, l.lstride, l.lpitch, l.loff);
+        adj_seed_kernel<T, true><<<blocks_for(n), 256, 0, s>>>(nx, ny, l.nlam, grad_rho, lam, l.lstride, l.lpitch, l.loff,
+                                                               err);
     else
-        adj_seed_kernel<T, false><<<blocks_for(n), 256, 0, s>>>(nx, ny, l.nlam, grad_rho, lam, l.lstride, l.lpitch, l.loff);
+        adj_seed_kernel<T, false><<<blocks_for(n), 256, 0, s>>>(nx, ny, l.nlam, grad_rho, lam, l.lstride, l.lpitch,
+                                                                l.loff, err);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_adjoint_initial(int nx, int ny, const AdjLayout &l, const T *lam, T *grad_rho0, cudaStream_t s) {
+cudaError_t launch_adjoint_initial(int nx, int ny, const AdjLayout &l, const T *lam, T *grad_rho0, int *err,
+                                  cudaStream_t s) {
     const long long n = (long long)nx * ny;
-    adj_initial_kernel<T><<<blocks_for(n), 256, 0, s>>>(nx, ny, l.nlam, lam, l.lstride, l.lpitch, l.loff, grad_rho0);
+    adj_initial_kernel<T><<<blocks_for(n), 256, 0, s>>>(nx, ny, l.nlam, lam, l.lstride, l.lpitch, l.loff, grad_rho0,
+                                                        err);
     return cudaGetLastError();
 }
 
@@ -1003,8 +1033,9 @@ cudaError_t launch_density(long long n, const T *f, T *rho, cudaStream_t s) {
     template cudaError_t launch_adjoint_step<T>(const Model<T> &, T, T, bool, bool, bool, bool, const AdjLayout &, \
                                                 const T *, const T *, int, int, const T *, T *, T *, double *, int *, \
                                                 bool, cudaStream_t);                                        \
-    template cudaError_t launch_adjoint_seed<T>(int, int, bool, const AdjLayout &, const T *, T *, cudaStream_t); \
-    template cudaError_t launch_adjoint_initial<T>(int, int, const AdjLayout &, const T *, T *, cudaStream_t);   \
+    template cudaError_t launch_adjoint_seed<T>(int, int, bool, const AdjLayout &, const T *, T *, int *,         \
+                                                cudaStream_t);                                                   \
+    template cudaError_t launch_adjoint_initial<T>(int, int, const AdjLayout &, const T *, T *, int *, cudaStream_t); \
     template cudaError_t launch_density<T>(long long, const T *, T *, cudaStream_t);
 LBM_ADJ_INST(float)
 LBM_ADJ_INST(double)

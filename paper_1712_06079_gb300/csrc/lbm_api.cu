@@ -631,7 +631,7 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     cudaError_t e = cudaEventRecord(c->bw_start, c->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(as, c->bw_start, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(slots, 0, sizeof(double) * (nslots + 1), as);
-    if (e == cudaSuccess) e = launch_adjoint_seed<T>(nx, ny, tape_fused(c), lay, grad_rhoT, (T *)lam[0], as);
+    if (e == cudaSuccess) e = launch_adjoint_seed<T>(nx, ny, tape_fused(c), lay, grad_rhoT, (T *)lam[0], c->err, as);
     // The recompute of segment k - 1 runs on rstream while the adjoint steps of
     // segment k run on the context's stream: slot (k - 1) & 1 is free once the
     // adjoint of segment k + 1 (the slot's previous user) is done.
@@ -663,7 +663,7 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
         }
         if (e == cudaSuccess) e = cudaEventRecord(c->adj_done[sl], as);
     }
-    if (e == cudaSuccess) e = launch_adjoint_initial<T>(nx, ny, lay, (const T *)lam[li], grad_rho0, as);
+    if (e == cudaSuccess) e = launch_adjoint_initial<T>(nx, ny, lay, (const T *)lam[li], grad_rho0, c->err, as);
     if (e == cudaSuccess) e = launch_sum_slots(slots, nslots, slots + nslots, as);
     if (e == cudaSuccess) e = cudaEventRecord(c->bw_start, as);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->bw_start, 0);

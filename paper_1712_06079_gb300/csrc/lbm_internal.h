@@ -150,10 +150,11 @@ cudaError_t launch_adjoint_step(const Model<T> &m, T R, T aalp, bool sc, bool cd
 // lambda at the final step from dL/drho_T (rho_T = sum_i f_i).
 template <typename T>
 cudaError_t launch_adjoint_seed(int nx, int ny, bool padded, const AdjLayout &l, const T *grad_rho, T *lam,
-                                cudaStream_t s);
+                                int *err, cudaStream_t s);
 // dL/drho0 = sum_i w_i lambda_i at t = 0 (f = f^eq(rho0, 0)).
 template <typename T>
-cudaError_t launch_adjoint_initial(int nx, int ny, const AdjLayout &l, const T *lam, T *grad_rho0, cudaStream_t s);
+cudaError_t launch_adjoint_initial(int nx, int ny, const AdjLayout &l, const T *lam, T *grad_rho0, int *err,
+                                  cudaStream_t s);
 // *out = sum of nslots doubles in index order (one thread).
 cudaError_t launch_sum_slots(const double *slots, int nslots, double *out, cudaStream_t s);
 template <typename T>
