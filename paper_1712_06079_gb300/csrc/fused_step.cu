@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     auto load_f = [&](int s) {
         const float *src = A.f + (long long)wrapi(ys - 1 + SLAB * s + warp, ny) * nx + xgw;
         const float4 *p = reinterpret_cast<const float4 *>(src);
-#pragma unroll
         const bool ok = range_ok(src - A.f, 4, (long long)4 * A.n4, A.err);   // the plane-0 float4 (all planes alike)
+#pragma unroll
         for (int i = 0; i < 9; ++i, p += A.n4) fv[i] = ok ? ld_stream(p) : make_float4(0.f, 0.f, 0.f, 0.f);
     };
     // d/dy column recurrences: thread (warp, lane) follows ring column

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "lbm.h"
@@ -439,9 +440,11 @@ void free_tape(lbm_ctx *c) {
 template <typename T>
 cudaError_t tape_step(lbm_ctx *c, const Model<T> &m, const void *src, void *dst, void *qsrc, void *qdst,
                       float *rec) {
-    if (tape_fused(c))
-        return launch_fused_step(*(const Model<float> *)&m, is_sc(c), is_cdm(c), (const float *)src, (const float *)qsrc,
-                                 (float *)dst, (float *)qdst, c->err, seg_rows_of(c), c->stream, true, rec);
+    if constexpr (std::is_same_v<T, float>) {   // (FP64 contexts never take the single-pass kernel)
+        if (tape_fused(c))
+            return launch_fused_step(m, is_sc(c), is_cdm(c), (const float *)src, (const float *)qsrc, (float *)dst,
+                                     (float *)qdst, c->err, seg_rows_of(c), c->stream, true, rec);
+    }
     cudaError_t e = launch_potential<T>(m, is_sc(c), (const T *)src, (T *)qsrc, c->err, c->stream);
     if (e != cudaSuccess) return e;
     return launch_collide<T>(m, is_sc(c), is_cdm(c), (const T *)src, (const T *)qsrc, (T *)dst, c->stream);
@@ -541,9 +544,11 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
         if (tape_fused(c) && t % C == 0) return c->ckptq[t / C];
         return tape_fused(c) ? c->qpad_tape[t & 1] : c->q;
     };
-    if (tape_fused(c))
-        CK(c, launch_potential_padded(*(const Model<float> *)&m, is_sc(c), (const float *)c->ckpt[0],
-                                      (float *)qbuf(0), c->err, c->stream), "potential");
+    if constexpr (std::is_same_v<T, float>) {
+        if (tape_fused(c))
+            CK(c, launch_potential_padded(m, is_sc(c), (const float *)c->ckpt[0], (float *)qbuf(0), c->err, c->stream),
+               "potential");
+    }
     const void *cur = c->ckpt[0];
     for (int t = 0; t < nsteps; ++t) {
         void *dst = fbuf(t + 1);
@@ -598,29 +603,30 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     auto recompute = [&](int k, int sl, cudaStream_t s) {
         const int t0 = k * C, t1 = std::min(N, t0 + C);
         cudaError_t r = cudaSuccess;
-        if (tape_fused(c)) {
-            const Model<float> &mf = *(const Model<float> *)&m;
-            r = cudaMemcpyAsync(segqf(sl, 0), c->ckptq[k], sizeof(float) * (size_t)fused_q_pitch(nx) * ny,
-                                cudaMemcpyDeviceToDevice, s);
-            const void *cur = c->ckpt[k];
-            for (int t = t0; t < t1 && r == cudaSuccess; ++t) {
-                // (programmatic launches here too: plain ones, which hold no SM
-                // resources while they wait, made the sweep 4 % slower)
-                void *dst = c->tmp[(t + 1) & 1];
-                void *qn = t + 1 < t1 ? segqf(sl, t + 1 - t0) : c->qpad_tape[0];
-                r = launch_fused_step(mf, is_sc(c), is_cdm(c), (const float *)cur, (const float *)segqf(sl, t - t0),
-                                      (float *)dst, (float *)qn, c->err, rows, s, true, (float *)segrec(sl, t - t0));
-                cur = dst;
-            }
-        } else {
-            const void *cur = c->ckpt[k];
-            for (int t = t0; t < t1 && r == cudaSuccess; ++t) {
-                r = launch_potential<T>(m, is_sc(c), (const T *)cur, (T *)segqf(sl, t - t0), c->err, s);
-                if (r == cudaSuccess && t < t1 - 1) {
-                    r = launch_collide<T>(m, is_sc(c), is_cdm(c), (const T *)cur, (const T *)segqf(sl, t - t0),
-                                          (T *)segf(sl, t - t0), s);
-                    cur = segf(sl, t - t0);
+        if constexpr (std::is_same_v<T, float>) {   // (FP64 contexts never take the single-pass kernel)
+            if (tape_fused(c)) {
+                r = cudaMemcpyAsync(segqf(sl, 0), c->ckptq[k], sizeof(float) * (size_t)fused_q_pitch(nx) * ny,
+                                    cudaMemcpyDeviceToDevice, s);
+                const void *cur = c->ckpt[k];
+                for (int t = t0; t < t1 && r == cudaSuccess; ++t) {
+                    // (programmatic launches here too: plain ones, which hold no SM
+                    // resources while they wait, made the sweep 4 % slower)
+                    void *dst = c->tmp[(t + 1) & 1];
+                    void *qn = t + 1 < t1 ? segqf(sl, t + 1 - t0) : c->qpad_tape[0];
+                    r = launch_fused_step(m, is_sc(c), is_cdm(c), (const float *)cur, (const float *)segqf(sl, t - t0),
+                                          (float *)dst, (float *)qn, c->err, rows, s, true, (float *)segrec(sl, t - t0));
+                    cur = dst;
                 }
+                return r;
+            }
+        }
+        const void *cur = c->ckpt[k];
+        for (int t = t0; t < t1 && r == cudaSuccess; ++t) {
+            r = launch_potential<T>(m, is_sc(c), (const T *)cur, (T *)segqf(sl, t - t0), c->err, s);
+            if (r == cudaSuccess && t < t1 - 1) {
+                r = launch_collide<T>(m, is_sc(c), is_cdm(c), (const T *)cur, (const T *)segqf(sl, t - t0),
+                                      (T *)segf(sl, t - t0), s);
+                cur = segf(sl, t - t0);
             }
         }
         return r;
