@@ -51,7 +51,8 @@ typedef enum {
     LBM_E_CUDA = 3,     /* a CUDA runtime call failed */
     LBM_E_UNSTABLE = 4, /* the device error word saw a NaN or rho <= 0 */
     LBM_E_TIMEOUT = 5,  /* a bounded device-side wait gave up */
-    LBM_E_STATE = 6     /* call out of order (e.g. step before init) */
+    LBM_E_STATE = 6,    /* call out of order (e.g. step before init) */
+    LBM_E_IO = 7        /* a saved-state file could not be written or read, or is not one */
 } lbm_status;
 
 /* Equations of state (Sec. 5.2): van der Waals (Eq. 24), Carnahan-Starling
@@ -439,6 +440,25 @@ lbm_status lbm_debug_alloc_stats(long long *live_device, long long *live_host);
  * pattern changed (synchronises the device), or -1 in the normal build,
  * which has neither checks nor canaries. */
 lbm_status lbm_debug_check_canaries(long long *damaged);
+
+/* Saved lattice states (not a passage of the paper: checkpoint and resume).
+ * lbm_save writes the current distributions in the storage precision to the
+ * file `path` (created or truncated), with a header of the lattice's
+ * parameters, for a context on the single-pass kernel the stencil field its
+ * next step reads, and a checksum.  LBM_E_STATE before initialisation,
+ * LBM_E_UNSTABLE for a lattice in the error state, LBM_E_IO if the file cannot
+ * be written.  Synchronising.
+ * lbm_load reads such a file into a context of the same nx, ny and precision
+ * (else LBM_E_INVALID; other parameters may differ: a restart at another
+ * temperature, say) and leaves it initialised on that state.  The saved
+ * stencil field is used where the context runs the single-pass kernel and
+ * every parameter the field depends on matches, so that a resumed run repeats
+ * an uninterrupted one bit for bit; otherwise the next step forms the field
+ * from the distributions.  LBM_E_IO for a file that cannot be read, is not a
+ * saved state, is truncated or fails its checksum; the context then keeps its
+ * state.  Synchronising. */
+lbm_status lbm_save(lbm_ctx *c, const char *path);
+lbm_status lbm_load(lbm_ctx *c, const char *path);
 
 /* Free everything the context owns.  NULL is a no-op. */
 void lbm_destroy(lbm_ctx *c);

@@ -988,6 +988,129 @@ lbm_status lbm_get_f(lbm_ctx *c, double *f) {
     return read_error_word(c);
 }
 
+}  // extern "C"
+
+namespace {
+
+// ---- saved states (lbm_save / lbm_load) ----
+// File: a fixed header, the current distributions in the storage precision
+// (nine planes of nx ny), for single-pass contexts the padded stencil field
+// the next step reads, and a checksum of those bytes.
+struct StateHeader {
+    char magic[8];            // "LBMSTAT1"
+    int32_t nx, ny, prec, eos, force, grad, hdm_radius, flags;
+    double a, b, R, omega, Tr, Tc, k, tau, G, rho0;
+    int64_t f_bytes, q_bytes;   // q_bytes 0: no stencil field saved
+};
+static_assert(sizeof(StateHeader) == 8 + 8 * 4 + 10 * 8 + 2 * 8, "fixed layout");
+const char kStateMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
+
+// FNV-1a over 64 chunks (hashed in parallel), then over the chunk hashes.
+uint64_t state_checksum(const unsigned char *p, size_t n) {
+    constexpr int kChunks = 64;
+    uint64_t h[kChunks];
+    parallel_for(kChunks * (1LL << 20), [&](long long lo, long long hi) {
+        for (long long k = lo >> 20; k < ((hi + (1LL << 20) - 1) >> 20) && k < kChunks; ++k) {
+            const size_t a = n * k / kChunks, b = n * (k + 1) / kChunks;
+            uint64_t x = 1469598103934665603ull;
+            for (size_t i = a; i < b; ++i) x = (x ^ p[i]) * 1099511628211ull;
+            h[k] = x;
+        }
+    });
+    uint64_t x = 1469598103934665603ull;
+    for (int k = 0; k < kChunks; ++k)
+        for (int byte = 0; byte < 8; ++byte) x = (x ^ ((h[k] >> (8 * byte)) & 0xff)) * 1099511628211ull;
+    return x;
+}
+
+// The parameters the saved stencil field depends on match the context's.
+bool same_physics(const StateHeader &h, const lbm_params &p) {
+    return h.eos == p.eos && h.force == p.force && h.grad == p.grad && h.hdm_radius == p.hdm_radius &&
+           (h.flags & LBM_FLAG_WALLS_Y) == (p.flags & LBM_FLAG_WALLS_Y) && h.a == p.a && h.b == p.b && h.R == p.R &&
+           h.omega == p.omega && h.Tr == p.Tr && h.Tc == p.Tc && h.k == p.k && h.G == p.G && h.rho0 == p.rho0;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_save(lbm_ctx *c, const char *path) {
+    lbm_status st = check_ready(c);
+    if (st != LBM_OK) return st;
+    if (!path) return fail(c, LBM_E_INVALID, "path is NULL");
+    if ((st = read_error_word(c)) != LBM_OK) return st;   // no state of a lattice in the error state
+    StateHeader h{};
+    std::memcpy(h.magic, kStateMagic, sizeof(h.magic));
+    const lbm_params &p = c->p;
+    h.nx = p.nx; h.ny = p.ny; h.prec = p.prec; h.eos = p.eos; h.force = p.force; h.grad = p.grad;
+    h.hdm_radius = p.hdm_radius; h.flags = p.flags;
+    h.a = p.a; h.b = p.b; h.R = p.R; h.omega = p.omega; h.Tr = p.Tr; h.Tc = p.Tc; h.k = p.k; h.tau = p.tau;
+    h.G = p.G; h.rho0 = p.rho0;
+    h.f_bytes = (int64_t)kQ * c->n * c->esz;
+    h.q_bytes = c->fused && c->qpad_valid ? (int64_t)sizeof(float) * fused_q_pitch(p.nx) * p.ny : 0;
+    if ((st = ensure_stage(c, h.f_bytes + h.q_bytes)) != LBM_OK) return st;
+    unsigned char *buf = (unsigned char *)c->stage;
+    CK(c, cudaMemcpyAsync(buf, c->f[c->cur], h.f_bytes, cudaMemcpyDeviceToHost, c->stream), "copy f");
+    if (h.q_bytes)
+        CK(c, cudaMemcpyAsync(buf + h.f_bytes, c->qpad[c->cur], h.q_bytes, cudaMemcpyDeviceToHost, c->stream),
+           "copy stencil field");
+    CK(c, cudaStreamSynchronize(c->stream), "sync state copy");
+    const uint64_t sum = state_checksum(buf, h.f_bytes + h.q_bytes);
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(c, LBM_E_IO, "cannot open %s for writing", path);
+    const bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 &&
+                    std::fwrite(buf, 1, h.f_bytes + h.q_bytes, fp) == (size_t)(h.f_bytes + h.q_bytes) &&
+                    std::fwrite(&sum, sizeof(sum), 1, fp) == 1;
+    if (std::fclose(fp) != 0 || !ok) return fail(c, LBM_E_IO, "writing %s failed", path);
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx *c, const char *path) {
+    if (!c) return LBM_E_INVALID;
+    if (!path) return fail(c, LBM_E_INVALID, "path is NULL");
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(c, LBM_E_IO, "cannot open %s", path);
+    StateHeader h{};
+    auto close_fail = [&](lbm_status s2, const char *why) {
+        std::fclose(fp);
+        return fail(c, s2, "%s: %s", path, why);
+    };
+    if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, kStateMagic, sizeof(h.magic)) != 0)
+        return close_fail(LBM_E_IO, "not a saved lattice state");
+    if (h.nx != c->p.nx || h.ny != c->p.ny || h.prec != c->p.prec)
+        return close_fail(LBM_E_INVALID, "lattice size or precision differs from the context's");
+    const int64_t fb = (int64_t)kQ * c->n * c->esz;
+    const int64_t qb_expected = (int64_t)sizeof(float) * fused_q_pitch(c->p.nx) * c->p.ny;
+    if (h.f_bytes != fb || (h.q_bytes != 0 && (h.prec != LBM_F32 || h.q_bytes != qb_expected)))
+        return close_fail(LBM_E_IO, "inconsistent header");
+    lbm_status st = ensure_stage(c, h.f_bytes + h.q_bytes);
+    if (st != LBM_OK) {
+        std::fclose(fp);
+        return st;
+    }
+    CK(c, cudaStreamSynchronize(c->stream), "sync before staging");
+    unsigned char *buf = (unsigned char *)c->stage;
+    uint64_t sum = 0;
+    if (std::fread(buf, 1, h.f_bytes + h.q_bytes, fp) != (size_t)(h.f_bytes + h.q_bytes) ||
+        std::fread(&sum, sizeof(sum), 1, fp) != 1)
+        return close_fail(LBM_E_IO, "truncated");
+    std::fclose(fp);
+    if (sum != state_checksum(buf, h.f_bytes + h.q_bytes)) return fail(c, LBM_E_IO, "%s: checksum mismatch", path);
+    c->cur = 0;
+    CK(c, cudaMemcpyAsync(c->f[0], buf, h.f_bytes, cudaMemcpyHostToDevice, c->stream), "copy f");
+    // the saved stencil field where this context reads one and the physics
+    // matches (a resumed run then repeats the uninterrupted one bit for bit);
+    // else the next step forms it from f
+    const bool use_q = h.q_bytes != 0 && c->fused && same_physics(h, c->p);
+    if (use_q)
+        CK(c, cudaMemcpyAsync(c->qpad[0], buf + h.f_bytes, h.q_bytes, cudaMemcpyHostToDevice, c->stream),
+           "copy stencil field");
+    CK(c, cudaStreamSynchronize(c->stream), "sync state copy");
+    st = mark_initialized(c);
+    c->qpad_valid = use_q;
+    return st;
+}
+
 lbm_status lbm_step(lbm_ctx *c, int nsteps) {
     NvtxRange nvtx("lbm_step");
     lbm_status st = check_ready(c);

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, E_INVALID, E_NOMEM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE = range(7)
+OK, E_INVALID, E_NOMEM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE, E_IO = range(8)
 EOS = {"vdw": 0, "cs": 1, "pr": 2, "rk": 3, "rks": 4, "psi_exp": 5}
 FORCE = {"sc": 0, "zc": 1}
 GRAD = {"hdm": 0, "cdm": 1}
@@ -108,6 +108,8 @@ SIGNATURES = {
     "lbm_destroy": (None, [_V]),
     "lbm_last_error": (ctypes.c_char_p, [_V]),
     "lbm_host_in_place": (ctypes.c_int, [_V]),
+    "lbm_save": (ctypes.c_int, [_V, ctypes.c_char_p]),
+    "lbm_load": (ctypes.c_int, [_V, ctypes.c_char_p]),
 }
 
 
@@ -285,6 +287,14 @@ class Lattice:
         r, vx, vy = out
         self._check(self._lib.lbm_moments(self._h, _dp(r), _dp(vx), _dp(vy)))
         return r, vx, vy
+
+    def save(self, path):
+        """Write the current state (and the single-pass kernel's stencil field) to a file."""
+        self._check(self._lib.lbm_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        """Resume from a file written by save() (same nx, ny and precision)."""
+        self._check(self._lib.lbm_load(self._h, os.fsencode(path)))
 
     def host_in_place(self) -> bool:
         """True if the device reads and writes this context's host arrays in place
