@@ -40,7 +40,7 @@
 // differentiates only D_bar.  The HDM stencils run at a compile-time radius
 // (26 in FP32, 40 in FP64) over weights that are zero past the folded radius
 // of the lattice; in the padded layout kernel B forms the tile's derivatives
-// once, in recurrence form (hdm_window4), before its per-cell work.  The
+// once, in recurrence form on packed pairs, before its per-cell work.  The
 // padded FP32 kernels are launched with programmatic serialization: A reads
 // the record and forms the forward quantities while the previous step's B
 // finishes, and every read of a predecessor's output and every write waits
@@ -274,7 +274,7 @@ constexpr int LO = 4;    // lambda halo columns staged (>= 1)
 
 // HDM derivatives of a padded FP32 tile (64 x 16 cells) of a staged field,
 // written to D[ly * 64 + lx] (along x) and D[1024 + ly * 64 + lx] (along y),
-// both radius-26 operators in recurrence form (hdm_window4).
+// both radius-26 operators in recurrence form on packed pairs (hdm_window4_paired).
 // Along x, tile row ly is staged at X + ly * XP with tile column c at X + ly *
 // XP + 28 + c; work items 0..255 take four cells of a row each from one
 // 60-value window of 16-byte loads.  Along y, tile cell (lx, ly) is staged at
@@ -289,6 +289,7 @@ __device__ __forceinline__ void tile_hdm(const float *X, int XP, const float *Y,
     const int item = threadIdx.x + blockDim.x * threadIdx.y;
     if (item >= 512) return;
     float t[60], d[4];
+    float2 tp[28];   // deviations paired about the window's centre (hdm_window4_paired)
 #pragma unroll
     for (int p = 0; p < 60; ++p) t[p] = 0.f;
     if (item < 256) {
@@ -301,8 +302,8 @@ __device__ __forceinline__ void tile_hdm(const float *X, int XP, const float *Y,
         }
         const float ref = mag(t[29]);
 #pragma unroll
-        for (int p = 2; p <= 57; ++p) t[p] = mag(t[p]) - ref;
-        hdm_window4(t, m.wx[1], m.wx[2], r, r5, r25, d);
+        for (int j = 0; j < 28; ++j) tp[j] = make_float2(mag(t[2 + j]) - ref, mag(t[57 - j]) - ref);
+        hdm_window4_paired(tp, m.wx[1], m.wx[2], r, r5, r25, d);
         *reinterpret_cast<float4 *>(D + ly * 64 + 4 * g) = make_float4(d[0], d[1], d[2], d[3]);
     } else {
         const int i = item - 256, cx = i & 63, h = i >> 6;
@@ -311,8 +312,8 @@ __device__ __forceinline__ void tile_hdm(const float *X, int XP, const float *Y,
         for (int p = 2; p <= 57; ++p) t[p] = col[(p - 2) * YP];
         const float ref = mag(t[29]);
 #pragma unroll
-        for (int p = 2; p <= 57; ++p) t[p] = mag(t[p]) - ref;
-        hdm_window4(t, m.wy[1], m.wy[2], r, r5, r25, d);
+        for (int j = 0; j < 28; ++j) tp[j] = make_float2(mag(t[2 + j]) - ref, mag(t[57 - j]) - ref);
+        hdm_window4_paired(tp, m.wy[1], m.wy[2], r, r5, r25, d);
 #pragma unroll
         for (int c = 0; c < 4; ++c) D[1024 + (4 * h + c) * 64 + cx] = d[c];
     }

@@ -105,7 +105,9 @@ constexpr size_t kOffQw = kQnBytes;
 constexpr size_t kAbBytes = sizeof(float) * 2 * 2 * SLAB * NW;  // P, Q of the slab rows, two slabs
 constexpr size_t kOffPs = kOffQw + kQwBytes;
 constexpr size_t kOffAb = kOffPs + kPsBytes;
-constexpr size_t kOffBar = kOffAb + kAbBytes;
+constexpr size_t kFqBytes = sizeof(float) * NW;                 // far parts of the d/dy backward sums
+constexpr size_t kOffFq = kOffAb + kAbBytes;
+constexpr size_t kOffBar = kOffFq + kFqBytes;
 constexpr size_t kSmemBytes = kOffBar + sizeof(uint64_t) * (QCH + 2);
 
 struct FusedArgs {
@@ -262,6 +264,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     float *qw = reinterpret_cast<float *>(smem + kOffQw);      // [2][SLAB][WW]
     float *ps = reinterpret_cast<float *>(smem + kOffPs);      // [3][PROWS][NW]
     float *ab = reinterpret_cast<float *>(smem + kOffAb);      // [2 slabs][2][SLAB][NW]: P_{y-1}, Q_{y+1}
+    float *fq = reinterpret_cast<float *>(smem + kOffFq);      // [NW]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // QCH chunk barriers + 2 row barriers
     uint64_t *row_bar = &bars[QCH];
 
@@ -341,19 +344,20 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         for (int i = 0; i < 9; ++i, p += A.n4) fv[i] = ok ? ld_stream(p) : make_float4(0.f, 0.f, 0.f, 0.f);
     };
     // d/dy column recurrences: thread (warp, lane) follows ring column
-    // 16 warp + lane % 16 (padded column x0 + QG - 4 + cl); lanes < 16 carry the
-    // forward sum P down the segment.  Its start P_(ys-2), over rows ys - 27 ..
-    // ys - 3 above the ring, and the column's reference value q(ys - 1) come from
-    // the padded field, with all loads in flight while the first copies land.
-    const int cl = 16 * warp + (lane & 15);
-    const bool fwdl = lane < 16;
+    // cl = 32 (warp % 4) + lane (padded column x0 + QG - 4 + cl); warps 0..3 carry
+    // the forward sum P down the segment, warps 4..7 form the backward sums.
+    // P's start P_(ys-2), over rows ys - 27 .. ys - 3 above the ring, and the
+    // column's reference value q(ys - 1) come from the padded field, with all
+    // loads in flight while the first copies land.
+    const bool fwdw = warp < SLAB / 2;
+    const int cl = 32 * (warp & (SLAB / 2 - 1)) + lane;
     auto mag = [](float v) { return SC ? fabsf(v) : v; };   // the stencil's field value
     float colref = 0.f, pcarry = 0.f;
     if (!CDMG && cl < ncols) {
         const float *g = A.qin + x0 + QG - 4 + cl;
         const int yr = WALLS ? mirror_index(ys - 1, ny) : (ys - 1 < 0 ? ys - 1 + ny : ys - 1);
         colref = mag(__ldg(g + (long long)yr * A.qpitch));
-        if (fwdl) {
+        if (fwdw) {
             float v[25];
 #pragma unroll
             for (int k = 0; k < 25; ++k) {
@@ -370,33 +374,51 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     // a column, P_y = t_(y-1) + r P_(y-1) and Q_y = t_(y+1) + r Q_(y+1),
     //   D_y = w_1 (q_(y+1) - q_(y-1)) + w_2 (Q_(y+1) - P_(y-1)).
     // Q_(y+1) of the slab's last row sums the 25 rows below it (the same
-    // truncation as the stencil): lanes >= 16 take the 12 nearest, lanes < 16
-    // the 13 farthest (one shuffle joins them); then lanes < 16 step P down
-    // the slab (carried across slabs) and lanes >= 16 step Q up it.  Every
-    // lane runs the same instructions on its own rows; all rows read lie in
-    // ring chunks s .. s + 4.  Slab s + 1's recurrences run at the end of slab
-    // s, so one barrier per slab serves them and the partial densities.
+    // truncation as the stencil): warp w + 4 takes the 12 nearest, warp w the
+    // 13 farthest, which it hands over through shared memory and a two-warp
+    // named barrier; then warp w steps P down the slab (carried across slabs)
+    // and warp w + 4 steps Q up it.  Every ring row a step reads lies in ring
+    // chunks s .. s + 4 at a compile-time offset from that chunk's slot.  Slab
+    // s + 1's recurrences run at the end of slab s, so one barrier per slab
+    // serves them and the partial densities (and orders the far parts' reuse).
     auto column_phase = [&](int s) {
-        const float *col = qn + cl;
-        const int y0r = SLAB * s + QBASE - 1;   // ring-relative row of the slab's first row
-        float x = 0.f;
-        int ri = (y0r + (fwdl ? 33 : 20)) % QRING;   // far part Y0+33 .. Y0+21, near part Y0+20 .. Y0+9
+        // row Y0 + d of the slab (Y0 its first row, -1 <= d <= 33) is row e % 8 of ring
+        // chunk s + e / 8, e = d + QBASE - 1
+        const float *cb[QAHEAD + 1];
+        int slot = s % QCH;
 #pragma unroll
-        for (int k = 0; k < 13; ++k) {
-            if (fwdl || k < 12) x = fmaf(A.ry, x, mag(col[ri * NW]) - colref);
-            ri = ri == 0 ? QRING - 1 : ri - 1;
+        for (int j = 0; j <= QAHEAD; ++j) {
+            cb[j] = qn + slot * SLAB * NW + cl;
+            slot = slot == QCH - 1 ? 0 : slot + 1;
         }
-        const float far = __shfl_sync(0xffffffffu, x, lane & 15);
-        float v = fwdl ? pcarry : fmaf(A.ry12, far, x);   // P_(Y0-1) or Q_(Y0+8)
-        ri = fwdl ? (y0r - 1) % QRING : (y0r + SLAB) % QRING;
-        float *dst = ab + (s & 1) * 2 * SLAB * NW + (fwdl ? 0 : SLAB * NW) + cl;
+        auto tq = [&](int d) { return mag(cb[(d + QBASE - 1) / SLAB][((d + QBASE - 1) % SLAB) * NW]) - colref; };
+        float *buf = ab + (s & 1) * 2 * SLAB * NW + cl;
+        const int bar_id = 1 + (warp & (SLAB / 2 - 1));
+        if (fwdw) {
+            float x = tq(33);   // the far part of Q_(Y0+8): rows Y0+33 .. Y0+21
 #pragma unroll
-        for (int k = 0; k < SLAB; ++k) {
-            dst[(fwdl ? k : SLAB - 1 - k) * NW] = v;     // P_(Y0+k-1) / Q_(Y0+8-k)
-            v = fmaf(A.ry, v, mag(col[ri * NW]) - colref);   // rows Y0-1+k / Y0+8-k
-            ri = fwdl ? (ri + 1 == QRING ? 0 : ri + 1) : (ri == 0 ? QRING - 1 : ri - 1);
+            for (int d = 32; d >= 21; --d) x = fmaf(A.ry, x, tq(d));
+            fq[cl] = x;
+            asm volatile("bar.arrive %0, %1;" ::"r"(bar_id), "r"(64) : "memory");
+            float v = pcarry;   // P_(Y0-1)
+#pragma unroll
+            for (int k = 0; k < SLAB; ++k) {
+                buf[k * NW] = v;                       // P_(Y0+k-1)
+                v = fmaf(A.ry, v, tq(k - 1));          // row Y0-1+k
+            }
+            pcarry = v;   // P_(Y0+7) = P of the next slab's first row minus one
+        } else {
+            float x = tq(20);   // the near part: rows Y0+20 .. Y0+9
+#pragma unroll
+            for (int d = 19; d >= 9; --d) x = fmaf(A.ry, x, tq(d));
+            asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(64) : "memory");
+            float v = fmaf(A.ry12, fq[cl], x);         // Q_(Y0+8)
+#pragma unroll
+            for (int k = 0; k < SLAB; ++k) {
+                buf[(2 * SLAB - 1 - k) * NW] = v;      // Q_(Y0+8-k)
+                v = fmaf(A.ry, v, tq(SLAB - k));       // row Y0+8-k
+            }
         }
-        if (fwdl) pcarry = v;   // P_(Y0+7) = P of the next slab's first row minus one
     };
 
     load_f(0);
@@ -431,20 +453,18 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
         // columns and store nothing.
         {
             float dx[4], dy[4], qc[4];
-            // moments of f(t) (Eq. 3), cells (0, 1) and (2, 3) as packed pairs
-            float2 r2[2] = {splat2(0.f), splat2(0.f)}, jx2[2] = {splat2(0.f), splat2(0.f)},
-                   jy2[2] = {splat2(0.f), splat2(0.f)};
+            // moments of f(t) (Eq. 3), cells (0, 1) and (2, 3) as packed pairs, from
+            // the sums over the populations moving east (1, 5, 8), west (3, 6, 7),
+            // north (2, 5, 6) and south (4, 7, 8): 14 additions instead of 21
+            float2 r2[2], jx2[2], jy2[2];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const float2 v[2] = {make_float2(fv[i].x, fv[i].y), make_float2(fv[i].z, fv[i].w)};
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    r2[h] = add2(r2[h], v[h]);
-                    if (ex(i) == 1) jx2[h] = add2(jx2[h], v[h]);
-                    if (ex(i) == -1) jx2[h] = sub2(jx2[h], v[h]);
-                    if (ey(i) == 1) jy2[h] = add2(jy2[h], v[h]);
-                    if (ey(i) == -1) jy2[h] = sub2(jy2[h], v[h]);
-                }
+            for (int h = 0; h < 2; ++h) {
+                auto v = [&](int i) { return h ? make_float2(fv[i].z, fv[i].w) : make_float2(fv[i].x, fv[i].y); };
+                const float2 east = add2(add2(v(1), v(5)), v(8)), west = add2(add2(v(3), v(6)), v(7));
+                const float2 north = add2(add2(v(2), v(5)), v(6)), south = add2(add2(v(4), v(7)), v(8));
+                r2[h] = add2(add2(add2(v(0), v(2)), v(4)), add2(east, west));
+                jx2[h] = sub2(east, west);
+                jy2[h] = sub2(north, south);
             }
             // for tau = 1 nothing after the moments reads f(t), so f(t) of the next
             // slab goes in flight here, across the derivatives and the collision
@@ -476,8 +496,9 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
                 }
             } else {
                 {   // d/dx: wide row columns 4 lane .. 4 lane + 59; cells at window positions 28..31.
-                    // The radius-26 operator in recurrence form (hdm_window4); each staged
-                    // value enters as its deviation t from the lane's second cell.
+                    // The radius-26 operator in recurrence form on packed pairs
+                    // (hdm_window4_paired); each staged value enters as its deviation
+                    // from the lane's second cell.
                     const float *qrow = qw + ((s & 1) * SLAB + warp) * WW + 4 * lane;
                     float t[60];
     #pragma unroll
@@ -488,9 +509,10 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     #pragma unroll
                     for (int c = 0; c < 4; ++c) qc[c] = t[28 + c];
                     const float qref = mag(t[29]);
+                    float2 tp[28];   // deviations paired about the window's centre
     #pragma unroll
-                    for (int p = 2; p <= 57; ++p) t[p] = mag(t[p]) - qref;
-                    hdm_window4(t, A.w1x, A.w2x, A.ry, A.ry5, A.ry25, dx);
+                    for (int j = 0; j < 28; ++j) tp[j] = make_float2(mag(t[2 + j]) - qref, mag(t[57 - j]) - qref);
+                    hdm_window4_paired(tp, A.w1x, A.w2x, A.ry, A.ry5, A.ry25, dx);
                 }
                 {   // d/dy from the column recurrences of this row
                     const float4 qa = *reinterpret_cast<const float4 *>(qn + ((ryc + 1) % QRING) * NW + 4 * lane);
@@ -518,10 +540,14 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             }
             // force and the two velocities of the forcing (Eq. 10, 22 / 7)
             float2 ux[2], uy[2], vx[2], vy[2], au[2], av[2], moved[2];
+            {   // the 4 densities positive and finite: the least above 0, the sum finite (a NaN or
+                // an infinity makes it not; a sum past the FP32 range flags a blown-up state too)
+                const float2 rs = add2(r2[0], r2[1]);
+                const float rmin = fminf(fminf(r2[0].x, r2[0].y), fminf(r2[1].x, r2[1].y));
+                unstable |= active && !(rmin > 0.f && rs.x + rs.y < INFINITY);
+            }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                unstable |= active && !(r2[h].x > 0.f && r2[h].x < INFINITY);   // NaN fails both
-                unstable |= active && !(r2[h].y > 0.f && r2[h].y < INFINITY);
                 const float2 gx = make_float2(dx[2 * h], dx[2 * h + 1]), gy = make_float2(dy[2 * h], dy[2 * h + 1]);
                 float2 Fx, Fy;
                 if (SC) {   // Eq. 22: F = -2 s Phi grad Phi, s Phi the stored field at the cell

@@ -155,4 +155,32 @@ __device__ __forceinline__ void hdm_window4(const float (&t)[60], float w1, floa
     for (int c = 0; c < 4; ++c) d[c] = fmaf(w1, t[29 + c] - t[27 + c], w2 * (Q[c] - P[c]));
 }
 
+// hdm_window4 on packed FP32 pairs.  The 56 deviations arrive as the pairs
+// tp[j] = (t_(2+j), t_(57-j)), j = 0..27, so that P's group g and Q's group
+// 4 - g run side by side (the same positions mirrored about the window's
+// centre), then the joins (P_0, Q_3) and the steps (P_c, Q_(3-c)).  Each
+// component is rounded as the scalar fma, so the result equals hdm_window4's
+// bit for bit with half the multiply-adds.
+__device__ __forceinline__ void hdm_window4_paired(const float2 (&tp)[28], float w1, float w2, float r, float r5,
+                                                   float r25, float (&d)[4]) {
+    const float2 r2 = make_float2(r, r), r52 = make_float2(r5, r5), mr25 = make_float2(-r25, -r25);
+    float2 G[5];
+#pragma unroll
+    for (int g = 0; g < 5; ++g) {
+        float2 x = tp[5 * g];
+#pragma unroll
+        for (int i = 1; i < 5; ++i) x = __ffma2_rn(r2, x, tp[5 * g + i]);
+        G[g] = x;                               // (group g of P_0, group 4 - g of Q_3)
+    }
+    float2 S[4];                                // S_c = (P_c, Q_(3-c))
+    S[0] = G[0];
+#pragma unroll
+    for (int g = 1; g < 5; ++g) S[0] = __ffma2_rn(r52, S[0], G[g]);
+#pragma unroll
+    for (int c = 1; c < 4; ++c) S[c] = __ffma2_rn(mr25, tp[c - 1], __ffma2_rn(r2, S[c - 1], tp[24 + c]));
+    auto at = [&](int p) { return p <= 29 ? tp[p - 2].x : tp[57 - p].y; };   // t_p, p = 27..32
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d[c] = fmaf(w1, at(29 + c) - at(27 + c), w2 * (S[3 - c].y - S[c].x));
+}
+
 }  // namespace lbm
