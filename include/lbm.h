@@ -263,8 +263,9 @@ lbm_status lbm_get_segment_rows(lbm_ctx *c, int *rows);
 
 /* Autotuner for the segment height (not a passage of the paper): times
  * `trials` (1..1000) launches of the single-pass step for every height
- * 8k - 2 <= min(ny, 1022), on the current state, keeps the fastest for the
- * context and returns it in *rows.  The state is kept: each trial reads f
+ * 8k - 2 <= min(ny, 1022), on the current state, re-times the six fastest in
+ * three interleaved rounds of 8 x `trials` launches each, keeps the one with
+ * the least total time for the context and returns it in *rows.  The state is kept: each trial reads f
  * and writes only the buffers that the next step overwrites.  *rows = 0 and
  * nothing timed when the context runs the two-pass step.  LBM_E_STATE before
  * initialisation, LBM_E_INVALID for a bad argument, LBM_E_UNSTABLE if the

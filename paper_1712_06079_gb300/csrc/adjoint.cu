@@ -46,9 +46,9 @@
 // finishes, and every read of a predecessor's output and every write waits
 // for it (griddepcontrol.wait).  T_bar
 // terms are summed over each warp in the working precision (32 terms), then
-// in FP64 over the warps of a CTA into one slot per CTA (no atomics, so the
-// sum is reproducible), over the steps in the same slots, and over the slots
-// in a fixed order at the end.
+// added in FP64 to one slot per warp of each CTA (one writer per slot and
+// launch, and the launches are ordered, so the sum is reproducible), over the
+// steps in the same slots, and over the slots in a fixed order at the end.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -182,22 +182,20 @@ struct AdjArgs {
     T r, r5, r25;   // r = (sqrt 5 - 3)/2 of Eq. 20's operator and its powers (padded FP32 tiles)
 };
 
-// Sum of v over the CTA (over each warp in T, then in FP64), added to *slot.
+// FP64 dL/dT slots of a tile kernel's CTAs: one per warp.
 template <typename T>
-__device__ __forceinline__ void block_sum_into(T v, double *slot) {
-    __shared__ double red[32];
+constexpr int adj_warps() { return AdjTile<T>::TX * AdjTile<T>::TYT / 32; }
+
+// Sum of v over each warp (in T), added in FP64 to the warp's own slot
+// cta_slots[w].  Each slot has one writer per launch and the launches are
+// ordered, so the sums are reproducible; the addition is issued without
+// waiting for its result, and no warp waits for the others.
+template <typename T>
+__device__ __forceinline__ void warp_sum_into(T v, double *cta_slots) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    const int nwarps = (blockDim.x * blockDim.y + 31) / 32;
-    if ((tid & 31) == 0) red[tid >> 5] = (double)v;
-    __syncthreads();
-    if (tid < 32) {
-        double s = tid < nwarps ? red[tid] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (tid == 0) *slot += s;
-    }
+    if ((tid & 31) == 0) atomicAdd(cta_slots + (tid >> 5), (double)v);
 }
 
 // Copies the rectangle [lx0, lx1) x [ly0, ly1) of a shared array of pitch P
@@ -515,7 +513,7 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_a_kernel(
             }
         }
     }
-    if (SC) block_sum_into(tacc, a.Tpart + blockIdx.x + gridDim.x * blockIdx.y);
+    if (SC) warp_sum_into(tacc, a.Tpart + (size_t)(blockIdx.x + gridDim.x * blockIdx.y) * adj_warps<T>());
 }
 
 // Kernel A in the padded FP32 layout of the single-pass kernel.  The forward
@@ -645,7 +643,7 @@ __global__ void __launch_bounds__(AdjTile<float>::TX *AdjTile<float>::TYT) adj_a
             }
         }
     }
-    if (SC) block_sum_into(tacc, a.Tpart + blockIdx.x + gridDim.x * blockIdx.y);
+    if (SC) warp_sum_into(tacc, a.Tpart + (size_t)(blockIdx.x + gridDim.x * blockIdx.y) * adj_warps<float>());
 }
 
 template <typename T, bool SC, bool CDM, bool TAU1, int KC, bool PAD>
@@ -773,7 +771,7 @@ __global__ void __launch_bounds__(AdjTile<T>::TX *AdjTile<T>::TYT) adj_b_kernel(
             }
         }
     }
-    block_sum_into(tacc, a.Tpart + blockIdx.x + gridDim.x * blockIdx.y);
+    warp_sum_into(tacc, a.Tpart + (size_t)(blockIdx.x + gridDim.x * blockIdx.y) * adj_warps<T>());
 }
 
 // lambda at the final step from dL/drho_T (rho_T = sum_i f_i): lambda_i = g
@@ -907,7 +905,7 @@ cudaError_t launch_adj_t(const AdjArgs<T> &a, bool overlap_prev, cudaStream_t s)
     e = launch_pdl(PAD && overlap_prev, ka, grid, block, smem_a, s, a);
     if (e != cudaSuccess) return e;
     AdjArgs<T> b = a;
-    b.Tpart = a.Tpart + grid.x * grid.y;
+    b.Tpart = a.Tpart + (size_t)grid.x * grid.y * adj_warps<T>();
     e = launch_pdl(PAD, kb, grid, block, smem_b, s, b);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -935,7 +933,7 @@ cudaError_t launch_adj_k(const AdjArgs<T> &a, bool padded, bool overlap_prev, cu
 template <typename T>
 int adjoint_slots(int nx, int ny) {
     const dim3 g = adj_grid<T>(nx, ny);
-    return 2 * (int)(g.x * g.y);
+    return 2 * (int)(g.x * g.y) * adj_warps<T>();
 }
 
 AdjLayout adjoint_layout(int nx, int ny, bool padded, bool tau1) {

@@ -136,11 +136,9 @@ __device__ __forceinline__ float4 ld_stream(const float4 *p) {
     return v;
 }
 
-__device__ __forceinline__ int wrapi(int i, int n) {
-    while (i < 0) i += n;
-    while (i >= n) i -= n;
-    return i;
-}
+// Periodic wrap of an index at most one period outside [0, n) (every row and
+// column index this file wraps lies in [-n, 2n))
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // Square root by the hardware's approximate instruction (sqrt.approx.f32, a
 // PTX instruction; a few ulp against the correctly rounded root, against the

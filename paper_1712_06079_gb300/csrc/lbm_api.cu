@@ -90,6 +90,14 @@ lbm_status model_scalars(const lbm_params &p, ModelScalars *s) {
 
 }  // namespace lbm
 
+// Reverse sweep: segment k's recomputed states (or records) and stencil fields
+// live in slot k % kTapeSlots, so the recompute on its own stream may run up
+// to kTapeSlots - 1 segments ahead of the adjoint steps.  Two: a third slot
+// (the recompute two segments ahead) measured no faster at 512^2, 5000 steps,
+// and either stream at the higher priority starved the other (11 % slower).
+constexpr int kTapeSlots = 2;
+static_assert(kTapeSlots >= 2, "the recompute runs at least one segment ahead");
+
 struct lbm_ctx {
     lbm_params p{};
     ModelScalars ms{};              // host scalars of p (temperature, EOS constants)
@@ -138,12 +146,12 @@ struct lbm_ctx {
     // inside a segment (single-pass contexts: the forward kernel's record of
     // every state of a segment), the stencil field of every state of a
     // segment, the adjoint ping-pong, kernel scratch and the FP64 dL/dT slots
-    // (two sets: the recompute of one segment runs on rstream while the
-    // adjoint steps of the next later segment run on astream)
+    // (kTapeSlots sets: the recompute of the next earlier segments runs on
+    // rstream while the adjoint steps of a segment run on astream)
     std::vector<void *> seg, segq;
     cudaStream_t rstream = nullptr;
     cudaStream_t astream = nullptr;   // the adjoint steps
-    cudaEvent_t rec_done[2] = {nullptr, nullptr}, adj_done[2] = {nullptr, nullptr}, bw_start = nullptr;
+    cudaEvent_t rec_done[kTapeSlots] = {}, adj_done[kTapeSlots] = {}, bw_start = nullptr;
     void *lam[2] = {nullptr, nullptr};
     void *aux = nullptr;
     double *slots = nullptr;
@@ -411,6 +419,8 @@ void free_tape(lbm_ctx *c) {
     for (int k = 0; k < 2; ++k) {
         dev_free(c->lam[k]);
         c->lam[k] = nullptr;
+    }
+    for (int k = 0; k < kTapeSlots; ++k) {
         if (c->rec_done[k]) cudaEventDestroy(c->rec_done[k]);
         if (c->adj_done[k]) cudaEventDestroy(c->adj_done[k]);
         c->rec_done[k] = c->adj_done[k] = nullptr;
@@ -496,16 +506,15 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
             // single-pass contexts keep the forward kernel's record of every state
             // of a segment (five planes); the others keep the states after the first
             const size_t sbytes = tape_fused(c) ? (size_t)5 * c->n * sizeof(float) : fbytes;
-            c->seg.assign(tape_fused(c) ? 2 * C : 2 * (C > 1 ? C - 1 : 0), nullptr);
-            c->segq.assign(2 * C, nullptr);
+            c->seg.assign(tape_fused(c) ? kTapeSlots * C : kTapeSlots * (C > 1 ? C - 1 : 0), nullptr);
+            c->segq.assign(kTapeSlots * C, nullptr);
             for (auto &p : c->seg) ok = ok && dev_alloc(&p, sbytes) == cudaSuccess;
             for (auto &p : c->segq) ok = ok && dev_alloc(&p, qbytes) == cudaSuccess;
-            // equal priorities: either stream favoured over the other (tried both
-            // ways) lets it starve the other and loses the overlap
+            // equal priorities (either stream favoured starves the other)
             ok = ok && cudaStreamCreateWithFlags(&c->rstream, cudaStreamNonBlocking) == cudaSuccess &&
                  cudaStreamCreateWithFlags(&c->astream, cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&c->bw_start, cudaEventDisableTiming) == cudaSuccess;
-            for (int k = 0; k < 2; ++k)
+            for (int k = 0; k < kTapeSlots; ++k)
                 ok = ok && cudaEventCreateWithFlags(&c->rec_done[k], cudaEventDisableTiming) == cudaSuccess &&
                      cudaEventCreateWithFlags(&c->adj_done[k], cudaEventDisableTiming) == cudaSuccess;
             ok = ok && dev_alloc(&c->lam[0], lbytes) == cudaSuccess && dev_alloc(&c->lam[1], lbytes) == cudaSuccess &&
@@ -522,25 +531,26 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
     CK(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");
     CK(c, launch_init<T>(m, rho0, nullptr, nullptr, (T *)c->ckpt[0], c->stream), "init kernel");
     // What the reverse sweep needs of the last two segments goes straight
-    // into its two slots, so the sweep starts with no recompute: segment k's
-    // stencil fields of states k C .. in slot k & 1, and its states k C + 1 ..
-    // (single-pass contexts: the records of states k C .., the states
-    // themselves staying in the scratch pair).
-    const int K = (nsteps - 1) / C, t0 = K * C, sl = K & 1, nseg = C > 1 ? C - 1 : 0;
+    // into their slots, so the sweep starts with no recompute: segment k's
+    // stencil fields of states k C .. in slot k % kTapeSlots, and its states
+    // k C + 1 .. (single-pass contexts: the records of states k C .., the
+    // states themselves staying in the scratch pair).
+    const int K = (nsteps - 1) / C, t0 = K * C, sl = K % kTapeSlots, nseg = C > 1 ? C - 1 : 0;
+    const int slp = (K + kTapeSlots - 1) % kTapeSlots;   // the slot of segment K - 1
     const int tp = K >= 1 ? t0 - C : t0;   // the first step of the taped segments
     auto fbuf = [&](int t) -> void * {   // where state t (>= 1) goes
         if (t % C == 0) return c->ckpt[t / C];
         if (!tape_fused(c) && t > t0 && t < nsteps) return c->seg[sl * nseg + (t - t0 - 1)];
-        if (!tape_fused(c) && t > tp && t < t0) return c->seg[(1 - sl) * nseg + (t - tp - 1)];
+        if (!tape_fused(c) && t > tp && t < t0) return c->seg[slp * nseg + (t - tp - 1)];
         return c->tmp[t & 1];
     };
     auto rbuf = [&](int t) -> float * {   // where the record of state t goes (single-pass)
         if (!tape_fused(c) || t < tp) return nullptr;
-        return (float *)c->seg[((t / C) & 1) * C + t % C];
+        return (float *)c->seg[((t / C) % kTapeSlots) * C + t % C];
     };
     auto qbuf = [&](int t) -> void * {   // the stencil field of state t
         if (t >= t0 && t < nsteps) return c->segq[sl * C + (t - t0)];
-        if (t >= tp && t < t0) return c->segq[(1 - sl) * C + (t - tp)];
+        if (t >= tp && t < t0) return c->segq[slp * C + (t - tp)];
         if (tape_fused(c) && t % C == 0) return c->ckptq[t / C];
         return tape_fused(c) ? c->qpad_tape[t & 1] : c->q;
     };
@@ -638,26 +648,28 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
     if (e == cudaSuccess) e = cudaStreamWaitEvent(as, c->bw_start, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(slots, 0, sizeof(double) * (nslots + 1), as);
     if (e == cudaSuccess) e = launch_adjoint_seed<T>(nx, ny, tape_fused(c), lay, grad_rhoT, (T *)lam[0], c->err, as);
-    // The recompute of segment k - 1 runs on rstream while the adjoint steps of
-    // segment k run on the context's stream: slot (k - 1) & 1 is free once the
-    // adjoint of segment k + 1 (the slot's previous user) is done.
+    // The recompute of segment j (into slot j % kTapeSlots) runs on rstream
+    // once the adjoint steps of segment j + kTapeSlots, the slot's previous
+    // user, are done; the adjoint steps of segment k (on astream) wait for
+    // its recompute.  So the recompute runs up to kTapeSlots - 1 segments
+    // ahead of the adjoint steps.
     const int K = (N - 1) / C;
-    if (e == cudaSuccess) e = cudaEventRecord(c->adj_done[0], as);   // orders rstream after the seed
-    if (e == cudaSuccess) e = cudaEventRecord(c->adj_done[1], as);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->rstream, c->adj_done[K & 1], 0);
+    for (int j = 0; j < kTapeSlots && e == cudaSuccess; ++j)   // orders rstream after the seed
+        e = cudaEventRecord(c->adj_done[j], as);
     // segments K and K - 1 are left in their slots by the forward
     const bool taped = c->tape_last_ready;
     c->tape_last_ready = false;   // the sweep reuses the slots
-    if (e == cudaSuccess && !taped) e = recompute(K, K & 1, c->rstream);
-    if (e == cudaSuccess) e = cudaEventRecord(c->rec_done[K & 1], c->rstream);
+    auto rec = [&](int j) {
+        cudaError_t r = cudaStreamWaitEvent(c->rstream, c->adj_done[j % kTapeSlots], 0);
+        if (r == cudaSuccess && !(taped && j >= K - 1)) r = recompute(j, j % kTapeSlots, c->rstream);
+        if (r == cudaSuccess) r = cudaEventRecord(c->rec_done[j % kTapeSlots], c->rstream);
+        return r;
+    };
+    for (int j = K; j >= std::max(0, K - kTapeSlots + 2) && e == cudaSuccess; --j) e = rec(j);
     int li = 0;
     for (int k = K; k >= 0 && e == cudaSuccess; --k) {
-        const int sl = k & 1;
-        if (k >= 1) {
-            e = cudaStreamWaitEvent(c->rstream, c->adj_done[(k - 1) & 1], 0);
-            if (e == cudaSuccess && !(taped && k == K)) e = recompute(k - 1, (k - 1) & 1, c->rstream);
-            if (e == cudaSuccess) e = cudaEventRecord(c->rec_done[(k - 1) & 1], c->rstream);
-        }
+        const int sl = k % kTapeSlots;
+        if (k - kTapeSlots + 1 >= 0) e = rec(k - kTapeSlots + 1);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(as, c->rec_done[sl], 0);
         const int t0 = k * C, t1 = std::min(N, t0 + C);
         for (int t = t1 - 1; t >= t0 && e == cudaSuccess; --t) {
@@ -847,24 +859,53 @@ lbm_status lbm_tune_segment_rows(lbm_ctx *c, int trials, int *rows) {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaError_t e = cudaEventCreate(&ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
-    int best = 0;
-    float best_ms = 0.f;
-    // heights 8k - 2 (whole slabs, no wasted collided rows) up to the lattice or 1022 rows
-    const int hmax = std::min(c->p.ny, 1022);
-    for (int h = 6; h <= hmax && e == cudaSuccess; h += 8) {
-        if ((c->p.ny + h - 1) / h > 65535) continue;
-        e = launch(h);   // warm-up
+    // time n launches at height h (after one warm-up launch)
+    auto time_height = [&](int h, int n, float *ms) {
+        e = launch(h);
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
-        for (int t = 0; t < trials && e == cudaSuccess; ++t) e = launch(h);
+        for (int t = 0; t < n && e == cudaSuccess; ++t) e = launch(h);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ev[0], ev[1]);
+        return e == cudaSuccess;
+    };
+    // Coarse scan: heights 8k - 2 (whole slabs, no wasted collided rows) up to
+    // the lattice or 1022 rows, `trials` launches each; the kFinal fastest go on.
+    constexpr int kFinal = 6, kRounds = 3;
+    int cand[kFinal];
+    float cand_ms[kFinal];
+    int ncand = 0;
+    const int hmax = std::min(c->p.ny, 1022);
+    for (int h = 6; h <= hmax; h += 8) {
+        if ((c->p.ny + h - 1) / h > 65535) continue;
         float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        if (e == cudaSuccess && (best == 0 || ms < best_ms)) {
-            best = h;
-            best_ms = ms;
+        if (!time_height(h, trials, &ms)) break;
+        int at = ncand < kFinal ? ncand++ : kFinal;   // insertion into the sorted list
+        while (at > 0 && cand_ms[at - 1] > ms) {
+            if (at < kFinal) {
+                cand[at] = cand[at - 1];
+                cand_ms[at] = cand_ms[at - 1];
+            }
+            --at;
+        }
+        if (at < kFinal) {
+            cand[at] = h;
+            cand_ms[at] = ms;
         }
     }
+    // Final: kRounds interleaved rounds of 8 x trials launches per candidate (a
+    // short scan's pick varies by a few tenths of a percent from one run to the
+    // next); the smallest total wins.
+    float total[kFinal] = {};
+    for (int r = 0; r < kRounds && e == cudaSuccess; ++r)
+        for (int i = 0; i < ncand && e == cudaSuccess; ++i) {
+            float ms = 0.f;
+            if (time_height(cand[i], 8 * trials, &ms)) total[i] += ms;
+        }
+    int bi = -1;
+    for (int i = 0; i < ncand; ++i)
+        if (bi < 0 || total[i] < total[bi]) bi = i;
+    const int best = bi < 0 ? 0 : cand[bi];
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
     CK(c, e, "segment-height trials");
