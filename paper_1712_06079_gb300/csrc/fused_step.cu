@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
 #pragma unroll
             for (int d = 32; d >= 21; --d) x = fmaf(A.ry, x, tq(d));
             fq[cl] = x;
+            __syncwarp();   // the aligned barrier instructions want the whole warp converged
             asm volatile("bar.arrive %0, %1;" ::"r"(bar_id), "r"(64) : "memory");
             float v = pcarry;   // P_(Y0-1)
 #pragma unroll
@@ -409,6 +410,7 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
             float x = tq(20);   // the near part: rows Y0+20 .. Y0+9
 #pragma unroll
             for (int d = 19; d >= 9; --d) x = fmaf(A.ry, x, tq(d));
+            __syncwarp();
             asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(64) : "memory");
             float v = fmaf(A.ry12, fq[cl], x);         // Q_(Y0+8)
 #pragma unroll
