@@ -25,6 +25,9 @@
 // cell can be formed on chip.  Launches use programmatic serialization: a
 // grid waits for the previous step at its top (griddepcontrol.wait), before
 // any read or write, so the next step's CTAs are scheduled while it drains.
+// Successive steps take the strips and segments in opposite orders, so the
+// first CTAs of a step read the rows the last CTAs of the previous step wrote
+// while those are still in L2.
 //
 // f(t) of a lane's 4 cells is read with nine float4 loads into registers,
 // issued during the previous slab (for tau = 1 right after its moments, which
@@ -121,6 +124,7 @@ struct FusedArgs {
     int qpitch;         // nx + 2 * QG
     int seg_h;          // rows per CTA segment
     int n4;             // float4s per population plane (nx ny / 4)
+    int rev;            // CTAs take the strips and segments in reverse order
     float w1x, w2x;     // d/dx weights w_1, w_2 (w_j = w_2 r^(j-2) for j >= 2)
     float w1y, w2y;     // d/dy weights
     float ry, ry5, ry12, ry25;  // r = (sqrt 5 - 3)/2 of Eq. 20's tridiagonal operator, and r^5, r^12, r^25
@@ -269,9 +273,13 @@ __global__ void __launch_bounds__(NTHR, 2) fused_step_kernel(const __grid_consta
     const Model<float> &m = A.m;
     const int nx = m.nx, ny = m.ny;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x0 = blockIdx.x * TXI;
+    // reversed on alternate steps: the first CTAs of a step then read the rows
+    // the last CTAs of the previous step wrote, while those are still in L2
+    const int bx = A.rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    const int by = A.rev ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+    const int x0 = bx * TXI;
     const int nint = min(TXI, nx - x0);             // interior columns (multiple of 4)
-    const int ys = blockIdx.y * A.seg_h;
+    const int ys = by * A.seg_h;
     const int hseg = min(A.seg_h, ny - ys);
     const int nslab = hseg > 6 ? (hseg - 6 + SLAB - 1) / SLAB + 1 : 1;
     const int nchunks = nslab + QAHEAD;
@@ -762,7 +770,8 @@ cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float 
 }
 
 cudaError_t launch_fused_step(const Model<float> &m, bool sc, bool cdm, const float *f, const float *qin,
-                              float *fout, float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl, float *rec) {
+                              float *fout, float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl, float *rec,
+                              bool rev) {
     if (rec && (m.walls || cdm)) return cudaErrorInvalidValue;
     FusedArgs a;
     a.m = m;
@@ -775,6 +784,7 @@ cudaError_t launch_fused_step(const Model<float> &m, bool sc, bool cdm, const fl
     a.qpitch = fused_q_pitch(m.nx);
     a.seg_h = seg_rows;
     a.n4 = (int)((long long)m.nx * m.ny / 4);
+    a.rev = rev ? 1 : 0;
     if (seg_rows < 1) return cudaErrorInvalidValue;
     dim3 grid((m.nx + TXI - 1) / TXI, (m.ny + seg_rows - 1) / seg_rows);
     if (grid.y > 65535) return cudaErrorInvalidValue;

@@ -141,6 +141,7 @@ struct lbm_ctx {
     void *tmp[2] = {nullptr, nullptr};
     void *qpad_tape[2] = {nullptr, nullptr};
     int tape_steps = -1, tape_C = 0;
+    bool fused_rev = false;         // the single-pass kernel's CTA order of the next step (alternates)
     bool tape_last_ready = false;   // the last two segments' states are in their sweep slots (set by the forward)
     // reverse sweep buffers, allocated with the tape: the states recomputed
     // inside a segment (single-pass contexts: the forward kernel's record of
@@ -304,9 +305,11 @@ cudaError_t step_fused(lbm_ctx *c, const Model<float> &m) {
     }
     e = timed_launch(c, 2, [&] {
         return launch_fused_step(m, is_sc(c), is_cdm(c), f, (const float *)c->qpad[c->cur], (float *)c->f[1 - c->cur],
-                                 (float *)c->qpad[1 - c->cur], c->err, seg_rows_of(c), c->stream);
+                                 (float *)c->qpad[1 - c->cur], c->err, seg_rows_of(c), c->stream, true, nullptr,
+                                 c->fused_rev);
     });
     if (e != cudaSuccess) return e;
+    c->fused_rev = !c->fused_rev;   // the CTA order alternates step by step
     if (c->timing) c->tm.steps += 1;
     c->cur = 1 - c->cur;
     return cudaSuccess;
@@ -449,11 +452,11 @@ void free_tape(lbm_ctx *c) {
 // or nullptr.
 template <typename T>
 cudaError_t tape_step(lbm_ctx *c, const Model<T> &m, const void *src, void *dst, void *qsrc, void *qdst,
-                      float *rec) {
+                      float *rec, bool rev) {
     if constexpr (std::is_same_v<T, float>) {   // (FP64 contexts never take the single-pass kernel)
         if (tape_fused(c))
             return launch_fused_step(m, is_sc(c), is_cdm(c), (const float *)src, (const float *)qsrc, (float *)dst,
-                                     (float *)qdst, c->err, seg_rows_of(c), c->stream, true, rec);
+                                     (float *)qdst, c->err, seg_rows_of(c), c->stream, true, rec, rev);
     }
     cudaError_t e = launch_potential<T>(m, is_sc(c), (const T *)src, (T *)qsrc, c->err, c->stream);
     if (e != cudaSuccess) return e;
@@ -562,7 +565,7 @@ lbm_status tape_forward(lbm_ctx *c, const T *rho0, int nsteps, int C, T *rhoT) {
     const void *cur = c->ckpt[0];
     for (int t = 0; t < nsteps; ++t) {
         void *dst = fbuf(t + 1);
-        CK(c, tape_step<T>(c, m, cur, dst, qbuf(t), qbuf(t + 1), rbuf(t)), "tape forward step");
+        CK(c, tape_step<T>(c, m, cur, dst, qbuf(t), qbuf(t + 1), rbuf(t), (t & 1) != 0), "tape forward step");
         cur = dst;
     }
     if (tape_fused(c)) {   // the checkpointed fields of the taped segments, for a later recompute
@@ -624,7 +627,8 @@ lbm_status tape_backward(lbm_ctx *c, const T *grad_rhoT, T *grad_rho0, double *g
                     void *dst = c->tmp[(t + 1) & 1];
                     void *qn = t + 1 < t1 ? segqf(sl, t + 1 - t0) : c->qpad_tape[0];
                     r = launch_fused_step(m, is_sc(c), is_cdm(c), (const float *)cur, (const float *)segqf(sl, t - t0),
-                                          (float *)dst, (float *)qn, c->err, rows, s, true, (float *)segrec(sl, t - t0));
+                                          (float *)dst, (float *)qn, c->err, rows, s, true, (float *)segrec(sl, t - t0),
+                                          (t & 1) != 0);
                     cur = dst;
                 }
                 return r;

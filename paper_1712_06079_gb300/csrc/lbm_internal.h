@@ -113,9 +113,12 @@ cudaError_t launch_potential_padded(const Model<float> &m, bool sc, const float 
 // the previous one drains; it waits for it before any access).  rec (periodic
 // HDM lattices only): also write the reverse mode's record of f(t), five planes of
 // nx ny floats: rho, jx, jy and the HDM derivatives Dx, Dy of the stencil field.
+// rev: the CTAs take the strips and segments in reverse order (results are the
+// same either way; alternated step by step, the first CTAs of a step read the
+// rows the last CTAs of the previous step wrote, while they are still in L2).
 cudaError_t launch_fused_step(const Model<float> &m, bool sc, bool cdm, const float *f, const float *qin,
                               float *fout, float *qout, int *err, int seg_rows, cudaStream_t s, bool pdl = true,
-                              float *rec = nullptr);
+                              float *rec = nullptr, bool rev = false);
 
 // Adjoint (reverse-time) step (adjoint.cu): from lambda = dL/df at t+1 and the
 // state f at t with its stencil field q (row y, column x at
