@@ -75,6 +75,32 @@ __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rsqrt_fast(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_fast(double x) { return 1.0 / sqrt(x); }
 
+// Two cells' values as one packed FP32 pair (Blackwell's paired add, multiply
+// and fma; each component rounds as the scalar operation), so that the local
+// adjoint of a thread's two cells runs as one pass.
+struct F2 {
+    float2 v;
+    F2() = default;
+    __device__ explicit F2(double c) : v(make_float2((float)c, (float)c)) {}
+    __device__ F2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ F2 f2_of(float2 x) {
+    F2 r;
+    r.v = x;
+    return r;
+}
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return f2_of(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return f2_of(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return f2_of(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return f2_of(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ F2 &operator+=(F2 &a, F2 b) { return a = a + b; }
+__device__ __forceinline__ F2 &operator-=(F2 &a, F2 b) { return a = a - b; }
+
+// a b + c: one fma (scalar types: the contraction the compiler forms anyway)
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ F2 fmadd(F2 a, F2 b, F2 c) { return f2_of(__ffma2_rn(a.v, b.v, c.v)); }
+
 // e_i . (vx, vy) from the signs of e_i (no multiplications by 0 or 1)
 template <typename T>
 __device__ __forceinline__ T dot_e(int i, T vx, T vy) {
@@ -348,45 +374,46 @@ __device__ __forceinline__ void adj_local(const T (&g)[kQ], T om1, T r, T inv, T
     T G0 = T(0), Gx = T(0), Gy = T(0), Rv = T(0), Hx = T(0), Hy = T(0), Ru = T(0);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-        const T gw = g[i] * wq<T>(i);
+        const T gw = g[i] * T(wq<double>(i));
         G0 += gw;
         if (i == 0) continue;
         const T ev = dot_e(i, vx, vy);
-        const T gt = gw * (T(3) + T(9) * ev);
+        const T gt = gw * fmadd(T(9), ev, T(3));
         if (ex(i) == 1) Gx += gt;
         if (ex(i) == -1) Gx -= gt;
         if (ey(i) == 1) Gy += gt;
         if (ey(i) == -1) Gy -= gt;
-        Rv += gw * ev * (T(3) + T(4.5) * ev);
+        Rv = fmadd(gw * ev, fmadd(T(4.5), ev, T(3)), Rv);
         if (!TAU1) {
             const T eu = dot_e(i, ux, uy);
-            const T gu = gw * (T(3) + T(9) * eu);
+            const T gu = gw * fmadd(T(9), eu, T(3));
             if (ex(i) == 1) Hx += gu;
             if (ex(i) == -1) Hx -= gu;
             if (ey(i) == 1) Hy += gu;
             if (ey(i) == -1) Hy -= gu;
-            Ru += gw * eu * (T(3) + T(4.5) * eu);
+            Ru = fmadd(gw * eu, fmadd(T(4.5), eu, T(3)), Ru);
         }
     }
-    const T vv = vx * vx + vy * vy;
-    rb = (T(1) - T(1.5) * vv) * G0 + Rv;
-    const T vbx = r * (Gx - T(3) * vx * G0), vby = r * (Gy - T(3) * vy * G0);
+    const T vv = fmadd(vx, vx, vy * vy);
+    rb = fmadd(fmadd(T(-1.5), vv, T(1)), G0, Rv);
+    const T vbx = r * fmadd(T(-3) * vx, G0, Gx), vby = r * fmadd(T(-3) * vy, G0, Gy);
     T ubx = vbx, uby = vby;
     if (!TAU1) {   // the f^eq(u) terms enter with the weights -(1 - omega) g_i
-        const T uu = ux * ux + uy * uy;
-        rb -= om1 * ((T(1) - T(1.5) * uu) * G0 + Ru);
-        ubx -= om1 * r * (Hx - T(3) * ux * G0);
-        uby -= om1 * r * (Hy - T(3) * uy * G0);
+        const T uu = fmadd(ux, ux, uy * uy);
+        rb -= om1 * fmadd(fmadd(T(-1.5), uu, T(1)), G0, Ru);
+        ubx -= om1 * r * fmadd(T(-3) * ux, G0, Hx);
+        uby -= om1 * r * fmadd(T(-3) * uy, G0, Hy);
     }
     const T Fbx = vbx * inv, Fby = vby * inv;
-    rb -= (vbx * Fx + vby * Fy) * inv * inv;
+    rb -= fmadd(vbx, Fx, vby * Fy) * inv * inv;
     jbx = ubx * inv;
     jby = uby * inv;
-    rb -= (ubx * ux + uby * uy) * inv;
+    rb -= fmadd(ubx, ux, uby * uy) * inv;
     if (SC) {
-        Dbx = T(-2) * sgn * phi * Fbx;
-        Dby = T(-2) * sgn * phi * Fby;
-        pc = T(-2) * sgn * (Fbx * Dx + Fby * Dy);
+        const T m2s = T(-2) * sgn;
+        Dbx = m2s * phi * Fbx;
+        Dby = m2s * phi * Fby;
+        pc = m2s * fmadd(Fbx, Dx, Fby * Dy);
     } else {
         Dbx = -Fbx;
         Dby = -Fby;
@@ -595,17 +622,17 @@ __global__ void __launch_bounds__(AdjTile<float>::TX *AdjTile<float>::TYT) adj_a
         }
         if (!cta_wait_copies(bar, 1, 0, a.err)) return;
     }
+    static_assert(NC == 2, "the local adjoint runs on the thread's two cells as packed pairs");
     float tacc = 0.0f;
     const int xp = xc + 1 == nx ? 0 : xc + 1, xm = xc == 0 ? nx - 1 : xc - 1;
+    float gk[NC][kQ];   // g_i = lambda_i(x + e_i) of both cells
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-        const int ly = threadIdx.y + k * TYT, y = y0 + ly;
-        const bool valid = x < nx && y < ny;
-        const int yc = min(y, ny - 1);
+        const int ly = threadIdx.y + k * TYT;
+        const int yc = min(y0 + ly, ny - 1);
         const int yp = yc + 1 == ny ? 0 : yc + 1, ym = yc == 0 ? ny - 1 : yc - 1;
-        float g[kQ];
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) {  // g_i = lambda_i(x + e_i)
+        for (int i = 0; i < kQ; ++i) {
             if (TAU1) {   // lambda_i = rho_bar + e_i . j_bar, by the signs of e_i
                 const int o = (ly + 1 + ey(i)) * LW + (LO + lx + ex(i));
                 float gi = L[o];
@@ -613,16 +640,30 @@ __global__ void __launch_bounds__(AdjTile<float>::TX *AdjTile<float>::TYT) adj_a
                 if (ex(i) == -1) gi -= L[LW * LH + o];
                 if (ey(i) == 1) gi += L[2 * LW * LH + o];
                 if (ey(i) == -1) gi -= L[2 * LW * LH + o];
-                g[i] = gi;
+                gk[k][i] = gi;
             } else {
                 const int dxs = ex(i) == 1 ? xp : (ex(i) == -1 ? xm : xc);
                 const int dys = ey(i) == 1 ? yp : (ey(i) == -1 ? ym : yc);
-                g[i] = ld_chk(a.lam, i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs, a.nl, a.m.chk);
+                gk[k][i] = ld_chk(a.lam, i * a.lstride + (long long)dys * a.lpitch + a.loff + dxs, a.nl, a.m.chk);
             }
         }
-        float rb, jbx, jby, Dbx, Dby, pc;
-        adj_local<float, SC, TAU1>(g, 1.0f - m.omega, r_k[k], inv_k[k], ux_k[k], uy_k[k], vx_k[k], vy_k[k], Fx_k[k],
-                                   Fy_k[k], Dx_k[k], Dy_k[k], phi_k[k], sgn_k[k], rb, jbx, jby, Dbx, Dby, pc);
+    }
+    F2 g2[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g2[i] = F2(gk[0][i], gk[1][i]);
+    auto pair = [](const float (&v)[NC]) { return F2(v[0], v[1]); };
+    const float om1 = 1.0f - m.omega;
+    F2 rb2, jbx2, jby2, Dbx2, Dby2, pc2;
+    adj_local<F2, SC, TAU1>(g2, F2(om1, om1), pair(r_k), pair(inv_k), pair(ux_k), pair(uy_k), pair(vx_k),
+                            pair(vy_k), pair(Fx_k), pair(Fy_k), pair(Dx_k), pair(Dy_k), pair(phi_k), pair(sgn_k), rb2,
+                            jbx2, jby2, Dbx2, Dby2, pc2);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int y = y0 + threadIdx.y + k * TYT;
+        const bool valid = x < nx && y < ny;
+        float rb = k ? rb2.v.y : rb2.v.x;
+        const float jbx = k ? jbx2.v.y : jbx2.v.x, jby = k ? jby2.v.y : jby2.v.x;
+        const float Dbx = k ? Dbx2.v.y : Dbx2.v.x, Dby = k ? Dby2.v.y : Dby2.v.x, pc = k ? pc2.v.y : pc2.v.x;
         if (SC) {
             rb += pc * kap_k[k];
             if (valid) tacc += pc * th_k[k];
