@@ -202,7 +202,7 @@ struct AdjArgs {
     T *aux;         // D_bar_x, D_bar_y, partial rho_bar, rho[, j_bar_x, j_bar_y]
     long long dstride;
     int dpitch, doff;
-    double *Tpart;  // one FP64 slot per CTA of A, then per CTA of B
+    double *Tpart;  // one FP64 slot per warp of each CTA of A, then of B
     int *err;       // error word (a bounded wait that gave up)
     long long nf, nq, nl, nd;   // elements of f (or the record), q, each lambda buffer, aux (checked build)
     T r, r5, r25;   // r = (sqrt 5 - 3)/2 of Eq. 20's operator and its powers (padded FP32 tiles)
