@@ -240,6 +240,21 @@ def source_digest(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
+def launch_time(timing: dict, region_ms: float, steps: int):
+    """The dominant kernel of the accounting pass (`Lattice.timing()` of the
+    same steps with per-launch events) and its average launch duration in the
+    timed region: when that region launches only this kernel, once per step,
+    the region's time over the launches; otherwise the accounting pass's own
+    (serialised) per-launch time.  Returns (kernel, launch_ms, isolated_ms,
+    launches in the timed region, whether the region time was used)."""
+    kern = timing["kernels"]
+    dominant = max(kern, key=lambda k: kern[k]["ms"])
+    isolated_ms = kern[dominant]["ms"] / kern[dominant]["count"]
+    only = len(kern) == 1 and kern[dominant]["count"] == timing["steps"]
+    launches = timing["launches"] * steps // max(timing["steps"], 1)
+    return dominant, (region_ms / steps if only else isolated_ms), isolated_ms, launches, only
+
+
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
@@ -394,15 +409,7 @@ def run_ours(args):
     if rank != 0:
         return 0
     kern = timing["kernels"]
-    dominant = max(kern, key=lambda k: kern[k]["ms"])
-    isolated_ms = kern[dominant]["ms"] / kern[dominant]["count"]
-    # the timed region launches only the dominant kernel (one launch per step,
-    # as the accounting pass shows), so its average launch duration there is
-    # the region's time over the launches; the accounting pass's serialised
-    # per-launch duration is reported beside it
-    only = len(kern) == 1 and kern[dominant]["count"] == timing["steps"]
-    launches = timing["launches"] * args.steps // max(timing["steps"], 1)
-    avg_ms = ms / args.steps if only else isolated_ms
+    dominant, avg_ms, isolated_ms, launches, only = launch_time(timing, ms, args.steps)
     # algorithmic bytes: the method's 72 B per cell update (9 f in, 9 f out);
     # the kernel's own 80 B (the stored potential field read and written once
     # more) and ncu's DRAM bytes are reported beside it

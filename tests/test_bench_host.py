@@ -27,3 +27,17 @@ def test_source_digest_ignores_comments_only():
     assert bench.strip_comments("int a = 1;") != bench.strip_comments("int a = 2;")
     # string literals keep their comment-like contents
     assert "//" in bench.strip_comments('const char *s = "a // b";')
+
+
+def test_launch_time_uses_the_timed_region_only_for_a_single_kernel():
+    # one kernel, one launch per step: the region's time over the launches
+    t = {"steps": 100, "launches": 100, "kernels": {"fused_step": {"ms": 23.0, "count": 100}}}
+    k, launch_ms, iso, n, only = bench.launch_time(t, region_ms=22.0 * 2, steps=200)
+    assert (k, n, only) == ("fused_step", 200, True)
+    assert abs(launch_ms - 0.22) < 1e-12 and abs(iso - 0.23) < 1e-12
+    # two kernels per step (the two-pass path): the serialised per-launch time of the dominant one
+    t = {"steps": 10, "launches": 20,
+         "kernels": {"potential": {"ms": 1.0, "count": 10}, "collide": {"ms": 5.0, "count": 10}}}
+    k, launch_ms, iso, n, only = bench.launch_time(t, region_ms=70.0, steps=10)
+    assert (k, n, only) == ("collide", 20, False)
+    assert launch_ms == iso == 0.5
